@@ -1,0 +1,322 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics.
+
+Nothing here compares the oracle with itself or with the CUDA library.  Each
+test checks the oracle against something independent: a library routine
+(numpy's Gauss-Legendre, scipy's adaptive quadrature), an exact symbolic
+derivation of the integral definitions (sympy), closed forms and textbook
+special cases, exact invariants (integer shifts are permutations, mass), the
+exact solution of eq. (advection) (translation), the convergence order k+1
+of the projection (Sec. II-A), and a brute-force projection that never forms
+the update matrices.
+"""
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1603_07008_gb300 import workloads as W
+
+
+# ---------------------------------------------------------------- quadrature
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 12, 20])
+def test_gauss_legendre_matches_numpy(n):
+    x, w = O.gauss_legendre(n)
+    X, Wt = np.polynomial.legendre.leggauss(n)
+    assert np.max(np.abs(x - X)) < 1e-15
+    assert np.max(np.abs(w - Wt)) < 1e-14
+
+
+@pytest.mark.parametrize("n", [2, 4, 5, 12])
+def test_gauss_legendre_exact_on_monomials(n):
+    x, w = O.gauss_legendre(n)
+    for p in range(2 * n):
+        exact = 0.0 if p % 2 else 2.0 / (p + 1)
+        assert abs(np.dot(w, x ** p) - exact) < 1e-14
+
+
+def test_legendre_matches_numpy():
+    xs = np.linspace(-1, 1, 17)
+    for j in range(7):
+        c = np.zeros(j + 1)
+        c[j] = 1
+        ref = np.polynomial.legendre.legval(xs, c)
+        got = np.array([O.legendre(j, v) for v in xs])
+        assert np.max(np.abs(got - ref)) < 1e-14
+
+
+# ---------------------------------------------------------------- A and B
+
+def _sympy_ab(k, alpha):
+    """A, B from their integral definitions, integrated exactly by sympy."""
+    sp = pytest.importorskip("sympy")
+    xi = sp.Symbol("xi")
+    a = sp.Rational(alpha.numerator, alpha.denominator)
+    o = k + 1
+    A = [[None] * o for _ in range(o)]
+    B = [[None] * o for _ in range(o)]
+    for j in range(o):
+        for l in range(o):
+            Pj = sp.legendre(j, xi)
+            A[j][l] = sp.Rational(2 * j + 1, 2) * sp.integrate(Pj * sp.legendre(l, xi - 2 * a), (xi, 2 * a - 1, 1))
+            B[j][l] = sp.Rational(2 * j + 1, 2) * sp.integrate(Pj * sp.legendre(l, xi + 2 - 2 * a), (xi, -1, 2 * a - 1))
+    return A, B
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("alpha", [Fraction(3, 8), Fraction(1, 3), Fraction(1, 2), Fraction(37, 100),
+                                   Fraction(1, 1024), Fraction(1023, 1024)])
+def test_ab_matches_exact_symbolic_integrals(k, alpha):
+    A, B = O.ab_matrices(k, float(alpha))
+    As, Bs = _sympy_ab(k, alpha)
+    o = k + 1
+    for j in range(o):
+        for l in range(o):
+            assert abs(A[j, l] - float(As[j][l])) < 4e-15, (j, l)
+            assert abs(B[j, l] - float(Bs[j][l])) < 4e-15, (j, l)
+
+
+def test_ab_dyadic_alpha_three_eighths_k2():
+    """At alpha = 3/8 every entry is a dyadic rational; check them exactly
+    (values from the symbolic integrals, compared with the rational itself)."""
+    As, Bs = _sympy_ab(2, Fraction(3, 8))
+    A, B = O.ab_matrices(2, 0.375)
+    for j in range(3):
+        for l in range(3):
+            qa, qb = Fraction(str(As[j][l])), Fraction(str(Bs[j][l]))
+            assert qa.denominator & (qa.denominator - 1) == 0   # power of two
+            assert abs(A[j, l] - float(qa)) <= 2 * np.finfo(float).eps * max(1, abs(float(qa)))
+            assert abs(B[j, l] - float(qb)) <= 2 * np.finfo(float).eps * max(1, abs(float(qb)))
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.1, 0.37, 0.5, 0.9])
+def test_k0_is_donor_cell(alpha):
+    """k = 0 is first-order upwind: u_i <- u_i - alpha (u_i - u_{i-1})."""
+    A, B = O.ab_matrices(0, alpha)
+    u = np.array([0.3, -1.2, 2.5, 0.7, 1.1])
+    upwind = u - alpha * (u - np.roll(u, 1))
+    got = O.sweep(u.reshape(-1, 1), [5], 0, 0, -1, alpha)[:, 0]
+    assert np.max(np.abs(got - upwind)) < 1e-15
+    assert abs(A[0, 0] - (1 - alpha)) < 1e-15 and abs(B[0, 0] - alpha) < 1e-15
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_ab_identities(k):
+    o = k + 1
+    A0, B0 = O.ab_matrices(k, 0.0)
+    assert np.array_equal(A0, np.eye(o)) and np.array_equal(B0, np.zeros((o, o)))
+    sign = np.array([[(-1) ** (j + l) for l in range(o)] for j in range(o)])
+    for a in [0.013, 0.25, 0.37, 0.5, 0.81]:
+        A, B = O.ab_matrices(k, a)
+        Ar, _ = O.ab_matrices(k, 1.0 - a)
+        # reflection: B(a) = S A(1-a) S
+        assert np.max(np.abs(B - sign * Ar)) < 1e-14
+        # row 0: mass conservation; column 0: constants are preserved
+        assert np.max(np.abs((A + B)[0, :] - np.eye(o)[0])) < 1e-15
+        assert np.max(np.abs((A + B)[:, 0] - np.eye(o)[:, 0])) < 1e-15
+    # alpha -> 1 is the pure neighbour copy
+    A, B = O.ab_matrices(k, 1.0 - 2.0 ** -40)
+    assert np.max(np.abs(B - np.eye(o))) < 1e-10 and np.max(np.abs(A)) < 1e-10
+
+
+def test_shift_split():
+    assert O.shift_split(0.37) == (0, 0.37)
+    assert O.shift_split(2.0) == (2, 0.0)
+    assert O.shift_split(-0.25) == (-1, 0.75)
+    sg, a = O.shift_split(-1e-20)      # s - floor(s) rounds to 1 -> next integer
+    assert sg == 0 and a == 0.0
+    assert O.shift_split(-3.0) == (-3, 0.0)
+
+
+# ---------------------------------------------------------------- sweeps
+
+def _rand(n, k, seed):
+    return W.random_coefficients(int(np.prod(n)), k, len(n), seed)
+
+
+@pytest.mark.parametrize("n,dim,shift_dim", [((7,), 0, -1), ((5, 3), 0, 1), ((5, 3), 1, 0),
+                                             ((3, 4, 2), 2, 0), ((3, 4, 2), 1, -1)])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_integer_shift_is_bit_exact_roll(n, dim, shift_dim, k):
+    u = _rand(n, k, 11)
+    ncls = 1 if shift_dim < 0 else n[shift_dim]
+    shifts = np.array([(-1) ** c * (c * 3 + 2) for c in range(ncls)], dtype=float)
+    got = O.sweep(u, n, k, dim, shift_dim, shifts)
+    ref = np.empty_like(u)
+    # reshape to [n_{d-1}, ..., n_0, ncoef] and roll each line by its shift
+    shp = tuple(reversed(n)) + (u.shape[1],)
+    U = u.reshape(shp)
+    R = ref.reshape(shp)
+    ax = len(n) - 1 - dim
+    for c in range(ncls):
+        s = int(shifts[c])
+        if shift_dim < 0:
+            R[...] = np.roll(U, s, axis=ax)
+        else:
+            sl = [slice(None)] * (len(n) + 1)
+            sl[len(n) - 1 - shift_dim] = c
+            R[tuple(sl)] = np.roll(U, s, axis=ax)[tuple(sl)]
+    assert np.array_equal(got, ref)
+
+
+def test_full_period_shift_returns_bit_exactly():
+    n = (6, 4)
+    u = _rand(n, 2, 3)
+    assert np.array_equal(O.sweep(u, n, 2, 0, -1, 6.0), u)
+    assert np.array_equal(O.sweep(u, n, 2, 1, -1, -8.0), u)
+
+
+@pytest.mark.parametrize("n,k", [((8,), 1), ((8,), 3), ((5, 4), 2), ((3, 3, 2), 1)])
+def test_bruteforce_projection_agrees(n, k):
+    u = _rand(n, k, 5)
+    rng = np.random.default_rng(1)
+    for dim in range(len(n)):
+        for shift_dim in [-1] + [m for m in range(len(n)) if m != dim]:
+            ncls = 1 if shift_dim < 0 else n[shift_dim]
+            shifts = rng.uniform(-2.5 * n[dim], 2.5 * n[dim], size=ncls)
+            a = O.sweep(u, n, k, dim, shift_dim, shifts)
+            b = O.bruteforce_sweep(u, n, k, dim, shift_dim, shifts, nq=12)
+            assert np.max(np.abs(a - b)) < 1e-13 * max(1.0, np.max(np.abs(u)))
+
+
+def test_mass_conserved_and_l2_nonincreasing():
+    n = (16, 8)
+    k = 2
+    g = W.Grid(n=n, lo=(0.0, -1.0), hi=(2.0, 3.0), pair=(1, -1))
+    u = _rand(n, k, 7)
+    m0 = O.mass(u, g, k)
+    wts = O.l2_weights(k, 2)
+    norm = lambda v: math.sqrt(float(np.sum(v * v * wts)))
+    rng = np.random.default_rng(2)
+    for it in range(20):
+        dim = it % 2
+        s = rng.uniform(-3, 3, size=n[1 - dim])
+        v = O.sweep(u, n, k, dim, 1 - dim, s)
+        assert norm(v) <= norm(u) * (1 + 1e-15)
+        u = v
+    assert abs(O.mass(u, g, k) - m0) <= 1e-14 * np.sum(np.abs(u[:, 0])) * 0.5
+
+
+def test_one_full_period_in_fractional_steps():
+    """Translating by one period in fractional steps returns to the start up
+    to the projection error, which shrinks at order k+1."""
+    errs = []
+    for N in (32, 64):
+        g = W.Grid(n=(N,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+        u0 = O.project(g, 2, 8, np.array([1.0]), np.array([[[100.0, 0.5, 0.0, 0.0]]]))
+        u = u0
+        steps = 4 * N // 3 + 1
+        s = N / steps
+        for _ in range(steps):
+            u = O.sweep(u, (N,), 2, 0, -1, s)
+        errs.append(O.rel_l2(u, u0, 2, 1))
+    assert errs[1] < errs[0] / 6 and errs[1] < 2e-3
+
+
+def _periodic_gauss(T):
+    return np.ones(3), np.array([[[100.0, 0.5 + T + d, 0.0, 0.0]] for d in (-1, 0, 1)])
+
+
+@pytest.mark.parametrize("k,lo_order", [(0, 0.8), (1, 1.9), (2, 2.9), (3, 3.8)])
+def test_convergence_order_vs_exact_translation(k, lo_order):
+    """Against the projected exact solution u0(x - aT) of eq. (advection)."""
+    errs = []
+    for N in (64, 128, 256):
+        g = W.Grid(n=(N,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+        u = O.project(g, k, 8, *_periodic_gauss(0.0))
+        s = 0.37
+        steps = int(round(0.25 * N / s))
+        for _ in range(steps):
+            u = O.sweep(u, g.n, k, 0, -1, s)
+        T = steps * s / N
+        errs.append(O.rel_l2(u, O.project(g, k, 8, *_periodic_gauss(T)), k, 1))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > lo_order, orders
+
+
+def test_config1_close_to_exact_solution():
+    p = W.config1()
+    g = p.grid
+    u = O.project(g, p.k, p.nq, p.weights, p.params)
+    h = (g.hi[0] - g.lo[0]) / g.n[0]
+    s = p.velocity * p.dt / h
+    for _ in range(p.steps):
+        u = O.sweep(u, g.n, p.k, 0, -1, s)
+    T = p.steps * p.velocity * p.dt
+    w, prm = _periodic_gauss(T)
+    ex = O.project(g, p.k, p.nq, w, prm)
+    assert O.rel_l2(u, ex, p.k, 1) < 1e-7
+
+
+# ---------------------------------------------------------------- projection
+
+def test_projection_of_polynomials_is_exact():
+    """eq. (cj) reproduces a polynomial's own Legendre coefficients.  On a cell
+    with centre x_c and width h, x = x_c + h xi / 2, so the linear function has
+    c0 = x_c, c1 = h/2 and nothing else.  The factor family holds
+    sin(eps x)/eps = x - eps^2 x^3/6 + ..., close enough to x for eps = 1e-5."""
+    g = W.Grid(n=(5,), lo=(-1.0,), hi=(2.0,), pair=(-1,))
+    eps = 1e-5
+    c = O.project(g, 2, 5, np.array([1.0 / eps]), np.array([[[0.0, 0.0, eps, -math.pi / 2]]]))
+    h = 3.0 / 5
+    xc = -1.0 + (np.arange(5) + 0.5) * h
+    assert np.max(np.abs(c[:, 0] - xc)) < 1e-9
+    assert np.max(np.abs(c[:, 1] - h / 2)) < 1e-9
+    assert np.max(np.abs(c[:, 2])) < 1e-9
+    one = O.project(g, 3, 2, np.array([2.5]), np.array([[[0.0, 0.0, 0.0, 0.0]]]))
+    assert np.max(np.abs(one[:, 0] - 2.5)) < 1e-15 and np.max(np.abs(one[:, 1:])) < 1e-15
+
+
+def test_projection_matches_adaptive_quadrature():
+    scipy_integrate = pytest.importorskip("scipy.integrate")
+    p = W.config1()
+    g = p.grid
+    c = O.project(g, p.k, p.nq, p.weights, p.params)
+    h = 1.0 / 1024
+    for i in (0, 300, 511, 512, 700):
+        xc = (i + 0.5) * h
+        for j in range(3):
+            f = lambda xi: math.exp(-100 * (xc + h * xi / 2 - 0.5) ** 2) * np.polynomial.legendre.legval(xi, [0] * j + [1])
+            ref = (2 * j + 1) / 2 * scipy_integrate.quad(f, -1, 1, epsabs=1e-16, epsrel=1e-14)[0]
+            assert abs(c[i, j] - ref) < 1e-14
+
+
+def test_mass_of_maxwellian_workload_closed_form():
+    """int_0^{4pi} int_{-6}^{6} M(v)(1 + 0.01 cos(x/2)) dv dx = 4 pi erf(6/sqrt 2)."""
+    p = W.config2(n=64, steps=1)
+    u = O.project(p.grid, p.k, p.nq, p.weights, p.params)
+    ref = 4 * math.pi * math.erf(6 / math.sqrt(2))
+    assert abs(O.mass(u, p.grid, p.k) - ref) / ref < 1e-12
+
+
+# ---------------------------------------------------------------- bookkeeping
+
+def test_sample_after_matches_full_grid():
+    p = W.config3(n=6, steps=1)
+    g = p.grid
+    u = O.project(g, p.k, p.nq, p.weights, p.params)
+    sched = O.schedule(g, "strang", p.dt, p.field_list())
+    full = u
+    for dim, sd, s in sched:
+        full = O.sweep(full, g.n, p.k, dim, sd, s)
+    cells = [0, 17, 433, g.cells - 1]
+    got = O.sample_after(g, p.k, p.nq, p.weights, p.params, sched, cells)
+    assert np.array_equal(got, full[cells])
+
+
+def test_schedule_structure():
+    p = W.config3(n=4, steps=1)
+    sched = O.schedule(p.grid, "strang", 0.1, p.field_list())
+    assert [d for d, _, _ in sched] == [0, 1, 2, 3, 0, 1]
+    assert [sd for _, sd, _ in sched] == [2, 3, 0, 1, 2, 3]
+    lie = O.schedule(p.grid, "lie", 0.1, p.field_list())
+    assert [d for d, _, _ in lie] == [0, 1, 2, 3]
+    # the x-sweep shift is v * tau / h_x with v at the v-cell centres
+    h_x = 4 * math.pi / 4
+    h_v = 12.0 / 4
+    v = -6 + (np.arange(4) + 0.5) * h_v
+    assert np.allclose(sched[0][2], v * 0.05 / h_x, rtol=1e-15, atol=0)
+    E = p.field_list()[0]
+    assert np.allclose(sched[2][2], E * 0.1 / h_v, rtol=1e-15, atol=0)
