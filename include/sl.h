@@ -1,0 +1,247 @@
+/*
+ * sl.h -- C ABI of the GB300 (sm_103a) semi-Lagrangian discontinuous Galerkin
+ * projection-sweep library (libsl.so).
+ *
+ * Method: L. Einkemmer, "A mixed precision semi-Lagrangian algorithm and its
+ * performance on accelerators", HPCS 2016 (arXiv:1603.07008).
+ *
+ *   - Sec. II: time splitting reduces the Vlasov equation to a sequence of
+ *     one-dimensional constant-coefficient advections, eq. (advection),
+ *     u_t + a u_x = 0, whose exact solution is a translation.
+ *   - Sec. II-A: on every cell the solution is a polynomial of degree p
+ *     (o = p+1 coefficients) in the Legendre basis, coefficients by eq. (cj).
+ *     Translating and projecting back gives the update rule
+ *         c_i^{n+1} = A c_{i*}^n + B c_{i*+1}^n
+ *     with o x o matrices A, B that depend only on the time step.
+ *   - Sec. II-A, III-A: c_0 carries the mass, so keeping c_0 in FP64 and the
+ *     other coefficients in lower precision conserves mass to double precision.
+ *
+ * Conventions of this library (readings of the paper):
+ *   - shift in cells s = a*tau/h = sigma + alpha, sigma = floor(s), alpha in
+ *     [0,1); source cells of cell i are i-sigma (matrix A) and i-sigma-1
+ *     (matrix B); every dimension is periodic.
+ *   - d dimensions (1..6) with a tensor-product Legendre basis, o^d
+ *     coefficients per cell, multi-index J = sum_m j_m o^m (j_0 fastest);
+ *     cells in row-major order with dimension 0 fastest.  A sweep along
+ *     dimension m applies the 1D update to every fibre of coefficients that
+ *     varies only in j_m; the shift is constant along each line and may
+ *     depend on one orthogonal cell coordinate (shift_dim).
+ *   - Vlasov-type splitting: x-dimension m is paired with v-dimension
+ *     pair[m].  The x-sweep along m moves with the cell-centre velocity of
+ *     its v-cell, the v-sweep along pair[m] with the field E_m sampled at the
+ *     x_m cell centres.
+ *
+ * Storage modes (the "split coefficient store"):
+ *   SL_FP64      every coefficient in FP64 (the paper's "# double = o").
+ *   SL_MIX_FP32  cell mean c_{0..0} in an FP64 plane, all other coefficients
+ *                in FP32 planes ("# double = 1"); mean row computed in FP64.
+ *   SL_MIX_BF16, SL_MIX_FP16
+ *                mean in FP64, the others in BF16 / FP16 scaled per cell by a
+ *                power of two stored in an FP32 plane; arithmetic in FP32.
+ *                (Not in the paper: a further compression step of the same
+ *                idea.)  Requires o^d <= 128.
+ *
+ * Memory: sl_create allocates the device state (two copies, ping-pong) with
+ * cudaMalloc and owns it; sl_destroy frees it.  Host arrays passed in are
+ * owned by the caller and only read (or written) during the call.  All device
+ * work is ordered on the CUDA stream given to sl_create (NULL = legacy
+ * default stream).  Calls that return results to the host (sl_mass,
+ * sl_get_coeffs, sl_get_cells, sl_batch_mass, sl_batch_get_coeffs,
+ * sl_profile_query) synchronise that stream; the others only enqueue work.
+ * A context must not be used from two host threads at once.
+ *
+ * Errors: every call returns an sl_status; nothing is thrown across the ABI.
+ * On failure sl_last_error(ctx) (or sl_last_error(NULL) when no context
+ * exists yet) returns a message.  Invalid arguments are rejected before any
+ * device work is enqueued, so the state is unchanged.
+ */
+#ifndef SL_H
+#define SL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SL_MAX_DIM 6
+#define SL_MAX_DEGREE 3
+
+typedef enum {
+    SL_OK = 0,
+    SL_EINVAL = -1,    /* invalid argument (grid, degree, dimension, size, non-finite value) */
+    SL_ENOMEM = -2,    /* device or host allocation failed */
+    SL_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
+    SL_ETIMEOUT = -4,  /* a bounded device-side loop gave up (error flag set by a kernel) */
+    SL_ENAN = -5,      /* non-finite value in an input array */
+    SL_ENOTSUP = -6    /* valid request this build does not support (e.g. scaled mode with o^d > 128) */
+} sl_status;
+
+typedef enum {
+    SL_FP64 = 0,
+    SL_MIX_FP32 = 1,
+    SL_MIX_BF16 = 2,
+    SL_MIX_FP16 = 3
+} sl_storage;
+
+typedef enum {
+    SL_LIE = 0,     /* x-dims with dt, then v-dims with dt */
+    SL_STRANG = 1   /* x-dims with dt/2, v-dims with dt, x-dims with dt/2 */
+} sl_splitting;
+
+/* Periodic box [lo_m, hi_m) with n_m cells per dimension, m < ndim.
+ * pair[m] >= 0: x-dimension m is advected with the velocity coordinate
+ * pair[m]; pair[m] = -1 otherwise.  Unused entries are ignored. */
+typedef struct {
+    int32_t ndim;
+    int64_t n[SL_MAX_DIM];
+    double lo[SL_MAX_DIM];
+    double hi[SL_MAX_DIM];
+    int32_t pair[SL_MAX_DIM];
+} sl_grid;
+
+typedef struct sl_ctx sl_ctx;
+
+/* Sizes of a context's state (one copy of the ping-pong pair). */
+typedef struct {
+    int64_t cells;          /* prod n_m */
+    int64_t ncoef;          /* o^d */
+    int64_t dof;            /* cells * ncoef */
+    int64_t plane_stride;   /* elements between consecutive coefficient planes */
+    int64_t state_bytes;    /* algorithmic bytes of one state: cells * (8 + (o^d-1) * elem [+ 4 scale]) */
+    int64_t alloc_bytes;    /* device bytes allocated by the context (both copies + tables) */
+    int32_t degree;
+    int32_t storage;        /* sl_storage */
+} sl_info;
+
+/* ---------------------------------------------------------------- setup */
+
+/* Create a context for `grid`, polynomial degree `degree` (0..3, o = degree+1
+ * Legendre coefficients per dimension, Sec. II-A) and storage mode `storage`.
+ * `cuda_stream` is a cudaStream_t (may be NULL).  Allocates two copies of the
+ * state on the current device.  The state starts at zero.
+ * Errors: SL_EINVAL (ndim not in 1..6, n_m < 1, hi_m <= lo_m, degree out of
+ * range, bad pair), SL_ENOTSUP (scaled mode with o^d > 128), SL_ENOMEM,
+ * SL_ECUDA. */
+sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
+                    sl_ctx** out);
+
+/* Free the context and its device memory (after synchronising its stream).
+ * NULL is ignored. */
+void sl_destroy(sl_ctx* ctx);
+
+/* Last error message of `ctx`, or of the calling thread's last failed
+ * sl_create / sl_batch_create when ctx is NULL.  Never NULL. */
+const char* sl_last_error(const sl_ctx* ctx);
+
+/* Fill *out with the context's sizes.  Host only. */
+sl_status sl_get_info(const sl_ctx* ctx, sl_info* out);
+
+/* Bytes of one state (the algorithmic byte model) without creating a
+ * context: cells * (8 + (o^d - 1) * elem (+ 4 for the per-cell scale)),
+ * elem = 8 / 4 / 2 / 2 for SL_FP64 / SL_MIX_FP32 / SL_MIX_BF16 / SL_MIX_FP16.
+ * Sec. III-A gives the memory reduction this model implies (1.6x for
+ * 1D order 4 with c_0 in FP64).  Host only. */
+sl_status sl_state_bytes(const sl_grid* grid, int degree, sl_storage storage, int64_t* bytes);
+
+/* Evaluate the update matrices A(alpha), B(alpha) of Sec. II-A (update rule)
+ * on the host from the exact polynomial-in-alpha tables the device kernels
+ * use.  A, B: row-major o x o FP64, caller-owned.  alpha in [0,1).
+ * Host only (no device work). */
+sl_status sl_ab_host(int degree, double alpha, double* A, double* B);
+
+/* ---------------------------------------------------------------- data */
+
+/* Upload coefficients: host_aos is [cells][o^d] FP64 (layout above),
+ * caller-owned.  The library splits them into the mean plane and the
+ * low-precision planes (round to nearest even; per-cell power-of-two scale in
+ * the scaled modes).  Errors: SL_EINVAL (NULL), SL_ENAN (non-finite input,
+ * state unchanged), SL_ECUDA. */
+sl_status sl_set_coeffs(sl_ctx* ctx, const double* host_aos);
+
+/* Download all coefficients, decoded to FP64, into host_aos [cells][o^d].
+ * Synchronises. */
+sl_status sl_get_coeffs(sl_ctx* ctx, double* host_aos);
+
+/* Download the coefficients of `ncells` cells (flat indices, each in
+ * [0, cells)) into host_out [ncells][o^d].  Synchronises. */
+sl_status sl_get_cells(sl_ctx* ctx, const int64_t* cells, int64_t ncells, double* host_out);
+
+/* Raw planes in the store's own layout (for checkpoints and for callers that
+ * keep the state on the host between steps):
+ *   mean  [cells]            FP64 cell means c_{0..0}
+ *   hi    [o^d - 1][cells]   coefficient J >= 1 at hi[(J-1)*cells + cell], in
+ *                            the store's element type (FP64, FP32, or the
+ *                            BF16 / FP16 bit patterns)
+ *   scale [cells]            FP32 per-cell scales (scaled modes; NULL otherwise)
+ * sl_set_planes enqueues the host-to-device copies on the context's stream
+ * and returns; the host arrays must stay valid and unchanged until the stream
+ * has passed them (sl_synchronize).  Pinned host memory makes the copies
+ * asynchronous.  Values are copied verbatim, without validation.
+ * sl_get_planes copies the current state out and synchronises. */
+sl_status sl_set_planes(sl_ctx* ctx, const double* mean, const void* hi, const float* scale);
+sl_status sl_get_planes(sl_ctx* ctx, double* mean, void* hi, float* scale);
+
+/* Project an initial condition onto the cells, eq. (cj), on the device:
+ *   u0(x) = sum_t weights[t] prod_m g_{t,m}(x_m),
+ *   g(x)  = exp(-gamma (x - mu)^2) cos(kappa x + phi),
+ * params[(t*ndim + m)*4 + {0,1,2,3}] = {gamma, mu, kappa, phi}.  Each
+ * dimension uses an nq-point Gauss-Legendre rule (1 <= nq <= 32).  The
+ * tensor-product rule on a product factorises, so the cost is one 1D
+ * projection per factor and cell coordinate.  Host arrays, caller-owned. */
+sl_status sl_project(sl_ctx* ctx, int nq, int nterms, const double* weights,
+                     const double* params);
+
+/* ---------------------------------------------------------------- the sweep */
+
+/* One sweep along `dim`: every cell gets A(alpha) c[i-sigma] + B(alpha)
+ * c[i-sigma-1] (Sec. II-A, update rule) along that dimension.
+ * shift_dim = -1: one shift for all lines, nshift = 1.
+ * shift_dim = q != dim: shifts[i] applies to the lines whose coordinate along
+ * q is i, nshift = n[q].  Shifts are in cells (a * tau / h_dim), host array,
+ * caller-owned.  Matrices are built on the device for every shift class.
+ * Errors: SL_EINVAL (dim / shift_dim / nshift), SL_ENAN (non-finite shift). */
+sl_status sl_advect(sl_ctx* ctx, int dim, int shift_dim, const double* shifts, int64_t nshift);
+
+/* Electric fields for the v-sweeps: for every x-dimension m (pair[m] >= 0) in
+ * increasing m, n[m] samples of E_m at the x_m cell centres, concatenated.
+ * count must equal the sum of those n[m].  Copied to the device. */
+sl_status sl_set_fields(sl_ctx* ctx, const double* fields, int64_t count);
+
+/* nsteps split time steps of size dt (Sec. II, splitting): Lie or Strang
+ * over the x/v pairs of the grid.  x-sweep along m: shift v_j tau / h_m with
+ * v_j the cell centre of v-dimension pair[m]; v-sweep along pair[m]: shift
+ * E_m(x_i) tau / h_{pair[m]}.  Needs sl_set_fields when the grid has pairs.
+ * Enqueues only. */
+sl_status sl_step(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
+
+/* Mass M = (prod_m h_m) sum_i c_{i;0..0} (Sec. II-A: c_0 is the cell mean),
+ * reduced in FP64 with a fixed-shape tree (run-to-run deterministic).
+ * Synchronises. */
+sl_status sl_mass(sl_ctx* ctx, double* out);
+
+/* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
+ * replay it with sl_graph_launch.  Fields must be set before capture; a later
+ * sl_set_fields is not seen by the graph until it is captured again. */
+sl_status sl_graph_capture(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
+sl_status sl_graph_launch(sl_ctx* ctx);
+
+/* Wait for all work of the context's stream. */
+sl_status sl_synchronize(sl_ctx* ctx);
+
+/* ---------------------------------------------------------------- profiling */
+
+/* When enabled, every sweep-kernel launch is bracketed by CUDA events on the
+ * context's stream.  sl_profile_query synchronises and returns, since the
+ * last reset, the number of sweep launches, their summed device time (ms) and
+ * their summed algorithmic bytes (read + write of every state coefficient
+ * once), then resets the counters.  Off by default. */
+sl_status sl_profile_enable(sl_ctx* ctx, int enable);
+sl_status sl_profile_query(sl_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SL_H */

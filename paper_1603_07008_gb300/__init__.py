@@ -1,0 +1,369 @@
+"""GB300 (sm_103a) semi-Lagrangian discontinuous Galerkin projection sweep.
+
+Python binding of ``libsl.so`` (declared in ``include/sl.h``).  The functions
+below carry the C names and only marshal arguments: every step of the sweep,
+the matrix construction, the mass reduction, the codec and the projection run
+in the library's CUDA kernels.  There is no CPU fallback: if the library
+cannot be built or loaded, ``lib()`` raises.
+
+Method: L. Einkemmer, "A mixed precision semi-Lagrangian algorithm and its
+performance on accelerators", HPCS 2016 (arXiv:1603.07008), Sec. II-A.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+__all__ = [
+    "SL_OK", "SL_EINVAL", "SL_ENOMEM", "SL_ECUDA", "SL_ETIMEOUT", "SL_ENAN", "SL_ENOTSUP",
+    "SL_FP64", "SL_MIX_FP32", "SL_MIX_BF16", "SL_MIX_FP16", "SL_LIE", "SL_STRANG", "STORAGE",
+    "SlError", "sl_grid", "make_grid", "lib", "library_path", "Context",
+    "sl_create", "sl_destroy", "sl_last_error", "sl_get_info", "sl_state_bytes", "sl_ab_host",
+    "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
+    "sl_set_fields", "sl_step", "sl_mass", "sl_graph_capture", "sl_graph_launch",
+    "sl_synchronize", "sl_profile_enable", "sl_profile_query",
+]
+
+SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
+SL_FP64, SL_MIX_FP32, SL_MIX_BF16, SL_MIX_FP16 = 0, 1, 2, 3
+SL_LIE, SL_STRANG = 0, 1
+STORAGE = {"fp64": SL_FP64, "mix_fp32": SL_MIX_FP32, "mix_bf16": SL_MIX_BF16, "mix_fp16": SL_MIX_FP16}
+SPLITTING = {"lie": SL_LIE, "strang": SL_STRANG}
+MAX_DIM = 6
+
+
+class SlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"sl status {status}: {msg}")
+        self.status = status
+
+
+class sl_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("n", ctypes.c_int64 * MAX_DIM),
+                ("lo", ctypes.c_double * MAX_DIM), ("hi", ctypes.c_double * MAX_DIM),
+                ("pair", ctypes.c_int32 * MAX_DIM)]
+
+
+class sl_info(ctypes.Structure):
+    _fields_ = [("cells", ctypes.c_int64), ("ncoef", ctypes.c_int64), ("dof", ctypes.c_int64),
+                ("plane_stride", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
+                ("alloc_bytes", ctypes.c_int64), ("degree", ctypes.c_int32),
+                ("storage", ctypes.c_int32)]
+
+
+def make_grid(g) -> sl_grid:
+    """sl_grid from any object with n, lo, hi, pair sequences (or an sl_grid)."""
+    if isinstance(g, sl_grid):
+        return g
+    s = sl_grid()
+    nd = len(g.n)
+    s.ndim = nd
+    for m in range(MAX_DIM):
+        s.n[m] = int(g.n[m]) if m < nd else 1
+        s.lo[m] = float(g.lo[m]) if m < nd else 0.0
+        s.hi[m] = float(g.hi[m]) if m < nd else 1.0
+        s.pair[m] = int(g.pair[m]) if m < nd else -1
+    return s
+
+
+_lock = threading.Lock()
+_lib = None
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+
+
+def library_path() -> str:
+    from . import build as _b
+    return _b.LIB
+
+
+def lib():
+    """Load libsl.so, building it with nvcc first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        from . import build as _b
+        try:
+            path = _b.build()
+        except Exception as e:  # no silent fallback: the CUDA library is the product
+            raise RuntimeError(f"libsl.so could not be built: {e}") from e
+        L = ctypes.CDLL(path)
+        st = ctypes.c_int
+        sig = {
+            "sl_create": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int, _vp,
+                               ctypes.POINTER(_vp)]),
+            "sl_destroy": (None, [_vp]),
+            "sl_last_error": (ctypes.c_char_p, [_vp]),
+            "sl_get_info": (st, [_vp, ctypes.POINTER(sl_info)]),
+            "sl_state_bytes": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int, _i64p]),
+            "sl_ab_host": (st, [ctypes.c_int, ctypes.c_double, _dp, _dp]),
+            "sl_set_coeffs": (st, [_vp, _dp]),
+            "sl_get_coeffs": (st, [_vp, _dp]),
+            "sl_get_cells": (st, [_vp, _i64p, ctypes.c_int64, _dp]),
+            "sl_set_planes": (st, [_vp, _dp, _vp, ctypes.POINTER(ctypes.c_float)]),
+            "sl_get_planes": (st, [_vp, _dp, _vp, ctypes.POINTER(ctypes.c_float)]),
+            "sl_project": (st, [_vp, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+            "sl_advect": (st, [_vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int64]),
+            "sl_set_fields": (st, [_vp, _dp, ctypes.c_int64]),
+            "sl_step": (st, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+            "sl_mass": (st, [_vp, _dp]),
+            "sl_graph_capture": (st, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+            "sl_graph_launch": (st, [_vp]),
+            "sl_synchronize": (st, [_vp]),
+            "sl_profile_enable": (st, [_vp, ctypes.c_int]),
+            "sl_profile_query": (st, [_vp, _i64p, _dp, _dp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return _lib
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a: np.ndarray, t=_dp):
+    return a.ctypes.data_as(t)
+
+
+def sl_last_error(ctx=None) -> str:
+    r = lib().sl_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def _check(status: int, ctx=None):
+    if status != SL_OK:
+        raise SlError(status, sl_last_error(ctx))
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return int(stream.cuda_stream)
+    return int(stream)
+
+
+def sl_create(grid, degree: int, storage, stream=None):
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    g = make_grid(grid)
+    out = _vp()
+    _check(lib().sl_create(ctypes.byref(g), int(degree), st, _stream_handle(stream), ctypes.byref(out)))
+    return out
+
+
+def sl_destroy(ctx):
+    if ctx:
+        lib().sl_destroy(ctx)
+
+
+def sl_get_info(ctx) -> dict:
+    i = sl_info()
+    _check(lib().sl_get_info(ctx, ctypes.byref(i)), ctx)
+    return {k: getattr(i, k) for k, _ in sl_info._fields_}
+
+
+def sl_state_bytes(grid, degree: int, storage) -> int:
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    b = ctypes.c_int64()
+    g = make_grid(grid)
+    _check(lib().sl_state_bytes(ctypes.byref(g), int(degree), st, ctypes.byref(b)))
+    return b.value
+
+
+def sl_ab_host(degree: int, alpha: float) -> Tuple[np.ndarray, np.ndarray]:
+    o = degree + 1
+    A = np.zeros((o, o))
+    B = np.zeros((o, o))
+    _check(lib().sl_ab_host(int(degree), float(alpha), _ptr(A), _ptr(B)))
+    return A, B
+
+
+def sl_set_coeffs(ctx, u: np.ndarray):
+    u_ = _f64(u)
+    info = sl_get_info(ctx)
+    if u_.size != info["dof"]:
+        raise ValueError(f"expected {info['dof']} coefficients, got {u_.size}")
+    _check(lib().sl_set_coeffs(ctx, _ptr(u_)), ctx)
+
+
+def sl_get_coeffs(ctx) -> np.ndarray:
+    info = sl_get_info(ctx)
+    out = np.empty((info["cells"], info["ncoef"]))
+    _check(lib().sl_get_coeffs(ctx, _ptr(out)), ctx)
+    return out
+
+
+def sl_get_cells(ctx, cells) -> np.ndarray:
+    info = sl_get_info(ctx)
+    c = np.ascontiguousarray(cells, dtype=np.int64)
+    out = np.empty((c.size, info["ncoef"]))
+    _check(lib().sl_get_cells(ctx, _ptr(c, _i64p), c.size, _ptr(out)), ctx)
+    return out
+
+
+_ELEM = {SL_FP64: np.float64, SL_MIX_FP32: np.float32, SL_MIX_BF16: np.uint16,
+         SL_MIX_FP16: np.uint16}
+
+
+def plane_arrays(ctx):
+    """Host numpy arrays (mean, hi, scale) shaped for sl_get_planes / sl_set_planes."""
+    info = sl_get_info(ctx)
+    st = info["storage"]
+    mean = np.empty(info["cells"], dtype=np.float64)
+    hi = np.empty((info["ncoef"] - 1, info["cells"]), dtype=_ELEM[st])
+    scale = np.empty(info["cells"], dtype=np.float32) if st in (SL_MIX_BF16, SL_MIX_FP16) else None
+    return mean, hi, scale
+
+
+def sl_set_planes(ctx, mean, hi, scale=None):
+    """Enqueue the copy of raw planes (host arrays or raw host addresses).
+    The memory must stay valid until the context's stream passes the copy."""
+    fp = ctypes.POINTER(ctypes.c_float)
+    m = mean if isinstance(mean, int) else _ptr(mean)
+    m = ctypes.cast(m, _dp) if isinstance(mean, int) else m
+    h = hi if isinstance(hi, int) else hi.ctypes.data
+    s = None if scale is None else (ctypes.cast(scale, fp) if isinstance(scale, int) else scale.ctypes.data_as(fp))
+    _check(lib().sl_set_planes(ctx, m, ctypes.c_void_p(h), s), ctx)
+
+
+def sl_get_planes(ctx, mean=None, hi=None, scale=None):
+    if mean is None:
+        mean, hi, scale = plane_arrays(ctx)
+    fp = ctypes.POINTER(ctypes.c_float)
+    s = None if scale is None else scale.ctypes.data_as(fp)
+    _check(lib().sl_get_planes(ctx, _ptr(mean), ctypes.c_void_p(hi.ctypes.data), s), ctx)
+    return mean, hi, scale
+
+
+def sl_project(ctx, nq: int, weights, params):
+    w = _f64(weights)
+    p = _f64(params)
+    _check(lib().sl_project(ctx, int(nq), int(w.size), _ptr(w), _ptr(p)), ctx)
+
+
+def sl_advect(ctx, dim: int, shift_dim: int, shifts):
+    s = _f64(np.atleast_1d(shifts))
+    _check(lib().sl_advect(ctx, int(dim), int(shift_dim), _ptr(s), s.size), ctx)
+
+
+def sl_set_fields(ctx, fields):
+    if isinstance(fields, (list, tuple)):
+        f = _f64(np.concatenate([np.ravel(x) for x in fields])) if fields else np.zeros(0)
+    else:
+        f = _f64(fields)
+    _check(lib().sl_set_fields(ctx, _ptr(f), f.size), ctx)
+
+
+def _split(s) -> int:
+    return SPLITTING[s] if isinstance(s, str) else int(s)
+
+
+def sl_step(ctx, splitting, dt: float, nsteps: int):
+    _check(lib().sl_step(ctx, _split(splitting), float(dt), int(nsteps)), ctx)
+
+
+def sl_mass(ctx) -> float:
+    m = ctypes.c_double()
+    _check(lib().sl_mass(ctx, ctypes.byref(m)), ctx)
+    return m.value
+
+
+def sl_graph_capture(ctx, splitting, dt: float, nsteps: int):
+    _check(lib().sl_graph_capture(ctx, _split(splitting), float(dt), int(nsteps)), ctx)
+
+
+def sl_graph_launch(ctx):
+    _check(lib().sl_graph_launch(ctx), ctx)
+
+
+def sl_synchronize(ctx):
+    _check(lib().sl_synchronize(ctx), ctx)
+
+
+def sl_profile_enable(ctx, enable: bool = True):
+    _check(lib().sl_profile_enable(ctx, 1 if enable else 0), ctx)
+
+
+def sl_profile_query(ctx) -> Tuple[int, float, float]:
+    n = ctypes.c_int64()
+    ms = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(lib().sl_profile_query(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)), ctx)
+    return n.value, ms.value, b.value
+
+
+class Context:
+    """Owns one sl_ctx handle; methods forward to the functions above."""
+
+    def __init__(self, grid, degree: int, storage, stream=None):
+        self.grid = grid
+        self.degree = degree
+        self.storage = storage
+        self.handle = sl_create(grid, degree, storage, stream)
+        self.info = sl_get_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sl_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_coeffs(self, u):
+        sl_set_coeffs(self.handle, u)
+
+    def get_coeffs(self) -> np.ndarray:
+        return sl_get_coeffs(self.handle)
+
+    def get_cells(self, cells) -> np.ndarray:
+        return sl_get_cells(self.handle, cells)
+
+    def project(self, nq, weights, params):
+        sl_project(self.handle, nq, weights, params)
+
+    def advect(self, dim, shift_dim, shifts):
+        sl_advect(self.handle, dim, shift_dim, shifts)
+
+    def set_fields(self, fields):
+        sl_set_fields(self.handle, fields)
+
+    def step(self, splitting, dt, nsteps=1):
+        sl_step(self.handle, splitting, dt, nsteps)
+
+    def mass(self) -> float:
+        return sl_mass(self.handle)
+
+    def graph_capture(self, splitting, dt, nsteps):
+        sl_graph_capture(self.handle, splitting, dt, nsteps)
+
+    def graph_launch(self):
+        sl_graph_launch(self.handle)
+
+    def synchronize(self):
+        sl_synchronize(self.handle)
+
+    def profile_enable(self, on=True):
+        sl_profile_enable(self.handle, on)
+
+    def profile_query(self):
+        return sl_profile_query(self.handle)

@@ -1,0 +1,927 @@
+// sl_api.cu -- host side of libsl.so: the C ABI of include/sl.h.
+//
+// A context owns one device allocation holding two copies of the split
+// coefficient store (ping-pong: every sweep reads one copy and writes the
+// other), the per-shift-class tables, the mass-reduction partials and the
+// field samples.  All device work goes to the context's stream; only calls
+// that hand results to the host synchronise it.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sl.h"
+#include "sl_internal.cuh"
+
+using namespace sl;
+
+struct sl_ctx {
+    sl_grid g{};
+    int K = 0, O = 1, ndim = 1;
+    Mode mode = M_FP64;
+    cudaStream_t st = nullptr;
+    int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
+    size_t elem = 8;
+    int64_t state_bytes = 0;
+
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    Planes planes[2]{};
+    int cur = 0;
+
+    int maxcls = 1;
+    int32_t* d_sigma = nullptr;
+    double* d_alpha = nullptr;
+    double* d_ab64 = nullptr;
+    float* d_ab32 = nullptr;
+    double* d_shifts = nullptr;
+    double* d_fields = nullptr;
+    int64_t nfields = 0;
+    bool fields_set = false;
+    double* d_partials = nullptr;
+    double* d_mass = nullptr;
+    int mass_nblk = 1;
+    double* h_mass = nullptr;   // pinned
+
+    double* d_stage = nullptr;  // lazily allocated AoS staging for set/get
+    int64_t stage_cells = 0;
+    double* d_proj = nullptr;   // lazily allocated projection workspace
+    size_t proj_bytes = 0;
+
+    PolyTab poly{};
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_start = -1;       // copy index the first graph starts from
+    int graph_flip = 0;         // sweeps per graph mod 2
+    bool capturing = false;
+
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+    int64_t prof_launches = 0;
+
+    struct Tune {
+        int block = 256;
+        int ft = 1;
+        uint32_t chunk = 0;
+    } tune[SL_MAX_DIM];
+
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_err = buf;
+    return s;
+}
+
+sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what)
+{
+    return fail(c, SL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define SL_CUDA(ctx, call)                                          \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
+    } while (0)
+
+size_t elem_size(int mode)
+{
+    switch (mode) {
+    case M_FP64: return 8;
+    case M_F32: return 4;
+    default: return 2;
+    }
+}
+
+int64_t ipow(int64_t b, int e)
+{
+    int64_t r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c)
+{
+    if (!g) return fail(c, SL_EINVAL, "grid is NULL");
+    if (g->ndim < 1 || g->ndim > SL_MAX_DIM)
+        return fail(c, SL_EINVAL, "ndim must be in 1..%d (got %d)", SL_MAX_DIM, g->ndim);
+    if (degree < 0 || degree > SL_MAX_DEGREE)
+        return fail(c, SL_EINVAL, "degree must be in 0..%d (got %d)", SL_MAX_DEGREE, degree);
+    if (storage < SL_FP64 || storage > SL_MIX_FP16)
+        return fail(c, SL_EINVAL, "unknown storage mode %d", storage);
+    double cells = 1.0;
+    for (int m = 0; m < g->ndim; ++m) {
+        if (g->n[m] < 1) return fail(c, SL_EINVAL, "n[%d] must be >= 1 (got %lld)", m, (long long)g->n[m]);
+        if (!std::isfinite(g->lo[m]) || !std::isfinite(g->hi[m]) || !(g->hi[m] > g->lo[m]))
+            return fail(c, SL_EINVAL, "dimension %d needs finite lo < hi", m);
+        cells *= double(g->n[m]);
+    }
+    int used[SL_MAX_DIM] = {0};
+    for (int m = 0; m < g->ndim; ++m) {
+        const int p = g->pair[m];
+        if (p == -1) continue;
+        if (p < 0 || p >= g->ndim || p == m)
+            return fail(c, SL_EINVAL, "pair[%d] = %d is not another dimension", m, p);
+        if (g->pair[p] != -1) return fail(c, SL_EINVAL, "v-dimension %d is itself paired", p);
+        if (used[p]++) return fail(c, SL_EINVAL, "v-dimension %d paired twice", p);
+    }
+    if (cells > double(0x7fffffff))
+        return fail(c, SL_ENOTSUP, "grid has %.0f cells; this build indexes cells with 31 bits", cells);
+    const int64_t nc = ipow(degree + 1, g->ndim);
+    if ((storage == SL_MIX_BF16 || storage == SL_MIX_FP16) && nc > kMaxScaledCoef)
+        return fail(c, SL_ENOTSUP, "scaled storage needs o^d <= %d (got %lld)", kMaxScaledCoef,
+                    (long long)nc);
+    return SL_OK;
+}
+
+int64_t state_bytes_of(int64_t cells, int64_t ncoef, int mode)
+{
+    int64_t b = cells * (8 + (ncoef - 1) * int64_t(elem_size(mode)));
+    if (mode == M_BF16 || mode == M_FP16) b += cells * 4;
+    return b;
+}
+
+double cell_width(const sl_grid& g, int m) { return (g.hi[m] - g.lo[m]) / double(g.n[m]); }
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Default launch shape for a sweep along dimension m.
+void default_tune(sl_ctx* c, int m)
+{
+    auto& t = c->tune[m];
+    const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
+    t.ft = 1;
+    if (m == 0) {
+        t.block = 256;
+        t.chunk = 0;
+        return;
+    }
+    t.block = 128;
+    const int64_t N = c->g.n[m];
+    const int64_t lines = c->cells / N;
+    const int64_t nfg = scaled ? 1 : (c->nfib + t.ft - 1) / t.ft;
+    // enough threads for a few waves of 2048 resident threads on 152 SMs
+    const int64_t want = int64_t(152) * 2048 * 2;
+    int64_t nchunk = (want + lines * nfg - 1) / (lines * nfg);
+    if (nchunk < 1) nchunk = 1;
+    int64_t chunk = (N + nchunk - 1) / nchunk;
+    if (chunk < 4) chunk = 4;
+    if (chunk > N) chunk = N;
+    while (((N + chunk - 1) / chunk) * nfg > 65535) chunk *= 2;
+    if (chunk > N) chunk = N;
+    t.chunk = uint32_t(chunk);
+}
+
+SweepArgs make_args(sl_ctx* c, int dim, int shift_dim)
+{
+    SweepArgs a{};
+    a.src = c->planes[c->cur];
+    a.dst = c->planes[c->cur ^ 1];
+    a.tab.sigma = c->d_sigma;
+    a.tab.alpha = c->d_alpha;
+    a.tab.ab64 = c->d_ab64;
+    a.tab.ab32 = c->d_ab32;
+    a.cells = uint32_t(c->cells);
+    a.N = uint32_t(c->g.n[dim]);
+    int64_t inner = 1;
+    for (int q = 0; q < dim; ++q) inner *= c->g.n[q];
+    a.inner = uint32_t(inner);
+    a.lines = uint32_t(c->cells / c->g.n[dim]);
+    a.pstride = c->pstride;
+    a.fdN.set(a.N);
+    a.fdInner.set(a.inner);
+    if (shift_dim < 0) {
+        a.cls_src = 0;
+    } else {
+        // The class is the coordinate along shift_dim.  For the strided
+        // kernel a line is (outer, inner): shift_dim < dim lies in the inner
+        // index, shift_dim > dim in the outer index.  The unit-stride kernel
+        // (dim = 0) passes the line index as the outer index.
+        int64_t div = 1;
+        if (shift_dim < dim) {
+            a.cls_src = 1;
+            for (int q = 0; q < shift_dim; ++q) div *= c->g.n[q];
+        } else {
+            a.cls_src = 2;
+            for (int q = dim + 1; q < shift_dim; ++q) div *= c->g.n[q];
+        }
+        a.fdCls.set(uint32_t(div));
+        a.fdClsMod.set(uint32_t(c->g.n[shift_dim]));
+    }
+    a.ostride = int(ipow(c->O, dim));
+    a.nfib = int(c->nfib);
+    const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
+    const auto& t = c->tune[dim];
+    a.nfg = scaled ? 1 : int((c->nfib + t.ft - 1) / t.ft);
+    a.chunk = dim == 0 ? 0 : t.chunk;
+    return a;
+}
+
+cudaEvent_t take_event(sl_ctx* c)
+{
+    if (!c->ev_free.empty()) {
+        cudaEvent_t e = c->ev_free.back();
+        c->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// One sweep along dim using the shift table already built on the stream.
+sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
+{
+    SweepLaunch L{};
+    L.args = make_args(c, dim, shift_dim);
+    L.K = c->K;
+    L.mode = c->mode;
+    L.unit = dim == 0;
+    L.ft = (c->mode == M_BF16 || c->mode == M_FP16) ? int(c->nfib) : c->tune[dim].ft;
+    L.block = c->tune[dim].block;
+    L.stream = c->st;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = c->prof && !c->capturing;
+    if (prof) {
+        e0 = take_event(c);
+        e1 = take_event(c);
+        if (!e0 || !e1) return fail(c, SL_ECUDA, "cudaEventCreate failed");
+        SL_CUDA(c, cudaEventRecord(e0, c->st));
+    }
+    cudaError_t e = (c->mode == M_BF16 || c->mode == M_FP16) ? launch_sweep_scaled(L)
+                                                              : launch_sweep_fp(L);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel launch");
+    if (prof) {
+        SL_CUDA(c, cudaEventRecord(e1, c->st));
+        c->ev_used.emplace_back(e0, e1);
+        c->prof_launches++;
+    }
+    c->cur ^= 1;
+    return SL_OK;
+}
+
+sl_status build_table(sl_ctx* c, int dim, int nclass, const ShiftSource& src)
+{
+    cudaError_t e = launch_ab_build(c->K, nclass, uint32_t(c->g.n[dim]), src, c->poly, c->d_sigma,
+                                    c->d_alpha, c->d_ab64, c->d_ab32, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "ab_build launch");
+    return SL_OK;
+}
+
+// The sweeps of one split step: (dim, tau factor).
+struct SubStep {
+    int dim;
+    double frac;
+};
+
+std::vector<SubStep> plan_of(const sl_ctx* c, sl_splitting sp)
+{
+    std::vector<int> xd, vd;
+    for (int m = 0; m < c->ndim; ++m)
+        if (c->g.pair[m] >= 0) {
+            xd.push_back(m);
+            vd.push_back(c->g.pair[m]);
+        }
+    std::vector<SubStep> p;
+    if (sp == SL_STRANG) {
+        for (int m : xd) p.push_back({m, 0.5});
+        for (int v : vd) p.push_back({v, 1.0});
+        for (int m : xd) p.push_back({m, 0.5});
+    } else {
+        for (int m : xd) p.push_back({m, 1.0});
+        for (int v : vd) p.push_back({v, 1.0});
+    }
+    return p;
+}
+
+// Offset of the field of x-dimension m inside d_fields.
+int64_t field_offset(const sl_ctx* c, int xdim)
+{
+    int64_t off = 0;
+    for (int m = 0; m < xdim; ++m)
+        if (c->g.pair[m] >= 0) off += c->g.n[m];
+    return off;
+}
+
+sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
+{
+    const std::vector<SubStep> plan = plan_of(c, sp);
+    for (int s = 0; s < nsteps; ++s) {
+        for (const SubStep& ss : plan) {
+            const double tau = ss.frac * dt;
+            ShiftSource src{};
+            int shift_dim, nclass;
+            if (c->g.pair[ss.dim] >= 0) {
+                // x-sweep: velocity = cell centre of the paired v-dimension
+                const int p = c->g.pair[ss.dim];
+                src.kind = 1;
+                src.lo = c->g.lo[p];
+                src.hv = cell_width(c->g, p);
+                src.tau = tau;
+                src.h = cell_width(c->g, ss.dim);
+                shift_dim = p;
+                nclass = int(c->g.n[p]);
+            } else {
+                // v-sweep: velocity = E_m at the x_m cell centres
+                int xm = -1;
+                for (int m = 0; m < c->ndim; ++m)
+                    if (c->g.pair[m] == ss.dim) xm = m;
+                src.kind = 2;
+                src.data = c->d_fields + field_offset(c, xm);
+                src.tau = tau;
+                src.h = cell_width(c->g, ss.dim);
+                shift_dim = xm;
+                nclass = int(c->g.n[xm]);
+            }
+            sl_status r = build_table(c, ss.dim, nclass, src);
+            if (r != SL_OK) return r;
+            r = run_sweep(c, ss.dim, shift_dim);
+            if (r != SL_OK) return r;
+        }
+    }
+    return SL_OK;
+}
+
+sl_status ensure_stage(sl_ctx* c)
+{
+    if (c->d_stage) return SL_OK;
+    const int64_t bytes_target = int64_t(64) << 20;
+    int64_t n = bytes_target / (c->ncoef * 8);
+    if (n < 1) n = 1;
+    if (n > c->cells) n = c->cells;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, size_t(n) * c->ncoef * 8);
+    if (e != cudaSuccess) return fail(c, SL_ENOMEM, "staging allocation: %s", cudaGetErrorString(e));
+    c->d_stage = static_cast<double*>(p);
+    c->stage_cells = n;
+    return SL_OK;
+}
+
+CodecArgs codec_of(const sl_ctx* c)
+{
+    CodecArgs a{};
+    a.p = c->planes[c->cur];
+    a.pstride = c->pstride;
+    a.ncoef = int(c->ncoef);
+    a.mode = c->mode;
+    return a;
+}
+
+void drop_graph(sl_ctx* c)
+{
+    for (auto& g : c->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    c->graph_start = -1;
+}
+
+}  // namespace
+
+// ======================================================================
+// ABI
+// ======================================================================
+
+extern "C" {
+
+const char* sl_last_error(const sl_ctx* ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_err.c_str();
+}
+
+sl_status sl_state_bytes(const sl_grid* grid, int degree, sl_storage storage, int64_t* bytes)
+{
+    sl_status s = check_grid(grid, degree, storage, nullptr);
+    if (s != SL_OK) return s;
+    if (!bytes) return fail(nullptr, SL_EINVAL, "bytes is NULL");
+    int64_t cells = 1;
+    for (int m = 0; m < grid->ndim; ++m) cells *= grid->n[m];
+    *bytes = state_bytes_of(cells, ipow(degree + 1, grid->ndim), storage);
+    return SL_OK;
+}
+
+sl_status sl_ab_host(int degree, double alpha, double* A, double* B)
+{
+    if (degree < 0 || degree > SL_MAX_DEGREE) return fail(nullptr, SL_EINVAL, "degree out of range");
+    if (!(alpha >= 0.0) || !(alpha < 1.0)) return fail(nullptr, SL_EINVAL, "alpha must be in [0,1)");
+    if (!A || !B) return fail(nullptr, SL_EINVAL, "NULL output");
+    PolyTab t;
+    build_poly_table(degree, &t);
+    const int O = degree + 1, deg = 2 * degree + 1;
+    const double x = alpha - 0.5;
+    for (int j = 0; j < O; ++j)
+        for (int l = 0; l < O; ++l) {
+            double va, vb;
+            if (alpha == 0.0) {
+                va = j == l ? 1.0 : 0.0;
+                vb = 0.0;
+            } else {
+                va = t.a[j][l][deg];
+                vb = t.b[j][l][deg];
+                for (int p = deg - 1; p >= 0; --p) {
+                    va = std::fma(va, x, t.a[j][l][p]);
+                    vb = std::fma(vb, x, t.b[j][l][p]);
+                }
+            }
+            A[j * O + l] = va;
+            B[j * O + l] = vb;
+        }
+    return SL_OK;
+}
+
+sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
+                    sl_ctx** out)
+{
+    if (!out) return fail(nullptr, SL_EINVAL, "out is NULL");
+    *out = nullptr;
+    sl_status s = check_grid(grid, degree, storage, nullptr);
+    if (s != SL_OK) return s;
+
+    sl_ctx* c = new (std::nothrow) sl_ctx();
+    if (!c) return fail(nullptr, SL_ENOMEM, "host allocation failed");
+    c->g = *grid;
+    for (int m = c->g.ndim; m < SL_MAX_DIM; ++m) {
+        c->g.n[m] = 1;
+        c->g.pair[m] = -1;
+    }
+    c->K = degree;
+    c->O = degree + 1;
+    c->ndim = grid->ndim;
+    c->mode = Mode(storage);
+    c->st = static_cast<cudaStream_t>(cuda_stream);
+    c->cells = 1;
+    for (int m = 0; m < c->ndim; ++m) c->cells *= grid->n[m];
+    c->ncoef = ipow(c->O, c->ndim);
+    c->nfib = ipow(c->O, c->ndim - 1);
+    c->pstride = int64_t(align_up(size_t(c->cells), 64));
+    c->elem = elem_size(storage);
+    c->state_bytes = state_bytes_of(c->cells, c->ncoef, storage);
+    for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
+    build_poly_table(degree, &c->poly);
+    for (int m = 0; m < c->ndim; ++m) default_tune(c, m);
+
+    const bool scaled = storage == SL_MIX_BF16 || storage == SL_MIX_FP16;
+    // layout of the single allocation
+    const size_t A = 256;
+    size_t off = 0;
+    size_t o_state[2][3];
+    for (int b = 0; b < 2; ++b) {
+        o_state[b][0] = off;
+        off = align_up(off + size_t(c->pstride) * 8, A);
+        o_state[b][1] = off;
+        off = align_up(off + size_t(c->pstride) * size_t(c->ncoef - 1) * c->elem, A);
+        o_state[b][2] = off;
+        if (scaled) off = align_up(off + size_t(c->pstride) * 4, A);
+    }
+    const size_t O2 = size_t(c->O) * c->O * 2;
+    const size_t o_sigma = off;
+    off = align_up(off + size_t(c->maxcls) * 4, A);
+    const size_t o_alpha = off;
+    off = align_up(off + size_t(c->maxcls) * 8, A);
+    const size_t o_ab64 = off;
+    off = align_up(off + size_t(c->maxcls) * O2 * 8, A);
+    const size_t o_ab32 = off;
+    off = align_up(off + size_t(c->maxcls) * O2 * 4, A);
+    const size_t o_shifts = off;
+    off = align_up(off + size_t(c->maxcls) * 8, A);
+    int64_t nf = 0;
+    for (int m = 0; m < c->ndim; ++m)
+        if (c->g.pair[m] >= 0) nf += c->g.n[m];
+    c->nfields = nf;
+    const size_t o_fields = off;
+    off = align_up(off + size_t(std::max<int64_t>(nf, 1)) * 8, A);
+    c->mass_nblk = mass_blocks(uint32_t(c->cells));
+    const size_t o_part = off;
+    off = align_up(off + size_t(c->mass_nblk) * 8, A);
+    const size_t o_mass = off;
+    off = align_up(off + 8, A);
+    c->mem_bytes = off;
+
+    cudaError_t e = cudaMalloc(&c->mem, c->mem_bytes);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(nullptr, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
+    }
+    char* base = static_cast<char*>(c->mem);
+    for (int b = 0; b < 2; ++b) {
+        c->planes[b].mean = reinterpret_cast<double*>(base + o_state[b][0]);
+        c->planes[b].hi = base + o_state[b][1];
+        c->planes[b].scale = scaled ? reinterpret_cast<float*>(base + o_state[b][2]) : nullptr;
+    }
+    c->d_sigma = reinterpret_cast<int32_t*>(base + o_sigma);
+    c->d_alpha = reinterpret_cast<double*>(base + o_alpha);
+    c->d_ab64 = reinterpret_cast<double*>(base + o_ab64);
+    c->d_ab32 = reinterpret_cast<float*>(base + o_ab32);
+    c->d_shifts = reinterpret_cast<double*>(base + o_shifts);
+    c->d_fields = reinterpret_cast<double*>(base + o_fields);
+    c->d_partials = reinterpret_cast<double*>(base + o_part);
+    c->d_mass = reinterpret_cast<double*>(base + o_mass);
+    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_mass), 8);
+    if (e != cudaSuccess) {
+        cudaFree(c->mem);
+        delete c;
+        return fail(nullptr, SL_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
+    }
+    // state starts at zero (the scale plane at zero decodes to zero too)
+    e = cudaMemsetAsync(c->mem, 0, c->mem_bytes, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) {
+        cudaFreeHost(c->h_mass);
+        cudaFree(c->mem);
+        delete c;
+        return fail(nullptr, SL_ECUDA, "initialising the state: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return SL_OK;
+}
+
+void sl_destroy(sl_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    drop_graph(c);
+    for (auto& pr : c->ev_used) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto e : c->ev_free) cudaEventDestroy(e);
+    if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_proj) cudaFree(c->d_proj);
+    if (c->h_mass) cudaFreeHost(c->h_mass);
+    if (c->mem) cudaFree(c->mem);
+    delete c;
+}
+
+sl_status sl_get_info(const sl_ctx* c, sl_info* out)
+{
+    if (!c || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
+    out->cells = c->cells;
+    out->ncoef = c->ncoef;
+    out->dof = c->cells * c->ncoef;
+    out->plane_stride = c->pstride;
+    out->state_bytes = c->state_bytes;
+    out->alloc_bytes = int64_t(c->mem_bytes) + (c->d_stage ? c->stage_cells * c->ncoef * 8 : 0) +
+                       int64_t(c->proj_bytes);
+    out->degree = c->K;
+    out->storage = c->mode;
+    return SL_OK;
+}
+
+sl_status sl_set_coeffs(sl_ctx* c, const double* host)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (!host) return fail(c, SL_EINVAL, "host array is NULL");
+    const int64_t n = c->cells * c->ncoef;
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(host[i])) return fail(c, SL_ENAN, "non-finite coefficient at index %lld", (long long)i);
+    sl_status s = ensure_stage(c);
+    if (s != SL_OK) return s;
+    const CodecArgs ca = codec_of(c);
+    for (int64_t first = 0; first < c->cells; first += c->stage_cells) {
+        const int64_t cnt = std::min(c->stage_cells, c->cells - first);
+        SL_CUDA(c, cudaMemcpyAsync(c->d_stage, host + first * c->ncoef, size_t(cnt) * c->ncoef * 8,
+                                   cudaMemcpyHostToDevice, c->st));
+        SL_CUDA(c, launch_encode(ca, c->d_stage, uint32_t(first), uint32_t(cnt), c->st));
+    }
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return SL_OK;
+}
+
+sl_status sl_get_coeffs(sl_ctx* c, double* host)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (!host) return fail(c, SL_EINVAL, "host array is NULL");
+    sl_status s = ensure_stage(c);
+    if (s != SL_OK) return s;
+    const CodecArgs ca = codec_of(c);
+    for (int64_t first = 0; first < c->cells; first += c->stage_cells) {
+        const int64_t cnt = std::min(c->stage_cells, c->cells - first);
+        SL_CUDA(c, launch_decode(ca, c->d_stage, uint32_t(first), uint32_t(cnt), c->st));
+        SL_CUDA(c, cudaMemcpyAsync(host + first * c->ncoef, c->d_stage, size_t(cnt) * c->ncoef * 8,
+                                   cudaMemcpyDeviceToHost, c->st));
+        SL_CUDA(c, cudaStreamSynchronize(c->st));
+    }
+    return SL_OK;
+}
+
+sl_status sl_get_cells(sl_ctx* c, const int64_t* cells, int64_t ncells, double* host)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (ncells < 0 || (ncells > 0 && (!cells || !host))) return fail(c, SL_EINVAL, "bad cell list");
+    if (ncells == 0) return SL_OK;
+    for (int64_t i = 0; i < ncells; ++i)
+        if (cells[i] < 0 || cells[i] >= c->cells)
+            return fail(c, SL_EINVAL, "cell index %lld out of range", (long long)cells[i]);
+    sl_status s = ensure_stage(c);
+    if (s != SL_OK) return s;
+    // stage layout: [idx block of int64][values]
+    const CodecArgs ca = codec_of(c);
+    const int64_t per = std::max<int64_t>(1, (c->stage_cells * c->ncoef * 8) / (8 + c->ncoef * 8));
+    for (int64_t first = 0; first < ncells; first += per) {
+        const int64_t cnt = std::min(per, ncells - first);
+        int64_t* d_idx = reinterpret_cast<int64_t*>(c->d_stage);
+        double* d_val = c->d_stage + cnt;
+        SL_CUDA(c, cudaMemcpyAsync(d_idx, cells + first, size_t(cnt) * 8, cudaMemcpyHostToDevice, c->st));
+        SL_CUDA(c, launch_gather(ca, d_idx, uint32_t(cnt), d_val, c->st));
+        SL_CUDA(c, cudaMemcpyAsync(host + first * c->ncoef, d_val, size_t(cnt) * c->ncoef * 8,
+                                   cudaMemcpyDeviceToHost, c->st));
+        SL_CUDA(c, cudaStreamSynchronize(c->st));
+    }
+    return SL_OK;
+}
+
+static sl_status planes_args(sl_ctx* c, const void* mean, const void* hi, const void* scale)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
+    if (!mean || (c->ncoef > 1 && !hi)) return fail(c, SL_EINVAL, "NULL plane");
+    if (scaled && !scale) return fail(c, SL_EINVAL, "scaled store needs the scale plane");
+    if (c->capturing) return fail(c, SL_EINVAL, "plane copies cannot be captured");
+    return SL_OK;
+}
+
+sl_status sl_set_planes(sl_ctx* c, const double* mean, const void* hi, const float* scale)
+{
+    sl_status s = planes_args(c, mean, hi, scale);
+    if (s != SL_OK) return s;
+    const Planes& p = c->planes[c->cur];
+    SL_CUDA(c, cudaMemcpyAsync(p.mean, mean, size_t(c->cells) * 8, cudaMemcpyHostToDevice, c->st));
+    if (c->ncoef > 1)
+        SL_CUDA(c, cudaMemcpy2DAsync(p.hi, size_t(c->pstride) * c->elem, hi, size_t(c->cells) * c->elem,
+                                     size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
+                                     cudaMemcpyHostToDevice, c->st));
+    if (p.scale)
+        SL_CUDA(c, cudaMemcpyAsync(p.scale, scale, size_t(c->cells) * 4, cudaMemcpyHostToDevice, c->st));
+    return SL_OK;
+}
+
+sl_status sl_get_planes(sl_ctx* c, double* mean, void* hi, float* scale)
+{
+    sl_status s = planes_args(c, mean, hi, scale);
+    if (s != SL_OK) return s;
+    const Planes& p = c->planes[c->cur];
+    SL_CUDA(c, cudaMemcpyAsync(mean, p.mean, size_t(c->cells) * 8, cudaMemcpyDeviceToHost, c->st));
+    if (c->ncoef > 1)
+        SL_CUDA(c, cudaMemcpy2DAsync(hi, size_t(c->cells) * c->elem, p.hi, size_t(c->pstride) * c->elem,
+                                     size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
+                                     cudaMemcpyDeviceToHost, c->st));
+    if (p.scale)
+        SL_CUDA(c, cudaMemcpyAsync(scale, p.scale, size_t(c->cells) * 4, cudaMemcpyDeviceToHost, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return SL_OK;
+}
+
+sl_status sl_project(sl_ctx* c, int nq, int nterms, const double* weights, const double* params)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (nq < 1 || nq > kMaxQuad) return fail(c, SL_EINVAL, "nq must be in 1..%d", kMaxQuad);
+    if (nterms < 0 || (nterms > 0 && (!weights || !params))) return fail(c, SL_EINVAL, "bad terms");
+    for (int i = 0; i < nterms; ++i)
+        if (!std::isfinite(weights[i])) return fail(c, SL_ENAN, "non-finite weight");
+    for (int i = 0; i < nterms * c->ndim * 4; ++i)
+        if (!std::isfinite(params[i])) return fail(c, SL_ENAN, "non-finite factor parameter");
+    ProjectArgs pa{};
+    pa.ndim = c->ndim;
+    pa.K = c->K;
+    pa.nq = nq;
+    pa.nterms = nterms;
+    uint32_t nmax = 1;
+    for (int m = 0; m < c->ndim; ++m) {
+        pa.n[m] = uint32_t(c->g.n[m]);
+        pa.lo[m] = c->g.lo[m];
+        pa.h[m] = cell_width(c->g, m);
+        nmax = std::max<uint32_t>(nmax, pa.n[m]);
+    }
+    // Gauss-Legendre nodes and weights: roots of P_nq by Newton's method.
+    for (int i = 0; i < nq; ++i) {
+        double z = std::cos(M_PI * (nq - i - 0.25) / (nq + 0.5));
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int m = 2; m <= nq; ++m) {
+                const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+                p0 = p1;
+                p1 = p2;
+            }
+            const double dp = nq * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) <= 1e-17) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int m = 2; m <= nq; ++m) {
+            const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+            p0 = p1;
+            p1 = p2;
+        }
+        const double dp = nq * (z * p1 - p0) / (z * z - 1.0);
+        pa.node[i] = z;
+        pa.weight[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    const size_t tab_n = size_t(std::max(nterms, 1)) * c->ndim * nmax * c->O;
+    const size_t need = (tab_n + size_t(std::max(nterms, 1)) * (1 + c->ndim * 4)) * 8;
+    if (need > c->proj_bytes) {
+        if (c->d_proj) {
+            cudaStreamSynchronize(c->st);
+            cudaFree(c->d_proj);
+            c->d_proj = nullptr;
+            c->proj_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_proj), need);
+        if (e != cudaSuccess) return fail(c, SL_ENOMEM, "projection workspace: %s", cudaGetErrorString(e));
+        c->proj_bytes = need;
+    }
+    double* d_tab = c->d_proj;
+    double* d_w = d_tab + tab_n;
+    double* d_p = d_w + std::max(nterms, 1);
+    if (nterms > 0) {
+        SL_CUDA(c, cudaMemcpyAsync(d_w, weights, size_t(nterms) * 8, cudaMemcpyHostToDevice, c->st));
+        SL_CUDA(c, cudaMemcpyAsync(d_p, params, size_t(nterms) * c->ndim * 4 * 8,
+                                   cudaMemcpyHostToDevice, c->st));
+    }
+    SL_CUDA(c, launch_project(pa, d_w, d_p, d_tab, nmax, codec_of(c), uint32_t(c->cells), c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return SL_OK;
+}
+
+sl_status sl_advect(sl_ctx* c, int dim, int shift_dim, const double* shifts, int64_t nshift)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (dim < 0 || dim >= c->ndim) return fail(c, SL_EINVAL, "dim %d out of range", dim);
+    if (shift_dim < -1 || shift_dim >= c->ndim || shift_dim == dim)
+        return fail(c, SL_EINVAL, "shift_dim %d invalid for dim %d", shift_dim, dim);
+    const int64_t expect = shift_dim < 0 ? 1 : c->g.n[shift_dim];
+    if (nshift != expect) return fail(c, SL_EINVAL, "nshift = %lld, expected %lld", (long long)nshift, (long long)expect);
+    if (!shifts) return fail(c, SL_EINVAL, "shifts is NULL");
+    for (int64_t i = 0; i < nshift; ++i)
+        if (!std::isfinite(shifts[i]) || std::fabs(shifts[i]) > 1e15)
+            return fail(c, SL_ENAN, "shift %lld is not finite or too large", (long long)i);
+    if (c->capturing) return fail(c, SL_EINVAL, "sl_advect cannot be captured (host shifts)");
+    SL_CUDA(c, cudaMemcpyAsync(c->d_shifts, shifts, size_t(nshift) * 8, cudaMemcpyHostToDevice, c->st));
+    ShiftSource src{};
+    src.kind = 0;
+    src.data = c->d_shifts;
+    sl_status s = build_table(c, dim, int(nshift), src);
+    if (s != SL_OK) return s;
+    return run_sweep(c, dim, shift_dim);
+}
+
+sl_status sl_set_fields(sl_ctx* c, const double* fields, int64_t count)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (count != c->nfields) return fail(c, SL_EINVAL, "count = %lld, expected %lld", (long long)count, (long long)c->nfields);
+    if (count == 0) {
+        c->fields_set = true;
+        return SL_OK;
+    }
+    if (!fields) return fail(c, SL_EINVAL, "fields is NULL");
+    for (int64_t i = 0; i < count; ++i)
+        if (!std::isfinite(fields[i])) return fail(c, SL_ENAN, "non-finite field sample %lld", (long long)i);
+    SL_CUDA(c, cudaMemcpyAsync(c->d_fields, fields, size_t(count) * 8, cudaMemcpyHostToDevice, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    c->fields_set = true;
+    return SL_OK;
+}
+
+static sl_status check_step_args(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (sp != SL_LIE && sp != SL_STRANG) return fail(c, SL_EINVAL, "unknown splitting %d", int(sp));
+    if (!std::isfinite(dt)) return fail(c, SL_ENAN, "dt is not finite");
+    if (nsteps < 0) return fail(c, SL_EINVAL, "nsteps < 0");
+    bool any = false;
+    for (int m = 0; m < c->ndim; ++m) any |= c->g.pair[m] >= 0;
+    if (!any) return fail(c, SL_EINVAL, "grid has no x/v pairs to split");
+    if (c->nfields > 0 && !c->fields_set) return fail(c, SL_EINVAL, "fields not set (sl_set_fields)");
+    return SL_OK;
+}
+
+sl_status sl_step(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
+{
+    sl_status s = check_step_args(c, sp, dt, nsteps);
+    if (s != SL_OK) return s;
+    return enqueue_steps(c, sp, dt, nsteps);
+}
+
+sl_status sl_mass(sl_ctx* c, double* out)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, SL_EINVAL, "out is NULL");
+    double vol = 1.0;
+    for (int m = 0; m < c->ndim; ++m) vol *= cell_width(c->g, m);
+    SL_CUDA(c, launch_mass(c->planes[c->cur].mean, uint32_t(c->cells), c->d_partials, c->mass_nblk,
+                           vol, c->d_mass, c->st));
+    SL_CUDA(c, cudaMemcpyAsync(c->h_mass, c->d_mass, 8, cudaMemcpyDeviceToHost, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    *out = *c->h_mass;
+    return SL_OK;
+}
+
+sl_status sl_graph_capture(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
+{
+    sl_status s = check_step_args(c, sp, dt, nsteps);
+    if (s != SL_OK) return s;
+    if (!c->st) return fail(c, SL_EINVAL, "graph capture needs a non-default stream");
+    drop_graph(c);
+    const int start = c->cur;
+    const int sweeps = int(plan_of(c, sp).size()) * nsteps;
+    const int flip = sweeps & 1;
+    const int ngraphs = flip ? 2 : 1;
+    for (int gi = 0; gi < ngraphs; ++gi) {
+        c->cur = start ^ gi;
+        cudaGraph_t graph = nullptr;
+        SL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        s = enqueue_steps(c, sp, dt, nsteps);
+        c->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+        if (s != SL_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            c->cur = start;
+            drop_graph(c);
+            return s;
+        }
+        if (e != cudaSuccess) {
+            c->cur = start;
+            drop_graph(c);
+            return cuda_fail(c, e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(&c->gexec[gi], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->cur = start;
+            drop_graph(c);
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+    }
+    c->cur = start;
+    c->graph_start = start;
+    c->graph_flip = flip;
+    return SL_OK;
+}
+
+sl_status sl_graph_launch(sl_ctx* c)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (c->graph_start < 0) return fail(c, SL_EINVAL, "no graph captured");
+    const int gi = c->cur == c->graph_start ? 0 : 1;
+    if (!c->gexec[gi]) return fail(c, SL_EINVAL, "no graph for the current buffer parity");
+    SL_CUDA(c, cudaGraphLaunch(c->gexec[gi], c->st));
+    c->cur ^= c->graph_flip;
+    return SL_OK;
+}
+
+sl_status sl_synchronize(sl_ctx* c)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return SL_OK;
+}
+
+sl_status sl_profile_enable(sl_ctx* c, int enable)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    c->prof = enable != 0;
+    return SL_OK;
+}
+
+sl_status sl_profile_query(sl_ctx* c, int64_t* launches, double* ms, double* bytes)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    double tot = 0.0;
+    for (auto& pr : c->ev_used) {
+        float t = 0.0f;
+        SL_CUDA(c, cudaEventElapsedTime(&t, pr.first, pr.second));
+        tot += t;
+        c->ev_free.push_back(pr.first);
+        c->ev_free.push_back(pr.second);
+    }
+    c->ev_used.clear();
+    if (launches) *launches = c->prof_launches;
+    if (ms) *ms = tot;
+    if (bytes) *bytes = 2.0 * double(c->state_bytes) * double(c->prof_launches);
+    c->prof_launches = 0;
+    return SL_OK;
+}
+
+}  // extern "C"

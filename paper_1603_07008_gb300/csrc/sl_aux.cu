@@ -1,0 +1,373 @@
+// sl_aux.cu -- the small kernels around the sweep: shift decomposition and
+// construction of A(alpha), B(alpha) per shift class, the FP64 mass
+// reduction, encoding/decoding of the split store, and the initial
+// projection eq. (cj).
+#include "sl_sweep.cuh"
+
+namespace sl {
+
+// ---------------------------------------------------------------- A, B
+
+// One thread per shift class.  s = a tau / h in cells (from an array, from
+// the cell-centre velocity of a v-dimension, or from field samples), split as
+// sigma = floor(s), alpha = s - sigma (alpha rounding to 1 moves to the next
+// integer), sigma reduced into [0, N).  The entries of A and B are the exact
+// polynomials of Sec. II-A's projection integrals, stored centred at
+// alpha = 1/2 and evaluated by Horner's rule; alpha = 0 is the exact identity.
+__global__ void k_ab_build(int K, int nclass, uint32_t N, ShiftSource src, PolyTab tab,
+                           int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                           double* __restrict__ ab64, float* __restrict__ ab32)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclass) return;
+    double s;
+    if (src.kind == 0) {
+        s = src.data[c];
+    } else if (src.kind == 1) {
+        const double v = __dadd_rn(src.lo, __dmul_rn(double(c) + 0.5, src.hv));
+        s = __ddiv_rn(__dmul_rn(v, src.tau), src.h);
+    } else {
+        s = __ddiv_rn(__dmul_rn(src.data[c], src.tau), src.h);
+    }
+    const double f = floor(s);
+    double a = s - f;
+    long long sg = (long long)f;
+    if (a >= 1.0) {
+        sg += 1;
+        a = 0.0;
+    }
+    long long r = sg % (long long)N;
+    if (r < 0) r += N;
+    sigma[c] = int32_t(r);
+    alpha[c] = a;
+
+    const int O = K + 1;
+    const int deg = 2 * K + 1;
+    const double t = a - 0.5;
+    double* m64 = ab64 + size_t(c) * 2 * O * O;
+    float* m32 = ab32 + size_t(c) * 2 * O * O;
+    for (int j = 0; j < O; ++j) {
+        for (int l = 0; l < O; ++l) {
+            double va, vb;
+            if (a == 0.0) {
+                va = (j == l) ? 1.0 : 0.0;
+                vb = 0.0;
+            } else {
+                va = tab.a[j][l][deg];
+                vb = tab.b[j][l][deg];
+                for (int p = deg - 1; p >= 0; --p) {
+                    va = fma(va, t, tab.a[j][l][p]);
+                    vb = fma(vb, t, tab.b[j][l][p]);
+                }
+            }
+            m64[j * O + l] = va;
+            m64[O * O + j * O + l] = vb;
+            m32[j * O + l] = __double2float_rn(va);
+            m32[O * O + j * O + l] = __double2float_rn(vb);
+        }
+    }
+}
+
+cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,
+                            const PolyTab& tab, int32_t* sigma, double* alpha, double* ab64,
+                            float* ab32, cudaStream_t st)
+{
+    const int block = 128;
+    k_ab_build<<<(nclass + block - 1) / block, block, 0, st>>>(K, nclass, N, src, tab, sigma,
+                                                              alpha, ab64, ab32);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- mass
+
+constexpr int kMassThreads = 256;
+constexpr int kMassMaxBlocks = 1024;
+
+int mass_blocks(uint32_t cells)
+{
+    int64_t b = (int64_t(cells) + kMassThreads * 8 - 1) / (kMassThreads * 8);
+    if (b < 1) b = 1;
+    if (b > kMassMaxBlocks) b = kMassMaxBlocks;
+    return int(b);
+}
+
+__device__ __forceinline__ double block_sum(double v)
+{
+    __shared__ double red[kMassThreads / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < kMassThreads / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    }
+    return s;   // valid in thread 0
+}
+
+// Fixed-shape reduction: the grid size depends only on the cell count, each
+// thread sums a fixed strided subset, warps reduce by shuffles, blocks write
+// partials, and one block sums the partials in a fixed order.
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial(const double* __restrict__ mean,
+                                                               uint32_t cells,
+                                                               double* __restrict__ partials)
+{
+    double s = 0.0;
+    for (uint32_t c = blockIdx.x * kMassThreads + threadIdx.x; c < cells;
+         c += gridDim.x * kMassThreads)
+        s += mean[c];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* __restrict__ partials,
+                                                             int n, double vol,
+                                                             double* __restrict__ out)
+{
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += kMassThreads) s += partials[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) out[0] = vol * s;
+}
+
+cudaError_t launch_mass(const double* mean, uint32_t cells, double* partials, int nblocks,
+                        double vol, double* out, cudaStream_t st)
+{
+    k_mass_partial<<<nblocks, kMassThreads, 0, st>>>(mean, cells, partials);
+    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, vol, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- codec
+
+template <int MODE>
+__device__ void encode_cell(const CodecArgs& c, const double* v, uint32_t cell)
+{
+    using T = typename St<MODE>::T;
+    c.p.mean[cell] = v[0];
+    if constexpr (MODE == M_FP64) {
+        for (int J = 1; J < c.ncoef; ++J) plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = v[J];
+    } else if constexpr (MODE == M_F32) {
+        for (int J = 1; J < c.ncoef; ++J)
+            plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = __double2float_rn(v[J]);
+    } else {
+        double mx = 0.0;
+        for (int J = 1; J < c.ncoef; ++J) mx = fmax(mx, fabs(v[J]));
+        float s, inv;
+        pow2_scale(__double2float_rn(mx), s, inv);
+        c.p.scale[cell] = s;
+        for (int J = 1; J < c.ncoef; ++J) {
+            const double x = v[J] * double(inv);   // exact: inv is a power of two
+            T* dst = plane_ptr_w<T>(c.p.hi, c.pstride, J) + cell;
+            if constexpr (MODE == M_BF16)
+                *dst = __double2bfloat16(x);
+            else
+                *dst = __double2half(x);
+        }
+    }
+}
+
+template <int MODE>
+__device__ void decode_cell(const CodecArgs& c, uint32_t cell, double* out)
+{
+    using T = typename St<MODE>::T;
+    out[0] = c.p.mean[cell];
+    double s = 1.0;
+    if constexpr (St<MODE>::scaled) s = double(c.p.scale[cell]);
+    for (int J = 1; J < c.ncoef; ++J) {
+        const T raw = plane_ptr<T>(c.p.hi, c.pstride, J)[cell];
+        double x;
+        if constexpr (MODE == M_FP64)
+            x = raw;
+        else if constexpr (MODE == M_F32)
+            x = double(raw);
+        else if constexpr (MODE == M_BF16)
+            x = double(__bfloat162float(raw));
+        else
+            x = double(__half2float(raw));
+        out[J] = x * s;
+    }
+}
+
+template <int MODE>
+__global__ void k_encode(CodecArgs c, const double* __restrict__ aos, uint32_t first,
+                         uint32_t count)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    encode_cell<MODE>(c, aos + size_t(t) * c.ncoef, first + t);
+}
+
+template <int MODE>
+__global__ void k_decode(CodecArgs c, double* __restrict__ aos, uint32_t first, uint32_t count)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    decode_cell<MODE>(c, first + t, aos + size_t(t) * c.ncoef);
+}
+
+template <int MODE>
+__global__ void k_gather(CodecArgs c, const int64_t* __restrict__ cells, uint32_t count,
+                         double* __restrict__ aos)
+{
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    decode_cell<MODE>(c, uint32_t(cells[t]), aos + size_t(t) * c.ncoef);
+}
+
+#define SL_MODE_SWITCH(mode, CALL)                     \
+    switch (mode) {                                    \
+    case M_FP64: { constexpr int MD = M_FP64; CALL; } break; \
+    case M_F32: { constexpr int MD = M_F32; CALL; } break;   \
+    case M_BF16: { constexpr int MD = M_BF16; CALL; } break; \
+    case M_FP16: { constexpr int MD = M_FP16; CALL; } break; \
+    default: return cudaErrorInvalidValue;             \
+    }
+
+cudaError_t launch_encode(const CodecArgs& c, const double* aos, uint32_t first, uint32_t count,
+                          cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const int b = 128;
+    SL_MODE_SWITCH(c.mode, (k_encode<MD><<<(count + b - 1) / b, b, 0, st>>>(c, aos, first, count)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode(const CodecArgs& c, double* aos, uint32_t first, uint32_t count,
+                          cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const int b = 128;
+    SL_MODE_SWITCH(c.mode, (k_decode<MD><<<(count + b - 1) / b, b, 0, st>>>(c, aos, first, count)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const CodecArgs& c, const int64_t* cells, uint32_t count, double* aos,
+                          cudaStream_t st)
+{
+    if (count == 0) return cudaSuccess;
+    const int b = 128;
+    SL_MODE_SWITCH(c.mode, (k_gather<MD><<<(count + b - 1) / b, b, 0, st>>>(c, cells, count, aos)));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- projection
+
+__device__ __forceinline__ double legendre_dev(int j, double x)
+{
+    if (j == 0) return 1.0;
+    double pm = 1.0, p = x;
+    for (int n = 1; n < j; ++n) {
+        const double pn = ((2.0 * n + 1.0) * x * p - n * pm) / (n + 1.0);
+        pm = p;
+        p = pn;
+    }
+    return p;
+}
+
+// 1D projections of every factor: tab[((t*ndim + m)*nmax + i)*o + j] =
+// (2j+1)/2 sum_q w_q g_{t,m}(x_i + h t_q / 2) P_j(t_q)   (eq. (cj)).
+__global__ void k_project_1d(ProjectArgs pa, const double* __restrict__ params,
+                             double* __restrict__ tab, uint32_t nmax)
+{
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t total = uint32_t(pa.nterms) * pa.ndim * nmax;
+    if (idx >= total) return;
+    const uint32_t i = idx % nmax;
+    const uint32_t tm = idx / nmax;
+    const int m = int(tm % pa.ndim);
+    if (i >= pa.n[m]) return;
+    const double* prm = params + size_t(tm) * 4;
+    const double xc = pa.lo[m] + (double(i) + 0.5) * pa.h[m];
+    const int O = pa.K + 1;
+    for (int j = 0; j < O; ++j) {
+        double acc = 0.0;
+        for (int q = 0; q < pa.nq; ++q) {
+            const double x = xc + 0.5 * pa.h[m] * pa.node[q];
+            const double d = x - prm[1];
+            const double g = exp(-prm[0] * d * d) * cos(prm[2] * x + prm[3]);
+            acc += pa.weight[q] * g * legendre_dev(j, pa.node[q]);
+        }
+        tab[size_t(idx) * O + j] = 0.5 * (2.0 * j + 1.0) * acc;
+    }
+}
+
+// Coefficient J of a cell: sum_t w_t prod_m tab[t][m][i_m][j_m].
+__device__ double project_coef(const ProjectArgs& pa, const double* w, const double* tab,
+                               uint32_t nmax, const uint32_t* im, int J)
+{
+    const int O = pa.K + 1;
+    int jm[kMaxDim];
+    int r = J;
+    for (int m = 0; m < pa.ndim; ++m) {
+        jm[m] = r % O;
+        r /= O;
+    }
+    double v = 0.0;
+    for (int t = 0; t < pa.nterms; ++t) {
+        double p = w[t];
+        for (int m = 0; m < pa.ndim; ++m)
+            p *= tab[((size_t(t) * pa.ndim + m) * nmax + im[m]) * O + jm[m]];
+        v += p;
+    }
+    return v;
+}
+
+template <int MODE>
+__global__ void k_project_cells(ProjectArgs pa, const double* __restrict__ w,
+                                const double* __restrict__ tab, uint32_t nmax, CodecArgs c,
+                                uint32_t cells)
+{
+    using T = typename St<MODE>::T;
+    const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= cells) return;
+    uint32_t im[kMaxDim];
+    uint32_t r = cell;
+    for (int m = 0; m < pa.ndim; ++m) {
+        im[m] = r % pa.n[m];
+        r /= pa.n[m];
+    }
+    c.p.mean[cell] = project_coef(pa, w, tab, nmax, im, 0);
+    if constexpr (!St<MODE>::scaled) {
+        for (int J = 1; J < c.ncoef; ++J) {
+            const double v = project_coef(pa, w, tab, nmax, im, J);
+            if constexpr (MODE == M_FP64)
+                plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = v;
+            else
+                plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = __double2float_rn(v);
+        }
+    } else {
+        double mx = 0.0;
+        for (int J = 1; J < c.ncoef; ++J) mx = fmax(mx, fabs(project_coef(pa, w, tab, nmax, im, J)));
+        float s, inv;
+        pow2_scale(__double2float_rn(mx), s, inv);
+        c.p.scale[cell] = s;
+        for (int J = 1; J < c.ncoef; ++J) {
+            const double x = project_coef(pa, w, tab, nmax, im, J) * double(inv);
+            T* dst = plane_ptr_w<T>(c.p.hi, c.pstride, J) + cell;
+            if constexpr (MODE == M_BF16)
+                *dst = __double2bfloat16(x);
+            else
+                *dst = __double2half(x);
+        }
+    }
+}
+
+cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const double* d_params,
+                           double* d_tab, uint32_t nmax, const CodecArgs& c, uint32_t cells,
+                           cudaStream_t st)
+{
+    const int b = 128;
+    const uint32_t total = uint32_t(pa.nterms) * pa.ndim * nmax;
+    if (total > 0) k_project_1d<<<(total + b - 1) / b, b, 0, st>>>(pa, d_params, d_tab, nmax);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    SL_MODE_SWITCH(c.mode, (k_project_cells<MD><<<(cells + b - 1) / b, b, 0, st>>>(
+                               pa, d_weights, d_tab, nmax, c, cells)));
+    return cudaGetLastError();
+}
+
+}  // namespace sl

@@ -1,0 +1,162 @@
+// sl_internal.cuh -- structures shared by the sLdG device kernels and the host
+// side of libsl.so.  Not part of the public ABI (include/sl.h is).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+namespace sl {
+
+// Storage modes, numerically equal to sl_storage.
+enum Mode : int { M_FP64 = 0, M_F32 = 1, M_BF16 = 2, M_FP16 = 3 };
+
+constexpr int kMaxDim = 6;
+constexpr int kMaxK = 3;
+constexpr int kMaxO = kMaxK + 1;
+constexpr int kMaxPolyDeg = 2 * kMaxK + 1;   // entries of A(alpha), B(alpha) are polynomials of this degree
+constexpr int kMaxScaledCoef = 128;          // o^d limit of the per-cell-scaled modes (registers per thread)
+constexpr int kMaxQuad = 32;
+
+// Unsigned 32-bit division by a run-time constant d >= 1 with a multiply-high
+// and a shift (Granlund & Montgomery, "Division by invariant integers using
+// multiplication", PLDI 1994, round-up variant): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(n, m) + n) >> l.
+// The sum is formed in 64 bits, so the identity holds for every 32-bit n.
+struct FastDiv {
+    uint32_t d, m, l;
+    FastDiv() : d(1), m(1), l(0) {}
+    explicit FastDiv(uint32_t div) { set(div); }
+    void set(uint32_t div)
+    {
+        d = div;
+        l = 0;
+        while ((uint64_t(1) << l) < div) ++l;
+        m = uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << l) - div)) / div + 1);
+    }
+    __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const
+    {
+#ifdef __CUDA_ARCH__
+        uint32_t t = __umulhi(n, m);
+#else
+        uint32_t t = uint32_t((uint64_t(n) * m) >> 32);
+#endif
+        return uint32_t((uint64_t(t) + n) >> l);
+    }
+    __host__ __device__ __forceinline__ uint32_t mod(uint32_t n) const { return n - div(n) * d; }
+};
+
+// One split copy of the state: FP64 mean plane, low-precision planes for the
+// other o^d - 1 coefficients (coefficient J >= 1 lives at hi + (J-1)*pstride),
+// and the per-cell FP32 scale plane of the scaled modes.
+struct Planes {
+    double* mean;
+    void* hi;
+    float* scale;
+};
+
+// Per shift class: sigma reduced into [0, N), alpha in [0,1), and the
+// matrices A (first o*o) and B (next o*o), row-major, in FP64 and FP32.
+struct ShiftTable {
+    const int32_t* sigma;
+    const double* alpha;
+    const double* ab64;   // [class][2][o][o]
+    const float* ab32;    // [class][2][o][o]
+};
+
+// Geometry of one sweep along dimension `dim` of the flattened grid viewed as
+// [outer][N][inner]: a line is an (outer, inner) pair, its cells are
+// base + i*inner, base = outer*N*inner + inner_index.
+struct SweepArgs {
+    Planes src, dst;
+    ShiftTable tab;
+    uint32_t cells;      // < 2^31
+    uint32_t N;          // extent along the sweep dimension
+    uint32_t inner;      // prod_{q<dim} n_q
+    uint32_t lines;      // cells / N
+    int64_t pstride;     // elements between coefficient planes
+    FastDiv fdN;         // divides by N   (unit-stride kernel: cell -> line)
+    FastDiv fdInner;     // divides by inner (strided kernel: line -> outer)
+    FastDiv fdCls;       // line coordinate -> shift class: (x / cdiv) % cmod
+    FastDiv fdClsMod;
+    int cls_src;         // 0: one class, 1: from the inner index, 2: from the outer index
+    int ostride;         // o^dim
+    int nfib;            // o^(d-1) fibres per cell
+    int nfg;             // fibre groups (gridDim.y = nfg * nchunk for the strided kernel)
+    uint32_t chunk;      // cells per thread along the line (strided kernel)
+};
+
+// Coefficient plane pointer helpers.
+template <typename T>
+__host__ __device__ __forceinline__ const T* plane_ptr(const void* hi, int64_t pstride, int J)
+{
+    return static_cast<const T*>(hi) + int64_t(J - 1) * pstride;
+}
+template <typename T>
+__host__ __device__ __forceinline__ T* plane_ptr_w(void* hi, int64_t pstride, int J)
+{
+    return static_cast<T*>(hi) + int64_t(J - 1) * pstride;
+}
+
+// Launch request handed from the host side to the per-family launchers.
+struct SweepLaunch {
+    SweepArgs args;
+    int K;
+    int mode;
+    int unit;            // 1: sweep along dimension 0
+    int ft;              // fibres per thread (non-scaled modes)
+    int block;           // threads per block
+    cudaStream_t stream;
+};
+
+cudaError_t launch_sweep_fp(const SweepLaunch& L);       // M_FP64, M_F32
+cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
+
+// Coefficients of the entries of A(alpha) and B(alpha) as polynomials in
+// alpha, exact rationals rounded once to FP64: a[j][l][p] alpha^p.
+struct PolyTab {
+    double a[kMaxO][kMaxO][kMaxPolyDeg + 1];
+    double b[kMaxO][kMaxO][kMaxPolyDeg + 1];
+};
+void build_poly_table(int K, PolyTab* out);   // host, exact rational arithmetic
+
+// Where the shift of class c comes from.
+struct ShiftSource {
+    int kind;            // 0: shifts[c]; 1: (lo + (c+1/2) hv) * tau / h; 2: field[c] * tau / h
+    const double* data;  // shifts (kind 0) or field samples (kind 2)
+    double lo, hv, tau, h;
+};
+
+cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,
+                            const PolyTab& tab, int32_t* sigma, double* alpha, double* ab64,
+                            float* ab32, cudaStream_t st);
+
+cudaError_t launch_mass(const double* mean, uint32_t cells, double* partials, int nblocks,
+                        double vol, double* out, cudaStream_t st);
+int mass_blocks(uint32_t cells);
+
+struct CodecArgs {
+    Planes p;
+    int64_t pstride;
+    int ncoef;
+    int mode;
+};
+cudaError_t launch_encode(const CodecArgs& c, const double* aos, uint32_t first, uint32_t count,
+                          cudaStream_t st);
+cudaError_t launch_decode(const CodecArgs& c, double* aos, uint32_t first, uint32_t count,
+                          cudaStream_t st);
+cudaError_t launch_gather(const CodecArgs& c, const int64_t* cells, uint32_t count, double* aos,
+                          cudaStream_t st);
+
+struct ProjectArgs {
+    int ndim, K, nq, nterms;
+    uint32_t n[kMaxDim];
+    double lo[kMaxDim], h[kMaxDim];
+    double node[kMaxQuad], weight[kMaxQuad];
+};
+cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const double* d_params,
+                           double* d_tab, uint32_t nmax, const CodecArgs& c, uint32_t cells,
+                           cudaStream_t st);
+
+}  // namespace sl

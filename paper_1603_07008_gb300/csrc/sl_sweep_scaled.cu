@@ -1,0 +1,73 @@
+// sl_sweep_scaled.cu -- instantiations and launcher of the sweep kernels for
+// the FP64-mean / per-cell-scaled BF16 or FP16 store.  One thread holds every
+// fibre of its cell, because the new scale is the maximum over the whole
+// cell; the fibre count o^(d-1) is therefore a template parameter.
+#include "sl_sweep.cuh"
+
+namespace sl {
+
+namespace {
+
+template <int K, int MODE, int NF>
+cudaError_t launch_one(const SweepLaunch& L)
+{
+    const SweepArgs& a = L.args;
+    if (a.nfib != NF || a.nfg != 1) return cudaErrorInvalidValue;
+    if (L.unit) {
+        dim3 grid((a.cells + L.block - 1) / L.block, 1);
+        k_sweep_unit<K, MODE, NF><<<grid, L.block, 0, L.stream>>>(a);
+    } else {
+        const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
+        dim3 grid((a.lines + L.block - 1) / L.block, nchunk);
+        k_sweep_strided<K, MODE, NF><<<grid, L.block, 0, L.stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_mode(const SweepLaunch& L)
+{
+    const int nf = L.args.nfib;
+    switch (L.K) {
+    case 0:
+        if (nf == 1) return launch_one<0, MODE, 1>(L);
+        break;
+    case 1:
+        switch (nf) {
+        case 1: return launch_one<1, MODE, 1>(L);
+        case 2: return launch_one<1, MODE, 2>(L);
+        case 4: return launch_one<1, MODE, 4>(L);
+        case 8: return launch_one<1, MODE, 8>(L);
+        case 16: return launch_one<1, MODE, 16>(L);
+        case 32: return launch_one<1, MODE, 32>(L);
+        }
+        break;
+    case 2:
+        switch (nf) {
+        case 1: return launch_one<2, MODE, 1>(L);
+        case 3: return launch_one<2, MODE, 3>(L);
+        case 9: return launch_one<2, MODE, 9>(L);
+        case 27: return launch_one<2, MODE, 27>(L);
+        }
+        break;
+    case 3:
+        switch (nf) {
+        case 1: return launch_one<3, MODE, 1>(L);
+        case 4: return launch_one<3, MODE, 4>(L);
+        case 16: return launch_one<3, MODE, 16>(L);
+        }
+        break;
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_scaled(const SweepLaunch& L)
+{
+    if (L.mode == M_BF16) return launch_mode<M_BF16>(L);
+    if (L.mode == M_FP16) return launch_mode<M_FP16>(L);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace sl

@@ -1,0 +1,354 @@
+"""Parity of the CUDA sweep library (through its C ABI) with the CPU oracle.
+
+Tolerances (stated for the method's outputs):
+  * FP64 store:        max |gpu - oracle| / max |oracle| <= 1e-12
+  * mixed FP32 store:  relative function-space L2 <= 1e-5 after 100 steps
+  * BF16 / FP16 store: relative function-space L2 <= 1e-2
+  * every store:       relative mass drift <= 1e-13 after 1000 steps
+  * integer shifts:    bit-exact permutation.
+All inputs are seeded; the oracle never sees a value computed on the GPU.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1603_07008_gb300 as S
+from paper_1603_07008_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+MIX_TOL = 1e-5
+LP_TOL = 1e-2
+MASS_TOL = 1e-13
+
+
+def _grid(n, lo=None, hi=None, pair=None):
+    d = len(n)
+    return W.Grid(n=tuple(n), lo=tuple(lo or (0.0,) * d), hi=tuple(hi or (1.0,) * d),
+                  pair=tuple(pair or (-1,) * d))
+
+
+def _rand(n, k, seed):
+    return W.random_coefficients(int(np.prod(n)), k, len(n), seed)
+
+
+def _shifts(rng, n, dim, shift_dim, scale=2.5):
+    cnt = 1 if shift_dim < 0 else n[shift_dim]
+    return rng.uniform(-scale * n[dim], scale * n[dim], size=cnt)
+
+
+SHAPES = [(1,), (2,), (7,), (33,), (64,), (5, 3), (31, 2), (3, 7, 2), (4, 3, 2, 3),
+          (2, 3, 1, 2, 3), (2, 2, 3, 2, 1, 2)]
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_fp64_single_sweeps_match_oracle(n, k):
+    if (k + 1) ** len(n) > 1024:
+        pytest.skip("large coefficient count covered elsewhere")
+    rng = np.random.default_rng(hash((n, k)) % 2**32)
+    u = _rand(n, k, 1)
+    with S.Context(_grid(n), k, "fp64") as ctx:
+        for dim in range(len(n)):
+            for sd in [-1] + [m for m in range(len(n)) if m != dim]:
+                s = _shifts(rng, n, dim, sd)
+                ctx.set_coeffs(u)
+                ctx.advect(dim, sd, s)
+                got = ctx.get_coeffs()
+                ref = O.sweep(u, n, k, dim, sd, s)
+                assert O.rel_max(got, ref) <= FP64_TOL, (dim, sd)
+
+
+@pytest.mark.parametrize("n", [(7,), (5, 3), (3, 4, 2), (2, 3, 2, 3)])
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_integer_shifts_are_bit_exact(n, k):
+    u = _rand(n, k, 2)
+    with S.Context(_grid(n), k, "fp64") as ctx:
+        for dim in range(len(n)):
+            for sd in [-1] + [m for m in range(len(n)) if m != dim]:
+                cnt = 1 if sd < 0 else n[sd]
+                s = np.array([(-1) ** c * (3 * c + 1) for c in range(cnt)], dtype=float)
+                ctx.set_coeffs(u)
+                ctx.advect(dim, sd, s)
+                assert np.array_equal(ctx.get_coeffs(), O.sweep(u, n, k, dim, sd, s))
+
+
+@pytest.mark.parametrize("storage", ["mix_fp32", "mix_bf16", "mix_fp16"])
+def test_integer_shifts_permute_the_stored_values(storage):
+    """In the low-precision stores an integer shift moves stored values
+    unchanged: the result is the periodic roll of what was stored."""
+    n = (6, 5, 3)
+    k = 1
+    with S.Context(_grid(n), k, storage) as ctx:
+        ctx.set_coeffs(_rand(n, k, 3))
+        before = ctx.get_coeffs()
+        for dim, sh in [(0, 2.0), (1, -7.0), (2, 4.0)]:
+            ctx.advect(dim, -1, [sh])
+            after = ctx.get_coeffs()
+            B = before.reshape(tuple(reversed(n)) + (-1,))
+            ref = np.roll(B, int(sh), axis=len(n) - 1 - dim).reshape(before.shape)
+            assert np.array_equal(after, ref)
+            before = after
+
+
+def test_projection_matches_oracle():
+    for p in [W.config1(), W.config2(n=48, steps=1), W.config3(n=6, steps=1),
+              W.config5(n=3, steps=1)]:
+        with S.Context(p.grid, p.k, "fp64") as ctx:
+            ctx.project(p.nq, p.weights, p.params)
+            got = ctx.get_coeffs()
+        ref = O.project(p.grid, p.k, p.nq, p.weights, p.params)
+        assert O.rel_max(got, ref) <= 1e-14, p.name
+
+
+def test_config1_fp64_100_steps():
+    """1D, N = 1024, k = 2, dt = 0.37/N, 100 steps, all FP64."""
+    p = W.config1()
+    g = p.grid
+    h = (g.hi[0] - g.lo[0]) / g.n[0]
+    s = p.velocity * p.dt / h
+    u0 = O.project(g, p.k, p.nq, p.weights, p.params)
+    ref = u0
+    for _ in range(p.steps):
+        ref = O.sweep(ref, g.n, p.k, 0, -1, s)
+    with S.Context(g, p.k, p.storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        m0 = ctx.mass()
+        for _ in range(p.steps):
+            ctx.advect(0, -1, [s])
+        got = ctx.get_coeffs()
+        m1 = ctx.mass()
+    assert O.rel_max(got, ref) <= FP64_TOL
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+@pytest.mark.parametrize("n,k", [((5, 3), 2), ((7, 2, 3), 1), ((4, 3, 2, 3), 2), ((33,), 3)])
+def test_mixed_fp32_single_sweeps(n, k):
+    rng = np.random.default_rng(7)
+    u = _rand(n, k, 4)
+    with S.Context(_grid(n), k, "mix_fp32") as ctx:
+        for dim in range(len(n)):
+            for sd in [-1] + [m for m in range(len(n)) if m != dim]:
+                s = _shifts(rng, n, dim, sd)
+                ctx.set_coeffs(u)
+                stored = ctx.get_coeffs()
+                ctx.advect(dim, sd, s)
+                got = ctx.get_coeffs()
+                # against the oracle applied to exactly what was stored
+                ref = O.sweep(stored, n, k, dim, sd, s)
+                assert O.rel_l2(got, ref, k, len(n)) <= 1e-6
+                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-14 * np.max(np.abs(ref))
+
+
+def _strang_oracle(p, steps):
+    u = O.project(p.grid, p.k, p.nq, p.weights, p.params)
+    return O.step(u, p.grid, p.k, "strang", p.dt, steps, p.field_list())
+
+
+def _strang_gpu(p, storage, steps, graph=False):
+    with S.Context(p.grid, p.k, storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, steps)
+        out = ctx.get_coeffs()
+        m1 = ctx.mass()
+    return out, abs(m1 - m0) / abs(m0)
+
+
+@pytest.mark.parametrize("cfg", ["2d", "4d"])
+def test_strang_fp64_matches_oracle(cfg):
+    p = W.config2(n=40, steps=5) if cfg == "2d" else W.config3(n=8, steps=2)
+    ref = _strang_oracle(p, p.steps)
+    got, drift = _strang_gpu(p, "fp64", p.steps)
+    assert O.rel_max(got, ref) <= FP64_TOL
+    assert drift <= MASS_TOL
+
+
+def test_config2_mixed_fp32_100_steps_full_size():
+    """2D x-v, 512 x 512, k = 2, FP64 means + FP32 higher coefficients,
+    Strang, dt = 0.1: relative L2 against the FP64 oracle after 100 steps."""
+    p = W.config2(n=512, steps=100)
+    ref = _strang_oracle(p, 100)
+    got, drift = _strang_gpu(p, "mix_fp32", 100)
+    err = O.rel_l2(got, ref, p.k, 2)
+    assert err <= MIX_TOL, err
+    assert drift <= MASS_TOL
+
+
+def test_config2_fp64_full_size():
+    p = W.config2(n=512, steps=20)
+    ref = _strang_oracle(p, 20)
+    got, drift = _strang_gpu(p, "fp64", 20)
+    assert O.rel_max(got, ref) <= FP64_TOL
+    assert drift <= MASS_TOL
+
+
+@pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
+@pytest.mark.parametrize("cfg", ["6d", "4d", "2d"])
+def test_scaled_stores_match_oracle(storage, cfg):
+    if cfg == "6d":
+        p = W.config5(n=4, steps=2)
+    elif cfg == "4d":
+        p = W.config3(n=6, steps=2)
+    else:
+        p = W.config2(n=64, steps=20)
+    ref = _strang_oracle(p, p.steps)
+    got, drift = _strang_gpu(p, storage, p.steps)
+    err = O.rel_l2(got, ref, p.k, p.grid.ndim)
+    assert err <= LP_TOL, err
+    assert drift <= MASS_TOL
+
+
+@pytest.mark.parametrize("storage", ["fp64", "mix_fp32", "mix_bf16", "mix_fp16"])
+def test_mass_drift_1000_steps(storage):
+    p = W.config2(n=64, steps=1000)
+    k = 2 if storage in ("fp64", "mix_fp32") else 1
+    p.k = k
+    with S.Context(p.grid, k, storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, 1000)
+        m1 = ctx.mass()
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+@pytest.mark.parametrize("storage", ["fp64", "mix_fp32", "mix_bf16"])
+def test_mass_drift_1d_1000_steps(storage):
+    p = W.config1()
+    k = 2 if storage != "mix_bf16" else 1
+    h = 1.0 / 1024
+    s = p.velocity * p.dt / h
+    with S.Context(p.grid, k, storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        m0 = ctx.mass()
+        for _ in range(1000):
+            ctx.advect(0, -1, [s])
+        m1 = ctx.mass()
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+def test_config3_full_size_sampled_after_one_step():
+    """4D 64^4, k = 2, mixed FP32: one Strang step (6 sweeps) on the GPU
+    against the oracle evaluated on the dependency cones of sampled cells."""
+    p = W.config3(n=64, steps=1)
+    rng = np.random.default_rng(0)
+    cells = np.concatenate([[0, p.grid.cells - 1], rng.integers(0, p.grid.cells, 10)])
+    sched = O.schedule(p.grid, "strang", p.dt, p.field_list())
+    ref = O.sample_after(p.grid, p.k, p.nq, p.weights, p.params, sched, cells)
+    with S.Context(p.grid, p.k, "mix_fp32") as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, 1)
+        got = ctx.get_cells(cells)
+        m1 = ctx.mass()
+    for i in range(len(cells)):
+        assert O.rel_l2(got[i:i + 1], ref[i:i + 1], p.k, 4) <= 1e-5
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+@pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
+def test_config5_full_size_sampled_after_one_step(storage):
+    """6D 20^6, k = 1, FP64 means + scaled BF16/FP16: one Strang step
+    (9 sweeps) against the oracle on sampled dependency cones."""
+    p = W.config5(n=20, steps=1)
+    rng = np.random.default_rng(1)
+    cells = np.concatenate([[0, p.grid.cells - 1], rng.integers(0, p.grid.cells, 4)])
+    sched = O.schedule(p.grid, "strang", p.dt, p.field_list())
+    ref = O.sample_after(p.grid, p.k, p.nq, p.weights, p.params, sched, cells)
+    with S.Context(p.grid, p.k, storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, 1)
+        got = ctx.get_cells(cells)
+        m1 = ctx.mass()
+    assert O.rel_l2(got, ref, p.k, 6) <= LP_TOL
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+def test_graph_replay_matches_step():
+    p = W.config2(n=48, steps=1)
+    import torch
+    s = torch.cuda.Stream()
+    with S.Context(p.grid, p.k, "mix_fp32", stream=s) as a, \
+            S.Context(p.grid, p.k, "mix_fp32", stream=s) as b:
+        for c in (a, b):
+            c.project(p.nq, p.weights, p.params)
+            c.set_fields(p.field_list())
+        a.step("strang", p.dt, 6)
+        b.graph_capture("strang", p.dt, 3)   # 9 sweeps: odd, two graphs alternate
+        b.graph_launch()
+        b.graph_launch()
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+
+
+def test_codec_round_trip():
+    n = (9, 4)
+    k = 2
+    u = _rand(n, k, 9)
+    with S.Context(_grid(n), k, "fp64") as c:
+        c.set_coeffs(u)
+        assert np.array_equal(c.get_coeffs(), u)
+    with S.Context(_grid(n), k, "mix_fp32") as c:
+        c.set_coeffs(u)
+        got = c.get_coeffs()
+        assert np.array_equal(got[:, 0], u[:, 0])
+        assert np.array_equal(got[:, 1:], u[:, 1:].astype(np.float32).astype(np.float64))
+    for st, rel in (("mix_bf16", 2.0 ** -8), ("mix_fp16", 2.0 ** -11)):
+        with S.Context(_grid(n), k, st) as c:
+            c.set_coeffs(u)
+            got = c.get_coeffs()
+            assert np.array_equal(got[:, 0], u[:, 0])
+            cmax = np.max(np.abs(u[:, 1:]), axis=1, keepdims=True)
+            assert np.all(np.abs(got[:, 1:] - u[:, 1:]) <= rel * cmax)
+
+
+def test_get_cells_matches_full_download():
+    n = (5, 6, 7)
+    u = _rand(n, 1, 12)
+    with S.Context(_grid(n), 1, "mix_bf16") as c:
+        c.set_coeffs(u)
+        full = c.get_coeffs()
+        idx = np.array([0, 7, 100, 209, 3])
+        assert np.array_equal(c.get_cells(idx), full[idx])
+
+
+def test_invalid_calls_leave_state_unchanged():
+    n = (8, 4)
+    u = _rand(n, 1, 13)
+    with S.Context(_grid(n, pair=(1, -1)), 1, "fp64") as c:
+        c.set_coeffs(u)
+        for args, code in [((0, -1, [float("nan")]), S.SL_ENAN),
+                           ((0, 1, [0.1, 0.2]), S.SL_EINVAL),
+                           ((2, -1, [0.1]), S.SL_EINVAL),
+                           ((0, 0, [0.1] * 8), S.SL_EINVAL)]:
+            with pytest.raises(S.SlError) as e:
+                c.advect(*args)
+            assert e.value.status == code
+        with pytest.raises(S.SlError) as e:
+            c.step("strang", 0.1, 1)            # fields not set
+        assert e.value.status == S.SL_EINVAL
+        bad = u.copy()
+        bad[3, 1] = np.inf
+        with pytest.raises(S.SlError) as e:
+            c.set_coeffs(bad)
+        assert e.value.status == S.SL_ENAN
+        assert np.array_equal(c.get_coeffs(), u)
+
+
+def test_profile_counts_sweeps():
+    p = W.config2(n=64, steps=1)
+    with S.Context(p.grid, p.k, "mix_fp32") as c:
+        c.project(p.nq, p.weights, p.params)
+        c.set_fields(p.field_list())
+        c.profile_enable(True)
+        c.step("strang", p.dt, 4)
+        n, ms, b = c.profile_query()
+    assert n == 12 and ms > 0
+    assert b == 12 * 2 * c.info["state_bytes"]
