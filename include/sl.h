@@ -221,6 +221,34 @@ sl_status sl_step(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
  * Synchronises. */
 sl_status sl_mass(sl_ctx* ctx, double* out);
 
+/* Allocation-free mass reduction.  The paper has no counterpart: this entry
+ * point exists for callers that cannot let a library call cudaMalloc -- for
+ * example a host application that owns all device memory through its own
+ * pool or arena, or a latency-critical loop where a cudaMalloc (which may
+ * synchronise the device) is not allowed.  It computes
+ *     *d_out = cell_volume * sum_{i < cells} d_mean[i]
+ * with the same fixed-shape FP64 reduction as sl_mass, but its scratch (the
+ * per-block partial sums) is a fixed 8 KB __device__ array inside the
+ * library (1024 FP64 slots), which every GPU that loads the library keeps
+ * until the process exits.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   d_mean       device pointer, `cells` FP64 values (caller-owned)
+ *   cells        1 .. 2^31 - 1; anything else returns SL_EINVAL
+ *   cell_volume  product of the cell widths (SL_ENAN if NaN)
+ *   d_out        device pointer to one FP64 result (caller-owned)
+ *   cuda_stream  cudaStream_t the work is enqueued on (NULL = legacy default)
+ * Enqueues only; the result is valid once the stream reaches it.  The first
+ * call on a device looks up the scratch array's device address on that device
+ * (the current one), so make that first call before any stream capture.  All
+ * calls share the one scratch array: calls whose work overlaps on the GPU
+ * (different streams, no ordering between them) race and may return wrong
+ * sums.  Each call rewrites every scratch slot it reads, so a previous call's
+ * leftovers never leak into a result.  Errors: SL_EINVAL (NULL pointer or
+ * cells out of range), SL_ENAN, SL_ECUDA (address lookup or launch failed).
+ * sl_last_error does not cover this call. */
+sl_status sl_mass_noalloc(const double* d_mean, int64_t cells, double cell_volume, double* d_out,
+                          void* cuda_stream);
+
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later
  * sl_set_fields is not seen by the graph until it is captured again. */

@@ -25,7 +25,7 @@ __all__ = [
     "sl_create", "sl_destroy", "sl_last_error", "sl_get_info", "sl_state_bytes", "sl_ab_host",
     "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
     "sl_set_fields", "sl_step", "sl_mass", "sl_graph_capture", "sl_graph_launch",
-    "sl_synchronize", "sl_profile_enable", "sl_profile_query",
+    "sl_synchronize", "sl_profile_enable", "sl_profile_query", "sl_mass_noalloc",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -118,6 +118,7 @@ def lib():
             "sl_synchronize": (st, [_vp]),
             "sl_profile_enable": (st, [_vp, ctypes.c_int]),
             "sl_profile_query": (st, [_vp, _i64p, _dp, _dp]),
+            "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -300,6 +301,18 @@ def sl_profile_query(ctx) -> Tuple[int, float, float]:
     b = ctypes.c_double()
     _check(lib().sl_profile_query(ctx, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)), ctx)
     return n.value, ms.value, b.value
+
+
+def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, stream=None):
+    """Allocation-free mass reduction on raw device addresses (integers):
+    enqueues d_out[0] = cell_volume * sum(d_mean[:cells]) on `stream`."""
+    st = lib().sl_mass_noalloc(ctypes.c_void_p(int(d_mean)), int(cells), float(cell_volume),
+                               ctypes.c_void_p(int(d_out)), _stream_handle(stream))
+    if st != SL_OK:
+        why = {SL_EINVAL: "NULL pointer or cells outside [1, 2^31 - 1]",
+               SL_ENAN: "cell_volume is NaN",
+               SL_ECUDA: "scratch address lookup or kernel launch failed"}.get(st, "failed")
+        raise SlError(st, f"sl_mass_noalloc: {why}")
 
 
 class Context:
