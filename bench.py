@@ -205,6 +205,7 @@ def gpu_steps(S, W, p, storage, stream, steps, warmup, profile):
     ctx = S.Context(p.grid, p.k, storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
+    ctx.autotune(3)
     m0 = ctx.mass()
     for _ in range(warmup):
         ctx.step("strang", p.dt, 1)
@@ -252,7 +253,8 @@ def run_ours(args):
         prof = ctx.profile_query() if profile else None
         ctx.profile_enable(False)
         m1 = ctx.mass()
-        info = ctx.info
+        info = dict(ctx.info)
+        info["tune"] = [ctx.get_tune(d) for d in range(p.grid.ndim)]
         ctx.close()
         return ms, prof, abs(m1 - m0) / abs(m0), clk, info
 
@@ -297,7 +299,7 @@ def run_ours(args):
                        "cells": p.grid.cells, "coef_per_cell": p.ncoef, "dof": dof,
                        "sweeps_per_step": sweeps_per_step, "state_bytes": info["state_bytes"],
                        "l2": f"state {info['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}", "tune": info["tune"]},
             "mass_drift": drift,
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved_gbs / peak_gbs, "traffic": None,
@@ -326,6 +328,7 @@ def run_e2e(S, W, p, args, stream, world, dev):
     ctx = S.Context(p.grid, p.k, args.storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
+    ctx.autotune(3)
     mean, hi, scale = S.plane_arrays(ctx.handle)
     # pinned host copies of the planes
     t_mean = torch.empty(mean.size, dtype=torch.float64, pin_memory=True)

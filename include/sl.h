@@ -258,6 +258,34 @@ sl_status sl_graph_launch(sl_ctx* ctx);
 /* Wait for all work of the context's stream. */
 sl_status sl_synchronize(sl_ctx* ctx);
 
+/* ---------------------------------------------------------------- launch shapes */
+
+/* Launch shape of the sweep kernel along one dimension.
+ *   block              threads per block (multiple of 32; <= 256 for dimension 0,
+ *                      <= 128 otherwise)
+ *   fibres_per_thread  coefficient fibres one thread updates: 1, 2, 3, 4 or 9
+ *                      along dimension 0; 1, 2 or 3 otherwise.  The scaled
+ *                      stores always give a thread every fibre of its cell.
+ *   unroll             cells per walk step along dimensions > 0: 1, 2 or 4
+ *                      (4 only with 1 or 2 fibres per thread)
+ *   chunk              cells one thread walks along dimensions > 0 (1..n_dim)
+ * Every shape computes the same result; only the speed differs. */
+typedef struct {
+    int32_t block;
+    int32_t fibres_per_thread;
+    int32_t unroll;
+    int64_t chunk;
+} sl_tune;
+
+sl_status sl_get_tune(const sl_ctx* ctx, int dim, sl_tune* out);
+/* Errors: SL_EINVAL for a shape this build does not provide. */
+sl_status sl_set_tune(sl_ctx* ctx, int dim, const sl_tune* tune);
+
+/* Autotuner: for every dimension, time each provided launch shape `reps`
+ * times on the current state (out of place, so the state is unchanged) and
+ * keep the fastest.  Synchronises.  Must not be called during a capture. */
+sl_status sl_autotune(sl_ctx* ctx, int reps);
+
 /* ---------------------------------------------------------------- profiling */
 
 /* When enabled, every sweep-kernel launch is bracketed by CUDA events on the

@@ -26,6 +26,7 @@ __all__ = [
     "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
     "sl_set_fields", "sl_step", "sl_mass", "sl_graph_capture", "sl_graph_launch",
     "sl_synchronize", "sl_profile_enable", "sl_profile_query", "sl_mass_noalloc",
+    "sl_get_tune", "sl_set_tune", "sl_autotune",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -40,6 +41,11 @@ class SlError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"sl status {status}: {msg}")
         self.status = status
+
+
+class sl_tune(ctypes.Structure):
+    _fields_ = [("block", ctypes.c_int32), ("fibres_per_thread", ctypes.c_int32),
+                ("unroll", ctypes.c_int32), ("chunk", ctypes.c_int64)]
 
 
 class sl_grid(ctypes.Structure):
@@ -118,6 +124,9 @@ def lib():
             "sl_synchronize": (st, [_vp]),
             "sl_profile_enable": (st, [_vp, ctypes.c_int]),
             "sl_profile_query": (st, [_vp, _i64p, _dp, _dp]),
+            "sl_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
+            "sl_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
+            "sl_autotune": (st, [_vp, ctypes.c_int]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
@@ -303,6 +312,22 @@ def sl_profile_query(ctx) -> Tuple[int, float, float]:
     return n.value, ms.value, b.value
 
 
+def sl_get_tune(ctx, dim: int) -> dict:
+    t = sl_tune()
+    _check(lib().sl_get_tune(ctx, int(dim), ctypes.byref(t)), ctx)
+    return {k: getattr(t, k) for k, _ in sl_tune._fields_}
+
+
+def sl_set_tune(ctx, dim: int, block: int, fibres_per_thread: int = 1, unroll: int = 1,
+                chunk: int = 0):
+    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(chunk))
+    _check(lib().sl_set_tune(ctx, int(dim), ctypes.byref(t)), ctx)
+
+
+def sl_autotune(ctx, reps: int = 3):
+    _check(lib().sl_autotune(ctx, int(reps)), ctx)
+
+
 def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, stream=None):
     """Allocation-free mass reduction on raw device addresses (integers):
     enqueues d_out[0] = cell_volume * sum(d_mean[:cells]) on `stream`."""
@@ -374,6 +399,15 @@ class Context:
 
     def synchronize(self):
         sl_synchronize(self.handle)
+
+    def autotune(self, reps=3):
+        sl_autotune(self.handle, reps)
+
+    def get_tune(self, dim):
+        return sl_get_tune(self.handle, dim)
+
+    def set_tune(self, dim, **kw):
+        sl_set_tune(self.handle, dim, **kw)
 
     def profile_enable(self, on=True):
         sl_profile_enable(self.handle, on)

@@ -67,6 +67,7 @@ struct sl_ctx {
     struct Tune {
         int block = 256;
         int ft = 1;
+        int unroll = 1;
         uint32_t chunk = 0;
     } tune[SL_MAX_DIM];
 
@@ -163,22 +164,18 @@ double cell_width(const sl_grid& g, int m) { return (g.hi[m] - g.lo[m]) / double
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Default launch shape for a sweep along dimension m.
-void default_tune(sl_ctx* c, int m)
+bool is_scaled(const sl_ctx* c) { return c->mode == M_BF16 || c->mode == M_FP16; }
+
+int64_t fibre_groups(const sl_ctx* c, int ft) { return is_scaled(c) ? 1 : (c->nfib + ft - 1) / ft; }
+
+// Chunk length of the strided walk: long enough to amortise the extra load at
+// the start of a chunk, short enough to give a few waves of 2048 resident
+// threads on 152 SMs, and no more than 65535 grid rows.
+uint32_t chunk_for(const sl_ctx* c, int m, int ft)
 {
-    auto& t = c->tune[m];
-    const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
-    t.ft = 1;
-    if (m == 0) {
-        t.block = 256;
-        t.chunk = 0;
-        return;
-    }
-    t.block = 128;
     const int64_t N = c->g.n[m];
     const int64_t lines = c->cells / N;
-    const int64_t nfg = scaled ? 1 : (c->nfib + t.ft - 1) / t.ft;
-    // enough threads for a few waves of 2048 resident threads on 152 SMs
+    const int64_t nfg = fibre_groups(c, ft);
     const int64_t want = int64_t(152) * 2048 * 2;
     int64_t nchunk = (want + lines * nfg - 1) / (lines * nfg);
     if (nchunk < 1) nchunk = 1;
@@ -187,7 +184,31 @@ void default_tune(sl_ctx* c, int m)
     if (chunk > N) chunk = N;
     while (((N + chunk - 1) / chunk) * nfg > 65535) chunk *= 2;
     if (chunk > N) chunk = N;
-    t.chunk = uint32_t(chunk);
+    return uint32_t(chunk);
+}
+
+// Launch shapes compiled into the library.
+bool unit_ft_ok(int ft) { return ft == 1 || ft == 2 || ft == 3 || ft == 4 || ft == 9; }
+bool strided_ok(int ft, int u)
+{
+    return (ft == 1 && (u == 1 || u == 2 || u == 4)) || (ft == 2 && (u == 1 || u == 2 || u == 4)) ||
+           (ft == 3 && (u == 1 || u == 2));
+}
+
+// Default launch shape for a sweep along dimension m.
+void default_tune(sl_ctx* c, int m)
+{
+    auto& t = c->tune[m];
+    t.ft = 1;
+    if (m == 0) {
+        t.block = 256;
+        t.unroll = 1;
+        t.chunk = 0;
+        return;
+    }
+    t.block = 128;
+    t.unroll = is_scaled(c) ? 1 : 2;
+    t.chunk = chunk_for(c, m, t.ft);
 }
 
 SweepArgs make_args(sl_ctx* c, int dim, int shift_dim)
@@ -228,9 +249,8 @@ SweepArgs make_args(sl_ctx* c, int dim, int shift_dim)
     }
     a.ostride = int(ipow(c->O, dim));
     a.nfib = int(c->nfib);
-    const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
     const auto& t = c->tune[dim];
-    a.nfg = scaled ? 1 : int((c->nfib + t.ft - 1) / t.ft);
+    a.nfg = int(fibre_groups(c, t.ft));
     a.chunk = dim == 0 ? 0 : t.chunk;
     return a;
 }
@@ -247,17 +267,24 @@ cudaEvent_t take_event(sl_ctx* c)
     return e;
 }
 
-// One sweep along dim using the shift table already built on the stream.
-sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
+cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
 {
     SweepLaunch L{};
     L.args = make_args(c, dim, shift_dim);
     L.K = c->K;
     L.mode = c->mode;
     L.unit = dim == 0;
-    L.ft = (c->mode == M_BF16 || c->mode == M_FP16) ? int(c->nfib) : c->tune[dim].ft;
+    L.ft = is_scaled(c) ? int(c->nfib) : c->tune[dim].ft;
+    L.unroll = c->tune[dim].unroll;
     L.block = c->tune[dim].block;
     L.stream = c->st;
+    return is_scaled(c) ? launch_sweep_scaled(L) : c->mode == M_FP64 ? launch_sweep_f64(L)
+                                                                      : launch_sweep_f32(L);
+}
+
+// One sweep along dim using the shift table already built on the stream.
+sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
+{
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = c->prof && !c->capturing;
     if (prof) {
@@ -266,8 +293,7 @@ sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
         if (!e0 || !e1) return fail(c, SL_ECUDA, "cudaEventCreate failed");
         SL_CUDA(c, cudaEventRecord(e0, c->st));
     }
-    cudaError_t e = (c->mode == M_BF16 || c->mode == M_FP16) ? launch_sweep_scaled(L)
-                                                              : launch_sweep_fp(L);
+    cudaError_t e = launch_only(c, dim, shift_dim);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel launch");
     if (prof) {
         SL_CUDA(c, cudaEventRecord(e1, c->st));
@@ -493,15 +519,14 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
         o_state[b][2] = off;
         if (scaled) off = align_up(off + size_t(c->pstride) * 4, A);
     }
-    const size_t O2 = size_t(c->O) * c->O * 2;
     const size_t o_sigma = off;
     off = align_up(off + size_t(c->maxcls) * 4, A);
     const size_t o_alpha = off;
     off = align_up(off + size_t(c->maxcls) * 8, A);
     const size_t o_ab64 = off;
-    off = align_up(off + size_t(c->maxcls) * O2 * 8, A);
+    off = align_up(off + size_t(c->maxcls) * ab_stride64(c->O) * 8, A);
     const size_t o_ab32 = off;
-    off = align_up(off + size_t(c->maxcls) * O2 * 4, A);
+    off = align_up(off + size_t(c->maxcls) * ab_stride32(c->O) * 4, A);
     const size_t o_shifts = off;
     off = align_up(off + size_t(c->maxcls) * 8, A);
     int64_t nf = 0;
@@ -895,6 +920,135 @@ sl_status sl_synchronize(sl_ctx* c)
     if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
     SL_CUDA(c, cudaStreamSynchronize(c->st));
     return SL_OK;
+}
+
+sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
+{
+    if (!c || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (dim < 0 || dim >= c->ndim) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "dim out of range");
+    const auto& t = c->tune[dim];
+    out->block = t.block;
+    out->fibres_per_thread = is_scaled(c) ? int32_t(c->nfib) : t.ft;
+    out->unroll = t.unroll;
+    out->chunk = dim == 0 ? 0 : int64_t(t.chunk);
+    return SL_OK;
+}
+
+static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
+{
+    const int maxb = dim == 0 ? 256 : 128;
+    if (t->block < 32 || t->block > maxb || t->block % 32)
+        return fail(c, SL_EINVAL, "block must be a multiple of 32 in [32, %d]", maxb);
+    if (!is_scaled(c)) {
+        if (dim == 0 && !unit_ft_ok(t->fibres_per_thread))
+            return fail(c, SL_EINVAL, "fibres_per_thread %d not provided along dimension 0",
+                        t->fibres_per_thread);
+        if (dim > 0 && !strided_ok(t->fibres_per_thread, t->unroll))
+            return fail(c, SL_EINVAL, "(fibres_per_thread %d, unroll %d) not provided",
+                        t->fibres_per_thread, t->unroll);
+    }
+    if (dim > 0) {
+        const int64_t N = c->g.n[dim];
+        if (t->chunk < 1 || t->chunk > N) return fail(c, SL_EINVAL, "chunk must be in [1, n_dim]");
+        const int ft = is_scaled(c) ? 1 : t->fibres_per_thread;
+        if (((N + t->chunk - 1) / t->chunk) * fibre_groups(c, ft) > 65535)
+            return fail(c, SL_EINVAL, "too many chunks x fibre groups for one launch");
+    }
+    return SL_OK;
+}
+
+sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
+{
+    if (!c || !t) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (dim < 0 || dim >= c->ndim) return fail(c, SL_EINVAL, "dim out of range");
+    sl_status s = check_tune(c, dim, t);
+    if (s != SL_OK) return s;
+    auto& d = c->tune[dim];
+    d.block = t->block;
+    d.ft = is_scaled(c) ? 1 : t->fibres_per_thread;
+    d.unroll = is_scaled(c) ? 1 : (dim == 0 ? 1 : t->unroll);
+    d.chunk = dim == 0 ? 0 : uint32_t(t->chunk);
+    return SL_OK;
+}
+
+static int natural_shift_dim(const sl_ctx* c, int m)
+{
+    if (c->g.pair[m] >= 0) return c->g.pair[m];
+    for (int q = 0; q < c->ndim; ++q)
+        if (c->g.pair[q] == m) return q;
+    return -1;
+}
+
+sl_status sl_autotune(sl_ctx* c, int reps)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot autotune during a capture");
+    if (reps < 1) reps = 1;
+    if (reps > 50) reps = 50;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    SL_CUDA(c, cudaEventCreate(&e0));
+    SL_CUDA(c, cudaEventCreate(&e1));
+    sl_status result = SL_OK;
+    for (int m = 0; m < c->ndim && result == SL_OK; ++m) {
+        const int sd = natural_shift_dim(c, m);
+        const int nclass = sd < 0 ? 1 : int(c->g.n[sd]);
+        std::vector<double> sh(size_t(nclass), 0.37);
+        cudaError_t e = cudaMemcpyAsync(c->d_shifts, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, c->st);
+        if (e != cudaSuccess) {
+            result = cuda_fail(c, e, "autotune shifts");
+            break;
+        }
+        ShiftSource src{};
+        src.kind = 0;
+        src.data = c->d_shifts;
+        result = build_table(c, m, nclass, src);
+        if (result != SL_OK) break;
+
+        std::vector<sl_ctx::Tune> cand;
+        if (m == 0) {
+            if (is_scaled(c)) {
+                for (int b : {64, 128, 256}) cand.push_back({b, 1, 1, 0});
+            } else {
+                for (int ft : {1, 2, 3, 4, 9})
+                    if (ft == 1 || ft <= c->nfib)
+                        for (int b : {128, 256}) cand.push_back({b, ft, 1, 0});
+            }
+        } else {
+            if (is_scaled(c)) {
+                for (int b : {64, 128}) cand.push_back({b, 1, 1, chunk_for(c, m, 1)});
+            } else {
+                const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
+                for (auto& x : fu)
+                    if (x[0] == 1 || x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0])});
+            }
+        }
+        const sl_ctx::Tune keep = c->tune[m];
+        sl_ctx::Tune best = keep;
+        float best_ms = 1e30f;
+        for (const auto& t : cand) {
+            c->tune[m] = t;
+            e = launch_only(c, m, sd);   // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
+            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_only(c, m, sd);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                c->tune[m] = keep;
+                result = cuda_fail(c, e, "autotune launch");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        c->tune[m] = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
 }
 
 sl_status sl_profile_enable(sl_ctx* c, int enable)

@@ -44,8 +44,8 @@ __global__ void k_ab_build(int K, int nclass, uint32_t N, ShiftSource src, PolyT
     const int O = K + 1;
     const int deg = 2 * K + 1;
     const double t = a - 0.5;
-    double* m64 = ab64 + size_t(c) * 2 * O * O;
-    float* m32 = ab32 + size_t(c) * 2 * O * O;
+    double* m64 = ab64 + size_t(c) * ab_stride64(O);
+    float* m32 = ab32 + size_t(c) * ab_stride32(O);
     for (int j = 0; j < O; ++j) {
         for (int l = 0; l < O; ++l) {
             double va, vb;

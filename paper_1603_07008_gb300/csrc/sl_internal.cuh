@@ -58,11 +58,16 @@ struct Planes {
 
 // Per shift class: sigma reduced into [0, N), alpha in [0,1), and the
 // matrices A (first o*o) and B (next o*o), row-major, in FP64 and FP32.
+// Each class's record is padded to a multiple of 16 bytes so that the sweep
+// kernels read it with vector loads.
+__host__ __device__ constexpr int ab_stride32(int O) { return (2 * O * O + 3) / 4 * 4; }
+__host__ __device__ constexpr int ab_stride64(int O) { return (2 * O * O + 1) / 2 * 2; }
+
 struct ShiftTable {
     const int32_t* sigma;
     const double* alpha;
-    const double* ab64;   // [class][2][o][o]
-    const float* ab32;    // [class][2][o][o]
+    const double* ab64;   // [class][ab_stride64(o)]: A then B
+    const float* ab32;    // [class][ab_stride32(o)]: A then B
 };
 
 // Geometry of one sweep along dimension `dim` of the flattened grid viewed as
@@ -106,11 +111,13 @@ struct SweepLaunch {
     int mode;
     int unit;            // 1: sweep along dimension 0
     int ft;              // fibres per thread (non-scaled modes)
+    int unroll;          // cells per walk step of the strided kernel
     int block;           // threads per block
     cudaStream_t stream;
 };
 
-cudaError_t launch_sweep_fp(const SweepLaunch& L);       // M_FP64, M_F32
+cudaError_t launch_sweep_f64(const SweepLaunch& L);      // M_FP64
+cudaError_t launch_sweep_f32(const SweepLaunch& L);      // M_F32
 cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
 
 // Coefficients of the entries of A(alpha) and B(alpha) as polynomials in

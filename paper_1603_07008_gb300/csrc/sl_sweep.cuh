@@ -105,26 +105,46 @@ struct Mats {
 
     __device__ __forceinline__ void load(const ShiftTable& t, uint32_t cls, bool need_f0)
     {
-        const double* m64 = t.ab64 + size_t(cls) * 2 * O * O;
+        // one class record, read with 16-byte vector loads
         if constexpr (sizeof(R) == 8) {
+            constexpr int S = ab_stride64(O);
+            const double2* p = reinterpret_cast<const double2*>(t.ab64 + size_t(cls) * S);
+            double v[S];
+#pragma unroll
+            for (int q = 0; q < S / 2; ++q) {
+                const double2 x = __ldg(p + q);
+                v[2 * q] = x.x;
+                v[2 * q + 1] = x.y;
+            }
 #pragma unroll
             for (int j = 0; j < O; ++j)
 #pragma unroll
                 for (int l = 0; l < O; ++l) {
-                    a[j][l] = __ldg(m64 + j * O + l);
-                    b[j][l] = __ldg(m64 + O * O + j * O + l);
+                    a[j][l] = v[j * O + l];
+                    b[j][l] = v[O * O + j * O + l];
                 }
         } else {
-            const float* m32 = t.ab32 + size_t(cls) * 2 * O * O;
+            constexpr int S = ab_stride32(O);
+            const float4* p = reinterpret_cast<const float4*>(t.ab32 + size_t(cls) * S);
+            float v[S];
+#pragma unroll
+            for (int q = 0; q < S / 4; ++q) {
+                const float4 x = __ldg(p + q);
+                v[4 * q] = x.x;
+                v[4 * q + 1] = x.y;
+                v[4 * q + 2] = x.z;
+                v[4 * q + 3] = x.w;
+            }
 #pragma unroll
             for (int j = 0; j < O; ++j)
 #pragma unroll
                 for (int l = 0; l < O; ++l) {
-                    a[j][l] = __ldg(m32 + j * O + l);
-                    b[j][l] = __ldg(m32 + O * O + j * O + l);
+                    a[j][l] = v[j * O + l];
+                    b[j][l] = v[O * O + j * O + l];
                 }
         }
         if (need_f0) {
+            const double* m64 = t.ab64 + size_t(cls) * ab_stride64(O);
 #pragma unroll
             for (int l = 0; l < O; ++l) {
                 a0[l] = __ldg(m64 + l);
@@ -295,9 +315,11 @@ __global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
 
 // Sweep along dimension m > 0: one thread per line (and fibre group and
 // chunk of the line, blockIdx.y = chunk * nfg + group).  The thread walks the
-// target cells i0 .. i1-1 of its chunk; the source cell i - sigma of one
-// step is the source cell i - sigma - 1 of the next, so it stays in registers.
-template <int K, int MODE, int FT>
+// target cells i0 .. i1-1 of its chunk, U cells per step: it issues the loads
+// of the U new source cells first, then computes and stores the U targets.
+// The source cell i - sigma of one target is the source cell i - sigma - 1
+// of the next, so every source value is loaded once.
+template <int K, int MODE, int FT, int U>
 __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
 {
     constexpr int O = K + 1;
@@ -329,11 +351,36 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
     ia += ia < 0 ? int32_t(a.N) : 0;
     int32_t ib = ia - 1;
     ib += ib < 0 ? int32_t(a.N) : 0;
+    const int32_t N = int32_t(a.N);
 
-    CellVals<K, MODE, FT> prev, cur, out;
+    CellVals<K, MODE, FT> prev;
     load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(ib) * a.inner, jb, a.ostride, fbase,
                            a.nfib, prev);
-    for (uint32_t i = i0; i < i1; ++i) {
+    uint32_t i = i0;
+    if constexpr (U > 1) {
+        for (; i + U <= i1; i += U) {
+            CellVals<K, MODE, FT> cur[U];
+#pragma unroll
+            for (int s = 0; s < U; ++s) {
+                int32_t x = ia + s;
+                x -= x >= N ? N : 0;
+                load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(x) * a.inner, jb,
+                                       a.ostride, fbase, a.nfib, cur[s]);
+            }
+#pragma unroll
+            for (int s = 0; s < U; ++s) {
+                CellVals<K, MODE, FT> out;
+                combine<K, MODE, FT>(M, cur[s], s == 0 ? prev : cur[s - 1], fbase, a.nfib, out);
+                store_cell<K, MODE, FT>(a.dst, a.pstride, base + (i + s) * a.inner, jb, a.ostride,
+                                        fbase, a.nfib, out);
+            }
+            prev = cur[U - 1];
+            ia += U;
+            ia -= ia >= N ? N : 0;
+        }
+    }
+    for (; i < i1; ++i) {
+        CellVals<K, MODE, FT> cur, out;
         load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(ia) * a.inner, jb, a.ostride,
                                fbase, a.nfib, cur);
         combine<K, MODE, FT>(M, cur, prev, fbase, a.nfib, out);
@@ -341,7 +388,7 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
                                 out);
         prev = cur;
         ++ia;
-        if (ia == int32_t(a.N)) ia = 0;
+        if (ia == N) ia = 0;
     }
 }
 

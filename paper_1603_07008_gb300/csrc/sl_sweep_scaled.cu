@@ -19,7 +19,9 @@ cudaError_t launch_one(const SweepLaunch& L)
     } else {
         const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
         dim3 grid((a.lines + L.block - 1) / L.block, nchunk);
-        k_sweep_strided<K, MODE, NF><<<grid, L.block, 0, L.stream>>>(a);
+        // two cells per walk step while the per-thread cell stays small
+        constexpr int U = NF * (K + 1) <= 16 ? 2 : 1;
+        k_sweep_strided<K, MODE, NF, U><<<grid, L.block, 0, L.stream>>>(a);
     }
     return cudaGetLastError();
 }

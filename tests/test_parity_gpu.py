@@ -352,3 +352,100 @@ def test_profile_counts_sweeps():
         n, ms, b = c.profile_query()
     assert n == 12 and ms > 0
     assert b == 12 * 2 * c.info["state_bytes"]
+
+
+UNIT_FT = [1, 2, 3, 4, 9]
+STRIDED_SHAPES = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]
+
+
+@pytest.mark.parametrize("storage", ["fp64", "mix_fp32"])
+@pytest.mark.parametrize("n,k", [((37, 5, 3), 2), ((6, 9, 4), 1), ((3, 4, 5), 3)])
+def test_every_launch_shape_gives_identical_results(storage, n, k):
+    """Fibres per thread, unroll, block size and chunk length change only the
+    work distribution: every shape must give bit-identical output, and the
+    output must match the oracle."""
+    rng = np.random.default_rng(21)
+    u = _rand(n, k, 22)
+    g = _grid(n)
+    with S.Context(g, k, storage) as ctx:
+        for dim in range(len(n)):
+            sd = (dim + 1) % len(n)
+            s = _shifts(rng, n, dim, sd)
+            ctx.set_coeffs(u)
+            ctx.advect(dim, sd, s)
+            ref_gpu = ctx.get_coeffs()
+            ref = O.sweep(ctx_stored(u, storage), n, k, dim, sd, s)
+            if storage == "fp64":
+                assert O.rel_max(ref_gpu, ref) <= FP64_TOL
+            else:
+                assert O.rel_l2(ref_gpu, ref, k, len(n)) <= 1e-6
+            shapes = []
+            if dim == 0:
+                shapes = [dict(block=b, fibres_per_thread=f) for f in UNIT_FT for b in (64, 256)]
+            else:
+                for f, un in STRIDED_SHAPES:
+                    for ch in (1, 3, n[dim]):
+                        shapes.append(dict(block=128, fibres_per_thread=f, unroll=un, chunk=ch))
+                shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=2))
+            for sh in shapes:
+                ctx.set_tune(dim, **sh)
+                ctx.set_coeffs(u)
+                ctx.advect(dim, sd, s)
+                assert np.array_equal(ctx.get_coeffs(), ref_gpu), (dim, sh)
+
+
+def ctx_stored(u, storage):
+    if storage == "fp64":
+        return u
+    v = u.copy()
+    v[:, 1:] = v[:, 1:].astype(np.float32).astype(np.float64)
+    return v
+
+
+@pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
+def test_scaled_launch_shapes_identical(storage):
+    n = (5, 7, 3, 2)
+    k = 1
+    rng = np.random.default_rng(5)
+    u = _rand(n, k, 6)
+    with S.Context(_grid(n), k, storage) as ctx:
+        for dim in range(len(n)):
+            s = _shifts(rng, n, dim, -1)
+            ctx.set_coeffs(u)
+            ctx.advect(dim, -1, s)
+            ref = ctx.get_coeffs()
+            for b in (32, 64, 128):
+                sh = dict(block=b) if dim == 0 else dict(block=b, chunk=2)
+                ctx.set_tune(dim, **sh)
+                ctx.set_coeffs(u)
+                ctx.advect(dim, -1, s)
+                assert np.array_equal(ctx.get_coeffs(), ref)
+
+
+def test_set_tune_rejects_shapes_not_built():
+    with S.Context(_grid((8, 8)), 2, "mix_fp32") as ctx:
+        for dim, sh in [(0, dict(block=512)), (0, dict(block=100)), (0, dict(block=128, fibres_per_thread=5)),
+                        (1, dict(block=256, fibres_per_thread=1, unroll=1, chunk=8)),
+                        (1, dict(block=128, fibres_per_thread=3, unroll=4, chunk=8)),
+                        (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=0)),
+                        (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=9))]:
+            with pytest.raises(S.SlError) as e:
+                ctx.set_tune(dim, **sh)
+            assert e.value.status == S.SL_EINVAL
+
+
+def test_autotune_keeps_state_and_results():
+    p = W.config3(n=10, steps=2)
+    with S.Context(p.grid, p.k, "mix_fp32") as a, S.Context(p.grid, p.k, "mix_fp32") as b:
+        for c in (a, b):
+            c.project(p.nq, p.weights, p.params)
+            c.set_fields(p.field_list())
+        before = b.get_coeffs()
+        b.autotune(2)
+        assert np.array_equal(b.get_coeffs(), before)
+        a.step("strang", p.dt, 2)
+        b.step("strang", p.dt, 2)
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+        for d in range(4):
+            t = b.get_tune(d)
+            assert t["block"] >= 32
