@@ -53,6 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--shapes", default=None,
+                    help="JSON list of per-dimension launch shapes (sl_set_tune fields) used "
+                         "instead of the autotuner, e.g. to profile one fixed kernel")
     return ap.parse_args(argv)
 
 
@@ -200,12 +203,20 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def gpu_steps(S, W, p, storage, stream, steps, warmup, profile):
+def apply_shapes(ctx, shapes):
+    if shapes is None:
+        ctx.autotune(3)
+        return
+    for d, sh in enumerate(json.loads(shapes)):
+        ctx.set_tune(d, **sh)
+
+
+def gpu_steps(S, W, p, storage, stream, steps, warmup, profile, shapes=None):
     import torch
     ctx = S.Context(p.grid, p.k, storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
-    ctx.autotune(3)
+    apply_shapes(ctx, shapes if storage == p.storage else None)
     m0 = ctx.mass()
     for _ in range(warmup):
         ctx.step("strang", p.dt, 1)
@@ -238,7 +249,8 @@ def run_ours(args):
     peaks, peak_src = measured_peaks()
 
     def timed(storage, profile):
-        ctx, m0, e0, e1 = gpu_steps(S, W, p, storage, stream, args.steps, args.warmup, profile)
+        ctx, m0, e0, e1 = gpu_steps(S, W, p, storage, stream, args.steps, args.warmup, profile,
+                                    args.shapes)
         barrier(world)
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
@@ -251,10 +263,16 @@ def run_ours(args):
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
         prof = ctx.profile_query() if profile else None
+        dims = ctx.profile_dims() if profile else None
         ctx.profile_enable(False)
         m1 = ctx.mass()
         info = dict(ctx.info)
         info["tune"] = [ctx.get_tune(d) for d in range(p.grid.ndim)]
+        if dims:
+            nd, msd = dims
+            info["per_dim"] = [{"dim": d, "launches": nd[d], "ms_per_launch": msd[d] / max(nd[d], 1),
+                                "gbs": 2.0 * info["state_bytes"] / (msd[d] / max(nd[d], 1) / 1e3) / 1e9
+                                if nd[d] else None} for d in range(p.grid.ndim)]
         ctx.close()
         return ms, prof, abs(m1 - m0) / abs(m0), clk, info
 
@@ -276,7 +294,8 @@ def run_ours(args):
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64_max / args.steps,
                 "sweep_ms": sms64 / max(nl64, 1),
                 "sweep_gbs": (sb64 / max(nl64, 1)) / (sms64 / max(nl64, 1) / 1000.0) / 1e9,
-                "mass_drift": drift64, "state_bytes": info64["state_bytes"], "clocks": clk64}
+                "mass_drift": drift64, "state_bytes": info64["state_bytes"], "clocks": clk64,
+                "per_dim": info64.get("per_dim")}
 
     e2e = None
     if not args.no_e2e:
@@ -305,7 +324,7 @@ def run_ours(args):
                          "frac": achieved_gbs / peak_gbs, "traffic": None,
                          "kernel": "sweep (all dims)", "peak_source": peak_src,
                          "bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg_sweep_ms,
-                         "launches": nl},
+                         "launches": nl, "per_dim": info.get("per_dim")},
             "fp64": fp64,
             "speedup_mixed_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "e2e": e2e,
@@ -328,7 +347,7 @@ def run_e2e(S, W, p, args, stream, world, dev):
     ctx = S.Context(p.grid, p.k, args.storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
-    ctx.autotune(3)
+    apply_shapes(ctx, args.shapes)
     mean, hi, scale = S.plane_arrays(ctx.handle)
     # pinned host copies of the planes
     t_mean = torch.empty(mean.size, dtype=torch.float64, pin_memory=True)

@@ -269,11 +269,18 @@ sl_status sl_synchronize(sl_ctx* ctx);
  *   unroll             cells per walk step along dimensions > 0: 1, 2 or 4
  *                      (4 only with 1 or 2 fibres per thread)
  *   chunk              cells one thread walks along dimensions > 0 (1..n_dim)
+ *   pipeline           0: the walk keeps the previous cell in registers;
+ *                      4 or 8: the walk streams its source rows through a
+ *                      per-thread cp.async ring of that many rows in shared
+ *                      memory (FP64 and FP32 stores, dimensions > 0, with 1 or
+ *                      2 fibres per thread, or 3 with pipeline 4; unroll
+ *                      is ignored)
  * Every shape computes the same result; only the speed differs. */
 typedef struct {
     int32_t block;
     int32_t fibres_per_thread;
     int32_t unroll;
+    int32_t pipeline;
     int64_t chunk;
 } sl_tune;
 
@@ -295,6 +302,11 @@ sl_status sl_autotune(sl_ctx* ctx, int reps);
  * once), then resets the counters.  Off by default. */
 sl_status sl_profile_enable(sl_ctx* ctx, int enable);
 sl_status sl_profile_query(sl_ctx* ctx, int64_t* launches, double* ms, double* bytes);
+
+/* The per-dimension split of the last sl_profile_query: launches[m] and ms[m]
+ * for every sweep dimension m < ndim (caller arrays of SL_MAX_DIM entries).
+ * Host only. */
+sl_status sl_profile_dims(const sl_ctx* ctx, int64_t* launches, double* ms);
 
 #ifdef __cplusplus
 }

@@ -26,7 +26,7 @@ __all__ = [
     "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
     "sl_set_fields", "sl_step", "sl_mass", "sl_graph_capture", "sl_graph_launch",
     "sl_synchronize", "sl_profile_enable", "sl_profile_query", "sl_mass_noalloc",
-    "sl_get_tune", "sl_set_tune", "sl_autotune",
+    "sl_get_tune", "sl_set_tune", "sl_autotune", "sl_profile_dims",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -45,7 +45,7 @@ class SlError(RuntimeError):
 
 class sl_tune(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("fibres_per_thread", ctypes.c_int32),
-                ("unroll", ctypes.c_int32), ("chunk", ctypes.c_int64)]
+                ("unroll", ctypes.c_int32), ("pipeline", ctypes.c_int32), ("chunk", ctypes.c_int64)]
 
 
 class sl_grid(ctypes.Structure):
@@ -124,6 +124,7 @@ def lib():
             "sl_synchronize": (st, [_vp]),
             "sl_profile_enable": (st, [_vp, ctypes.c_int]),
             "sl_profile_query": (st, [_vp, _i64p, _dp, _dp]),
+            "sl_profile_dims": (st, [_vp, _i64p, _dp]),
             "sl_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_autotune": (st, [_vp, ctypes.c_int]),
@@ -312,6 +313,14 @@ def sl_profile_query(ctx) -> Tuple[int, float, float]:
     return n.value, ms.value, b.value
 
 
+def sl_profile_dims(ctx):
+    """(launches[6], ms[6]) per sweep dimension of the last sl_profile_query."""
+    n = (ctypes.c_int64 * MAX_DIM)()
+    ms = (ctypes.c_double * MAX_DIM)()
+    _check(lib().sl_profile_dims(ctx, n, ms), ctx)
+    return list(n), list(ms)
+
+
 def sl_get_tune(ctx, dim: int) -> dict:
     t = sl_tune()
     _check(lib().sl_get_tune(ctx, int(dim), ctypes.byref(t)), ctx)
@@ -319,8 +328,8 @@ def sl_get_tune(ctx, dim: int) -> dict:
 
 
 def sl_set_tune(ctx, dim: int, block: int, fibres_per_thread: int = 1, unroll: int = 1,
-                chunk: int = 0):
-    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(chunk))
+                chunk: int = 0, pipeline: int = 0):
+    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(pipeline), int(chunk))
     _check(lib().sl_set_tune(ctx, int(dim), ctypes.byref(t)), ctx)
 
 
@@ -414,3 +423,6 @@ class Context:
 
     def profile_query(self):
         return sl_profile_query(self.handle)
+
+    def profile_dims(self):
+        return sl_profile_dims(self.handle)

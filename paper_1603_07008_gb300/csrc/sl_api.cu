@@ -62,13 +62,17 @@ struct sl_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+    std::vector<int> ev_dim;
     int64_t prof_launches = 0;
+    int64_t last_dim_launches[SL_MAX_DIM] = {0};
+    double last_dim_ms[SL_MAX_DIM] = {0};
 
     struct Tune {
         int block = 256;
         int ft = 1;
         int unroll = 1;
         uint32_t chunk = 0;
+        int pipeline = 0;
     } tune[SL_MAX_DIM];
 
     std::string err;
@@ -189,6 +193,7 @@ uint32_t chunk_for(const sl_ctx* c, int m, int ft)
 
 // Launch shapes compiled into the library.
 bool unit_ft_ok(int ft) { return ft == 1 || ft == 2 || ft == 3 || ft == 4 || ft == 9; }
+bool async_ok(int ft, int p) { return (p == 4 && ft >= 1 && ft <= 3) || (p == 8 && (ft == 1 || ft == 2)); }
 bool strided_ok(int ft, int u)
 {
     return (ft == 1 && (u == 1 || u == 2 || u == 4)) || (ft == 2 && (u == 1 || u == 2 || u == 4)) ||
@@ -276,6 +281,7 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.unit = dim == 0;
     L.ft = is_scaled(c) ? int(c->nfib) : c->tune[dim].ft;
     L.unroll = c->tune[dim].unroll;
+    L.pipeline = dim == 0 ? 0 : c->tune[dim].pipeline;
     L.block = c->tune[dim].block;
     L.stream = c->st;
     return is_scaled(c) ? launch_sweep_scaled(L) : c->mode == M_FP64 ? launch_sweep_f64(L)
@@ -298,6 +304,7 @@ sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
     if (prof) {
         SL_CUDA(c, cudaEventRecord(e1, c->st));
         c->ev_used.emplace_back(e0, e1);
+        c->ev_dim.push_back(dim);
         c->prof_launches++;
     }
     c->cur ^= 1;
@@ -922,6 +929,16 @@ sl_status sl_synchronize(sl_ctx* c)
     return SL_OK;
 }
 
+sl_status sl_profile_dims(const sl_ctx* c, int64_t* launches, double* ms)
+{
+    if (!c || !launches || !ms) return fail(nullptr, SL_EINVAL, "NULL argument");
+    for (int m = 0; m < SL_MAX_DIM; ++m) {
+        launches[m] = c->last_dim_launches[m];
+        ms[m] = c->last_dim_ms[m];
+    }
+    return SL_OK;
+}
+
 sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
 {
     if (!c || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
@@ -930,6 +947,7 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
     out->block = t.block;
     out->fibres_per_thread = is_scaled(c) ? int32_t(c->nfib) : t.ft;
     out->unroll = t.unroll;
+    out->pipeline = t.pipeline;
     out->chunk = dim == 0 ? 0 : int64_t(t.chunk);
     return SL_OK;
 }
@@ -943,9 +961,15 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
         if (dim == 0 && !unit_ft_ok(t->fibres_per_thread))
             return fail(c, SL_EINVAL, "fibres_per_thread %d not provided along dimension 0",
                         t->fibres_per_thread);
-        if (dim > 0 && !strided_ok(t->fibres_per_thread, t->unroll))
+        if (dim > 0 && t->pipeline == 0 && !strided_ok(t->fibres_per_thread, t->unroll))
             return fail(c, SL_EINVAL, "(fibres_per_thread %d, unroll %d) not provided",
                         t->fibres_per_thread, t->unroll);
+        if (dim > 0 && t->pipeline != 0 && !async_ok(t->fibres_per_thread, t->pipeline))
+            return fail(c, SL_EINVAL, "(fibres_per_thread %d, pipeline %d) not provided",
+                        t->fibres_per_thread, t->pipeline);
+        if (dim == 0 && t->pipeline != 0) return fail(c, SL_EINVAL, "pipeline applies to dimensions > 0");
+    } else if (t->pipeline != 0) {
+        return fail(c, SL_EINVAL, "the scaled stores have no cp.async pipeline");
     }
     if (dim > 0) {
         const int64_t N = c->g.n[dim];
@@ -967,6 +991,7 @@ sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
     d.block = t->block;
     d.ft = is_scaled(c) ? 1 : t->fibres_per_thread;
     d.unroll = is_scaled(c) ? 1 : (dim == 0 ? 1 : t->unroll);
+    d.pipeline = is_scaled(c) || dim == 0 ? 0 : t->pipeline;
     d.chunk = dim == 0 ? 0 : uint32_t(t->chunk);
     return SL_OK;
 }
@@ -1007,19 +1032,25 @@ sl_status sl_autotune(sl_ctx* c, int reps)
         std::vector<sl_ctx::Tune> cand;
         if (m == 0) {
             if (is_scaled(c)) {
-                for (int b : {64, 128, 256}) cand.push_back({b, 1, 1, 0});
+                for (int b : {64, 128, 256}) cand.push_back({b, 1, 1, 0, 0});
             } else {
                 for (int ft : {1, 2, 3, 4, 9})
                     if (ft == 1 || ft <= c->nfib)
-                        for (int b : {128, 256}) cand.push_back({b, ft, 1, 0});
+                        for (int b : {128, 256}) cand.push_back({b, ft, 1, 0, 0});
             }
         } else {
             if (is_scaled(c)) {
-                for (int b : {64, 128}) cand.push_back({b, 1, 1, chunk_for(c, m, 1)});
+                for (int b : {64, 128}) cand.push_back({b, 1, 1, chunk_for(c, m, 1), 0});
             } else {
                 const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
                 for (auto& x : fu)
-                    if (x[0] == 1 || x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0])});
+                    if (x[0] == 1 || x[0] <= c->nfib)
+                        cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0]), 0});
+                const int fp[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {3, 4}};
+                for (auto& x : fp)
+                    if (x[0] == 1 || x[0] <= c->nfib)
+                        for (int b : {64, 128})
+                            cand.push_back({b, x[0], 1, chunk_for(c, m, x[0]), x[1]});
             }
         }
         const sl_ctx::Tune keep = c->tune[m];
@@ -1063,14 +1094,22 @@ sl_status sl_profile_query(sl_ctx* c, int64_t* launches, double* ms, double* byt
     if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
     SL_CUDA(c, cudaStreamSynchronize(c->st));
     double tot = 0.0;
-    for (auto& pr : c->ev_used) {
+    for (int m = 0; m < SL_MAX_DIM; ++m) {
+        c->last_dim_launches[m] = 0;
+        c->last_dim_ms[m] = 0.0;
+    }
+    for (size_t q = 0; q < c->ev_used.size(); ++q) {
+        auto& pr = c->ev_used[q];
         float t = 0.0f;
         SL_CUDA(c, cudaEventElapsedTime(&t, pr.first, pr.second));
         tot += t;
+        c->last_dim_launches[c->ev_dim[q]]++;
+        c->last_dim_ms[c->ev_dim[q]] += t;
         c->ev_free.push_back(pr.first);
         c->ev_free.push_back(pr.second);
     }
     c->ev_used.clear();
+    c->ev_dim.clear();
     if (launches) *launches = c->prof_launches;
     if (ms) *ms = tot;
     if (bytes) *bytes = 2.0 * double(c->state_bytes) * double(c->prof_launches);

@@ -112,6 +112,7 @@ struct SweepLaunch {
     int unit;            // 1: sweep along dimension 0
     int ft;              // fibres per thread (non-scaled modes)
     int unroll;          // cells per walk step of the strided kernel
+    int pipeline;        // > 0: strided kernel with a cp.async ring of this many rows
     int block;           // threads per block
     cudaStream_t stream;
 };

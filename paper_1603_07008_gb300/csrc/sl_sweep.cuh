@@ -392,4 +392,147 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
     }
 }
 
+// ---------------------------------------------------------------- strided, cp.async ring
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem)
+{
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async element size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(smem)), "l"(gmem),
+                 "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Dynamic shared memory of k_sweep_strided_async for `block` threads.
+template <int K, int MODE, int FT, int P>
+constexpr size_t strided_async_smem(int block)
+{
+    return size_t(P + 1) * size_t(block) * (8 + size_t(FT) * (K + 1) * sizeof(typename St<MODE>::T));
+}
+
+// Same walk as k_sweep_strided, but the source rows are fetched P rows ahead
+// with cp.async into a per-thread ring of P+1 row slots in shared memory, so
+// every thread keeps P rows of loads in flight while it computes.  A thread
+// only reads slots it filled itself (cp.async.wait_group makes them visible
+// to the issuing thread), so no block barrier is needed; a slot is refilled
+// one iteration after it was read and its values were used.
+template <int K, int MODE, int FT, int P>
+__global__ void __launch_bounds__(128) k_sweep_strided_async(const SweepArgs a)
+{
+    static_assert(!St<MODE>::scaled, "cp.async ring needs 4- or 8-byte elements");
+    using T = typename St<MODE>::T;
+    constexpr int O = K + 1;
+    constexpr int S = P + 1;
+    constexpr int V = FT * O;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t nthr = blockDim.x;
+    const uint32_t tid = threadIdx.x;
+    double* sm_mean = reinterpret_cast<double*>(smem_raw);
+    T* sm_val = reinterpret_cast<T*>(smem_raw + size_t(S) * nthr * 8);
+
+    const uint32_t line = blockIdx.x * blockDim.x + tid;
+    if (line >= a.lines) return;
+    const uint32_t grp = blockIdx.y % uint32_t(a.nfg);
+    const uint32_t chunk = blockIdx.y / uint32_t(a.nfg);
+    const int fbase = int(grp) * FT;
+    const uint32_t outer = a.fdInner.div(line);
+    const uint32_t inn = line - outer * a.inner;
+    const uint32_t base = outer * a.N * a.inner + inn;
+    const uint32_t cls = shift_class(a, inn, outer);
+    const int32_t sig = __ldg(a.tab.sigma + cls);
+    const uint32_t i0 = chunk * a.chunk;
+    uint32_t i1 = i0 + a.chunk;
+    if (i1 > a.N) i1 = a.N;
+    if (i0 >= i1) return;
+    const int32_t N = int32_t(a.N);
+
+    int jb[FT];
+#pragma unroll
+    for (int u = 0; u < FT; ++u) {
+        const int f = fbase + u;
+        jb[u] = (f / a.ostride) * (O * a.ostride) + (f % a.ostride);
+    }
+    Mats<K, MODE> M;
+    M.load(a.tab, cls, fbase == 0);
+
+    // rows in consumption order: row 0 is source cell i0-sigma-1, row q >= 1
+    // the source cell i0+q-1-sigma of target i0+q-1; all periodic in N
+    const int nrows = int(i1 - i0) + 1;
+    int32_t frow = int32_t(i0) - sig - 1;
+    frow += frow < 0 ? N : 0;
+    frow += frow < 0 ? N : 0;
+
+    auto fetch = [&](int slot, uint32_t cell) {
+#pragma unroll
+        for (int u = 0; u < FT; ++u) {
+            if (fbase + u >= a.nfib) break;
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                const int J = jb[u] + l * a.ostride;
+                if (J == 0)
+                    cp_async<8>(sm_mean + size_t(slot) * nthr + tid, a.src.mean + cell);
+                else
+                    cp_async<sizeof(T)>(sm_val + (size_t(slot) * V + u * O + l) * nthr + tid,
+                                        plane_ptr<T>(a.src.hi, a.pstride, J) + cell);
+            }
+        }
+    };
+    auto read = [&](int slot, CellVals<K, MODE, FT>& cv) {
+#pragma unroll
+        for (int u = 0; u < FT; ++u) {
+            if (fbase + u >= a.nfib) break;
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                const int J = jb[u] + l * a.ostride;
+                if (J == 0) {
+                    cv.m = sm_mean[size_t(slot) * nthr + tid];
+                    cv.v[u][0] = 0;
+                } else {
+                    cv.v[u][l] = sm_val[(size_t(slot) * V + u * O + l) * nthr + tid];
+                }
+            }
+        }
+    };
+
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        if (q < nrows) {
+            fetch(q, base + uint32_t(frow) * a.inner);
+            ++frow;
+            frow -= frow >= N ? N : 0;
+        }
+        cp_async_commit();
+    }
+    CellVals<K, MODE, FT> prev, cur;
+    int slot = 0;           // slot of row q
+    int rslot = P;          // slot that row q + P goes to (= slot of row q - 1)
+    for (int q = 0; q < nrows; ++q) {
+        cp_async_wait<P - 1>();
+        read(slot, cur);
+        if (q + P < nrows) {
+            fetch(rslot, base + uint32_t(frow) * a.inner);
+            ++frow;
+            frow -= frow >= N ? N : 0;
+        }
+        cp_async_commit();
+        if (q > 0) {
+            CellVals<K, MODE, FT> out;
+            combine<K, MODE, FT>(M, cur, prev, fbase, a.nfib, out);
+            store_cell<K, MODE, FT>(a.dst, a.pstride, base + (i0 + uint32_t(q) - 1) * a.inner, jb,
+                                    a.ostride, fbase, a.nfib, out);
+        }
+        prev = cur;
+        rslot = slot;
+        slot = slot + 1 == S ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
+}
+
 }  // namespace sl

@@ -356,6 +356,7 @@ def test_profile_counts_sweeps():
 
 UNIT_FT = [1, 2, 3, 4, 9]
 STRIDED_SHAPES = [(1, 1), (1, 2), (1, 4), (2, 1), (2, 2), (2, 4), (3, 1), (3, 2)]
+ASYNC_SHAPES = [(1, 4), (1, 8), (2, 4), (2, 8), (3, 4)]
 
 
 @pytest.mark.parametrize("storage", ["fp64", "mix_fp32"])
@@ -387,6 +388,10 @@ def test_every_launch_shape_gives_identical_results(storage, n, k):
                     for ch in (1, 3, n[dim]):
                         shapes.append(dict(block=128, fibres_per_thread=f, unroll=un, chunk=ch))
                 shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=2))
+                for f, pl in ASYNC_SHAPES:
+                    for ch in (1, 2, n[dim]):
+                        for b in (32, 128):
+                            shapes.append(dict(block=b, fibres_per_thread=f, pipeline=pl, chunk=ch))
             for sh in shapes:
                 ctx.set_tune(dim, **sh)
                 ctx.set_coeffs(u)
@@ -428,7 +433,9 @@ def test_set_tune_rejects_shapes_not_built():
                         (1, dict(block=256, fibres_per_thread=1, unroll=1, chunk=8)),
                         (1, dict(block=128, fibres_per_thread=3, unroll=4, chunk=8)),
                         (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=0)),
-                        (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=9))]:
+                        (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=9)),
+                        (1, dict(block=128, fibres_per_thread=3, pipeline=8, chunk=8)),
+                        (0, dict(block=128, fibres_per_thread=1, pipeline=4))]:
             with pytest.raises(S.SlError) as e:
                 ctx.set_tune(dim, **sh)
             assert e.value.status == S.SL_EINVAL
