@@ -958,6 +958,9 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
     if (t->block < 32 || t->block > maxb || t->block % 32)
         return fail(c, SL_EINVAL, "block must be a multiple of 32 in [32, %d]", maxb);
     if (!is_scaled(c)) {
+        if (t->fibres_per_thread > c->nfib)
+            return fail(c, SL_EINVAL, "fibres_per_thread %d exceeds the %lld fibres of a cell",
+                        t->fibres_per_thread, (long long)c->nfib);
         if (dim == 0 && !unit_ft_ok(t->fibres_per_thread))
             return fail(c, SL_EINVAL, "fibres_per_thread %d not provided along dimension 0",
                         t->fibres_per_thread);
@@ -967,6 +970,8 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
         if (dim > 0 && t->pipeline != 0 && !async_ok(t->fibres_per_thread, t->pipeline))
             return fail(c, SL_EINVAL, "(fibres_per_thread %d, pipeline %d) not provided",
                         t->fibres_per_thread, t->pipeline);
+        if (dim > 0 && t->pipeline != 0 && t->block != 64 && t->block != 128)
+            return fail(c, SL_EINVAL, "the cp.async walk runs with 64 or 128 threads per block");
         if (dim == 0 && t->pipeline != 0) return fail(c, SL_EINVAL, "pipeline applies to dimensions > 0");
     } else if (t->pipeline != 0) {
         return fail(c, SL_EINVAL, "the scaled stores have no cp.async pipeline");
@@ -1035,7 +1040,7 @@ sl_status sl_autotune(sl_ctx* c, int reps)
                 for (int b : {64, 128, 256}) cand.push_back({b, 1, 1, 0, 0});
             } else {
                 for (int ft : {1, 2, 3, 4, 9})
-                    if (ft == 1 || ft <= c->nfib)
+                    if (ft <= c->nfib)
                         for (int b : {128, 256}) cand.push_back({b, ft, 1, 0, 0});
             }
         } else {
@@ -1044,11 +1049,10 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             } else {
                 const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
                 for (auto& x : fu)
-                    if (x[0] == 1 || x[0] <= c->nfib)
-                        cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0]), 0});
+                    if (x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0]), 0});
                 const int fp[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {3, 4}};
                 for (auto& x : fp)
-                    if (x[0] == 1 || x[0] <= c->nfib)
+                    if (x[0] <= c->nfib)
                         for (int b : {64, 128})
                             cand.push_back({b, x[0], 1, chunk_for(c, m, x[0]), x[1]});
             }

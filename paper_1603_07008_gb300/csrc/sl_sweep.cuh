@@ -7,16 +7,25 @@
 // freedom against 4o-1 flops (Sec. II-A), so the kernels are HBM-bound on
 // CUDA cores; no tensor cores are involved.
 //
-// Two launch shapes:
-//   * unit stride (sweep along dimension 0): one thread per target cell,
-//     consecutive threads on consecutive cells of a line, so every plane
-//     access of a warp is one coalesced segment.  The second source cell
-//     (i-sigma-1) is the first source cell of the neighbouring lane, so its
-//     load is served by L1.
+// Launch shapes:
+//   * unit stride (sweep along dimension 0): one thread per target cell and
+//     group of FT fibres; consecutive threads on consecutive cells of a line,
+//     so every plane access of a warp is one coalesced segment.  The second
+//     source cell (i-sigma-1) is the first source cell of the neighbouring
+//     lane, so its load is served by L1.
 //   * strided (sweep along dimension m > 0): one thread per line (consecutive
 //     threads on consecutive inner indices, again coalesced), walking along
-//     the sweep dimension and keeping the previous source cell in registers,
-//     so every source value is read from HBM once.
+//     the sweep dimension.  The source cell i-sigma of one target is the
+//     source cell i-sigma-1 of the next, so every source value is read once.
+//     Either the walk keeps U cells of loads in flight in registers
+//     (k_sweep_strided), or it streams its rows P rows ahead through a
+//     per-thread cp.async ring in shared memory (k_sweep_strided_async).
+//
+// A thread's fibre group either contains the fibre of the cell mean (group 0)
+// or not; the two cases are separate instantiations of the kernel body, so
+// the mean's special handling costs nothing elsewhere.  The last group of a
+// cell may be partial; its missing fibres repeat the last valid one, whose
+// values are then computed and stored twice by the same thread.
 //
 // Precision (split store): the cell mean c_{0..0} lives in an FP64 plane.
 // Its row is computed in FP64 in the form
@@ -89,7 +98,7 @@ __device__ __forceinline__ void pow2_scale(float mx, float& s, float& inv)
 
 template <int K, int MODE, int FT>
 struct CellVals {
-    typename St<MODE>::R v[FT][K + 1];   // v[u][0] of fibre 0 is unused: the mean is in m
+    typename St<MODE>::R v[FT][K + 1];   // v[0][0] of the mean's group is unused: the mean is in m
     double m;
 };
 
@@ -103,7 +112,8 @@ struct Mats {
     double aj0[O];  // column 0 of A in FP64 (l = 0 term of the mean's fibre)
     double alpha;
 
-    __device__ __forceinline__ void load(const ShiftTable& t, uint32_t cls, bool need_f0)
+    template <bool MEAN>
+    __device__ __forceinline__ void load(const ShiftTable& t, uint32_t cls)
     {
         // one class record, read with 16-byte vector loads
         if constexpr (sizeof(R) == 8) {
@@ -143,7 +153,7 @@ struct Mats {
                     b[j][l] = v[O * O + j * O + l];
                 }
         }
-        if (need_f0) {
+        if constexpr (MEAN) {
             const double* m64 = t.ab64 + size_t(cls) * ab_stride64(O);
 #pragma unroll
             for (int l = 0; l < O; ++l) {
@@ -155,63 +165,33 @@ struct Mats {
     }
 };
 
-// Load the FT fibres (base coefficient indices jb[u], stride ostride along the
-// fibre) of cell c.  Fibre index f = fbase + u; fibres >= nfib are skipped.
-template <int K, int MODE, int FT>
-__device__ __forceinline__ void load_cell(const Planes& p, int64_t pstride, uint32_t c,
-                                          const int (&jb)[FT], int ostride, int fbase, int nfib,
-                                          CellVals<K, MODE, FT>& cv)
-{
-    using T = typename St<MODE>::T;
-    constexpr int O = K + 1;
-    float s = 1.0f;
-    if constexpr (St<MODE>::scaled) s = __ldg(p.scale + c);
-#pragma unroll
-    for (int u = 0; u < FT; ++u) {
-        if (fbase + u >= nfib) break;
-#pragma unroll
-        for (int l = 0; l < O; ++l) {
-            const int J = jb[u] + l * ostride;
-            if (J == 0) {
-                cv.m = __ldg(p.mean + c);
-                cv.v[u][0] = 0;
-            } else {
-                auto raw = ld_raw(plane_ptr<T>(p.hi, pstride, J) + c);
-                if constexpr (St<MODE>::scaled) raw *= s;
-                cv.v[u][l] = raw;
-            }
-        }
-    }
-}
-
 // New values of one target cell from its source cells a (= i - sigma) and
-// b (= i - sigma - 1).
-template <int K, int MODE, int FT>
+// b (= i - sigma - 1).  With MEAN, fibre 0 of the group is the mean's fibre.
+template <int K, int MODE, int FT, bool MEAN>
 __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K, MODE, FT>& a,
-                                        const CellVals<K, MODE, FT>& b, int fbase, int nfib,
+                                        const CellVals<K, MODE, FT>& b,
                                         CellVals<K, MODE, FT>& out)
 {
     using R = typename St<MODE>::R;
     constexpr int O = K + 1;
 #pragma unroll
     for (int u = 0; u < FT; ++u) {
-        if (fbase + u >= nfib) break;
-        if (fbase + u == 0) {
+        if (MEAN && u == 0) {
             double d = a.m + M.alpha * (b.m - a.m);
 #pragma unroll
-            for (int l = 1; l < O; ++l) d += M.a0[l] * (double(a.v[u][l]) - double(b.v[u][l]));
+            for (int l = 1; l < O; ++l) d += M.a0[l] * (double(a.v[0][l]) - double(b.v[0][l]));
             out.m = d;
-            out.v[u][0] = 0;
+            out.v[0][0] = 0;
             const double dm = a.m - b.m;
 #pragma unroll
             for (int j = 1; j < O; ++j) {
                 R acc = R(M.aj0[j] * dm);
 #pragma unroll
                 for (int l = 1; l < O; ++l) {
-                    acc = fma(M.a[j][l], a.v[u][l], acc);
-                    acc = fma(M.b[j][l], b.v[u][l], acc);
+                    acc = fma(M.a[j][l], a.v[0][l], acc);
+                    acc = fma(M.b[j][l], b.v[0][l], acc);
                 }
-                out.v[u][j] = acc;
+                out.v[0][j] = acc;
             }
         } else {
 #pragma unroll
@@ -228,9 +208,119 @@ __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K
     }
 }
 
-template <int K, int MODE, int FT>
+// Base coefficient index of fibre f along a sweep whose fibre stride is
+// ostride = o^dim: the fibre holds J = jb + l * ostride, l = 0..k.
+__device__ __forceinline__ int fibre_base(int f, int O, int ostride)
+{
+    return (f / ostride) * (O * ostride) + (f % ostride);
+}
+
+// Fibre bases of a group, the missing fibres of a partial last group
+// repeating its last valid fibre.
+template <int FT>
+__device__ __forceinline__ void group_bases(int fbase, int nfib, int O, int ostride, int (&jb)[FT])
+{
+#pragma unroll
+    for (int u = 0; u < FT; ++u) {
+        int f = fbase + u;
+        if (f >= nfib) f = nfib - 1;
+        jb[u] = fibre_base(f, O, ostride);
+    }
+}
+
+// Per-thread pointers to the FT*(k+1) values of a group, offset by a base
+// cell; a cell at `off` cells from the base is p[u][l][off].
+template <int K, int MODE, int FT, bool MEAN>
+struct GroupPtrs {
+    using T = typename St<MODE>::T;
+    static constexpr int O = K + 1;
+    const T* s[FT][O];
+    T* d[FT][O];
+    const double* sm;
+    double* dm;
+
+    __device__ __forceinline__ void init(const Planes& src, const Planes& dst, int64_t pstride,
+                                         const int (&jb)[FT], int ostride, uint32_t base)
+    {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0) {
+                    sm = src.mean + base;
+                    dm = dst.mean + base;
+                    s[0][0] = nullptr;
+                    d[0][0] = nullptr;
+                } else {
+                    const int J = jb[u] + l * ostride;
+                    s[u][l] = plane_ptr<T>(src.hi, pstride, J) + base;
+                    d[u][l] = plane_ptr_w<T>(dst.hi, pstride, J) + base;
+                }
+            }
+    }
+
+    __device__ __forceinline__ void load(uint32_t off, CellVals<K, MODE, FT>& cv) const
+    {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0) {
+                    cv.m = __ldg(sm + off);
+                    cv.v[0][0] = 0;
+                } else {
+                    cv.v[u][l] = ld_raw(s[u][l] + off);
+                }
+            }
+    }
+
+    __device__ __forceinline__ void store(uint32_t off, const CellVals<K, MODE, FT>& cv) const
+    {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0)
+                    dm[off] = cv.m;
+                else
+                    st_raw(d[u][l] + off, cv.v[u][l]);
+            }
+    }
+};
+
+// Addresses formed per access (for the unit-stride kernel, whose threads
+// touch every value only two or three times, and for the scaled stores, whose
+// threads hold every fibre of a cell, too many values for a pointer table).
+// The scaled modes apply the cell's scale on load and the new scale (the
+// cell-wide maximum) on store.
+template <int K, int MODE, int FT, bool MEAN>
+__device__ __forceinline__ void load_cell(const Planes& p, int64_t pstride, uint32_t c,
+                                          const int (&jb)[FT], int ostride,
+                                          CellVals<K, MODE, FT>& cv)
+{
+    using T = typename St<MODE>::T;
+    constexpr int O = K + 1;
+    float s = 1.0f;
+    if constexpr (St<MODE>::scaled) s = __ldg(p.scale + c);
+#pragma unroll
+    for (int u = 0; u < FT; ++u)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            if (MEAN && u == 0 && l == 0) {
+                cv.m = __ldg(p.mean + c);
+                cv.v[0][0] = 0;
+            } else {
+                const int J = jb[u] + l * ostride;
+                auto v = ld_raw(plane_ptr<T>(p.hi, pstride, J) + c);
+                if constexpr (St<MODE>::scaled) v *= s;
+                cv.v[u][l] = v;
+            }
+        }
+}
+
+template <int K, int MODE, int FT, bool MEAN>
 __device__ __forceinline__ void store_cell(const Planes& p, int64_t pstride, uint32_t c,
-                                           const int (&jb)[FT], int ostride, int fbase, int nfib,
+                                           const int (&jb)[FT], int ostride,
                                            const CellVals<K, MODE, FT>& cv)
 {
     using T = typename St<MODE>::T;
@@ -238,33 +328,28 @@ __device__ __forceinline__ void store_cell(const Planes& p, int64_t pstride, uin
     constexpr int O = K + 1;
     R inv = R(1);
     if constexpr (St<MODE>::scaled) {
-        // one scale for the whole cell: the group holds every fibre
         float mx = 0.0f;
 #pragma unroll
-        for (int u = 0; u < FT; ++u) {
-            if (fbase + u >= nfib) break;
+        for (int u = 0; u < FT; ++u)
 #pragma unroll
             for (int l = 0; l < O; ++l) mx = fmaxf(mx, fabsf(cv.v[u][l]));
-        }
         float s;
         pow2_scale(mx, s, inv);
         p.scale[c] = s;
     }
 #pragma unroll
-    for (int u = 0; u < FT; ++u) {
-        if (fbase + u >= nfib) break;
+    for (int u = 0; u < FT; ++u)
 #pragma unroll
         for (int l = 0; l < O; ++l) {
-            const int J = jb[u] + l * ostride;
-            if (J == 0) {
+            if (MEAN && u == 0 && l == 0) {
                 p.mean[c] = cv.m;
             } else {
+                const int J = jb[u] + l * ostride;
                 R v = cv.v[u][l];
                 if constexpr (St<MODE>::scaled) v *= inv;
                 st_raw(plane_ptr_w<T>(p.hi, pstride, J) + c, v);
             }
         }
-    }
 }
 
 __device__ __forceinline__ uint32_t shift_class(const SweepArgs& a, uint32_t inner_idx,
@@ -277,13 +362,32 @@ __device__ __forceinline__ uint32_t shift_class(const SweepArgs& a, uint32_t inn
 
 // ---------------------------------------------------------------- unit stride
 
+template <int K, int MODE, int FT, bool MEAN>
+__device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32_t ca, uint32_t cb,
+                                          uint32_t cls, int fbase)
+{
+    constexpr int O = K + 1;
+    int jb[FT];
+    if constexpr (St<MODE>::scaled) {
+#pragma unroll
+        for (int u = 0; u < FT; ++u) jb[u] = u * O;   // fibre stride 1 along dimension 0
+    } else {
+        group_bases<FT>(fbase, a.nfib, O, 1, jb);
+    }
+    Mats<K, MODE> M;
+    M.template load<MEAN>(a.tab, cls);
+    CellVals<K, MODE, FT> va, vb, out;
+    load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, ca, jb, 1, va);
+    load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, cb, jb, 1, vb);
+    combine<K, MODE, FT, MEAN>(M, va, vb, out);
+    store_cell<K, MODE, FT, MEAN>(a.dst, a.pstride, c, jb, 1, out);
+}
+
 // Sweep along dimension 0: one thread per target cell (and fibre group
-// blockIdx.y).  For dimension 0 the fibre stride is 1, so the fibre with
-// index f holds coefficients f*o .. f*o + k.
+// blockIdx.y).
 template <int K, int MODE, int FT>
 __global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
 {
-    constexpr int O = K + 1;
     const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.cells) return;
     const int fbase = blockIdx.y * FT;
@@ -297,99 +401,126 @@ __global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
     ib += ib < 0 ? int32_t(a.N) : 0;
     const uint32_t ca = c - i + uint32_t(ia);
     const uint32_t cb = c - i + uint32_t(ib);
-
-    int jb[FT];
-#pragma unroll
-    for (int u = 0; u < FT; ++u) jb[u] = (fbase + u) * O;
-
-    Mats<K, MODE> M;
-    M.load(a.tab, cls, fbase == 0);
-    CellVals<K, MODE, FT> va, vb, out;
-    load_cell<K, MODE, FT>(a.src, a.pstride, ca, jb, 1, fbase, a.nfib, va);
-    load_cell<K, MODE, FT>(a.src, a.pstride, cb, jb, 1, fbase, a.nfib, vb);
-    combine<K, MODE, FT>(M, va, vb, fbase, a.nfib, out);
-    store_cell<K, MODE, FT>(a.dst, a.pstride, c, jb, 1, fbase, a.nfib, out);
+    if (St<MODE>::scaled || fbase == 0)
+        unit_body<K, MODE, FT, true>(a, c, ca, cb, cls, fbase);
+    else
+        unit_body<K, MODE, FT, false>(a, c, ca, cb, cls, fbase);
 }
 
 // ---------------------------------------------------------------- strided
 
-// Sweep along dimension m > 0: one thread per line (and fibre group and
-// chunk of the line, blockIdx.y = chunk * nfg + group).  The thread walks the
-// target cells i0 .. i1-1 of its chunk, U cells per step: it issues the loads
-// of the U new source cells first, then computes and stores the U targets.
-// The source cell i - sigma of one target is the source cell i - sigma - 1
-// of the next, so every source value is loaded once.
-template <int K, int MODE, int FT, int U>
-__global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
+struct LineSetup {
+    uint32_t base;    // cell at i = 0 of the line
+    uint32_t cls;
+    int32_t sig;
+    uint32_t i0, i1;  // target cells of this thread's chunk
+    int fbase;
+    bool active;
+};
+
+__device__ __forceinline__ LineSetup line_setup(const SweepArgs& a, int FT)
 {
-    constexpr int O = K + 1;
+    LineSetup L{};
     const uint32_t line = blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= a.lines) return;
+    L.active = false;
+    if (line >= a.lines) return L;
     const uint32_t grp = blockIdx.y % uint32_t(a.nfg);
     const uint32_t chunk = blockIdx.y / uint32_t(a.nfg);
-    const int fbase = int(grp) * FT;
+    L.fbase = int(grp) * FT;
     const uint32_t outer = a.fdInner.div(line);
     const uint32_t inn = line - outer * a.inner;
-    const uint32_t base = outer * a.N * a.inner + inn;
-    const uint32_t cls = shift_class(a, inn, outer);
-    const int32_t sig = __ldg(a.tab.sigma + cls);
-    const uint32_t i0 = chunk * a.chunk;
-    uint32_t i1 = i0 + a.chunk;
-    if (i1 > a.N) i1 = a.N;
-    if (i0 >= i1) return;
+    L.base = outer * a.N * a.inner + inn;
+    L.cls = shift_class(a, inn, outer);
+    L.sig = __ldg(a.tab.sigma + L.cls);
+    L.i0 = chunk * a.chunk;
+    L.i1 = L.i0 + a.chunk;
+    if (L.i1 > a.N) L.i1 = a.N;
+    L.active = L.i0 < L.i1;
+    return L;
+}
 
+template <int K, int MODE, int FT, int U, bool MEAN>
+__device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup& L)
+{
+    constexpr int O = K + 1;
+    constexpr bool SC = St<MODE>::scaled;
     int jb[FT];
+    if constexpr (SC) {
 #pragma unroll
-    for (int u = 0; u < FT; ++u) {
-        const int f = fbase + u;
-        jb[u] = (f / a.ostride) * (O * a.ostride) + (f % a.ostride);
+        for (int u = 0; u < FT; ++u) jb[u] = fibre_base(u, O, a.ostride);
+    } else {
+        group_bases<FT>(L.fbase, a.nfib, O, a.ostride, jb);
     }
-
     Mats<K, MODE> M;
-    M.load(a.tab, cls, fbase == 0);
-    int32_t ia = int32_t(i0) - sig;
-    ia += ia < 0 ? int32_t(a.N) : 0;
-    int32_t ib = ia - 1;
-    ib += ib < 0 ? int32_t(a.N) : 0;
+    M.template load<MEAN>(a.tab, L.cls);
     const int32_t N = int32_t(a.N);
+    int32_t ia = int32_t(L.i0) - L.sig;
+    ia += ia < 0 ? N : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? N : 0;
+
+    GroupPtrs<K, MODE, FT, MEAN> P;
+    if constexpr (!SC) P.init(a.src, a.dst, a.pstride, jb, a.ostride, L.base);
+    auto load_row = [&](int32_t row, CellVals<K, MODE, FT>& cv) {
+        if constexpr (SC)
+            load_cell<K, MODE, FT, true>(a.src, a.pstride, L.base + uint32_t(row) * a.inner, jb,
+                                         a.ostride, cv);
+        else
+            P.load(uint32_t(row) * a.inner, cv);
+    };
+    auto store_row = [&](uint32_t i, const CellVals<K, MODE, FT>& cv) {
+        if constexpr (SC)
+            store_cell<K, MODE, FT, true>(a.dst, a.pstride, L.base + i * a.inner, jb, a.ostride, cv);
+        else
+            P.store(i * a.inner, cv);
+    };
 
     CellVals<K, MODE, FT> prev;
-    load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(ib) * a.inner, jb, a.ostride, fbase,
-                           a.nfib, prev);
-    uint32_t i = i0;
+    load_row(ib, prev);
+    uint32_t i = L.i0;
     if constexpr (U > 1) {
-        for (; i + U <= i1; i += U) {
+        for (; i + U <= L.i1; i += U) {
             CellVals<K, MODE, FT> cur[U];
 #pragma unroll
             for (int s = 0; s < U; ++s) {
                 int32_t x = ia + s;
                 x -= x >= N ? N : 0;
-                load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(x) * a.inner, jb,
-                                       a.ostride, fbase, a.nfib, cur[s]);
+                load_row(x, cur[s]);
             }
 #pragma unroll
             for (int s = 0; s < U; ++s) {
                 CellVals<K, MODE, FT> out;
-                combine<K, MODE, FT>(M, cur[s], s == 0 ? prev : cur[s - 1], fbase, a.nfib, out);
-                store_cell<K, MODE, FT>(a.dst, a.pstride, base + (i + s) * a.inner, jb, a.ostride,
-                                        fbase, a.nfib, out);
+                combine<K, MODE, FT, MEAN>(M, cur[s], s == 0 ? prev : cur[s - 1], out);
+                store_row(i + s, out);
             }
             prev = cur[U - 1];
             ia += U;
             ia -= ia >= N ? N : 0;
         }
     }
-    for (; i < i1; ++i) {
+    for (; i < L.i1; ++i) {
         CellVals<K, MODE, FT> cur, out;
-        load_cell<K, MODE, FT>(a.src, a.pstride, base + uint32_t(ia) * a.inner, jb, a.ostride,
-                               fbase, a.nfib, cur);
-        combine<K, MODE, FT>(M, cur, prev, fbase, a.nfib, out);
-        store_cell<K, MODE, FT>(a.dst, a.pstride, base + i * a.inner, jb, a.ostride, fbase, a.nfib,
-                                out);
+        load_row(ia, cur);
+        combine<K, MODE, FT, MEAN>(M, cur, prev, out);
+        store_row(i, out);
         prev = cur;
         ++ia;
         if (ia == N) ia = 0;
     }
+}
+
+// Sweep along dimension m > 0: one thread per line (and fibre group and
+// chunk of the line, blockIdx.y = chunk * nfg + group), walking the target
+// cells of its chunk U cells per step with the loads of a step issued first.
+template <int K, int MODE, int FT, int U>
+__global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
+{
+    const LineSetup L = line_setup(a, FT);
+    if (!L.active) return;
+    if (St<MODE>::scaled || L.fbase == 0)
+        strided_body<K, MODE, FT, U, true>(a, L);
+    else
+        strided_body<K, MODE, FT, U, false>(a, L);
 }
 
 // ---------------------------------------------------------------- strided, cp.async ring
@@ -410,11 +541,99 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Dynamic shared memory of k_sweep_strided_async for `block` threads.
-template <int K, int MODE, int FT, int P>
-constexpr size_t strided_async_smem(int block)
+// Dynamic shared memory of k_sweep_strided_async with B threads per block:
+// P+1 row slots, each with one FP64 mean word and FT*(k+1) values per thread.
+template <int K, int MODE, int FT, int P, int B>
+constexpr size_t strided_async_smem()
 {
-    return size_t(P + 1) * size_t(block) * (8 + size_t(FT) * (K + 1) * sizeof(typename St<MODE>::T));
+    return size_t(P + 1) * size_t(B) * (8 + size_t(FT) * (K + 1) * sizeof(typename St<MODE>::T));
+}
+
+template <int K, int MODE, int FT, int P, int B, bool MEAN>
+__device__ __forceinline__ void async_body(const SweepArgs& a, const LineSetup& L)
+{
+    using T = typename St<MODE>::T;
+    constexpr int O = K + 1;
+    constexpr int S = P + 1;
+    constexpr int V = FT * O;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t tid = threadIdx.x;
+    // [slot][B] means, then [slot][V][B] values: every offset below is a
+    // compile-time constant from the thread's own column
+    double* sm_mean = reinterpret_cast<double*>(smem_raw) + tid;
+    T* sm_val = reinterpret_cast<T*>(smem_raw + size_t(S) * B * 8) + tid;
+
+    int jb[FT];
+    group_bases<FT>(L.fbase, a.nfib, O, a.ostride, jb);
+    Mats<K, MODE> M;
+    M.template load<MEAN>(a.tab, L.cls);
+    GroupPtrs<K, MODE, FT, MEAN> G;
+    G.init(a.src, a.dst, a.pstride, jb, a.ostride, L.base);
+
+    const int32_t N = int32_t(a.N);
+    // rows in consumption order: row 0 is source cell i0-sigma-1, row q >= 1
+    // the source cell i0+q-1-sigma of target i0+q-1; all periodic in N
+    const int nrows = int(L.i1 - L.i0) + 1;
+    int32_t frow = int32_t(L.i0) - L.sig - 1;
+    frow += frow < 0 ? N : 0;
+    frow += frow < 0 ? N : 0;
+
+    auto fetch = [&](int slot, uint32_t off) {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0)
+                    cp_async<8>(sm_mean + slot * B, G.sm + off);
+                else
+                    cp_async<sizeof(T)>(sm_val + (slot * V + u * O + l) * B, G.s[u][l] + off);
+            }
+    };
+    auto read = [&](int slot, CellVals<K, MODE, FT>& cv) {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0) {
+                    cv.m = sm_mean[slot * B];
+                    cv.v[0][0] = 0;
+                } else {
+                    cv.v[u][l] = sm_val[(slot * V + u * O + l) * B];
+                }
+            }
+    };
+
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        if (q < nrows) {
+            fetch(q, uint32_t(frow) * a.inner);
+            ++frow;
+            frow -= frow >= N ? N : 0;
+        }
+        cp_async_commit();
+    }
+    CellVals<K, MODE, FT> prev, cur;
+    int slot = 0;    // slot of row q
+    int rslot = P;   // slot that row q + P goes to (= slot of row q - 1)
+    for (int q = 0; q < nrows; ++q) {
+        cp_async_wait<P - 1>();
+        read(slot, cur);
+        if (q + P < nrows) {
+            fetch(rslot, uint32_t(frow) * a.inner);
+            ++frow;
+            frow -= frow >= N ? N : 0;
+        }
+        cp_async_commit();
+        if (q > 0) {
+            CellVals<K, MODE, FT> out;
+            combine<K, MODE, FT, MEAN>(M, cur, prev, out);
+            G.store((L.i0 + uint32_t(q) - 1) * a.inner, out);
+        }
+        prev = cur;
+        rslot = slot;
+        slot = slot + 1 == S ? 0 : slot + 1;
+    }
+    cp_async_wait<0>();
 }
 
 // Same walk as k_sweep_strided, but the source rows are fetched P rows ahead
@@ -422,117 +641,18 @@ constexpr size_t strided_async_smem(int block)
 // every thread keeps P rows of loads in flight while it computes.  A thread
 // only reads slots it filled itself (cp.async.wait_group makes them visible
 // to the issuing thread), so no block barrier is needed; a slot is refilled
-// one iteration after it was read and its values were used.
-template <int K, int MODE, int FT, int P>
-__global__ void __launch_bounds__(128) k_sweep_strided_async(const SweepArgs a)
+// one iteration after it was read and its values were used.  B threads per
+// block.
+template <int K, int MODE, int FT, int P, int B>
+__global__ void __launch_bounds__(B) k_sweep_strided_async(const SweepArgs a)
 {
     static_assert(!St<MODE>::scaled, "cp.async ring needs 4- or 8-byte elements");
-    using T = typename St<MODE>::T;
-    constexpr int O = K + 1;
-    constexpr int S = P + 1;
-    constexpr int V = FT * O;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t nthr = blockDim.x;
-    const uint32_t tid = threadIdx.x;
-    double* sm_mean = reinterpret_cast<double*>(smem_raw);
-    T* sm_val = reinterpret_cast<T*>(smem_raw + size_t(S) * nthr * 8);
-
-    const uint32_t line = blockIdx.x * blockDim.x + tid;
-    if (line >= a.lines) return;
-    const uint32_t grp = blockIdx.y % uint32_t(a.nfg);
-    const uint32_t chunk = blockIdx.y / uint32_t(a.nfg);
-    const int fbase = int(grp) * FT;
-    const uint32_t outer = a.fdInner.div(line);
-    const uint32_t inn = line - outer * a.inner;
-    const uint32_t base = outer * a.N * a.inner + inn;
-    const uint32_t cls = shift_class(a, inn, outer);
-    const int32_t sig = __ldg(a.tab.sigma + cls);
-    const uint32_t i0 = chunk * a.chunk;
-    uint32_t i1 = i0 + a.chunk;
-    if (i1 > a.N) i1 = a.N;
-    if (i0 >= i1) return;
-    const int32_t N = int32_t(a.N);
-
-    int jb[FT];
-#pragma unroll
-    for (int u = 0; u < FT; ++u) {
-        const int f = fbase + u;
-        jb[u] = (f / a.ostride) * (O * a.ostride) + (f % a.ostride);
-    }
-    Mats<K, MODE> M;
-    M.load(a.tab, cls, fbase == 0);
-
-    // rows in consumption order: row 0 is source cell i0-sigma-1, row q >= 1
-    // the source cell i0+q-1-sigma of target i0+q-1; all periodic in N
-    const int nrows = int(i1 - i0) + 1;
-    int32_t frow = int32_t(i0) - sig - 1;
-    frow += frow < 0 ? N : 0;
-    frow += frow < 0 ? N : 0;
-
-    auto fetch = [&](int slot, uint32_t cell) {
-#pragma unroll
-        for (int u = 0; u < FT; ++u) {
-            if (fbase + u >= a.nfib) break;
-#pragma unroll
-            for (int l = 0; l < O; ++l) {
-                const int J = jb[u] + l * a.ostride;
-                if (J == 0)
-                    cp_async<8>(sm_mean + size_t(slot) * nthr + tid, a.src.mean + cell);
-                else
-                    cp_async<sizeof(T)>(sm_val + (size_t(slot) * V + u * O + l) * nthr + tid,
-                                        plane_ptr<T>(a.src.hi, a.pstride, J) + cell);
-            }
-        }
-    };
-    auto read = [&](int slot, CellVals<K, MODE, FT>& cv) {
-#pragma unroll
-        for (int u = 0; u < FT; ++u) {
-            if (fbase + u >= a.nfib) break;
-#pragma unroll
-            for (int l = 0; l < O; ++l) {
-                const int J = jb[u] + l * a.ostride;
-                if (J == 0) {
-                    cv.m = sm_mean[size_t(slot) * nthr + tid];
-                    cv.v[u][0] = 0;
-                } else {
-                    cv.v[u][l] = sm_val[(size_t(slot) * V + u * O + l) * nthr + tid];
-                }
-            }
-        }
-    };
-
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        if (q < nrows) {
-            fetch(q, base + uint32_t(frow) * a.inner);
-            ++frow;
-            frow -= frow >= N ? N : 0;
-        }
-        cp_async_commit();
-    }
-    CellVals<K, MODE, FT> prev, cur;
-    int slot = 0;           // slot of row q
-    int rslot = P;          // slot that row q + P goes to (= slot of row q - 1)
-    for (int q = 0; q < nrows; ++q) {
-        cp_async_wait<P - 1>();
-        read(slot, cur);
-        if (q + P < nrows) {
-            fetch(rslot, base + uint32_t(frow) * a.inner);
-            ++frow;
-            frow -= frow >= N ? N : 0;
-        }
-        cp_async_commit();
-        if (q > 0) {
-            CellVals<K, MODE, FT> out;
-            combine<K, MODE, FT>(M, cur, prev, fbase, a.nfib, out);
-            store_cell<K, MODE, FT>(a.dst, a.pstride, base + (i0 + uint32_t(q) - 1) * a.inner, jb,
-                                    a.ostride, fbase, a.nfib, out);
-        }
-        prev = cur;
-        rslot = slot;
-        slot = slot + 1 == S ? 0 : slot + 1;
-    }
-    cp_async_wait<0>();
+    const LineSetup L = line_setup(a, FT);
+    if (!L.active) return;
+    if (L.fbase == 0)
+        async_body<K, MODE, FT, P, B, true>(a, L);
+    else
+        async_body<K, MODE, FT, P, B, false>(a, L);
 }
 
 }  // namespace sl

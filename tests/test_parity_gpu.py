@@ -381,16 +381,22 @@ def test_every_launch_shape_gives_identical_results(storage, n, k):
             else:
                 assert O.rel_l2(ref_gpu, ref, k, len(n)) <= 1e-6
             shapes = []
+            nfib = (k + 1) ** (len(n) - 1)
             if dim == 0:
-                shapes = [dict(block=b, fibres_per_thread=f) for f in UNIT_FT for b in (64, 256)]
+                shapes = [dict(block=b, fibres_per_thread=f) for f in UNIT_FT if f <= nfib
+                          for b in (64, 256)]
             else:
                 for f, un in STRIDED_SHAPES:
+                    if f > nfib:
+                        continue
                     for ch in (1, 3, n[dim]):
                         shapes.append(dict(block=128, fibres_per_thread=f, unroll=un, chunk=ch))
                 shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=2))
                 for f, pl in ASYNC_SHAPES:
+                    if f > nfib:
+                        continue
                     for ch in (1, 2, n[dim]):
-                        for b in (32, 128):
+                        for b in (64, 128):
                             shapes.append(dict(block=b, fibres_per_thread=f, pipeline=pl, chunk=ch))
             for sh in shapes:
                 ctx.set_tune(dim, **sh)
@@ -435,7 +441,8 @@ def test_set_tune_rejects_shapes_not_built():
                         (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=0)),
                         (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=9)),
                         (1, dict(block=128, fibres_per_thread=3, pipeline=8, chunk=8)),
-                        (0, dict(block=128, fibres_per_thread=1, pipeline=4))]:
+                        (0, dict(block=128, fibres_per_thread=1, pipeline=4)),
+                        (1, dict(block=32, fibres_per_thread=1, pipeline=4, chunk=8))]:
             with pytest.raises(S.SlError) as e:
                 ctx.set_tune(dim, **sh)
             assert e.value.status == S.SL_EINVAL
