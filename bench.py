@@ -33,6 +33,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -48,8 +50,11 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=64, help="cells per dimension of the 4D workload")
-    ap.add_argument("--storage", default="mix_fp32")
+    ap.add_argument("--workload", default="4d", choices=["4d", "2d", "batch", "6d", "1d"],
+                    help="4d: 64^4 k=2 (default); 2d: 512^2 k=2; batch: 256 uneven 2D problems; "
+                         "6d: 20^6 k=1; 1d: N=1024 k=2")
+    ap.add_argument("--n", type=int, default=None, help="cells per dimension (4d/2d/6d)")
+    ap.add_argument("--storage", default=None, help="store of the timed arm (default per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -211,22 +216,71 @@ def apply_shapes(ctx, shapes):
         ctx.set_tune(d, **sh)
 
 
-def gpu_steps(S, W, p, storage, stream, steps, warmup, profile, shapes=None):
-    import torch
-    ctx = S.Context(p.grid, p.k, storage, stream=stream)
-    ctx.project(p.nq, p.weights, p.params)
-    ctx.set_fields(p.field_list())
-    apply_shapes(ctx, shapes if storage == p.storage else None)
-    m0 = ctx.mass()
-    for _ in range(warmup):
-        ctx.step("strang", p.dt, 1)
-    ctx.synchronize()
-    if profile:
-        ctx.profile_query()      # reset counters
-        ctx.profile_enable(True)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    return ctx, m0, e0, e1
+DEFAULT_STORE = {"4d": "mix_fp32", "2d": "mix_fp32", "batch": "mix_fp32", "6d": "mix_bf16",
+                 "1d": "fp64"}
+DEFAULT_N = {"4d": 64, "2d": 512, "6d": 20, "1d": 1024}
+
+
+def make_problem(W, workload, n, storage):
+    if workload == "4d":
+        return W.config3(n=n, steps=1, storage=storage)
+    if workload == "2d":
+        return W.config2(n=n, steps=1, storage=storage)
+    if workload == "6d":
+        return W.config5(n=n, steps=1, storage=storage)
+    if workload == "1d":
+        return W.config1()
+    return W.config4(storage=storage)
+
+
+class Arm:
+    """One store of one workload behind the library's public API: a context,
+    or a batch for the batched workload."""
+
+    def __init__(self, S, W, args, storage, stream, shapes=None):
+        self.workload = args.workload
+        self.p = make_problem(W, args.workload, args.n, storage)
+        if self.workload == "batch":
+            probs = self.p
+            self.obj = S.Batch([q.grid for q in probs], [q.k for q in probs], storage, stream=stream)
+            for i, q in enumerate(probs):
+                self.obj.project(i, q.nq, q.weights, q.params)
+            self.obj.set_fields([q.field_list()[0] for q in probs])
+            self.obj.autotune(3)
+            self.dof = self.obj.info["dof"]
+            self.state_bytes = self.obj.info["state_bytes"]
+            self.sweeps = 3
+            self.dt = probs[0].dt
+        else:
+            p = self.p
+            self.obj = S.Context(p.grid, p.k, storage, stream=stream)
+            self.obj.project(p.nq, p.weights, p.params)
+            if p.splitting != "advect":
+                self.obj.set_fields(p.field_list())
+            apply_shapes(self.obj, shapes)
+            self.dof = p.dof
+            self.state_bytes = self.obj.info["state_bytes"]
+            self.sweeps = 1 if p.splitting == "advect" else 2 * len(p.grid.x_dims()) + len(p.grid.v_dims())
+            self.dt = p.dt
+            if p.splitting == "advect":
+                h = (p.grid.hi[0] - p.grid.lo[0]) / p.grid.n[0]
+                self.shift = p.velocity * p.dt / h
+
+    def step(self, n):
+        if self.workload == "1d":
+            for _ in range(n):
+                self.obj.advect(0, -1, [self.shift])
+        else:
+            self.obj.step("strang", self.dt, n)
+
+    def mass_total(self):
+        m = self.obj.mass()
+        return float(np.sum(m)) if self.workload == "batch" else m
+
+    def tunes(self):
+        if self.workload == "batch":
+            return None
+        return [self.obj.get_tune(d) for d in range(self.p.grid.ndim)]
 
 
 def run_ours(args):
@@ -243,41 +297,47 @@ def run_ours(args):
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.Stream(device=dev)
-    p = W.config3(n=args.n, steps=args.steps, storage=args.storage)
-    sweeps_per_step = 2 * len(p.grid.x_dims()) + len(p.grid.v_dims())
-    dof = p.dof
+    args.storage = args.storage or DEFAULT_STORE[args.workload]
+    args.n = args.n or DEFAULT_N.get(args.workload)
     peaks, peak_src = measured_peaks()
 
-    def timed(storage, profile):
-        ctx, m0, e0, e1 = gpu_steps(S, W, p, storage, stream, args.steps, args.warmup, profile,
-                                    args.shapes)
+    def timed(storage, shapes):
+        arm = Arm(S, W, args, storage, stream, shapes)
+        m0 = arm.mass_total()
+        for _ in range(args.warmup):
+            arm.step(1)
+        arm.obj.synchronize()
+        arm.obj.profile_query()
+        arm.obj.profile_enable(True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         barrier(world)
         clocks = ClockSampler(torch.cuda.current_device())
         clocks.start()
-        with torch.cuda.stream(stream):
-            torch.cuda.synchronize()
-            e0.record(stream)
-            ctx.step("strang", p.dt, args.steps)
-            e1.record(stream)
-            torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        arm.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
         clk = clocks.stop()
         ms = e0.elapsed_time(e1)
-        prof = ctx.profile_query() if profile else None
-        dims = ctx.profile_dims() if profile else None
-        ctx.profile_enable(False)
-        m1 = ctx.mass()
-        info = dict(ctx.info)
-        info["tune"] = [ctx.get_tune(d) for d in range(p.grid.ndim)]
+        prof = arm.obj.profile_query()
+        dims = arm.obj.profile_dims() if hasattr(arm.obj, "profile_dims") else None
+        arm.obj.profile_enable(False)
+        m1 = arm.mass_total()
+        info = {"state_bytes": arm.state_bytes, "dof": arm.dof, "sweeps": arm.sweeps,
+                "tune": arm.tunes()}
         if dims:
             nd, msd = dims
             info["per_dim"] = [{"dim": d, "launches": nd[d], "ms_per_launch": msd[d] / max(nd[d], 1),
-                                "gbs": 2.0 * info["state_bytes"] / (msd[d] / max(nd[d], 1) / 1e3) / 1e9
-                                if nd[d] else None} for d in range(p.grid.ndim)]
-        ctx.close()
+                                "gbs": 2.0 * arm.state_bytes / (msd[d] / max(nd[d], 1) / 1e3) / 1e9
+                                if nd[d] else None} for d in range(len(nd)) if nd[d]]
+        arm.obj.close()
         return ms, prof, abs(m1 - m0) / abs(m0), clk, info
 
-    ms, prof, drift, clk, info = timed(args.storage, True)
-    ms_max, units = aggregate(ms, float(args.steps * sweeps_per_step * dof), world, dev)
+    ms, prof, drift, clk, info = timed(args.storage, args.shapes)
+    units_local = float(args.steps * info["sweeps"] * info["dof"])
+    ms_max, units = aggregate(ms, units_local, world, dev)
     value = units / (ms_max / 1000.0)
     nl, sweep_ms, sweep_bytes = prof
     avg_sweep_ms = sweep_ms / max(nl, 1)
@@ -286,9 +346,9 @@ def run_ours(args):
     peak_gbs = float(peaks["hbm_gbs"])
 
     fp64 = None
-    if not args.no_fp64:
-        ms64, prof64, drift64, clk64, info64 = timed("fp64", True)
-        ms64_max, units64 = aggregate(ms64, float(args.steps * sweeps_per_step * dof), world, dev)
+    if not args.no_fp64 and args.storage != "fp64":
+        ms64, prof64, drift64, clk64, info64 = timed("fp64", None)
+        ms64_max, units64 = aggregate(ms64, units_local, world, dev)
         v64 = units64 / (ms64_max / 1000.0)
         nl64, sms64, sb64 = prof64
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64_max / args.steps,
@@ -298,26 +358,35 @@ def run_ours(args):
                 "per_dim": info64.get("per_dim")}
 
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.workload == "4d":
+        p = make_problem(W, "4d", args.n, args.storage)
         e2e = run_e2e(S, W, p, args, stream, world, dev)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu and args.workload == "4d":
         rate, secs, ndof, _ = time_oracle(64, 16, 2)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"2 Strang steps (6 sweeps each, {ndof:.3g} DoF updates, {secs:.1f} s) of "
                          "the 4D k=2 workload on a 64x64x16x16 sub-grid, FP64 oracle, one thread"}
 
     if rank == 0:
+        wl = {"4d": f"4d_xxvv_{args.n}^4_k2_{args.storage}_strang",
+              "2d": f"2d_xv_{args.n}^2_k2_{args.storage}_strang",
+              "6d": f"6d_xxxvvv_{args.n}^6_k1_{args.storage}_strang",
+              "1d": f"1d_n{args.n}_k2_{args.storage}_advect",
+              "batch": f"batch256_2d_xv_k1k2_{args.storage}_strang"}[args.workload]
+        l2note = (f"state {info['state_bytes'] / 1e9:.2f} GB > L2; no flush needed"
+                  if info["state_bytes"] > 4 * L2_BYTES else
+                  f"state {info['state_bytes'] / 1e6:.1f} MB fits in L2: GB/s is not an HBM figure")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.storage == "mix_fp32" else args.storage,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"mix_fp32": "f32+f64", "fp64": "f64", "mix_bf16": "bf16+f64",
+                      "mix_fp16": "f16+f64"}[args.storage],
             "data": "synthetic",
-            "config": {"workload": f"4d_xxvv_{args.n}^4_k2_{args.storage}_strang",
-                       "cells": p.grid.cells, "coef_per_cell": p.ncoef, "dof": dof,
-                       "sweeps_per_step": sweeps_per_step, "state_bytes": info["state_bytes"],
-                       "l2": f"state {info['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
+            "config": {"workload": wl, "dof": info["dof"], "sweeps_per_step": info["sweeps"],
+                       "state_bytes": info["state_bytes"], "l2": l2note,
                        "parallelism": f"replicas x{world}", "tune": info["tune"]},
             "mass_drift": drift,
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
@@ -328,7 +397,7 @@ def run_ours(args):
             "fp64": fp64,
             "speedup_mixed_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "e2e": e2e,
-            "gpu_launches": args.steps * sweeps_per_step * 2,
+            "gpu_launches": args.steps * info["sweeps"] * 2,
             "clocks": clk,
             "cpu_baseline": cpu,
         }

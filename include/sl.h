@@ -258,6 +258,51 @@ sl_status sl_graph_launch(sl_ctx* ctx);
 /* Wait for all work of the context's stream. */
 sl_status sl_synchronize(sl_ctx* ctx);
 
+/* ---------------------------------------------------------------- batches */
+
+/* Many independent problems advanced together (the sweeps are independent
+ * per problem, Sec. II-A; nothing is exchanged between problems).  Every
+ * split substep is one table launch over all problems and one persistent
+ * sweep launch over a work list of equal-sized tiles of all problems, so
+ * problems of very different sizes share the GPU evenly.
+ * All problems must have the same ndim and the same pair[] (the same split
+ * structure); extents, box and degree may differ.  Degrees 0..2; stores
+ * SL_FP64 and SL_MIX_FP32 (SL_ENOTSUP otherwise).  The batch owns one
+ * single-problem state per problem; every call below except the per-problem
+ * set/get/project is one launch (or one synchronisation) for the whole batch.
+ * Errors as for the single-problem calls; sl_batch_last_error gives the
+ * message (sl_last_error(NULL) for a failed sl_batch_create). */
+typedef struct sl_batch sl_batch;
+
+sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, sl_storage storage,
+                          void* cuda_stream, sl_batch** out);
+void sl_batch_destroy(sl_batch* batch);
+const char* sl_batch_last_error(const sl_batch* batch);
+/* Totals over all problems: cells, degrees of freedom, bytes of one state. */
+sl_status sl_batch_info(const sl_batch* batch, int64_t* cells, int64_t* dof, int64_t* state_bytes);
+/* Per-problem data, as sl_project / sl_set_coeffs / sl_get_coeffs. */
+sl_status sl_batch_project(sl_batch* batch, int prob, int nq, int nterms, const double* weights,
+                           const double* params);
+sl_status sl_batch_set_coeffs(sl_batch* batch, int prob, const double* host_aos);
+sl_status sl_batch_get_coeffs(sl_batch* batch, int prob, double* host_aos);
+/* Fields of every problem, concatenated in problem order (each as for
+ * sl_set_fields). */
+sl_status sl_batch_set_fields(sl_batch* batch, const double* fields, int64_t count);
+/* nsteps Lie or Strang steps of size dt for every problem (as sl_step). */
+sl_status sl_batch_step(sl_batch* batch, sl_splitting splitting, double dt, int nsteps);
+/* Mass of every problem into out[nprob]; synchronises. */
+sl_status sl_batch_mass(sl_batch* batch, double* out);
+sl_status sl_batch_graph_capture(sl_batch* batch, sl_splitting splitting, double dt, int nsteps);
+sl_status sl_batch_graph_launch(sl_batch* batch);
+sl_status sl_batch_synchronize(sl_batch* batch);
+/* Time the provided work-list shapes (fibres per thread, cells per walk step,
+ * chunks per line) for every dimension and keep the fastest. */
+sl_status sl_batch_autotune(sl_batch* batch, int reps);
+/* As sl_profile_enable / sl_profile_query, over the batched sweep launches;
+ * bytes = 2 x (sum of the problems' state bytes) per launch. */
+sl_status sl_batch_profile_enable(sl_batch* batch, int enable);
+sl_status sl_batch_profile_query(sl_batch* batch, int64_t* launches, double* ms, double* bytes);
+
 /* ---------------------------------------------------------------- launch shapes */
 
 /* Launch shape of the sweep kernel along one dimension.
@@ -266,8 +311,12 @@ sl_status sl_synchronize(sl_ctx* ctx);
  *   fibres_per_thread  coefficient fibres one thread updates: 1, 2, 3, 4 or 9
  *                      along dimension 0; 1, 2 or 3 otherwise.  The scaled
  *                      stores always give a thread every fibre of its cell.
- *   unroll             cells per walk step along dimensions > 0: 1, 2 or 4
- *                      (4 only with 1 or 2 fibres per thread)
+ *   unroll             along dimensions > 0: cells per walk step, 1, 2 or 4
+ *                      (4 only with 1 or 2 fibres per thread); along
+ *                      dimension 0: cells per thread, 1, or 16 / element size
+ *                      (4 for FP32, 2 for FP64) for the 16-byte vector form,
+ *                      which needs n_0 divisible by it and 1..4 fibres per
+ *                      thread (FP64 and FP32 stores)
  *   chunk              cells one thread walks along dimensions > 0 (1..n_dim)
  *   pipeline           0: the walk keeps the previous cell in registers;
  *                      4 or 8: the walk streams its source rows through a

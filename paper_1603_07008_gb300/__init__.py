@@ -26,7 +26,11 @@ __all__ = [
     "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
     "sl_set_fields", "sl_step", "sl_mass", "sl_graph_capture", "sl_graph_launch",
     "sl_synchronize", "sl_profile_enable", "sl_profile_query", "sl_mass_noalloc",
-    "sl_get_tune", "sl_set_tune", "sl_autotune", "sl_profile_dims",
+    "sl_get_tune", "sl_set_tune", "sl_autotune", "sl_profile_dims", "Batch",
+    "sl_batch_create", "sl_batch_destroy", "sl_batch_last_error", "sl_batch_info", "sl_batch_project",
+    "sl_batch_set_coeffs", "sl_batch_get_coeffs", "sl_batch_set_fields", "sl_batch_step",
+    "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
+    "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -128,6 +132,23 @@ def lib():
             "sl_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_autotune": (st, [_vp, ctypes.c_int]),
+            "sl_batch_create": (st, [ctypes.c_int, ctypes.POINTER(sl_grid), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.c_int, _vp, ctypes.POINTER(_vp)]),
+            "sl_batch_destroy": (None, [_vp]),
+            "sl_batch_last_error": (ctypes.c_char_p, [_vp]),
+            "sl_batch_info": (st, [_vp, _i64p, _i64p, _i64p]),
+            "sl_batch_project": (st, [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp]),
+            "sl_batch_set_coeffs": (st, [_vp, ctypes.c_int, _dp]),
+            "sl_batch_get_coeffs": (st, [_vp, ctypes.c_int, _dp]),
+            "sl_batch_set_fields": (st, [_vp, _dp, ctypes.c_int64]),
+            "sl_batch_step": (st, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+            "sl_batch_mass": (st, [_vp, _dp]),
+            "sl_batch_graph_capture": (st, [_vp, ctypes.c_int, ctypes.c_double, ctypes.c_int]),
+            "sl_batch_graph_launch": (st, [_vp]),
+            "sl_batch_synchronize": (st, [_vp]),
+            "sl_batch_autotune": (st, [_vp, ctypes.c_int]),
+            "sl_batch_profile_enable": (st, [_vp, ctypes.c_int]),
+            "sl_batch_profile_query": (st, [_vp, _i64p, _dp, _dp]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
@@ -426,3 +447,162 @@ class Context:
 
     def profile_dims(self):
         return sl_profile_dims(self.handle)
+
+
+# ---------------------------------------------------------------------------
+# batches
+
+
+def _bcheck(status: int, b):
+    if status != SL_OK:
+        r = lib().sl_batch_last_error(b)
+        raise SlError(status, r.decode() if r else "")
+
+
+def sl_batch_create(grids, degrees, storage, stream=None):
+    n = len(grids)
+    arr = (sl_grid * n)(*[make_grid(g) for g in grids])
+    deg = (ctypes.c_int * n)(*[int(d) for d in degrees])
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    out = _vp()
+    _check(lib().sl_batch_create(n, arr, deg, st, _stream_handle(stream), ctypes.byref(out)))
+    return out
+
+
+def sl_batch_destroy(b):
+    if b:
+        lib().sl_batch_destroy(b)
+
+
+def sl_batch_last_error(b=None) -> str:
+    r = lib().sl_batch_last_error(b)
+    return r.decode() if r else ""
+
+
+def sl_batch_info(b):
+    c, d, s = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _bcheck(lib().sl_batch_info(b, ctypes.byref(c), ctypes.byref(d), ctypes.byref(s)), b)
+    return {"cells": c.value, "dof": d.value, "state_bytes": s.value}
+
+
+def sl_batch_project(b, prob, nq, weights, params):
+    w = _f64(weights)
+    p = _f64(params)
+    _bcheck(lib().sl_batch_project(b, int(prob), int(nq), int(w.size), _ptr(w), _ptr(p)), b)
+
+
+def sl_batch_set_coeffs(b, prob, u):
+    u_ = _f64(u)
+    _bcheck(lib().sl_batch_set_coeffs(b, int(prob), _ptr(u_)), b)
+
+
+def sl_batch_get_coeffs(b, prob, cells, ncoef):
+    out = np.empty((cells, ncoef))
+    _bcheck(lib().sl_batch_get_coeffs(b, int(prob), _ptr(out)), b)
+    return out
+
+
+def sl_batch_set_fields(b, fields):
+    f = _f64(np.concatenate([np.ravel(x) for x in fields])) if len(fields) else np.zeros(0)
+    _bcheck(lib().sl_batch_set_fields(b, _ptr(f), f.size), b)
+
+
+def sl_batch_step(b, splitting, dt, nsteps):
+    _bcheck(lib().sl_batch_step(b, _split(splitting), float(dt), int(nsteps)), b)
+
+
+def sl_batch_mass(b, nprob):
+    out = np.empty(nprob)
+    _bcheck(lib().sl_batch_mass(b, _ptr(out)), b)
+    return out
+
+
+def sl_batch_graph_capture(b, splitting, dt, nsteps):
+    _bcheck(lib().sl_batch_graph_capture(b, _split(splitting), float(dt), int(nsteps)), b)
+
+
+def sl_batch_graph_launch(b):
+    _bcheck(lib().sl_batch_graph_launch(b), b)
+
+
+def sl_batch_synchronize(b):
+    _bcheck(lib().sl_batch_synchronize(b), b)
+
+
+def sl_batch_autotune(b, reps=3):
+    _bcheck(lib().sl_batch_autotune(b, int(reps)), b)
+
+
+def sl_batch_profile_enable(b, enable=True):
+    _bcheck(lib().sl_batch_profile_enable(b, 1 if enable else 0), b)
+
+
+def sl_batch_profile_query(b):
+    n, ms, by = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    _bcheck(lib().sl_batch_profile_query(b, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(by)), b)
+    return n.value, ms.value, by.value
+
+
+class Batch:
+    """Owns one sl_batch handle for a list of problems (objects with .grid, .k)."""
+
+    def __init__(self, grids, degrees, storage, stream=None):
+        self.grids = list(grids)
+        self.degrees = list(degrees)
+        self.handle = sl_batch_create(self.grids, self.degrees, storage, stream)
+        self.info = sl_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            sl_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def project(self, prob, nq, weights, params):
+        sl_batch_project(self.handle, prob, nq, weights, params)
+
+    def set_coeffs(self, prob, u):
+        sl_batch_set_coeffs(self.handle, prob, u)
+
+    def get_coeffs(self, prob):
+        g = self.grids[prob]
+        cells = int(np.prod(g.n))
+        return sl_batch_get_coeffs(self.handle, prob, cells, (self.degrees[prob] + 1) ** len(g.n))
+
+    def set_fields(self, fields):
+        sl_batch_set_fields(self.handle, fields)
+
+    def step(self, splitting, dt, nsteps=1):
+        sl_batch_step(self.handle, splitting, dt, nsteps)
+
+    def mass(self):
+        return sl_batch_mass(self.handle, len(self.grids))
+
+    def graph_capture(self, splitting, dt, nsteps):
+        sl_batch_graph_capture(self.handle, splitting, dt, nsteps)
+
+    def graph_launch(self):
+        sl_batch_graph_launch(self.handle)
+
+    def synchronize(self):
+        sl_batch_synchronize(self.handle)
+
+    def autotune(self, reps=3):
+        sl_batch_autotune(self.handle, reps)
+
+    def profile_enable(self, on=True):
+        sl_batch_profile_enable(self.handle, on)
+
+    def profile_query(self):
+        return sl_batch_profile_query(self.handle)

@@ -14,73 +14,28 @@
 #include <utility>
 #include <vector>
 
-#include "../../include/sl.h"
-#include "sl_internal.cuh"
+#include "sl_host.h"
 
 using namespace sl;
-
-struct sl_ctx {
-    sl_grid g{};
-    int K = 0, O = 1, ndim = 1;
-    Mode mode = M_FP64;
-    cudaStream_t st = nullptr;
-    int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
-    size_t elem = 8;
-    int64_t state_bytes = 0;
-
-    void* mem = nullptr;
-    size_t mem_bytes = 0;
-    Planes planes[2]{};
-    int cur = 0;
-
-    int maxcls = 1;
-    int32_t* d_sigma = nullptr;
-    double* d_alpha = nullptr;
-    double* d_ab64 = nullptr;
-    float* d_ab32 = nullptr;
-    double* d_shifts = nullptr;
-    double* d_fields = nullptr;
-    int64_t nfields = 0;
-    bool fields_set = false;
-    double* d_partials = nullptr;
-    double* d_mass = nullptr;
-    int mass_nblk = 1;
-    double* h_mass = nullptr;   // pinned
-
-    double* d_stage = nullptr;  // lazily allocated AoS staging for set/get
-    int64_t stage_cells = 0;
-    double* d_proj = nullptr;   // lazily allocated projection workspace
-    size_t proj_bytes = 0;
-
-    PolyTab poly{};
-
-    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-    int graph_start = -1;       // copy index the first graph starts from
-    int graph_flip = 0;         // sweeps per graph mod 2
-    bool capturing = false;
-
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_free;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
-    std::vector<int> ev_dim;
-    int64_t prof_launches = 0;
-    int64_t last_dim_launches[SL_MAX_DIM] = {0};
-    double last_dim_ms[SL_MAX_DIM] = {0};
-
-    struct Tune {
-        int block = 256;
-        int ft = 1;
-        int unroll = 1;
-        uint32_t chunk = 0;
-        int pipeline = 0;
-    } tune[SL_MAX_DIM];
-
-    std::string err;
-};
+using namespace sl::host;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace sl {
+namespace host {
+
+sl_status fail_to(std::string* err, sl_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    *(err ? err : &g_err) = buf;
+    return s;
+}
 
 sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...)
 {
@@ -101,11 +56,6 @@ sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what)
     return fail(c, SL_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define SL_CUDA(ctx, call)                                          \
-    do {                                                            \
-        cudaError_t e_ = (call);                                    \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);  \
-    } while (0)
 
 size_t elem_size(int mode)
 {
@@ -200,6 +150,15 @@ bool strided_ok(int ft, int u)
            (ft == 3 && (u == 1 || u == 2));
 }
 
+// Cells per thread of the 16-byte vector form along dimension 0 (0 if the
+// store or the extent does not allow it).
+int unit_vec_width(const sl_ctx* c)
+{
+    if (is_scaled(c)) return 0;
+    const int v = int(16 / c->elem);
+    return c->g.n[0] % v == 0 ? v : 0;
+}
+
 // Default launch shape for a sweep along dimension m.
 void default_tune(sl_ctx* c, int m)
 {
@@ -207,7 +166,7 @@ void default_tune(sl_ctx* c, int m)
     t.ft = 1;
     if (m == 0) {
         t.block = 256;
-        t.unroll = 1;
+        t.unroll = unit_vec_width(c) ? unit_vec_width(c) : 1;
         t.chunk = 0;
         return;
     }
@@ -216,11 +175,13 @@ void default_tune(sl_ctx* c, int m)
     t.chunk = chunk_for(c, m, t.ft);
 }
 
-SweepArgs make_args(sl_ctx* c, int dim, int shift_dim)
+SweepArgs make_args(sl_ctx* c, int dim, int shift_dim) { return make_args_parity(c, dim, shift_dim, c->cur); }
+
+SweepArgs make_args_parity(sl_ctx* c, int dim, int shift_dim, int parity)
 {
     SweepArgs a{};
-    a.src = c->planes[c->cur];
-    a.dst = c->planes[c->cur ^ 1];
+    a.src = c->planes[parity];
+    a.dst = c->planes[parity ^ 1];
     a.tab.sigma = c->d_sigma;
     a.tab.alpha = c->d_alpha;
     a.tab.ab64 = c->d_ab64;
@@ -320,11 +281,6 @@ sl_status build_table(sl_ctx* c, int dim, int nclass, const ShiftSource& src)
 }
 
 // The sweeps of one split step: (dim, tau factor).
-struct SubStep {
-    int dim;
-    double frac;
-};
-
 std::vector<SubStep> plan_of(const sl_ctx* c, sl_splitting sp)
 {
     std::vector<int> xd, vd;
@@ -428,7 +384,16 @@ void drop_graph(sl_ctx* c)
     c->graph_start = -1;
 }
 
-}  // namespace
+int natural_shift_dim(const sl_ctx* c, int m)
+{
+    if (c->g.pair[m] >= 0) return c->g.pair[m];
+    for (int q = 0; q < c->ndim; ++q)
+        if (c->g.pair[q] == m) return q;
+    return -1;
+}
+
+}  // namespace host
+}  // namespace sl
 
 // ======================================================================
 // ABI
@@ -961,9 +926,16 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
         if (t->fibres_per_thread > c->nfib)
             return fail(c, SL_EINVAL, "fibres_per_thread %d exceeds the %lld fibres of a cell",
                         t->fibres_per_thread, (long long)c->nfib);
-        if (dim == 0 && !unit_ft_ok(t->fibres_per_thread))
+        if (dim == 0 && t->unroll == 1 && !unit_ft_ok(t->fibres_per_thread))
             return fail(c, SL_EINVAL, "fibres_per_thread %d not provided along dimension 0",
                         t->fibres_per_thread);
+        if (dim == 0 && t->unroll != 1) {
+            if (t->unroll != unit_vec_width(c))
+                return fail(c, SL_EINVAL, "unroll along dimension 0 must be 1 or %d (n_0 divisible by it)",
+                            int(16 / c->elem));
+            if (t->fibres_per_thread < 1 || t->fibres_per_thread > 4)
+                return fail(c, SL_EINVAL, "the vector form takes 1..4 fibres per thread");
+        }
         if (dim > 0 && t->pipeline == 0 && !strided_ok(t->fibres_per_thread, t->unroll))
             return fail(c, SL_EINVAL, "(fibres_per_thread %d, unroll %d) not provided",
                         t->fibres_per_thread, t->unroll);
@@ -995,18 +967,10 @@ sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
     auto& d = c->tune[dim];
     d.block = t->block;
     d.ft = is_scaled(c) ? 1 : t->fibres_per_thread;
-    d.unroll = is_scaled(c) ? 1 : (dim == 0 ? 1 : t->unroll);
+    d.unroll = is_scaled(c) ? 1 : t->unroll;
     d.pipeline = is_scaled(c) || dim == 0 ? 0 : t->pipeline;
     d.chunk = dim == 0 ? 0 : uint32_t(t->chunk);
     return SL_OK;
-}
-
-static int natural_shift_dim(const sl_ctx* c, int m)
-{
-    if (c->g.pair[m] >= 0) return c->g.pair[m];
-    for (int q = 0; q < c->ndim; ++q)
-        if (c->g.pair[q] == m) return q;
-    return -1;
 }
 
 sl_status sl_autotune(sl_ctx* c, int reps)
@@ -1042,6 +1006,10 @@ sl_status sl_autotune(sl_ctx* c, int reps)
                 for (int ft : {1, 2, 3, 4, 9})
                     if (ft <= c->nfib)
                         for (int b : {128, 256}) cand.push_back({b, ft, 1, 0, 0});
+                if (const int v = unit_vec_width(c))
+                    for (int ft : {1, 2, 3, 4})
+                        if (ft <= c->nfib)
+                            for (int b : {128, 256}) cand.push_back({b, ft, v, 0, 0});
             }
         } else {
             if (is_scaled(c)) {

@@ -2,70 +2,21 @@
 // construction of A(alpha), B(alpha) per shift class, the FP64 mass
 // reduction, encoding/decoding of the split store, and the initial
 // projection eq. (cj).
+#include "sl_ab.cuh"
 #include "sl_sweep.cuh"
 
 namespace sl {
 
 // ---------------------------------------------------------------- A, B
 
-// One thread per shift class.  s = a tau / h in cells (from an array, from
-// the cell-centre velocity of a v-dimension, or from field samples), split as
-// sigma = floor(s), alpha = s - sigma (alpha rounding to 1 moves to the next
-// integer), sigma reduced into [0, N).  The entries of A and B are the exact
-// polynomials of Sec. II-A's projection integrals, stored centred at
-// alpha = 1/2 and evaluated by Horner's rule; alpha = 0 is the exact identity.
+// One thread per shift class; the arithmetic is in sl_ab.cuh.
 __global__ void k_ab_build(int K, int nclass, uint32_t N, ShiftSource src, PolyTab tab,
                            int32_t* __restrict__ sigma, double* __restrict__ alpha,
                            double* __restrict__ ab64, float* __restrict__ ab32)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nclass) return;
-    double s;
-    if (src.kind == 0) {
-        s = src.data[c];
-    } else if (src.kind == 1) {
-        const double v = __dadd_rn(src.lo, __dmul_rn(double(c) + 0.5, src.hv));
-        s = __ddiv_rn(__dmul_rn(v, src.tau), src.h);
-    } else {
-        s = __ddiv_rn(__dmul_rn(src.data[c], src.tau), src.h);
-    }
-    const double f = floor(s);
-    double a = s - f;
-    long long sg = (long long)f;
-    if (a >= 1.0) {
-        sg += 1;
-        a = 0.0;
-    }
-    long long r = sg % (long long)N;
-    if (r < 0) r += N;
-    sigma[c] = int32_t(r);
-    alpha[c] = a;
-
-    const int O = K + 1;
-    const int deg = 2 * K + 1;
-    const double t = a - 0.5;
-    double* m64 = ab64 + size_t(c) * ab_stride64(O);
-    float* m32 = ab32 + size_t(c) * ab_stride32(O);
-    for (int j = 0; j < O; ++j) {
-        for (int l = 0; l < O; ++l) {
-            double va, vb;
-            if (a == 0.0) {
-                va = (j == l) ? 1.0 : 0.0;
-                vb = 0.0;
-            } else {
-                va = tab.a[j][l][deg];
-                vb = tab.b[j][l][deg];
-                for (int p = deg - 1; p >= 0; --p) {
-                    va = fma(va, t, tab.a[j][l][p]);
-                    vb = fma(vb, t, tab.b[j][l][p]);
-                }
-            }
-            m64[j * O + l] = va;
-            m64[O * O + j * O + l] = vb;
-            m32[j * O + l] = __double2float_rn(va);
-            m32[O * O + j * O + l] = __double2float_rn(vb);
-        }
-    }
+    ab_class(K, shift_of(src, c), N, tab, c, sigma, alpha, ab64, ab32);
 }
 
 cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,

@@ -1,0 +1,576 @@
+// sl_batch_api.cu -- host side of the batched API (sl_batch_* in sl.h).
+//
+// A batch owns one single-problem context per problem (each with its own
+// ping-pong state, tables and fields).  All problems advance together: every
+// split substep is one table launch over all problems and one persistent
+// sweep launch over a work list of equal-sized tiles of all problems, so
+// uneven problem sizes balance across the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sl_host.h"
+
+using namespace sl;
+using namespace sl::host;
+
+struct sl_batch {
+    std::vector<sl_ctx*> probs;
+    int nprob = 0;
+    int ndim = 0;
+    sl::Mode mode = sl::M_F32;
+    cudaStream_t st = nullptr;
+    std::string err;
+    int parity = 0;   // copy every problem currently reads
+    int64_t state_bytes = 0;
+    int sms = 1;
+
+    // device arrays (one allocation)
+    void* mem = nullptr;
+    SweepArgs* d_args = nullptr;   // [dim][parity][prob]
+    int32_t* d_kdeg = nullptr;     // [prob]
+    BatchAB* d_ab = nullptr;       // [dim][prob]
+    PolyTab* d_tabs = nullptr;     // [degree 0..3]
+    BatchMass* d_mass_desc = nullptr;
+    double* d_mass = nullptr;      // [prob]
+    std::vector<double> h_mass;
+    int maxcls[SL_MAX_DIM] = {0};
+
+    // work lists per dimension
+    BatchItem* d_items[SL_MAX_DIM] = {nullptr};
+    int nitems[SL_MAX_DIM] = {0};
+    struct Tune {
+        int ft = 1;
+        int unroll = 1;
+        int chunk_div = 1;
+    } tune[SL_MAX_DIM];
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_start = -1;
+    int graph_flip = 0;
+    bool capturing = false;
+
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    int64_t prof_launches = 0;
+};
+
+namespace {
+
+sl_status bfail(sl_batch* b, sl_status s, const char* msg)
+{
+    if (b)
+        b->err = msg;
+    else
+        fail(nullptr, s, "%s", msg);
+    return s;
+}
+
+sl_status bcuda(sl_batch* b, cudaError_t e, const char* what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return bfail(b, SL_ECUDA, m.c_str());
+}
+
+#define SLB_CUDA(b, call)                                   \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return bcuda((b), e_, #call); \
+    } while (0)
+
+int min_fibres(const sl_batch* b)
+{
+    int64_t m = INT64_MAX;
+    for (auto* c : b->probs) m = std::min<int64_t>(m, c->nfib);
+    return int(m);
+}
+
+// Work items and sweep geometry of dimension m for the batch's current tune.
+sl_status rebuild_dim(sl_batch* b, int m)
+{
+    const auto& t = b->tune[m];
+    std::vector<BatchItem> items;
+    std::vector<SweepArgs> args(2 * size_t(b->nprob));
+    for (int p = 0; p < b->nprob; ++p) {
+        sl_ctx* c = b->probs[p];
+        c->tune[m].ft = t.ft;
+        c->tune[m].unroll = t.unroll;
+        c->tune[m].pipeline = 0;
+        const int64_t N = c->g.n[m];
+        c->tune[m].chunk = m == 0 ? 0 : uint32_t(std::max<int64_t>(1, (N + t.chunk_div - 1) / t.chunk_div));
+        const int sd = natural_shift_dim(c, m);
+        for (int par = 0; par < 2; ++par) args[size_t(par) * b->nprob + p] = make_args_parity(c, m, sd, par);
+        const SweepArgs& a = args[p];
+        const uint32_t nfg = uint32_t(a.nfg);
+        if (m == 0) {
+            const uint32_t tiles = (a.cells + kBatchBlock - 1) / kBatchBlock;
+            for (uint32_t g = 0; g < nfg; ++g)
+                for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * kBatchBlock, g, 0});
+        } else {
+            const uint32_t tiles = (a.lines + kBatchBlock - 1) / kBatchBlock;
+            const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
+            for (uint32_t g = 0; g < nfg; ++g)
+                for (uint32_t ch = 0; ch < nchunk; ++ch)
+                    for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * kBatchBlock, g, ch});
+        }
+    }
+    SLB_CUDA(b, cudaMemcpyAsync(b->d_args + size_t(m) * 2 * b->nprob, args.data(),
+                                args.size() * sizeof(SweepArgs), cudaMemcpyHostToDevice, b->st));
+    if (b->d_items[m]) {
+        SLB_CUDA(b, cudaStreamSynchronize(b->st));
+        cudaFree(b->d_items[m]);
+        b->d_items[m] = nullptr;
+    }
+    SLB_CUDA(b, cudaMalloc(&b->d_items[m], std::max<size_t>(1, items.size()) * sizeof(BatchItem)));
+    SLB_CUDA(b, cudaMemcpyAsync(b->d_items[m], items.data(), items.size() * sizeof(BatchItem),
+                                cudaMemcpyHostToDevice, b->st));
+    SLB_CUDA(b, cudaStreamSynchronize(b->st));
+    b->nitems[m] = int(items.size());
+    return SL_OK;
+}
+
+cudaEvent_t new_event()
+{
+    cudaEvent_t e = nullptr;
+    return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
+}
+
+sl_status batch_sweep(sl_batch* b, int m, double tau)
+{
+    SLB_CUDA(b, launch_batch_ab(b->d_ab + size_t(m) * b->nprob, b->d_tabs, b->nprob, b->maxcls[m], tau,
+                                b->st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const bool prof = b->prof && !b->capturing;
+    if (prof) {
+        e0 = new_event();
+        e1 = new_event();
+        if (!e0 || !e1) return bfail(b, SL_ECUDA, "cudaEventCreate failed");
+        SLB_CUDA(b, cudaEventRecord(e0, b->st));
+    }
+    const auto& t = b->tune[m];
+    const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll);
+    SLB_CUDA(b, launch_batch_sweep(b->mode, t.ft, t.unroll,
+                                   b->d_args + (size_t(m) * 2 + b->parity) * b->nprob, b->d_kdeg,
+                                   b->d_items[m], b->nitems[m], m == 0, blocks, b->st));
+    if (prof) {
+        SLB_CUDA(b, cudaEventRecord(e1, b->st));
+        b->ev.emplace_back(e0, e1);
+        b->prof_launches++;
+    }
+    b->parity ^= 1;
+    for (auto* c : b->probs) c->cur = b->parity;
+    return SL_OK;
+}
+
+sl_status batch_steps(sl_batch* b, sl_splitting sp, double dt, int nsteps)
+{
+    const std::vector<SubStep> plan = plan_of(b->probs[0], sp);
+    for (int s = 0; s < nsteps; ++s)
+        for (const SubStep& ss : plan) {
+            sl_status r = batch_sweep(b, ss.dim, ss.frac * dt);
+            if (r != SL_OK) return r;
+        }
+    return SL_OK;
+}
+
+sl_status check_prob(sl_batch* b, int p)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    if (p < 0 || p >= b->nprob) return bfail(b, SL_EINVAL, "problem index out of range");
+    return SL_OK;
+}
+
+sl_status forward(sl_batch* b, sl_ctx* c, sl_status s)
+{
+    if (s != SL_OK) b->err = c->err;
+    return s;
+}
+
+void drop_graph(sl_batch* b)
+{
+    for (auto& g : b->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    b->graph_start = -1;
+}
+
+sl_status check_steps(sl_batch* b, sl_splitting sp, double dt, int nsteps)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    if (sp != SL_LIE && sp != SL_STRANG) return bfail(b, SL_EINVAL, "unknown splitting");
+    if (!std::isfinite(dt)) return bfail(b, SL_ENAN, "dt is not finite");
+    if (nsteps < 0) return bfail(b, SL_EINVAL, "nsteps < 0");
+    for (auto* c : b->probs)
+        if (c->nfields > 0 && !c->fields_set) return bfail(b, SL_EINVAL, "fields not set (sl_batch_set_fields)");
+    return SL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, sl_storage storage,
+                          void* cuda_stream, sl_batch** out)
+{
+    if (!out) return fail(nullptr, SL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || nprob > 65535) return fail(nullptr, SL_EINVAL, "nprob must be in 1..65535");
+    if (!grids || !degrees) return fail(nullptr, SL_EINVAL, "grids or degrees is NULL");
+    if (storage != SL_FP64 && storage != SL_MIX_FP32)
+        return fail(nullptr, SL_ENOTSUP, "batches support the FP64 and mixed FP32 stores");
+    bool any_pair = false;
+    for (int p = 0; p < nprob; ++p) {
+        sl_status s = check_grid(&grids[p], degrees[p], storage, nullptr);
+        if (s != SL_OK) return s;
+        if (degrees[p] > kBatchMaxK) return fail(nullptr, SL_ENOTSUP, "batched degrees are 0..%d", kBatchMaxK);
+        if (grids[p].ndim != grids[0].ndim) return fail(nullptr, SL_EINVAL, "problems differ in ndim");
+        for (int m = 0; m < grids[0].ndim; ++m)
+            if (grids[p].pair[m] != grids[0].pair[m])
+                return fail(nullptr, SL_EINVAL, "problems differ in their x/v pairing");
+    }
+    for (int m = 0; m < grids[0].ndim; ++m) any_pair |= grids[0].pair[m] >= 0;
+    if (!any_pair) return fail(nullptr, SL_EINVAL, "batched problems need x/v pairs to split");
+
+    sl_batch* b = new (std::nothrow) sl_batch();
+    if (!b) return fail(nullptr, SL_ENOMEM, "host allocation failed");
+    b->nprob = nprob;
+    b->ndim = grids[0].ndim;
+    b->mode = sl::Mode(storage);
+    b->st = static_cast<cudaStream_t>(cuda_stream);
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        delete b;
+        return fail(nullptr, SL_ECUDA, "no CUDA device");
+    }
+    b->sms = prop.multiProcessorCount;
+    auto cleanup = [&](sl_status s) {
+        sl_batch_destroy(b);
+        return s;
+    };
+    for (int p = 0; p < nprob; ++p) {
+        sl_ctx* c = nullptr;
+        sl_status s = sl_create(&grids[p], degrees[p], storage, cuda_stream, &c);
+        if (s != SL_OK) return cleanup(s);
+        b->probs.push_back(c);
+        b->state_bytes += c->state_bytes;
+        for (int m = 0; m < b->ndim; ++m) {
+            const int sd = natural_shift_dim(c, m);
+            b->maxcls[m] = std::max<int>(b->maxcls[m], sd < 0 ? 1 : int(c->g.n[sd]));
+        }
+    }
+    // device arrays
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = (off + bytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_args = take(sizeof(SweepArgs) * 2 * b->ndim * nprob);
+    const size_t o_k = take(sizeof(int32_t) * nprob);
+    const size_t o_ab = take(sizeof(BatchAB) * b->ndim * nprob);
+    const size_t o_tabs = take(sizeof(PolyTab) * 4);
+    const size_t o_md = take(sizeof(BatchMass) * nprob);
+    const size_t o_m = take(sizeof(double) * nprob);
+    if (cudaMalloc(&b->mem, off) != cudaSuccess) return cleanup(fail(nullptr, SL_ENOMEM, "batch tables"));
+    char* base = static_cast<char*>(b->mem);
+    b->d_args = reinterpret_cast<SweepArgs*>(base + o_args);
+    b->d_kdeg = reinterpret_cast<int32_t*>(base + o_k);
+    b->d_ab = reinterpret_cast<BatchAB*>(base + o_ab);
+    b->d_tabs = reinterpret_cast<PolyTab*>(base + o_tabs);
+    b->d_mass_desc = reinterpret_cast<BatchMass*>(base + o_md);
+    b->d_mass = reinterpret_cast<double*>(base + o_m);
+    b->h_mass.resize(nprob);
+
+    std::vector<int32_t> kd(nprob);
+    std::vector<BatchAB> ab(size_t(b->ndim) * nprob);
+    std::vector<BatchMass> md(nprob);
+    std::vector<PolyTab> tabs(4);
+    for (int K = 0; K < 4; ++K) build_poly_table(K, &tabs[K]);
+    for (int p = 0; p < nprob; ++p) {
+        sl_ctx* c = b->probs[p];
+        kd[p] = c->K;
+        double vol = 1.0;
+        for (int m = 0; m < c->ndim; ++m) vol *= cell_width(c->g, m);
+        md[p] = BatchMass{{c->planes[0].mean, c->planes[1].mean}, uint32_t(c->cells), vol};
+        for (int m = 0; m < b->ndim; ++m) {
+            BatchAB& d = ab[size_t(m) * nprob + p];
+            d.K = c->K;
+            d.N = uint32_t(c->g.n[m]);
+            d.sigma = c->d_sigma;
+            d.alpha = c->d_alpha;
+            d.ab64 = c->d_ab64;
+            d.ab32 = c->d_ab32;
+            d.h = cell_width(c->g, m);
+            if (c->g.pair[m] >= 0) {
+                const int v = c->g.pair[m];
+                d.kind = 1;
+                d.nclass = int(c->g.n[v]);
+                d.lo = c->g.lo[v];
+                d.hv = cell_width(c->g, v);
+            } else {
+                const int xm = natural_shift_dim(c, m);
+                d.kind = 2;
+                d.nclass = xm < 0 ? 1 : int(c->g.n[xm]);
+                d.field = xm < 0 ? c->d_fields : c->d_fields + field_offset(c, xm);
+            }
+        }
+    }
+    if (cudaMemcpyAsync(b->d_kdeg, kd.data(), kd.size() * 4, cudaMemcpyHostToDevice, b->st) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_ab, ab.data(), ab.size() * sizeof(BatchAB), cudaMemcpyHostToDevice, b->st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(b->d_tabs, tabs.data(), tabs.size() * sizeof(PolyTab), cudaMemcpyHostToDevice,
+                        b->st) != cudaSuccess ||
+        cudaMemcpyAsync(b->d_mass_desc, md.data(), md.size() * sizeof(BatchMass), cudaMemcpyHostToDevice,
+                        b->st) != cudaSuccess ||
+        cudaStreamSynchronize(b->st) != cudaSuccess)
+        return cleanup(fail(nullptr, SL_ECUDA, "uploading batch tables"));
+    // default shapes: the most fibres per thread every problem allows, two
+    // cells per walk step, whole lines
+    const int ftmax = std::min(2, min_fibres(b));
+    for (int m = 0; m < b->ndim; ++m) {
+        b->tune[m].ft = ftmax;
+        b->tune[m].unroll = m == 0 ? 1 : 4;
+        b->tune[m].chunk_div = 1;
+        sl_status s = rebuild_dim(b, m);
+        if (s != SL_OK) {
+            fail(nullptr, s, "%s", b->err.c_str());
+            return cleanup(s);
+        }
+    }
+    *out = b;
+    return SL_OK;
+}
+
+void sl_batch_destroy(sl_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->st);
+    drop_graph(b);
+    for (auto& pr : b->ev) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto& it : b->d_items)
+        if (it) cudaFree(it);
+    if (b->mem) cudaFree(b->mem);
+    for (auto* c : b->probs) sl_destroy(c);
+    delete b;
+}
+
+const char* sl_batch_last_error(const sl_batch* b) { return b ? b->err.c_str() : sl_last_error(nullptr); }
+
+sl_status sl_batch_info(const sl_batch* b, int64_t* cells, int64_t* dof, int64_t* state_bytes)
+{
+    if (!b || !cells || !dof || !state_bytes) return fail(nullptr, SL_EINVAL, "NULL argument");
+    int64_t c = 0, d = 0;
+    for (auto* p : b->probs) {
+        c += p->cells;
+        d += p->cells * p->ncoef;
+    }
+    *cells = c;
+    *dof = d;
+    *state_bytes = b->state_bytes;
+    return SL_OK;
+}
+
+sl_status sl_batch_project(sl_batch* b, int p, int nq, int nterms, const double* weights,
+                           const double* params)
+{
+    sl_status s = check_prob(b, p);
+    if (s != SL_OK) return s;
+    return forward(b, b->probs[p], sl_project(b->probs[p], nq, nterms, weights, params));
+}
+
+sl_status sl_batch_set_coeffs(sl_batch* b, int p, const double* host_aos)
+{
+    sl_status s = check_prob(b, p);
+    if (s != SL_OK) return s;
+    return forward(b, b->probs[p], sl_set_coeffs(b->probs[p], host_aos));
+}
+
+sl_status sl_batch_get_coeffs(sl_batch* b, int p, double* host_aos)
+{
+    sl_status s = check_prob(b, p);
+    if (s != SL_OK) return s;
+    return forward(b, b->probs[p], sl_get_coeffs(b->probs[p], host_aos));
+}
+
+sl_status sl_batch_set_fields(sl_batch* b, const double* fields, int64_t count)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    int64_t need = 0;
+    for (auto* c : b->probs) need += c->nfields;
+    if (count != need) return bfail(b, SL_EINVAL, "field count does not match the batch");
+    if (need > 0 && !fields) return bfail(b, SL_EINVAL, "fields is NULL");
+    int64_t off = 0;
+    for (auto* c : b->probs) {
+        sl_status s = sl_set_fields(c, fields ? fields + off : nullptr, c->nfields);
+        if (s != SL_OK) return forward(b, c, s);
+        off += c->nfields;
+    }
+    return SL_OK;
+}
+
+sl_status sl_batch_step(sl_batch* b, sl_splitting sp, double dt, int nsteps)
+{
+    sl_status s = check_steps(b, sp, dt, nsteps);
+    if (s != SL_OK) return s;
+    return batch_steps(b, sp, dt, nsteps);
+}
+
+sl_status sl_batch_mass(sl_batch* b, double* out)
+{
+    if (!b || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (b->capturing) return bfail(b, SL_EINVAL, "cannot read the mass during a capture");
+    SLB_CUDA(b, launch_batch_mass(b->d_mass_desc, b->nprob, b->parity, b->d_mass, b->st));
+    SLB_CUDA(b, cudaMemcpyAsync(out, b->d_mass, size_t(b->nprob) * 8, cudaMemcpyDeviceToHost, b->st));
+    SLB_CUDA(b, cudaStreamSynchronize(b->st));
+    return SL_OK;
+}
+
+sl_status sl_batch_graph_capture(sl_batch* b, sl_splitting sp, double dt, int nsteps)
+{
+    sl_status s = check_steps(b, sp, dt, nsteps);
+    if (s != SL_OK) return s;
+    if (!b->st) return bfail(b, SL_EINVAL, "graph capture needs a non-default stream");
+    drop_graph(b);
+    const int start = b->parity;
+    const int sweeps = int(plan_of(b->probs[0], sp).size()) * nsteps;
+    const int flip = sweeps & 1;
+    for (int gi = 0; gi < (flip ? 2 : 1); ++gi) {
+        b->parity = start ^ gi;
+        for (auto* c : b->probs) c->cur = b->parity;
+        cudaGraph_t graph = nullptr;
+        SLB_CUDA(b, cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+        b->capturing = true;
+        s = batch_steps(b, sp, dt, nsteps);
+        b->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(b->st, &graph);
+        if (s == SL_OK && e == cudaSuccess) e = cudaGraphInstantiate(&b->gexec[gi], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (s != SL_OK || e != cudaSuccess) {
+            b->parity = start;
+            for (auto* c : b->probs) c->cur = start;
+            drop_graph(b);
+            return s != SL_OK ? s : bcuda(b, e, "graph capture");
+        }
+    }
+    b->parity = start;
+    for (auto* c : b->probs) c->cur = start;
+    b->graph_start = start;
+    b->graph_flip = flip;
+    return SL_OK;
+}
+
+sl_status sl_batch_graph_launch(sl_batch* b)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    if (b->graph_start < 0) return bfail(b, SL_EINVAL, "no graph captured");
+    const int gi = b->parity == b->graph_start ? 0 : 1;
+    if (!b->gexec[gi]) return bfail(b, SL_EINVAL, "no graph for the current buffer parity");
+    SLB_CUDA(b, cudaGraphLaunch(b->gexec[gi], b->st));
+    b->parity ^= b->graph_flip;
+    for (auto* c : b->probs) c->cur = b->parity;
+    return SL_OK;
+}
+
+sl_status sl_batch_synchronize(sl_batch* b)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    SLB_CUDA(b, cudaStreamSynchronize(b->st));
+    return SL_OK;
+}
+
+sl_status sl_batch_autotune(sl_batch* b, int reps)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    if (b->capturing) return bfail(b, SL_EINVAL, "cannot autotune during a capture");
+    reps = std::max(1, std::min(reps, 50));
+    const int ftmax = std::min(2, min_fibres(b));
+    cudaEvent_t e0 = new_event(), e1 = new_event();
+    if (!e0 || !e1) return bfail(b, SL_ECUDA, "cudaEventCreate failed");
+    sl_status result = SL_OK;
+    const bool prof = b->prof;
+    b->prof = false;
+    for (int m = 0; m < b->ndim && result == SL_OK; ++m) {
+        std::vector<sl_batch::Tune> cand;
+        for (int ft = 1; ft <= ftmax; ++ft) {
+            if (m == 0) {
+                cand.push_back({ft, 1, 1});
+            } else {
+                for (int u : {1, 4})
+                    for (int cd : {1, 2, 4}) cand.push_back({ft, u, cd});
+            }
+        }
+        sl_batch::Tune best = b->tune[m];
+        float best_ms = 1e30f;
+        for (const auto& t : cand) {
+            b->tune[m] = t;
+            result = rebuild_dim(b, m);
+            if (result != SL_OK) break;
+            // out of place and the parity is restored, so the state is unchanged
+            const int par = b->parity;
+            cudaError_t e = cudaSuccess;
+            float ms = 0.0f;
+            for (int r = -1; r < reps && e == cudaSuccess; ++r) {
+                if (r == 0) e = cudaEventRecord(e0, b->st);
+                if (e != cudaSuccess) break;
+                const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll);
+                e = launch_batch_sweep(b->mode, t.ft, t.unroll, b->d_args + (size_t(m) * 2 + par) * b->nprob,
+                                       b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, blocks, b->st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                result = bcuda(b, e, "batch autotune");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = t;
+            }
+        }
+        b->tune[m] = best;
+        if (result == SL_OK) result = rebuild_dim(b, m);
+    }
+    b->prof = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return result;
+}
+
+sl_status sl_batch_profile_enable(sl_batch* b, int enable)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    b->prof = enable != 0;
+    return SL_OK;
+}
+
+sl_status sl_batch_profile_query(sl_batch* b, int64_t* launches, double* ms, double* bytes)
+{
+    if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
+    SLB_CUDA(b, cudaStreamSynchronize(b->st));
+    double tot = 0.0;
+    for (auto& pr : b->ev) {
+        float t = 0.0f;
+        SLB_CUDA(b, cudaEventElapsedTime(&t, pr.first, pr.second));
+        tot += t;
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    b->ev.clear();
+    if (launches) *launches = b->prof_launches;
+    if (ms) *ms = tot;
+    if (bytes) *bytes = 2.0 * double(b->state_bytes) * double(b->prof_launches);
+    b->prof_launches = 0;
+    return SL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// sl_host.h -- host-side internals of libsl.so shared by the single-problem
+// API (sl_api.cu) and the batched API (sl_batch_api.cu).  Not part of the
+// public ABI (include/sl.h is).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/sl.h"
+#include "sl_internal.cuh"
+
+// One problem: its grid, store, ping-pong state, shift tables and launch shapes.
+struct sl_ctx {
+    sl_grid g{};
+    int K = 0, O = 1, ndim = 1;
+    sl::Mode mode = sl::M_FP64;
+    cudaStream_t st = nullptr;
+    int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
+    size_t elem = 8;
+    int64_t state_bytes = 0;
+
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    sl::Planes planes[2]{};
+    int cur = 0;
+
+    int maxcls = 1;
+    int32_t* d_sigma = nullptr;
+    double* d_alpha = nullptr;
+    double* d_ab64 = nullptr;
+    float* d_ab32 = nullptr;
+    double* d_shifts = nullptr;
+    double* d_fields = nullptr;
+    int64_t nfields = 0;
+    bool fields_set = false;
+    double* d_partials = nullptr;
+    double* d_mass = nullptr;
+    int mass_nblk = 1;
+    double* h_mass = nullptr;   // pinned
+
+    double* d_stage = nullptr;  // lazily allocated AoS staging for set/get
+    int64_t stage_cells = 0;
+    double* d_proj = nullptr;   // lazily allocated projection workspace
+    size_t proj_bytes = 0;
+
+    sl::PolyTab poly{};
+
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int graph_start = -1;       // copy index the first graph starts from
+    int graph_flip = 0;         // sweeps per graph mod 2
+    bool capturing = false;
+
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_used;
+    std::vector<int> ev_dim;
+    int64_t prof_launches = 0;
+    int64_t last_dim_launches[SL_MAX_DIM] = {0};
+    double last_dim_ms[SL_MAX_DIM] = {0};
+
+    struct Tune {
+        int block = 256;
+        int ft = 1;
+        int unroll = 1;
+        uint32_t chunk = 0;
+        int pipeline = 0;
+    } tune[SL_MAX_DIM];
+
+    std::string err;
+};
+
+namespace sl {
+namespace host {
+
+sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...);
+sl_status fail_to(std::string* err, sl_status s, const char* fmt, ...);
+sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what);
+sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c);
+bool is_scaled(const sl_ctx* c);
+int64_t fibre_groups(const sl_ctx* c, int ft);
+uint32_t chunk_for(const sl_ctx* c, int m, int ft);
+double cell_width(const sl_grid& g, int m);
+int64_t ipow(int64_t b, int e);
+// Sweep geometry along `dim`, reading copy `parity` and writing the other.
+SweepArgs make_args_parity(sl_ctx* c, int dim, int shift_dim, int parity);
+int natural_shift_dim(const sl_ctx* c, int m);
+int64_t field_offset(const sl_ctx* c, int xdim);
+
+struct SubStep {
+    int dim;
+    double frac;
+};
+std::vector<SubStep> plan_of(const sl_ctx* c, sl_splitting sp);
+
+}  // namespace host
+}  // namespace sl
+
+#define SL_CUDA(ctx, call)                                                 \
+    do {                                                                   \
+        cudaError_t e_ = (call);                                           \
+        if (e_ != cudaSuccess) return sl::host::cuda_fail((ctx), e_, #call); \
+    } while (0)

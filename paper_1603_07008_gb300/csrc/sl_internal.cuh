@@ -167,4 +167,50 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
                            double* d_tab, uint32_t nmax, const CodecArgs& c, uint32_t cells,
                            cudaStream_t st);
 
+// ---------------------------------------------------------------- batches
+
+// One work item of a batched sweep: threads cover the `kBatchBlock`
+// consecutive cells (sweep along dimension 0) or lines (other dimensions)
+// starting at `start` of problem `prob`, for fibre group `grp` and chunk
+// `chunk` of the lines.
+constexpr int kBatchBlock = 128;
+constexpr int kBatchMaxK = 2;   // degrees compiled into the batched sweep
+struct BatchItem {
+    uint32_t prob;
+    uint32_t start;
+    uint32_t grp;
+    uint32_t chunk;
+};
+
+// Per (problem, sweep dimension): where the shifts of its classes come from
+// and where its table goes.
+struct BatchAB {
+    int K;
+    uint32_t N;
+    int nclass;
+    int kind;              // 1: cell-centre velocity of a v-dimension, 2: field samples
+    const double* field;
+    double lo, hv, h;
+    int32_t* sigma;
+    double* alpha;
+    double* ab64;
+    float* ab32;
+};
+
+struct BatchMass {
+    const double* mean[2];   // mean plane of each copy
+    uint32_t cells;
+    double vol;
+};
+
+cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int nprob, int maxclass,
+                            double tau, cudaStream_t st);
+cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
+                               const int32_t* d_kdeg, const BatchItem* d_items, int nitems,
+                               int unit, int blocks, cudaStream_t st);
+// Resident blocks per SM of the batched sweep kernel for (mode, ft, unroll).
+int batch_sweep_occupancy(int mode, int ft, int unroll);
+cudaError_t launch_batch_mass(const BatchMass* d_desc, int nprob, int parity, double* d_out,
+                              cudaStream_t st);
+
 }  // namespace sl

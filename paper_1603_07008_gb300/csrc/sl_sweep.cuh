@@ -383,14 +383,10 @@ __device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32
     store_cell<K, MODE, FT, MEAN>(a.dst, a.pstride, c, jb, 1, out);
 }
 
-// Sweep along dimension 0: one thread per target cell (and fibre group
-// blockIdx.y).
+// Target cell c of a sweep along dimension 0, fibres fbase .. fbase+FT-1.
 template <int K, int MODE, int FT>
-__global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
+__device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fbase)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.cells) return;
-    const int fbase = blockIdx.y * FT;
     const uint32_t line = a.fdN.div(c);
     const uint32_t i = c - line * a.N;
     const uint32_t cls = shift_class(a, 0, line);
@@ -407,6 +403,176 @@ __global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
         unit_body<K, MODE, FT, false>(a, c, ca, cb, cls, fbase);
 }
 
+// Sweep along dimension 0: one thread per target cell (and fibre group
+// blockIdx.y).
+template <int K, int MODE, int FT>
+__global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.cells) return;
+    unit_cell<K, MODE, FT>(a, c, int(blockIdx.y) * FT);
+}
+
+// ---------------------------------------------------------------- unit stride, 128-bit vectors
+
+// V = 16 / sizeof(element) consecutive elements of a plane as 16-byte loads
+// and stores (p must be 16-byte aligned).
+template <typename T, int NV>
+__device__ __forceinline__ void ld_vec(const T* p, T* x)
+{
+    if constexpr (sizeof(T) == 4) {
+        static_assert(NV % 4 == 0, "float vectors");
+#pragma unroll
+        for (int q = 0; q < NV / 4; ++q) {
+            const float4 v = __ldg(reinterpret_cast<const float4*>(p) + q);
+            x[4 * q] = v.x;
+            x[4 * q + 1] = v.y;
+            x[4 * q + 2] = v.z;
+            x[4 * q + 3] = v.w;
+        }
+    } else {
+        static_assert(NV % 2 == 0, "double vectors");
+#pragma unroll
+        for (int q = 0; q < NV / 2; ++q) {
+            const double2 v = __ldg(reinterpret_cast<const double2*>(p) + q);
+            x[2 * q] = v.x;
+            x[2 * q + 1] = v.y;
+        }
+    }
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void st_vec(T* p, const T* x)
+{
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int q = 0; q < NV / 4; ++q)
+            reinterpret_cast<float4*>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < NV / 2; ++q) reinterpret_cast<double2*>(p)[q] = make_double2(x[2 * q], x[2 * q + 1]);
+    }
+}
+
+// w[j] = x[r + j], j = 0..V, for a runtime r in [0, V), by a select network
+// on the bits of r (no divergence, no local-memory indexing).
+template <typename R, int V>
+__device__ __forceinline__ void window(const R (&x)[2 * V], int r, R (&w)[V + 1])
+{
+    static_assert(V == 2 || V == 4, "vector widths");
+    if constexpr (V == 2) {
+#pragma unroll
+        for (int j = 0; j <= V; ++j) w[j] = (r & 1) ? x[j + 1] : x[j];
+    } else {
+        R y[V + 3];
+#pragma unroll
+        for (int j = 0; j < V + 3; ++j) y[j] = (r & 1) ? x[j + 1] : x[j];
+#pragma unroll
+        for (int j = 0; j <= V; ++j) w[j] = (r & 2) ? y[j + 2] : y[j];
+    }
+}
+
+// Cells c0 .. c0+V-1 of one line (V | n_0, so they share the line and its
+// shift).  Their sources are the V+1 consecutive cells b0 = i0-sigma-1 ..
+// i0-sigma+V-1 of the periodic line, which lie in two consecutive aligned
+// V-vectors of the line's ring of n_0/V vectors: loaded as 16-byte vectors,
+// the window is cut out by `window`, the V targets are stored as vectors.
+template <int K, int MODE, int FT, bool MEAN>
+__device__ __forceinline__ void unit_vec_body(const SweepArgs& a, uint32_t c0, uint32_t i0,
+                                              uint32_t cls, int fbase)
+{
+    using T = typename St<MODE>::T;
+    using R = typename St<MODE>::R;
+    static_assert(!St<MODE>::scaled, "vector form of the unscaled stores");
+    constexpr int V = 16 / sizeof(T);
+    constexpr int O = K + 1;
+    const int32_t N = int32_t(a.N);
+    const uint32_t ls = c0 - i0;   // first cell of the line
+    const int32_t sig = __ldg(a.tab.sigma + cls);
+    int32_t b0 = int32_t(i0) - sig - 1;
+    b0 += b0 < 0 ? N : 0;
+    b0 += b0 < 0 ? N : 0;
+    const int32_t q1 = b0 & ~(V - 1);
+    const int r = int(b0 - q1);
+    int32_t q2 = q1 + V;
+    q2 -= q2 >= N ? N : 0;
+
+    int jb[FT];
+    group_bases<FT>(fbase, a.nfib, O, 1, jb);
+    Mats<K, MODE> M;
+    M.template load<MEAN>(a.tab, cls);
+
+    R w[FT][O][V + 1];
+    double wm[V + 1];
+#pragma unroll
+    for (int u = 0; u < FT; ++u)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            if (MEAN && u == 0 && l == 0) {
+                double x[2 * V];
+                ld_vec<double, V>(a.src.mean + ls + q1, x);
+                ld_vec<double, V>(a.src.mean + ls + q2, x + V);
+                window<double, V>(x, r, wm);
+            } else {
+                const T* p = plane_ptr<T>(a.src.hi, a.pstride, jb[u] + l) + ls;
+                T x[2 * V];
+                ld_vec<T, V>(p + q1, x);
+                ld_vec<T, V>(p + q2, x + V);
+                window<R, V>(x, r, w[u][l]);
+            }
+        }
+    R o[FT][O][V];
+    double om[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        CellVals<K, MODE, FT> ca, cb, out;
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                ca.v[u][l] = w[u][l][v + 1];
+                cb.v[u][l] = w[u][l][v];
+            }
+        if constexpr (MEAN) {
+            ca.m = wm[v + 1];
+            cb.m = wm[v];
+        }
+        combine<K, MODE, FT, MEAN>(M, ca, cb, out);
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) o[u][l][v] = out.v[u][l];
+        if constexpr (MEAN) om[v] = out.m;
+    }
+#pragma unroll
+    for (int u = 0; u < FT; ++u)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            if (MEAN && u == 0 && l == 0)
+                st_vec<double, V>(a.dst.mean + c0, om);
+            else
+                st_vec<T, V>(plane_ptr_w<T>(a.dst.hi, a.pstride, jb[u] + l) + c0, o[u][l]);
+        }
+}
+
+// Sweep along dimension 0 with 16-byte vectors: one thread per V consecutive
+// target cells and fibre group (blockIdx.y); needs n_0 divisible by V.
+template <int K, int MODE, int FT>
+__global__ void __launch_bounds__(256) k_sweep_unit_vec(const SweepArgs a)
+{
+    constexpr int V = 16 / sizeof(typename St<MODE>::T);
+    const uint32_t c0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    if (c0 >= a.cells) return;
+    const int fbase = int(blockIdx.y) * FT;
+    const uint32_t line = a.fdN.div(c0);
+    const uint32_t i0 = c0 - line * a.N;
+    const uint32_t cls = shift_class(a, 0, line);
+    if (fbase == 0)
+        unit_vec_body<K, MODE, FT, true>(a, c0, i0, cls, fbase);
+    else
+        unit_vec_body<K, MODE, FT, false>(a, c0, i0, cls, fbase);
+}
+
 // ---------------------------------------------------------------- strided
 
 struct LineSetup {
@@ -418,14 +584,14 @@ struct LineSetup {
     bool active;
 };
 
-__device__ __forceinline__ LineSetup line_setup(const SweepArgs& a, int FT)
+// The thread's line (an (outer, inner) pair), its shift class, and the
+// target cells of chunk `chunk` of it.
+__device__ __forceinline__ LineSetup line_setup(const SweepArgs& a, uint32_t line, uint32_t grp,
+                                                uint32_t chunk, int FT)
 {
     LineSetup L{};
-    const uint32_t line = blockIdx.x * blockDim.x + threadIdx.x;
     L.active = false;
     if (line >= a.lines) return L;
-    const uint32_t grp = blockIdx.y % uint32_t(a.nfg);
-    const uint32_t chunk = blockIdx.y / uint32_t(a.nfg);
     L.fbase = int(grp) * FT;
     const uint32_t outer = a.fdInner.div(line);
     const uint32_t inn = line - outer * a.inner;
@@ -437,6 +603,12 @@ __device__ __forceinline__ LineSetup line_setup(const SweepArgs& a, int FT)
     if (L.i1 > a.N) L.i1 = a.N;
     L.active = L.i0 < L.i1;
     return L;
+}
+
+__device__ __forceinline__ LineSetup line_setup_grid(const SweepArgs& a, int FT)
+{
+    return line_setup(a, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y % uint32_t(a.nfg),
+                      blockIdx.y / uint32_t(a.nfg), FT);
 }
 
 template <int K, int MODE, int FT, int U, bool MEAN>
@@ -509,18 +681,24 @@ __device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup
     }
 }
 
+template <int K, int MODE, int FT, int U>
+__device__ __forceinline__ void strided_line(const SweepArgs& a, const LineSetup& L)
+{
+    if (St<MODE>::scaled || L.fbase == 0)
+        strided_body<K, MODE, FT, U, true>(a, L);
+    else
+        strided_body<K, MODE, FT, U, false>(a, L);
+}
+
 // Sweep along dimension m > 0: one thread per line (and fibre group and
 // chunk of the line, blockIdx.y = chunk * nfg + group), walking the target
 // cells of its chunk U cells per step with the loads of a step issued first.
 template <int K, int MODE, int FT, int U>
 __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
 {
-    const LineSetup L = line_setup(a, FT);
+    const LineSetup L = line_setup_grid(a, FT);
     if (!L.active) return;
-    if (St<MODE>::scaled || L.fbase == 0)
-        strided_body<K, MODE, FT, U, true>(a, L);
-    else
-        strided_body<K, MODE, FT, U, false>(a, L);
+    strided_line<K, MODE, FT, U>(a, L);
 }
 
 // ---------------------------------------------------------------- strided, cp.async ring
@@ -647,7 +825,7 @@ template <int K, int MODE, int FT, int P, int B>
 __global__ void __launch_bounds__(B) k_sweep_strided_async(const SweepArgs a)
 {
     static_assert(!St<MODE>::scaled, "cp.async ring needs 4- or 8-byte elements");
-    const LineSetup L = line_setup(a, FT);
+    const LineSetup L = line_setup_grid(a, FT);
     if (!L.active) return;
     if (L.fbase == 0)
         async_body<K, MODE, FT, P, B, true>(a, L);

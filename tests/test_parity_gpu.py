@@ -360,7 +360,8 @@ ASYNC_SHAPES = [(1, 4), (1, 8), (2, 4), (2, 8), (3, 4)]
 
 
 @pytest.mark.parametrize("storage", ["fp64", "mix_fp32"])
-@pytest.mark.parametrize("n,k", [((37, 5, 3), 2), ((6, 9, 4), 1), ((3, 4, 5), 3)])
+@pytest.mark.parametrize("n,k", [((37, 5, 3), 2), ((6, 9, 4), 1), ((3, 4, 5), 3), ((8, 3, 5), 2),
+                                 ((4, 6, 2), 1), ((12, 2, 3), 3)])
 def test_every_launch_shape_gives_identical_results(storage, n, k):
     """Fibres per thread, unroll, block size and chunk length change only the
     work distribution: every shape must give bit-identical output, and the
@@ -385,17 +386,21 @@ def test_every_launch_shape_gives_identical_results(storage, n, k):
             if dim == 0:
                 shapes = [dict(block=b, fibres_per_thread=f) for f in UNIT_FT if f <= nfib
                           for b in (64, 256)]
+                vw = 4 if storage == "mix_fp32" else 2
+                if n[0] % vw == 0:
+                    shapes += [dict(block=b, fibres_per_thread=f, unroll=vw) for f in (1, 2, 3, 4)
+                               if f <= nfib for b in (32, 256)]
             else:
                 for f, un in STRIDED_SHAPES:
                     if f > nfib:
                         continue
-                    for ch in (1, 3, n[dim]):
+                    for ch in sorted({1, min(3, n[dim]), n[dim]}):
                         shapes.append(dict(block=128, fibres_per_thread=f, unroll=un, chunk=ch))
-                shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=2))
+                shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=min(2, n[dim])))
                 for f, pl in ASYNC_SHAPES:
                     if f > nfib:
                         continue
-                    for ch in (1, 2, n[dim]):
+                    for ch in sorted({1, min(2, n[dim]), n[dim]}):
                         for b in (64, 128):
                             shapes.append(dict(block=b, fibres_per_thread=f, pipeline=pl, chunk=ch))
             for sh in shapes:
@@ -442,6 +447,8 @@ def test_set_tune_rejects_shapes_not_built():
                         (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=9)),
                         (1, dict(block=128, fibres_per_thread=3, pipeline=8, chunk=8)),
                         (0, dict(block=128, fibres_per_thread=1, pipeline=4)),
+                        (0, dict(block=128, fibres_per_thread=1, unroll=2)),
+                        (0, dict(block=128, fibres_per_thread=9, unroll=4)),
                         (1, dict(block=32, fibres_per_thread=1, pipeline=4, chunk=8))]:
             with pytest.raises(S.SlError) as e:
                 ctx.set_tune(dim, **sh)
