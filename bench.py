@@ -60,7 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--shapes", default=None,
                     help="JSON list of per-dimension launch shapes (sl_set_tune fields) used "
-                         "instead of the autotuner, e.g. to profile one fixed kernel")
+                         "instead of the autotuner, or 'default' for the library's defaults "
+                         "(e.g. to profile one fixed kernel)")
+    ap.add_argument("--nprob", type=int, default=256, help="problems of the batched workload")
     return ap.parse_args(argv)
 
 
@@ -212,6 +214,8 @@ def apply_shapes(ctx, shapes):
     if shapes is None:
         ctx.autotune(3)
         return
+    if shapes == "default":   # the library's default shapes, no autotuning
+        return
     for d, sh in enumerate(json.loads(shapes)):
         ctx.set_tune(d, **sh)
 
@@ -221,7 +225,7 @@ DEFAULT_STORE = {"4d": "mix_fp32", "2d": "mix_fp32", "batch": "mix_fp32", "6d": 
 DEFAULT_N = {"4d": 64, "2d": 512, "6d": 20, "1d": 1024}
 
 
-def make_problem(W, workload, n, storage):
+def make_problem(W, workload, n, storage, nprob=256):
     if workload == "4d":
         return W.config3(n=n, steps=1, storage=storage)
     if workload == "2d":
@@ -230,7 +234,7 @@ def make_problem(W, workload, n, storage):
         return W.config5(n=n, steps=1, storage=storage)
     if workload == "1d":
         return W.config1()
-    return W.config4(storage=storage)
+    return W.config4(nprob=nprob, storage=storage)
 
 
 class Arm:
@@ -239,14 +243,15 @@ class Arm:
 
     def __init__(self, S, W, args, storage, stream, shapes=None):
         self.workload = args.workload
-        self.p = make_problem(W, args.workload, args.n, storage)
+        self.p = make_problem(W, args.workload, args.n, storage, args.nprob)
         if self.workload == "batch":
             probs = self.p
             self.obj = S.Batch([q.grid for q in probs], [q.k for q in probs], storage, stream=stream)
             for i, q in enumerate(probs):
                 self.obj.project(i, q.nq, q.weights, q.params)
             self.obj.set_fields([q.field_list()[0] for q in probs])
-            self.obj.autotune(3)
+            if shapes != "default":
+                self.obj.autotune(3)
             self.dof = self.obj.info["dof"]
             self.state_bytes = self.obj.info["state_bytes"]
             self.sweeps = 3

@@ -310,7 +310,11 @@ sl_status sl_batch_profile_query(sl_batch* batch, int64_t* launches, double* ms,
  *                      <= 128 otherwise)
  *   fibres_per_thread  coefficient fibres one thread updates: 1, 2, 3, 4 or 9
  *                      along dimension 0; 1, 2 or 3 otherwise.  The scaled
- *                      stores always give a thread every fibre of its cell.
+ *                      stores need a cell-wide maximum: a thread takes every
+ *                      fibre of its cell (o^(d-1)) or a share of them, with
+ *                      the maximum exchanged in shared memory; the shares
+ *                      provided are 16, 8, 4 of 32 and 8, 4 of 16 fibres
+ *                      (k = 1), 9, 3 of 27 and 3 of 9 (k = 2), 4 of 16 (k = 3).
  *   unroll             along dimensions > 0: cells per walk step, 1, 2 or 4
  *                      (4 only with 1 or 2 fibres per thread); along
  *                      dimension 0: cells per thread, 1, or 16 / element size

@@ -159,11 +159,35 @@ int unit_vec_width(const sl_ctx* c)
     return c->g.n[0] % v == 0 ? v : 0;
 }
 
+// Fibres per thread the scaled stores provide: the whole cell, or a split of
+// its fibres over G cooperating threads (compiled splits only).
+std::vector<int> scaled_fts(const sl_ctx* c)
+{
+    const int64_t nf = c->nfib;
+    std::vector<int> v{int(nf)};
+    if (c->K == 1 && nf == 32) v.insert(v.end(), {16, 8, 4});
+    if (c->K == 1 && nf == 16) v.insert(v.end(), {8, 4});
+    if (c->K == 2 && nf == 27) v.insert(v.end(), {9, 3});
+    if (c->K == 2 && nf == 9) v.push_back(3);
+    if (c->K == 3 && nf == 16) v.push_back(4);
+    return v;
+}
+
+// The smallest provided fibre count of at most 16 values per thread, else
+// the whole cell.
+int scaled_default_ft(const sl_ctx* c)
+{
+    int best = int(c->nfib);
+    for (int f : scaled_fts(c))
+        if (f * c->O <= 16 && (best * c->O > 16 || f > best)) best = f;
+    return best;
+}
+
 // Default launch shape for a sweep along dimension m.
 void default_tune(sl_ctx* c, int m)
 {
     auto& t = c->tune[m];
-    t.ft = 1;
+    t.ft = is_scaled(c) ? scaled_default_ft(c) : 1;
     if (m == 0) {
         t.block = 256;
         t.unroll = unit_vec_width(c) ? unit_vec_width(c) : 1;
@@ -240,7 +264,7 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.K = c->K;
     L.mode = c->mode;
     L.unit = dim == 0;
-    L.ft = is_scaled(c) ? int(c->nfib) : c->tune[dim].ft;
+    L.ft = c->tune[dim].ft;
     L.unroll = c->tune[dim].unroll;
     L.pipeline = dim == 0 ? 0 : c->tune[dim].pipeline;
     L.block = c->tune[dim].block;
@@ -910,7 +934,7 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
     if (dim < 0 || dim >= c->ndim) return fail(const_cast<sl_ctx*>(c), SL_EINVAL, "dim out of range");
     const auto& t = c->tune[dim];
     out->block = t.block;
-    out->fibres_per_thread = is_scaled(c) ? int32_t(c->nfib) : t.ft;
+    out->fibres_per_thread = t.ft;
     out->unroll = t.unroll;
     out->pipeline = t.pipeline;
     out->chunk = dim == 0 ? 0 : int64_t(t.chunk);
@@ -945,8 +969,12 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
         if (dim > 0 && t->pipeline != 0 && t->block != 64 && t->block != 128)
             return fail(c, SL_EINVAL, "the cp.async walk runs with 64 or 128 threads per block");
         if (dim == 0 && t->pipeline != 0) return fail(c, SL_EINVAL, "pipeline applies to dimensions > 0");
-    } else if (t->pipeline != 0) {
-        return fail(c, SL_EINVAL, "the scaled stores have no cp.async pipeline");
+    } else {
+        if (t->pipeline != 0) return fail(c, SL_EINVAL, "the scaled stores have no cp.async pipeline");
+        const std::vector<int> ok = scaled_fts(c);
+        if (std::find(ok.begin(), ok.end(), t->fibres_per_thread) == ok.end())
+            return fail(c, SL_EINVAL, "fibres_per_thread %d is not a provided split of the %lld fibres",
+                        t->fibres_per_thread, (long long)c->nfib);
     }
     if (dim > 0) {
         const int64_t N = c->g.n[dim];
@@ -966,7 +994,7 @@ sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
     if (s != SL_OK) return s;
     auto& d = c->tune[dim];
     d.block = t->block;
-    d.ft = is_scaled(c) ? 1 : t->fibres_per_thread;
+    d.ft = t->fibres_per_thread;
     d.unroll = is_scaled(c) ? 1 : t->unroll;
     d.pipeline = is_scaled(c) || dim == 0 ? 0 : t->pipeline;
     d.chunk = dim == 0 ? 0 : uint32_t(t->chunk);
@@ -1001,7 +1029,12 @@ sl_status sl_autotune(sl_ctx* c, int reps)
         std::vector<sl_ctx::Tune> cand;
         if (m == 0) {
             if (is_scaled(c)) {
-                for (int b : {64, 128, 256}) cand.push_back({b, 1, 1, 0, 0});
+                for (int f : scaled_fts(c)) {
+                    if (f == c->nfib)
+                        for (int b : {64, 128, 256}) cand.push_back({b, f, 1, 0, 0});
+                    else
+                        cand.push_back({128, f, 1, 0, 0});
+                }
             } else {
                 for (int ft : {1, 2, 3, 4, 9})
                     if (ft <= c->nfib)
@@ -1013,7 +1046,12 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             }
         } else {
             if (is_scaled(c)) {
-                for (int b : {64, 128}) cand.push_back({b, 1, 1, chunk_for(c, m, 1), 0});
+                for (int f : scaled_fts(c)) {
+                    if (f == c->nfib)
+                        for (int b : {64, 128}) cand.push_back({b, f, 1, chunk_for(c, m, 1), 0});
+                    else
+                        cand.push_back({128, f, 1, chunk_for(c, m, 1), 0});
+                }
             } else {
                 const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
                 for (auto& x : fu)

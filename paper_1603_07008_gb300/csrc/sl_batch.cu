@@ -34,46 +34,66 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
 }
 
 // Persistent sweep over a work list: each block takes items blockIdx.x,
-// blockIdx.x + gridDim.x, ...; the problem's sweep geometry is copied into
-// shared memory once per item, and the problem's degree (0, 1 or 2) selects
-// the compiled variant (uniform across the block).  The loop is bounded by the
-// item count; no block waits on another.
-template <int MODE, int FT, int U>
-__global__ void __launch_bounds__(kBatchBlock) k_batch_sweep(const SweepArgs* __restrict__ args,
-                                                             const int32_t* __restrict__ kdeg,
-                                                             const BatchItem* __restrict__ items,
-                                                             int nitems, int unit)
+// blockIdx.x + gridDim.x, ...; the problem's sweep geometry is staged through
+// shared memory once per item and then held in registers, and the problem's
+// degree (0, 1 or 2) selects the compiled variant (uniform across the
+// block).  The loop is bounded by the item count; no block waits on another.
+// Sweeps along dimension 0 and along the other dimensions are separate
+// kernels, so each has its own register budget.
+template <bool UNIT>
+__device__ __forceinline__ SweepArgs stage_args(const SweepArgs* __restrict__ args, uint32_t prob,
+                                                uint32_t* raw)
 {
-    // raw storage: SweepArgs has host constructors, which shared memory cannot run
-    __shared__ __align__(16) unsigned char sa_raw[sizeof(SweepArgs)];
-    const SweepArgs& sa = *reinterpret_cast<const SweepArgs*>(sa_raw);
+    __syncthreads();   // the previous item is done with the staging buffer
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(args + prob);
+    for (int w = threadIdx.x; w < int(sizeof(SweepArgs) / 4); w += blockDim.x) raw[w] = src[w];
+    __syncthreads();
+    return *reinterpret_cast<const SweepArgs*>(raw);
+}
+
+template <int MODE, int FT>
+__global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __restrict__ args,
+                                                            const int32_t* __restrict__ kdeg,
+                                                            const BatchItem* __restrict__ items,
+                                                            int nitems, int reps)
+{
     static_assert(sizeof(SweepArgs) % 4 == 0, "word copy");
+    __shared__ __align__(16) uint32_t raw[sizeof(SweepArgs) / 4];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
-        __syncthreads();   // the previous item is done with sa
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(args + item.prob);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(sa_raw);
-        for (int w = threadIdx.x; w < int(sizeof(SweepArgs) / 4); w += blockDim.x) dst[w] = src[w];
-        __syncthreads();
+        const SweepArgs a = stage_args<true>(args, item.prob, raw);
         const int K = kdeg[item.prob];
-        const uint32_t idx = item.start + threadIdx.x;
-        if (unit) {
-            if (idx < sa.cells) {
-                const int fbase = int(item.grp) * FT;
-                switch (K) {
-                case 0: unit_cell<0, MODE, FT>(sa, idx, fbase); break;
-                case 1: unit_cell<1, MODE, FT>(sa, idx, fbase); break;
-                default: unit_cell<2, MODE, FT>(sa, idx, fbase); break;
-                }
+        const int fbase = int(item.grp) * FT;
+        // reps tiles of kBatchBlock consecutive cells
+        for (int r = 0; r < reps; ++r) {
+            const uint32_t c = item.start + threadIdx.x + uint32_t(r) * kBatchBlock;
+            if (c >= a.cells) break;
+            switch (K) {
+            case 0: unit_cell<0, MODE, FT>(a, c, fbase); break;
+            case 1: unit_cell<1, MODE, FT>(a, c, fbase); break;
+            default: unit_cell<2, MODE, FT>(a, c, fbase); break;
             }
-        } else {
-            const LineSetup L = line_setup(sa, idx, item.grp, item.chunk, FT);
-            if (L.active) {
-                switch (K) {
-                case 0: strided_line<0, MODE, FT, U>(sa, L); break;
-                case 1: strided_line<1, MODE, FT, U>(sa, L); break;
-                default: strided_line<2, MODE, FT, U>(sa, L); break;
-                }
+        }
+    }
+}
+
+template <int MODE, int FT, int U>
+__global__ void __launch_bounds__(kBatchBlock) k_batch_strided(const SweepArgs* __restrict__ args,
+                                                               const int32_t* __restrict__ kdeg,
+                                                               const BatchItem* __restrict__ items,
+                                                               int nitems)
+{
+    __shared__ __align__(16) uint32_t raw[sizeof(SweepArgs) / 4];
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const BatchItem item = items[it];
+        const SweepArgs a = stage_args<false>(args, item.prob, raw);
+        const int K = kdeg[item.prob];
+        const LineSetup L = line_setup(a, item.start + threadIdx.x, item.grp, item.chunk, FT);
+        if (L.active) {
+            switch (K) {
+            case 0: strided_line<0, MODE, FT, U>(a, L); break;
+            case 1: strided_line<1, MODE, FT, U>(a, L); break;
+            default: strided_line<2, MODE, FT, U>(a, L); break;
             }
         }
     }
@@ -83,20 +103,25 @@ namespace {
 
 template <int MODE, int FT, int U>
 cudaError_t launch_b(const SweepArgs* a, const int32_t* k, const BatchItem* items, int nitems,
-                     int unit, int blocks, cudaStream_t st)
+                     int unit, int reps, int blocks, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    k_batch_sweep<MODE, FT, U><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, unit);
+    if (unit)
+        k_batch_unit<MODE, FT><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, reps);
+    else
+        k_batch_strided<MODE, FT, U><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems);
     return cudaGetLastError();
 }
 
 template <int MODE, int FT, int U>
-int occ()
+int occ(int unit)
 {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_sweep<MODE, FT, U>, kBatchBlock, 0) !=
-        cudaSuccess)
-        return 1;
+    cudaError_t e = unit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_unit<MODE, FT>,
+                                                                         kBatchBlock, 0)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_strided<MODE, FT, U>,
+                                                                         kBatchBlock, 0);
+    if (e != cudaSuccess) return 1;
     return n < 1 ? 1 : n;
 }
 
@@ -117,15 +142,15 @@ int occ()
 
 cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
                                const int32_t* d_kdeg, const BatchItem* d_items, int nitems,
-                               int unit, int blocks, cudaStream_t st)
+                               int unit, int reps, int blocks, cudaStream_t st)
 {
-    SL_BATCH_SWITCH(return (launch_b<MD, F, UU>(d_args, d_kdeg, d_items, nitems, unit, blocks, st)))
+    SL_BATCH_SWITCH(return (launch_b<MD, F, UU>(d_args, d_kdeg, d_items, nitems, unit, reps, blocks, st)))
     return cudaErrorInvalidValue;
 }
 
-int batch_sweep_occupancy(int mode, int ft, int unroll)
+int batch_sweep_occupancy(int mode, int ft, int unroll, int unit)
 {
-    SL_BATCH_SWITCH(return (occ<MD, F, UU>()))
+    SL_BATCH_SWITCH(return (occ<MD, F, UU>(unit)))
     return 1;
 }
 

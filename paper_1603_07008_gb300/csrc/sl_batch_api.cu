@@ -44,8 +44,9 @@ struct sl_batch {
     int nitems[SL_MAX_DIM] = {0};
     struct Tune {
         int ft = 1;
-        int unroll = 1;
-        int chunk_div = 1;
+        int unroll = 1;   // cells per walk step (dimensions > 0)
+        int rows = 64;    // rows per work item (dimensions > 0)
+        int reps = 4;     // cell tiles per work item (dimension 0)
     } tune[SL_MAX_DIM];
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
@@ -100,15 +101,16 @@ sl_status rebuild_dim(sl_batch* b, int m)
         c->tune[m].unroll = t.unroll;
         c->tune[m].pipeline = 0;
         const int64_t N = c->g.n[m];
-        c->tune[m].chunk = m == 0 ? 0 : uint32_t(std::max<int64_t>(1, (N + t.chunk_div - 1) / t.chunk_div));
+        c->tune[m].chunk = m == 0 ? 0 : uint32_t(std::min<int64_t>(N, t.rows));
         const int sd = natural_shift_dim(c, m);
         for (int par = 0; par < 2; ++par) args[size_t(par) * b->nprob + p] = make_args_parity(c, m, sd, par);
         const SweepArgs& a = args[p];
         const uint32_t nfg = uint32_t(a.nfg);
         if (m == 0) {
-            const uint32_t tiles = (a.cells + kBatchBlock - 1) / kBatchBlock;
+            const uint32_t span = uint32_t(kBatchBlock * t.reps);
+            const uint32_t tiles = (a.cells + span - 1) / span;
             for (uint32_t g = 0; g < nfg; ++g)
-                for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * kBatchBlock, g, 0});
+                for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * span, g, 0});
         } else {
             const uint32_t tiles = (a.lines + kBatchBlock - 1) / kBatchBlock;
             const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
@@ -151,10 +153,10 @@ sl_status batch_sweep(sl_batch* b, int m, double tau)
         SLB_CUDA(b, cudaEventRecord(e0, b->st));
     }
     const auto& t = b->tune[m];
-    const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll);
+    const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
     SLB_CUDA(b, launch_batch_sweep(b->mode, t.ft, t.unroll,
                                    b->d_args + (size_t(m) * 2 + b->parity) * b->nprob, b->d_kdeg,
-                                   b->d_items[m], b->nitems[m], m == 0, blocks, b->st));
+                                   b->d_items[m], b->nitems[m], m == 0, t.reps, blocks, b->st));
     if (prof) {
         SLB_CUDA(b, cudaEventRecord(e1, b->st));
         b->ev.emplace_back(e0, e1);
@@ -330,13 +332,14 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
                         b->st) != cudaSuccess ||
         cudaStreamSynchronize(b->st) != cudaSuccess)
         return cleanup(fail(nullptr, SL_ECUDA, "uploading batch tables"));
-    // default shapes: the most fibres per thread every problem allows, two
-    // cells per walk step, whole lines
+    // default shapes: the most fibres per thread every problem allows, four
+    // cells per walk step, 64-row work items, four cell tiles per item
     const int ftmax = std::min(2, min_fibres(b));
     for (int m = 0; m < b->ndim; ++m) {
         b->tune[m].ft = ftmax;
         b->tune[m].unroll = m == 0 ? 1 : 4;
-        b->tune[m].chunk_div = 1;
+        b->tune[m].rows = 64;
+        b->tune[m].reps = 4;
         sl_status s = rebuild_dim(b, m);
         if (s != SL_OK) {
             fail(nullptr, s, "%s", b->err.c_str());
@@ -502,10 +505,10 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
         std::vector<sl_batch::Tune> cand;
         for (int ft = 1; ft <= ftmax; ++ft) {
             if (m == 0) {
-                cand.push_back({ft, 1, 1});
+                for (int r : {1, 4, 8}) cand.push_back({ft, 1, 64, r});
             } else {
                 for (int u : {1, 4})
-                    for (int cd : {1, 2, 4}) cand.push_back({ft, u, cd});
+                    for (int rows : {32, 64, 128}) cand.push_back({ft, u, rows, 4});
             }
         }
         sl_batch::Tune best = b->tune[m];
@@ -521,9 +524,10 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
             for (int r = -1; r < reps && e == cudaSuccess; ++r) {
                 if (r == 0) e = cudaEventRecord(e0, b->st);
                 if (e != cudaSuccess) break;
-                const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll);
+                const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
                 e = launch_batch_sweep(b->mode, t.ft, t.unroll, b->d_args + (size_t(m) * 2 + par) * b->nprob,
-                                       b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, blocks, b->st);
+                                       b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, t.reps, blocks,
+                                       b->st);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);

@@ -169,10 +169,10 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
 
 // ---------------------------------------------------------------- batches
 
-// One work item of a batched sweep: threads cover the `kBatchBlock`
-// consecutive cells (sweep along dimension 0) or lines (other dimensions)
-// starting at `start` of problem `prob`, for fibre group `grp` and chunk
-// `chunk` of the lines.
+// One work item of a batched sweep: the threads cover `reps` tiles of
+// `kBatchBlock` consecutive cells (sweep along dimension 0), or
+// `kBatchBlock` consecutive lines walking one chunk of rows (other
+// dimensions), starting at `start` of problem `prob`, for fibre group `grp`.
 constexpr int kBatchBlock = 128;
 constexpr int kBatchMaxK = 2;   // degrees compiled into the batched sweep
 struct BatchItem {
@@ -205,11 +205,12 @@ struct BatchMass {
 
 cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int nprob, int maxclass,
                             double tau, cudaStream_t st);
+// unit = 1: sweep along dimension 0, each item covering reps * kBatchBlock cells.
 cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
                                const int32_t* d_kdeg, const BatchItem* d_items, int nitems,
-                               int unit, int blocks, cudaStream_t st);
+                               int unit, int reps, int blocks, cudaStream_t st);
 // Resident blocks per SM of the batched sweep kernel for (mode, ft, unroll).
-int batch_sweep_occupancy(int mode, int ft, int unroll);
+int batch_sweep_occupancy(int mode, int ft, int unroll, int unit);
 cudaError_t launch_batch_mass(const BatchMass* d_desc, int nprob, int parity, double* d_out,
                               cudaStream_t st);
 

@@ -701,6 +701,175 @@ __global__ void __launch_bounds__(128) k_sweep_strided(const SweepArgs a)
     strided_line<K, MODE, FT, U>(a, L);
 }
 
+// ---------------------------------------------------------------- scaled stores, cooperative
+
+// The scaled stores need the maximum over every coefficient of a new cell.
+// When a cell has too many fibres for one thread's registers, G threads share
+// it: a block holds 32 cells or lines (threadIdx.x) times G fibre groups of
+// NF/G fibres (threadIdx.y).  Each thread computes its fibres, writes its
+// local maximum to shared memory, and after one block barrier every thread of
+// the cell reads the G maxima and encodes its values with the common scale.
+// The strided form alternates two shared buffers, so one barrier per row
+// suffices: a thread can only overwrite a buffer after every thread has
+// passed the next barrier, i.e. has finished reading it.  All threads of a
+// block walk the same rows (the chunk is per block), and threads past the
+// last line or cell still take part in every barrier.
+
+template <int K, int MODE, int FG>
+__device__ __forceinline__ void coop_combine(const Mats<K, MODE>& M, const CellVals<K, MODE, FG>& a,
+                                             const CellVals<K, MODE, FG>& b, bool mean,
+                                             CellVals<K, MODE, FG>& out)
+{
+    if (mean)
+        combine<K, MODE, FG, true>(M, a, b, out);
+    else
+        combine<K, MODE, FG, false>(M, a, b, out);
+}
+
+template <int K, int MODE, int FG>
+__device__ __forceinline__ void coop_load(const Planes& p, int64_t pstride, uint32_t c,
+                                          const int (&jb)[FG], int ostride, bool mean,
+                                          CellVals<K, MODE, FG>& cv)
+{
+    if (mean)
+        load_cell<K, MODE, FG, true>(p, pstride, c, jb, ostride, cv);
+    else
+        load_cell<K, MODE, FG, false>(p, pstride, c, jb, ostride, cv);
+}
+
+// Encode and store with the scale 1/inv; group 0 also stores the mean and s.
+template <int K, int MODE, int FG>
+__device__ __forceinline__ void coop_store(const Planes& p, int64_t pstride, uint32_t c,
+                                           const int (&jb)[FG], int ostride, bool mean, float s,
+                                           float inv, const CellVals<K, MODE, FG>& cv)
+{
+    using T = typename St<MODE>::T;
+    constexpr int O = K + 1;
+#pragma unroll
+    for (int u = 0; u < FG; ++u)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            if (mean && u == 0 && l == 0) {
+                p.mean[c] = cv.m;
+                p.scale[c] = s;
+            } else {
+                st_raw(plane_ptr_w<T>(p.hi, pstride, jb[u] + l * ostride) + c, cv.v[u][l] * inv);
+            }
+        }
+}
+
+template <int K, int MODE, int FG>
+__device__ __forceinline__ float local_max(const CellVals<K, MODE, FG>& cv)
+{
+    float mx = 0.0f;
+#pragma unroll
+    for (int u = 0; u < FG; ++u)
+#pragma unroll
+        for (int l = 0; l < K + 1; ++l) mx = fmaxf(mx, fabsf(cv.v[u][l]));   // v[0][0] of the mean group is 0
+    return mx;
+}
+
+template <int K, int MODE, int NF, int G>
+__global__ void __launch_bounds__(32 * G) k_sweep_unit_coop(const SweepArgs a)
+{
+    static_assert(St<MODE>::scaled && NF % G == 0, "cooperative scaled sweep");
+    constexpr int FG = NF / G;
+    constexpr int O = K + 1;
+    __shared__ float smax[G][32];
+    const int lane = threadIdx.x, g = threadIdx.y;
+    const uint32_t c = blockIdx.x * 32 + lane;
+    const bool active = c < a.cells;
+    const bool mean = g == 0;
+    const uint32_t cc = active ? c : 0;
+    const uint32_t line = a.fdN.div(cc);
+    const uint32_t i = cc - line * a.N;
+    const uint32_t cls = shift_class(a, 0, line);
+    const int32_t sig = __ldg(a.tab.sigma + cls);
+    int32_t ia = int32_t(i) - sig;
+    ia += ia < 0 ? int32_t(a.N) : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? int32_t(a.N) : 0;
+    int jb[FG];
+#pragma unroll
+    for (int u = 0; u < FG; ++u) jb[u] = (g * FG + u) * O;   // fibre stride 1 along dimension 0
+    Mats<K, MODE> M;
+    M.template load<true>(a.tab, cls);
+    CellVals<K, MODE, FG> va, vb, out;
+    if (active) {
+        coop_load<K, MODE, FG>(a.src, a.pstride, cc - i + uint32_t(ia), jb, 1, mean, va);
+        coop_load<K, MODE, FG>(a.src, a.pstride, cc - i + uint32_t(ib), jb, 1, mean, vb);
+        coop_combine<K, MODE, FG>(M, va, vb, mean, out);
+        smax[g][lane] = local_max<K, MODE, FG>(out);
+    }
+    __syncthreads();
+    if (!active) return;
+    float mx = 0.0f;
+#pragma unroll
+    for (int q = 0; q < G; ++q) mx = fmaxf(mx, smax[q][lane]);
+    float s, inv;
+    pow2_scale(mx, s, inv);
+    coop_store<K, MODE, FG>(a.dst, a.pstride, c, jb, 1, mean, s, inv, out);
+}
+
+template <int K, int MODE, int NF, int G>
+__global__ void __launch_bounds__(32 * G) k_sweep_strided_coop(const SweepArgs a)
+{
+    static_assert(St<MODE>::scaled && NF % G == 0, "cooperative scaled sweep");
+    constexpr int FG = NF / G;
+    constexpr int O = K + 1;
+    __shared__ float smax[2][G][32];
+    const int lane = threadIdx.x, g = threadIdx.y;
+    const uint32_t line = blockIdx.x * 32 + lane;
+    const bool active = line < a.lines;
+    const bool mean = g == 0;
+    const LineSetup L = line_setup(a, active ? line : 0, 0, blockIdx.y, 1);
+    if (!L.active) return;   // the chunk is empty for the whole block
+    int jb[FG];
+#pragma unroll
+    for (int u = 0; u < FG; ++u) jb[u] = fibre_base(g * FG + u, O, a.ostride);
+    Mats<K, MODE> M;
+    M.template load<true>(a.tab, L.cls);
+    const int32_t N = int32_t(a.N);
+    int32_t ia = int32_t(L.i0) - L.sig;
+    ia += ia < 0 ? N : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? N : 0;
+    // the loads of row i+1 are issued before row i's barrier and stores
+    CellVals<K, MODE, FG> prev, cur;
+    if (active) {
+        coop_load<K, MODE, FG>(a.src, a.pstride, L.base + uint32_t(ib) * a.inner, jb, a.ostride, mean,
+                               prev);
+        coop_load<K, MODE, FG>(a.src, a.pstride, L.base + uint32_t(ia) * a.inner, jb, a.ostride, mean,
+                               cur);
+    }
+    int buf = 0;
+    for (uint32_t i = L.i0; i < L.i1; ++i) {
+        ++ia;
+        if (ia == N) ia = 0;
+        CellVals<K, MODE, FG> nxt, out;
+        if (active) {
+            if (i + 1 < L.i1)
+                coop_load<K, MODE, FG>(a.src, a.pstride, L.base + uint32_t(ia) * a.inner, jb, a.ostride,
+                                       mean, nxt);
+            coop_combine<K, MODE, FG>(M, cur, prev, mean, out);
+            smax[buf][g][lane] = local_max<K, MODE, FG>(out);
+        }
+        __syncthreads();
+        if (active) {
+            float mx = 0.0f;
+#pragma unroll
+            for (int q = 0; q < G; ++q) mx = fmaxf(mx, smax[buf][q][lane]);
+            float s, inv;
+            pow2_scale(mx, s, inv);
+            coop_store<K, MODE, FG>(a.dst, a.pstride, L.base + i * a.inner, jb, a.ostride, mean, s, inv,
+                                    out);
+            prev = cur;
+            cur = nxt;
+        }
+        buf ^= 1;
+    }
+}
+
 // ---------------------------------------------------------------- strided, cp.async ring
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)

@@ -1,16 +1,59 @@
 // sl_sweep_scaled.cu -- instantiations and launcher of the sweep kernels for
-// the FP64-mean / per-cell-scaled BF16 or FP16 store.  One thread holds every
-// fibre of its cell, because the new scale is the maximum over the whole
-// cell; the fibre count o^(d-1) is therefore a template parameter.
+// the FP64-mean / per-cell-scaled BF16 or FP16 store.  The new scale is the
+// maximum over the whole cell, so one thread holds every fibre of its cell
+// (up to 16 values) or G threads share it through shared memory; the fibre
+// count o^(d-1) is therefore a template parameter.
 #include "sl_sweep.cuh"
 
 namespace sl {
 
 namespace {
 
+// Cells are shared by G threads of NF/G fibres each when the launch asks for
+// fewer fibres per thread than the cell has (G is a power of o, so it
+// divides the fibre count); otherwise one thread holds the whole cell.
+template <int K, int MODE, int NF, int G>
+cudaError_t launch_coop(const SweepLaunch& L)
+{
+    const SweepArgs& a = L.args;
+    if (a.nfib != NF || a.nfg != 1) return cudaErrorInvalidValue;
+    const dim3 block(32, G);
+    if (L.unit) {
+        k_sweep_unit_coop<K, MODE, NF, G><<<dim3((a.cells + 31) / 32), block, 0, L.stream>>>(a);
+    } else {
+        const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
+        k_sweep_strided_coop<K, MODE, NF, G><<<dim3((a.lines + 31) / 32, nchunk), block, 0, L.stream>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 template <int K, int MODE, int NF>
 cudaError_t launch_one(const SweepLaunch& L)
 {
+    if (L.ft != NF) {
+        const int G = NF / (L.ft > 0 ? L.ft : 1);
+        if (G * L.ft != NF) return cudaErrorInvalidValue;
+        if constexpr (K == 1 && NF == 32) {
+            if (G == 2) return launch_coop<K, MODE, NF, 2>(L);
+            if (G == 4) return launch_coop<K, MODE, NF, 4>(L);
+            if (G == 8) return launch_coop<K, MODE, NF, 8>(L);
+        }
+        if constexpr (K == 1 && NF == 16) {
+            if (G == 2) return launch_coop<K, MODE, NF, 2>(L);
+            if (G == 4) return launch_coop<K, MODE, NF, 4>(L);
+        }
+        if constexpr (K == 2 && NF == 27) {
+            if (G == 3) return launch_coop<K, MODE, NF, 3>(L);
+            if (G == 9) return launch_coop<K, MODE, NF, 9>(L);
+        }
+        if constexpr (K == 2 && NF == 9) {
+            if (G == 3) return launch_coop<K, MODE, NF, 3>(L);
+        }
+        if constexpr (K == 3 && NF == 16) {
+            if (G == 4) return launch_coop<K, MODE, NF, 4>(L);
+        }
+        return cudaErrorInvalidValue;
+    }
     const SweepArgs& a = L.args;
     if (a.nfib != NF || a.nfg != 1) return cudaErrorInvalidValue;
     if (L.unit) {

@@ -418,27 +418,43 @@ def ctx_stored(u, storage):
     return v
 
 
+SCALED_SPLITS = {((1, 6)): [32, 16, 8, 4], ((1, 5)): [16, 8, 4], ((2, 4)): [27, 9, 3],
+                 ((2, 3)): [9, 3], ((3, 3)): [16, 4], ((1, 4)): [8]}
+
+
 @pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
-def test_scaled_launch_shapes_identical(storage):
-    n = (5, 7, 3, 2)
-    k = 1
+@pytest.mark.parametrize("n,k", [((5, 7, 3, 2), 1), ((3, 2, 2, 3, 2, 2), 1), ((3, 4, 2, 3, 2), 1),
+                                 ((4, 3, 3, 2), 2), ((4, 3, 5), 3), ((5, 3, 4), 2)])
+def test_scaled_launch_shapes_identical(storage, n, k):
+    """Every block size and every split of a cell's fibres over cooperating
+    threads gives bit-identical results (the cell maximum does not depend
+    on the order it is taken in)."""
     rng = np.random.default_rng(5)
     u = _rand(n, k, 6)
+    splits = SCALED_SPLITS[(k, len(n))]
     with S.Context(_grid(n), k, storage) as ctx:
         for dim in range(len(n)):
             s = _shifts(rng, n, dim, -1)
             ctx.set_coeffs(u)
             ctx.advect(dim, -1, s)
             ref = ctx.get_coeffs()
-            for b in (32, 64, 128):
-                sh = dict(block=b) if dim == 0 else dict(block=b, chunk=2)
-                ctx.set_tune(dim, **sh)
-                ctx.set_coeffs(u)
-                ctx.advect(dim, -1, s)
-                assert np.array_equal(ctx.get_coeffs(), ref)
+            for f in splits:
+                for b in (32, 64, 128):
+                    sh = dict(block=b, fibres_per_thread=f)
+                    if dim > 0:
+                        sh["chunk"] = min(2, n[dim])
+                    ctx.set_tune(dim, **sh)
+                    ctx.set_coeffs(u)
+                    ctx.advect(dim, -1, s)
+                    assert np.array_equal(ctx.get_coeffs(), ref), (dim, f, b)
 
 
 def test_set_tune_rejects_shapes_not_built():
+    with S.Context(_grid((4, 3, 3, 2)), 2, "mix_bf16") as ctx:
+        for f in (1, 2, 5, 26):
+            with pytest.raises(S.SlError) as e:
+                ctx.set_tune(1, block=64, fibres_per_thread=f, chunk=2)
+            assert e.value.status == S.SL_EINVAL
     with S.Context(_grid((8, 8)), 2, "mix_fp32") as ctx:
         for dim, sh in [(0, dict(block=512)), (0, dict(block=100)), (0, dict(block=128, fibres_per_thread=5)),
                         (1, dict(block=256, fibres_per_thread=1, unroll=1, chunk=8)),
@@ -470,3 +486,26 @@ def test_autotune_keeps_state_and_results():
         for d in range(4):
             t = b.get_tune(d)
             assert t["block"] >= 32
+
+
+@pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
+@pytest.mark.parametrize("n,k", [((3, 4, 2, 3, 2), 1), ((4, 3, 5), 3), ((5, 2, 3, 2, 2, 2), 1),
+                                 ((3, 4, 3, 2), 2), ((5, 3, 4), 2)])
+def test_scaled_single_sweeps_every_fibre_split(storage, n, k):
+    """Cells with more than 16 values are shared by several threads (a
+    block-wide maximum for the scale); fewer are one thread's.  Both against
+    the oracle applied to exactly the stored input; the FP64 mean row to
+    rounding."""
+    rng = np.random.default_rng(31)
+    u = _rand(n, k, 32)
+    with S.Context(_grid(n), k, storage) as ctx:
+        for dim in range(len(n)):
+            for sd in [-1, (dim + 1) % len(n)]:
+                s = _shifts(rng, n, dim, sd)
+                ctx.set_coeffs(u)
+                stored = ctx.get_coeffs()
+                ctx.advect(dim, sd, s)
+                got = ctx.get_coeffs()
+                ref = O.sweep(stored, n, k, dim, sd, s)
+                assert O.rel_l2(got, ref, k, len(n)) <= 5e-3, (dim, sd)
+                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-14 * np.max(np.abs(ref))
