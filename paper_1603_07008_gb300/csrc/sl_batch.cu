@@ -34,34 +34,22 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
 }
 
 // Persistent sweep over a work list: each block takes items blockIdx.x,
-// blockIdx.x + gridDim.x, ...; the problem's sweep geometry is staged through
-// shared memory once per item and then held in registers, and the problem's
-// degree (0, 1 or 2) selects the compiled variant (uniform across the
-// block).  The loop is bounded by the item count; no block waits on another.
-// Sweeps along dimension 0 and along the other dimensions are separate
-// kernels, so each has its own register budget.
-template <bool UNIT>
-__device__ __forceinline__ SweepArgs stage_args(const SweepArgs* __restrict__ args, uint32_t prob,
-                                                uint32_t* raw)
-{
-    __syncthreads();   // the previous item is done with the staging buffer
-    const uint32_t* src = reinterpret_cast<const uint32_t*>(args + prob);
-    for (int w = threadIdx.x; w < int(sizeof(SweepArgs) / 4); w += blockDim.x) raw[w] = src[w];
-    __syncthreads();
-    return *reinterpret_cast<const SweepArgs*>(raw);
-}
-
+// blockIdx.x + gridDim.x, ...; every thread reads the problem's sweep
+// geometry straight from the (read-only, L1-cached) argument array, so items
+// need no block barrier, and the problem's degree (0, 1 or 2) selects the
+// compiled variant (uniform across the block).  The loop is bounded by the
+// item count; no block waits on another.  Sweeps along dimension 0 and along
+// the other dimensions are separate kernels, so each has its own register
+// budget.
 template <int MODE, int FT>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __restrict__ args,
                                                             const int32_t* __restrict__ kdeg,
                                                             const BatchItem* __restrict__ items,
                                                             int nitems, int reps)
 {
-    static_assert(sizeof(SweepArgs) % 4 == 0, "word copy");
-    __shared__ __align__(16) uint32_t raw[sizeof(SweepArgs) / 4];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
-        const SweepArgs a = stage_args<true>(args, item.prob, raw);
+        const SweepArgs a = args[item.prob];
         const int K = kdeg[item.prob];
         const int fbase = int(item.grp) * FT;
         // reps tiles of kBatchBlock consecutive cells
@@ -83,10 +71,9 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_strided(const SweepArgs* 
                                                                const BatchItem* __restrict__ items,
                                                                int nitems)
 {
-    __shared__ __align__(16) uint32_t raw[sizeof(SweepArgs) / 4];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
-        const SweepArgs a = stage_args<false>(args, item.prob, raw);
+        const SweepArgs a = args[item.prob];
         const int K = kdeg[item.prob];
         const LineSetup L = line_setup(a, item.start + threadIdx.x, item.grp, item.chunk, FT);
         if (L.active) {
