@@ -28,14 +28,16 @@
 // values are then computed and stored twice by the same thread.
 //
 // Precision (split store): the cell mean c_{0..0} lives in an FP64 plane.
-// Its row is computed in FP64 in the form
+// Its row is computed in the form
 //     c'_0 = a_0 + alpha (b_0 - a_0) + sum_{l>=1} A_0l (a_l - b_l),
 // which uses the exact identities A_00 + B_00 = 1 and B_0l = -A_0l (l >= 1)
 // of the projection, so the sum over a line telescopes and mass is conserved
-// to FP64 rounding (Sec. II-A, III-A).  The other rows of the mean's fibre
-// take the l = 0 term as the FP64 difference A_j0 (a_0 - b_0) (B_j0 = -A_j0),
-// rounded once to the arithmetic type; everything else is computed in the
-// arithmetic type of the mode (FP64, or FP32 for the mixed modes).
+// to FP64 rounding (Sec. II-A, III-A).  The donor part is FP64; in the
+// low-precision stores the sum is formed as FP64 differences of per-cell FP32
+// sums (see combine), which still telescope exactly.  The other rows of the
+// mean's fibre use B_j0 = -A_j0 for their l = 0 term; everything else is
+// computed in the arithmetic type of the mode (FP64, or FP32 for the mixed
+// modes).
 #pragma once
 
 #include "sl_internal.cuh"
@@ -177,22 +179,52 @@ __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K
 #pragma unroll
     for (int u = 0; u < FT; ++u) {
         if (MEAN && u == 0) {
-            double d = a.m + M.alpha * (b.m - a.m);
+            if constexpr (sizeof(R) == 8) {
+                double d = a.m + M.alpha * (b.m - a.m);
 #pragma unroll
-            for (int l = 1; l < O; ++l) d += M.a0[l] * (double(a.v[0][l]) - double(b.v[0][l]));
-            out.m = d;
-            out.v[0][0] = 0;
-            const double dm = a.m - b.m;
+                for (int l = 1; l < O; ++l) d += M.a0[l] * (a.v[0][l] - b.v[0][l]);
+                out.m = d;
+                const double dm = a.m - b.m;
 #pragma unroll
-            for (int j = 1; j < O; ++j) {
-                R acc = R(M.aj0[j] * dm);
+                for (int j = 1; j < O; ++j) {
+                    R acc = R(M.aj0[j] * dm);
+#pragma unroll
+                    for (int l = 1; l < O; ++l) {
+                        acc = fma(M.a[j][l], a.v[0][l], acc);
+                        acc = fma(M.b[j][l], b.v[0][l], acc);
+                    }
+                    out.v[0][j] = acc;
+                }
+            } else {
+                // Low-precision stores: the higher coefficients enter the mean
+                // row through G(c) = sum_{l>=1} fl32(A_0l c_l), a function of
+                // one cell (the matrices are fixed along a line), so the FP64
+                // differences G(a) - G(b) telescope exactly over the line and
+                // the mass stays conserved to FP64 rounding; only the donor
+                // part a_0 + alpha (b_0 - a_0) and the differences use the
+                // (slow) FP64 pipe.  The l = 0 term of the other rows uses
+                // a_0 - b_0 rounded once to FP32.
+                float ga = 0.0f, gb = 0.0f;
 #pragma unroll
                 for (int l = 1; l < O; ++l) {
-                    acc = fma(M.a[j][l], a.v[0][l], acc);
-                    acc = fma(M.b[j][l], b.v[0][l], acc);
+                    ga = fmaf(M.a[0][l], a.v[0][l], ga);
+                    gb = fmaf(M.a[0][l], b.v[0][l], gb);
                 }
-                out.v[0][j] = acc;
+                const double t = b.m - a.m;
+                out.m = fma(M.alpha, t, a.m) + (double(ga) - double(gb));
+                const float dm = float(-t);
+#pragma unroll
+                for (int j = 1; j < O; ++j) {
+                    R acc = M.a[j][0] * dm;
+#pragma unroll
+                    for (int l = 1; l < O; ++l) {
+                        acc = fma(M.a[j][l], a.v[0][l], acc);
+                        acc = fma(M.b[j][l], b.v[0][l], acc);
+                    }
+                    out.v[0][j] = acc;
+                }
             }
+            out.v[0][0] = 0;
         } else {
 #pragma unroll
             for (int j = 0; j < O; ++j) {

@@ -140,7 +140,9 @@ def test_mixed_fp32_single_sweeps(n, k):
                 # against the oracle applied to exactly what was stored
                 ref = O.sweep(stored, n, k, dim, sd, s)
                 assert O.rel_l2(got, ref, k, len(n)) <= 1e-6
-                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-14 * np.max(np.abs(ref))
+                # the mean row adds the FP32 higher coefficients' contribution
+                # rounded in FP32: at most a few FP32 ulps of those terms
+                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(stored[:, 1:]))
 
 
 def _strang_oracle(p, steps):
@@ -508,4 +510,4 @@ def test_scaled_single_sweeps_every_fibre_split(storage, n, k):
                 got = ctx.get_coeffs()
                 ref = O.sweep(stored, n, k, dim, sd, s)
                 assert O.rel_l2(got, ref, k, len(n)) <= 5e-3, (dim, sd)
-                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-14 * np.max(np.abs(ref))
+                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(stored[:, 1:]))
