@@ -113,6 +113,12 @@ typedef struct {
     int64_t alloc_bytes;    /* device bytes allocated by the context (both copies + tables) */
     int32_t degree;
     int32_t storage;        /* sl_storage */
+    int32_t record_slots;   /* 0: planar store (coefficient J >= 1 in plane J-1, planes
+                               plane_stride apart); R > 0: the scaled store keeps the
+                               higher coefficients of every cell in one record of R
+                               16-bit slots, slot J holding coefficient J (slot 0 and
+                               slots >= o^d are zero), chosen for 6D/5D with degree 1
+                               and 3D with degree 3 */
 } sl_info;
 
 /* ---------------------------------------------------------------- setup */
@@ -173,7 +179,9 @@ sl_status sl_get_cells(sl_ctx* ctx, const int64_t* cells, int64_t ncells, double
  *   mean  [cells]            FP64 cell means c_{0..0}
  *   hi    [o^d - 1][cells]   coefficient J >= 1 at hi[(J-1)*cells + cell], in
  *                            the store's element type (FP64, FP32, or the
- *                            BF16 / FP16 bit patterns)
+ *                            BF16 / FP16 bit patterns); with cell records
+ *                            (sl_info.record_slots = R > 0) hi is [cells][R]
+ *                            and coefficient J is hi[cell*R + J]
  *   scale [cells]            FP32 per-cell scales (scaled modes; NULL otherwise)
  * sl_set_planes enqueues the host-to-device copies on the context's stream
  * and returns; the host arrays must stay valid and unchanged until the stream

@@ -62,7 +62,7 @@ class sl_info(ctypes.Structure):
     _fields_ = [("cells", ctypes.c_int64), ("ncoef", ctypes.c_int64), ("dof", ctypes.c_int64),
                 ("plane_stride", ctypes.c_int64), ("state_bytes", ctypes.c_int64),
                 ("alloc_bytes", ctypes.c_int64), ("degree", ctypes.c_int32),
-                ("storage", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("record_slots", ctypes.c_int32)]
 
 
 def make_grid(g) -> sl_grid:
@@ -252,7 +252,10 @@ def plane_arrays(ctx):
     info = sl_get_info(ctx)
     st = info["storage"]
     mean = np.empty(info["cells"], dtype=np.float64)
-    hi = np.empty((info["ncoef"] - 1, info["cells"]), dtype=_ELEM[st])
+    if info["record_slots"]:
+        hi = np.empty((info["cells"], info["record_slots"]), dtype=_ELEM[st])
+    else:
+        hi = np.empty((info["ncoef"] - 1, info["cells"]), dtype=_ELEM[st])
     scale = np.empty(info["cells"], dtype=np.float32) if st in (SL_MIX_BF16, SL_MIX_FP16) else None
     return mean, hi, scale
 

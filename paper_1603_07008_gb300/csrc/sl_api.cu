@@ -165,6 +165,7 @@ std::vector<int> scaled_fts(const sl_ctx* c)
 {
     const int64_t nf = c->nfib;
     std::vector<int> v{int(nf)};
+    if (c->rec) return v;   // a record is always one thread's
     if (c->K == 1 && nf == 32) v.insert(v.end(), {16, 8, 4});
     if (c->K == 1 && nf == 16) v.insert(v.end(), {8, 4});
     if (c->K == 2 && nf == 27) v.insert(v.end(), {9, 3});
@@ -189,7 +190,7 @@ void default_tune(sl_ctx* c, int m)
     auto& t = c->tune[m];
     t.ft = is_scaled(c) ? scaled_default_ft(c) : 1;
     if (m == 0) {
-        t.block = 256;
+        t.block = c->rec ? 128 : 256;
         t.unroll = unit_vec_width(c) ? unit_vec_width(c) : 1;
         t.chunk = 0;
         return;
@@ -269,6 +270,9 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.pipeline = dim == 0 ? 0 : c->tune[dim].pipeline;
     L.block = c->tune[dim].block;
     L.stream = c->st;
+    L.dim = dim;
+    L.ndim = c->ndim;
+    L.rec = c->rec;
     return is_scaled(c) ? launch_sweep_scaled(L) : c->mode == M_FP64 ? launch_sweep_f64(L)
                                                                       : launch_sweep_f32(L);
 }
@@ -395,6 +399,7 @@ CodecArgs codec_of(const sl_ctx* c)
     a.pstride = c->pstride;
     a.ncoef = int(c->ncoef);
     a.mode = c->mode;
+    a.rec = c->rec;
     return a;
 }
 
@@ -497,6 +502,11 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
     c->nfib = ipow(c->O, c->ndim - 1);
     c->pstride = int64_t(align_up(size_t(c->cells), 64));
     c->elem = elem_size(storage);
+    // cell records for the scaled shapes that fill them (at most one padding
+    // slot besides slot 0): 6D and 5D with k = 1, 3D with k = 3
+    if ((storage == SL_MIX_BF16 || storage == SL_MIX_FP16) &&
+        ((degree == 1 && (grid->ndim == 6 || grid->ndim == 5)) || (degree == 3 && grid->ndim == 3)))
+        c->rec = int((c->ncoef + 7) / 8 * 8);
     c->state_bytes = state_bytes_of(c->cells, c->ncoef, storage);
     for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
     build_poly_table(degree, &c->poly);
@@ -511,7 +521,9 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
         o_state[b][0] = off;
         off = align_up(off + size_t(c->pstride) * 8, A);
         o_state[b][1] = off;
-        off = align_up(off + size_t(c->pstride) * size_t(c->ncoef - 1) * c->elem, A);
+        off = align_up(off + (c->rec ? size_t(c->cells) * c->rec * c->elem
+                                     : size_t(c->pstride) * size_t(c->ncoef - 1) * c->elem),
+                       A);
         o_state[b][2] = off;
         if (scaled) off = align_up(off + size_t(c->pstride) * 4, A);
     }
@@ -605,6 +617,7 @@ sl_status sl_get_info(const sl_ctx* c, sl_info* out)
                        int64_t(c->proj_bytes);
     out->degree = c->K;
     out->storage = c->mode;
+    out->record_slots = c->rec;
     return SL_OK;
 }
 
@@ -687,7 +700,10 @@ sl_status sl_set_planes(sl_ctx* c, const double* mean, const void* hi, const flo
     if (s != SL_OK) return s;
     const Planes& p = c->planes[c->cur];
     SL_CUDA(c, cudaMemcpyAsync(p.mean, mean, size_t(c->cells) * 8, cudaMemcpyHostToDevice, c->st));
-    if (c->ncoef > 1)
+    if (c->rec)
+        SL_CUDA(c, cudaMemcpyAsync(p.hi, hi, size_t(c->cells) * c->rec * c->elem, cudaMemcpyHostToDevice,
+                                   c->st));
+    else if (c->ncoef > 1)
         SL_CUDA(c, cudaMemcpy2DAsync(p.hi, size_t(c->pstride) * c->elem, hi, size_t(c->cells) * c->elem,
                                      size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
                                      cudaMemcpyHostToDevice, c->st));
@@ -702,7 +718,10 @@ sl_status sl_get_planes(sl_ctx* c, double* mean, void* hi, float* scale)
     if (s != SL_OK) return s;
     const Planes& p = c->planes[c->cur];
     SL_CUDA(c, cudaMemcpyAsync(mean, p.mean, size_t(c->cells) * 8, cudaMemcpyDeviceToHost, c->st));
-    if (c->ncoef > 1)
+    if (c->rec)
+        SL_CUDA(c, cudaMemcpyAsync(hi, p.hi, size_t(c->cells) * c->rec * c->elem, cudaMemcpyDeviceToHost,
+                                   c->st));
+    else if (c->ncoef > 1)
         SL_CUDA(c, cudaMemcpy2DAsync(hi, size_t(c->cells) * c->elem, p.hi, size_t(c->pstride) * c->elem,
                                      size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
                                      cudaMemcpyDeviceToHost, c->st));
@@ -943,7 +962,7 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
 
 static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
 {
-    const int maxb = dim == 0 ? 256 : 128;
+    const int maxb = dim == 0 && !c->rec ? 256 : 128;
     if (t->block < 32 || t->block > maxb || t->block % 32)
         return fail(c, SL_EINVAL, "block must be a multiple of 32 in [32, %d]", maxb);
     if (!is_scaled(c)) {
@@ -1031,7 +1050,8 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             if (is_scaled(c)) {
                 for (int f : scaled_fts(c)) {
                     if (f == c->nfib)
-                        for (int b : {64, 128, 256}) cand.push_back({b, f, 1, 0, 0});
+                        for (int b : {64, 128, 256})
+                            if (b <= 128 || !c->rec) cand.push_back({b, f, 1, 0, 0});
                     else
                         cand.push_back({128, f, 1, 0, 0});
                 }

@@ -100,10 +100,9 @@ __device__ void encode_cell(const CodecArgs& c, const double* v, uint32_t cell)
     using T = typename St<MODE>::T;
     c.p.mean[cell] = v[0];
     if constexpr (MODE == M_FP64) {
-        for (int J = 1; J < c.ncoef; ++J) plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = v[J];
+        for (int J = 1; J < c.ncoef; ++J) *coef_ptr<T>(c, J, cell) = v[J];
     } else if constexpr (MODE == M_F32) {
-        for (int J = 1; J < c.ncoef; ++J)
-            plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = __double2float_rn(v[J]);
+        for (int J = 1; J < c.ncoef; ++J) *coef_ptr<T>(c, J, cell) = __double2float_rn(v[J]);
     } else {
         double mx = 0.0;
         for (int J = 1; J < c.ncoef; ++J) mx = fmax(mx, fabs(v[J]));
@@ -112,7 +111,7 @@ __device__ void encode_cell(const CodecArgs& c, const double* v, uint32_t cell)
         c.p.scale[cell] = s;
         for (int J = 1; J < c.ncoef; ++J) {
             const double x = v[J] * double(inv);   // exact: inv is a power of two
-            T* dst = plane_ptr_w<T>(c.p.hi, c.pstride, J) + cell;
+            T* dst = coef_ptr<T>(c, J, cell);
             if constexpr (MODE == M_BF16)
                 *dst = __double2bfloat16(x);
             else
@@ -129,7 +128,7 @@ __device__ void decode_cell(const CodecArgs& c, uint32_t cell, double* out)
     double s = 1.0;
     if constexpr (St<MODE>::scaled) s = double(c.p.scale[cell]);
     for (int J = 1; J < c.ncoef; ++J) {
-        const T raw = plane_ptr<T>(c.p.hi, c.pstride, J)[cell];
+        const T raw = *coef_ptr<T>(c, J, cell);
         double x;
         if constexpr (MODE == M_FP64)
             x = raw;
@@ -286,9 +285,9 @@ __global__ void k_project_cells(ProjectArgs pa, const double* __restrict__ w,
         for (int J = 1; J < c.ncoef; ++J) {
             const double v = project_coef(pa, w, tab, nmax, im, J);
             if constexpr (MODE == M_FP64)
-                plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = v;
+                *coef_ptr<T>(c, J, cell) = v;
             else
-                plane_ptr_w<T>(c.p.hi, c.pstride, J)[cell] = __double2float_rn(v);
+                *coef_ptr<T>(c, J, cell) = __double2float_rn(v);
         }
     } else {
         double mx = 0.0;
@@ -298,7 +297,7 @@ __global__ void k_project_cells(ProjectArgs pa, const double* __restrict__ w,
         c.p.scale[cell] = s;
         for (int J = 1; J < c.ncoef; ++J) {
             const double x = project_coef(pa, w, tab, nmax, im, J) * double(inv);
-            T* dst = plane_ptr_w<T>(c.p.hi, c.pstride, J) + cell;
+            T* dst = coef_ptr<T>(c, J, cell);
             if constexpr (MODE == M_BF16)
                 *dst = __double2bfloat16(x);
             else

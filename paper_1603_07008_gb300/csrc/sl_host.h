@@ -18,6 +18,7 @@ struct sl_ctx {
     sl::Mode mode = sl::M_FP64;
     cudaStream_t st = nullptr;
     int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
+    int rec = 0;                // > 0: scaled store in cell records of rec 16-bit slots
     size_t elem = 8;
     int64_t state_bytes = 0;
 

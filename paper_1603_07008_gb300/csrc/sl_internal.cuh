@@ -114,6 +114,9 @@ struct SweepLaunch {
     int unroll;          // cells per walk step of the strided kernel
     int pipeline;        // > 0: strided kernel with a cp.async ring of this many rows
     int block;           // threads per block
+    int dim;             // sweep dimension
+    int ndim;            // grid dimensions
+    int rec;             // > 0: scaled store in cell records of this many slots
     cudaStream_t stream;
 };
 
@@ -149,7 +152,16 @@ struct CodecArgs {
     int64_t pstride;
     int ncoef;
     int mode;
+    int rec;             // > 0: higher coefficients in cell records of rec slots (slot J = coefficient J)
 };
+
+// Address of coefficient J >= 1 of a cell, planar or in records.
+template <typename T>
+__host__ __device__ __forceinline__ T* coef_ptr(const CodecArgs& c, int J, uint32_t cell)
+{
+    return c.rec ? static_cast<T*>(c.p.hi) + size_t(cell) * c.rec + J
+                 : static_cast<T*>(c.p.hi) + int64_t(J - 1) * c.pstride + cell;
+}
 cudaError_t launch_encode(const CodecArgs& c, const double* aos, uint32_t first, uint32_t count,
                           cudaStream_t st);
 cudaError_t launch_decode(const CodecArgs& c, double* aos, uint32_t first, uint32_t count,

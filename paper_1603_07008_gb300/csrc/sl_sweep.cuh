@@ -902,6 +902,206 @@ __global__ void __launch_bounds__(32 * G) k_sweep_strided_coop(const SweepArgs a
     }
 }
 
+// ---------------------------------------------------------------- scaled stores, cell records
+
+// Record layout of the scaled stores for the shapes that fill a record well:
+// the higher coefficients of a cell are one record of R = round_up(o^d, 8)
+// 16-bit slots, slot J holding coefficient J (slot 0 and the padding slots
+// stay zero).  A thread reads and writes a whole cell with 16-byte vectors;
+// with the sweep dimension M a template parameter, the slots of every fibre
+// are compile-time register positions.
+constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
+template <int K, int D>
+struct RecShape {
+    static constexpr int O = K + 1;
+    static constexpr int NC = ipow_c(O, D);
+    static constexpr int R = (NC + 7) / 8 * 8;
+    static constexpr int NV = R / 8;   // 16-byte vectors per record
+    static constexpr int NF = NC / O;  // fibres
+};
+
+// Slot of coefficient l of fibre f for a sweep along dimension M.
+template <int K, int M>
+__host__ __device__ constexpr int rec_slot(int f, int l)
+{
+    return (f / ipow_c(K + 1, M)) * ipow_c(K + 1, M + 1) + (f % ipow_c(K + 1, M)) + l * ipow_c(K + 1, M);
+}
+
+template <int MODE>
+__device__ __forceinline__ float dec16(uint32_t bits)
+{
+    if constexpr (MODE == M_BF16)
+        return __uint_as_float(bits << 16);
+    else
+        return __half2float(__ushort_as_half((unsigned short)bits));
+}
+template <int MODE>
+__device__ __forceinline__ uint32_t enc16(float v)
+{
+    if constexpr (MODE == M_BF16)
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    else
+        return __half_as_ushort(__float2half_rn(v));
+}
+
+template <int MODE, int NV>
+__device__ __forceinline__ float rec_get(const uint4 (&r)[NV], int J)
+{
+    const uint4& q = r[J / 8];
+    const int w = (J % 8) / 2;
+    const uint32_t word = w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w;
+    return dec16<MODE>((J & 1) ? (word >> 16) : (word & 0xffffu));
+}
+
+// New record of one cell from the records of its source cells a and b.
+template <int K, int MODE, int D, int M>
+__device__ __forceinline__ void rec_combine(const Mats<K, MODE>& M_, const uint4 (&ra)[RecShape<K, D>::NV],
+                                            float sa, double ma, const uint4 (&rb)[RecShape<K, D>::NV],
+                                            float sb, double mb, float (&out)[RecShape<K, D>::R],
+                                            double& om)
+{
+    using RS = RecShape<K, D>;
+    constexpr int O = K + 1;
+#pragma unroll
+    for (int f = 0; f < RS::NF; ++f) {
+        CellVals<K, MODE, 1> va, vb, vo;
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            const int J = rec_slot<K, M>(f, l);
+            va.v[0][l] = J == 0 ? 0.0f : rec_get<MODE, RS::NV>(ra, J) * sa;
+            vb.v[0][l] = J == 0 ? 0.0f : rec_get<MODE, RS::NV>(rb, J) * sb;
+        }
+        if (f == 0) {
+            va.m = ma;
+            vb.m = mb;
+            combine<K, MODE, 1, true>(M_, va, vb, vo);
+            om = vo.m;
+        } else {
+            combine<K, MODE, 1, false>(M_, va, vb, vo);
+        }
+#pragma unroll
+        for (int l = 0; l < O; ++l) out[rec_slot<K, M>(f, l)] = vo.v[0][l];
+    }
+}
+
+// Scale (cell-wide maximum) and pack a record; slot 0 and padding are zero.
+template <int K, int MODE, int D>
+__device__ __forceinline__ float rec_pack(float (&out)[RecShape<K, D>::R], uint4 (&ro)[RecShape<K, D>::NV])
+{
+    using RS = RecShape<K, D>;
+    float mx = 0.0f;
+#pragma unroll
+    for (int J = 1; J < RS::NC; ++J) mx = fmaxf(mx, fabsf(out[J]));
+    float s, inv;
+    pow2_scale(mx, s, inv);
+#pragma unroll
+    for (int q = 0; q < RS::NV; ++q) {
+        uint32_t w[4];
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const int J0 = 8 * q + 2 * h, J1 = J0 + 1;
+            const uint32_t lo = (J0 >= 1 && J0 < RS::NC) ? enc16<MODE>(out[J0] * inv) : 0u;
+            const uint32_t hi = (J1 >= 1 && J1 < RS::NC) ? enc16<MODE>(out[J1] * inv) : 0u;
+            w[h] = lo | (hi << 16);
+        }
+        ro[q] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    return s;
+}
+
+template <int K, int D>
+__device__ __forceinline__ void rec_load(const void* hi, uint32_t c, uint4 (&r)[RecShape<K, D>::NV])
+{
+    const uint4* p = static_cast<const uint4*>(hi) + size_t(c) * RecShape<K, D>::NV;
+#pragma unroll
+    for (int q = 0; q < RecShape<K, D>::NV; ++q) r[q] = __ldg(p + q);
+}
+
+template <int K, int D>
+__device__ __forceinline__ void rec_store(void* hi, uint32_t c, const uint4 (&r)[RecShape<K, D>::NV])
+{
+    uint4* p = static_cast<uint4*>(hi) + size_t(c) * RecShape<K, D>::NV;
+#pragma unroll
+    for (int q = 0; q < RecShape<K, D>::NV; ++q) p[q] = r[q];
+}
+
+// Sweep along dimension 0 on cell records: one thread per target cell.
+template <int K, int MODE, int D>
+__global__ void __launch_bounds__(128) k_sweep_unit_rec(const SweepArgs a)
+{
+    using RS = RecShape<K, D>;
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.cells) return;
+    const uint32_t line = a.fdN.div(c);
+    const uint32_t i = c - line * a.N;
+    const uint32_t cls = shift_class(a, 0, line);
+    const int32_t sig = __ldg(a.tab.sigma + cls);
+    int32_t ia = int32_t(i) - sig;
+    ia += ia < 0 ? int32_t(a.N) : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? int32_t(a.N) : 0;
+    const uint32_t ca = c - i + uint32_t(ia);
+    const uint32_t cb = c - i + uint32_t(ib);
+    Mats<K, MODE> M;
+    M.template load<true>(a.tab, cls);
+    uint4 ra[RS::NV], rb[RS::NV];
+    rec_load<K, D>(a.src.hi, ca, ra);
+    rec_load<K, D>(a.src.hi, cb, rb);
+    float out[RS::R];
+    double om;
+    rec_combine<K, MODE, D, 0>(M, ra, __ldg(a.src.scale + ca), __ldg(a.src.mean + ca), rb,
+                               __ldg(a.src.scale + cb), __ldg(a.src.mean + cb), out, om);
+    uint4 ro[RS::NV];
+    const float s = rec_pack<K, MODE, D>(out, ro);
+    rec_store<K, D>(a.dst.hi, c, ro);
+    a.dst.scale[c] = s;
+    a.dst.mean[c] = om;
+}
+
+// Sweep along dimension M > 0 on cell records: one thread per line walking
+// its chunk, the previous source record kept in registers.
+template <int K, int MODE, int D, int M>
+__global__ void __launch_bounds__(128) k_sweep_strided_rec(const SweepArgs a)
+{
+    using RS = RecShape<K, D>;
+    const LineSetup L = line_setup_grid(a, 1);
+    if (!L.active) return;
+    Mats<K, MODE> Mt;
+    Mt.template load<true>(a.tab, L.cls);
+    const int32_t N = int32_t(a.N);
+    int32_t ia = int32_t(L.i0) - L.sig;
+    ia += ia < 0 ? N : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? N : 0;
+    uint4 prev[RS::NV];
+    uint32_t cb = L.base + uint32_t(ib) * a.inner;
+    rec_load<K, D>(a.src.hi, cb, prev);
+    float sp = __ldg(a.src.scale + cb);
+    double mp = __ldg(a.src.mean + cb);
+    for (uint32_t i = L.i0; i < L.i1; ++i) {
+        const uint32_t ca = L.base + uint32_t(ia) * a.inner;
+        uint4 cur[RS::NV];
+        rec_load<K, D>(a.src.hi, ca, cur);
+        const float sc = __ldg(a.src.scale + ca);
+        const double mc = __ldg(a.src.mean + ca);
+        float out[RS::R];
+        double om;
+        rec_combine<K, MODE, D, M>(Mt, cur, sc, mc, prev, sp, mp, out, om);
+        uint4 ro[RS::NV];
+        const float s = rec_pack<K, MODE, D>(out, ro);
+        const uint32_t c = L.base + i * a.inner;
+        rec_store<K, D>(a.dst.hi, c, ro);
+        a.dst.scale[c] = s;
+        a.dst.mean[c] = om;
+#pragma unroll
+        for (int q = 0; q < RS::NV; ++q) prev[q] = cur[q];
+        sp = sc;
+        mp = mc;
+        ++ia;
+        if (ia == N) ia = 0;
+    }
+}
+
 // ---------------------------------------------------------------- strided, cp.async ring
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)

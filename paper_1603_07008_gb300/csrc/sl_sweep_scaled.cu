@@ -69,9 +69,48 @@ cudaError_t launch_one(const SweepLaunch& L)
     return cudaGetLastError();
 }
 
+// Cell-record layout (shapes whose records are nearly full): the sweep
+// dimension is a template parameter of the strided kernel.
+template <int K, int MODE, int D>
+cudaError_t launch_rec(const SweepLaunch& L)
+{
+    const SweepArgs& a = L.args;
+    if (L.block > 128 || L.ndim != D || L.rec != RecShape<K, D>::R) return cudaErrorInvalidValue;
+    if (L.unit) {
+        k_sweep_unit_rec<K, MODE, D><<<(a.cells + L.block - 1) / L.block, L.block, 0, L.stream>>>(a);
+        return cudaGetLastError();
+    }
+    const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
+    const dim3 grid((a.lines + L.block - 1) / L.block, nchunk);
+    switch (L.dim) {
+    case 1: k_sweep_strided_rec<K, MODE, D, 1><<<grid, L.block, 0, L.stream>>>(a); break;
+    case 2:
+        if constexpr (D > 2) k_sweep_strided_rec<K, MODE, D, 2><<<grid, L.block, 0, L.stream>>>(a);
+        break;
+    case 3:
+        if constexpr (D > 3) k_sweep_strided_rec<K, MODE, D, 3><<<grid, L.block, 0, L.stream>>>(a);
+        break;
+    case 4:
+        if constexpr (D > 4) k_sweep_strided_rec<K, MODE, D, 4><<<grid, L.block, 0, L.stream>>>(a);
+        break;
+    case 5:
+        if constexpr (D > 5) k_sweep_strided_rec<K, MODE, D, 5><<<grid, L.block, 0, L.stream>>>(a);
+        break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (L.dim >= D) return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch_mode(const SweepLaunch& L)
 {
+    if (L.rec) {
+        if (L.K == 1 && L.ndim == 6) return launch_rec<1, MODE, 6>(L);
+        if (L.K == 1 && L.ndim == 5) return launch_rec<1, MODE, 5>(L);
+        if (L.K == 3 && L.ndim == 3) return launch_rec<3, MODE, 3>(L);
+        return cudaErrorInvalidValue;
+    }
     const int nf = L.args.nfib;
     switch (L.K) {
     case 0:

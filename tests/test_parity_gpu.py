@@ -435,13 +435,17 @@ def test_scaled_launch_shapes_identical(storage, n, k):
     u = _rand(n, k, 6)
     splits = SCALED_SPLITS[(k, len(n))]
     with S.Context(_grid(n), k, storage) as ctx:
+        if ctx.info["record_slots"]:
+            splits = splits[:1]   # a cell record is always one thread's
         for dim in range(len(n)):
             s = _shifts(rng, n, dim, -1)
             ctx.set_coeffs(u)
             ctx.advect(dim, -1, s)
             ref = ctx.get_coeffs()
             for f in splits:
-                for b in (32, 64, 128):
+                for b in (32, 64, 128, 256):
+                    if b == 256 and (dim > 0 or ctx.info["record_slots"]):
+                        continue
                     sh = dict(block=b, fibres_per_thread=f)
                     if dim > 0:
                         sh["chunk"] = min(2, n[dim])
@@ -511,3 +515,35 @@ def test_scaled_single_sweeps_every_fibre_split(storage, n, k):
                 ref = O.sweep(stored, n, k, dim, sd, s)
                 assert O.rel_l2(got, ref, k, len(n)) <= 5e-3, (dim, sd)
                 assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(stored[:, 1:]))
+
+
+@pytest.mark.parametrize("storage", ["mix_bf16", "mix_fp16"])
+@pytest.mark.parametrize("n,k,slots", [((3, 2, 2, 3, 2, 2), 1, 64), ((3, 4, 2, 3, 2), 1, 32),
+                                       ((4, 3, 5), 3, 64), ((4, 3, 3, 2), 2, 0)])
+def test_record_layout_raw_planes(storage, n, k, slots):
+    """Scaled shapes whose cells fill a record keep the higher coefficients
+    in per-cell records: slot J is coefficient J, slot 0 and the padding are
+    zero, and the raw planes round-trip."""
+    u = _rand(n, k, 41)
+    with S.Context(_grid(n), k, storage) as ctx:
+        assert ctx.info["record_slots"] == slots
+        ctx.set_coeffs(u)
+        ctx.advect(0, -1, [0.3])
+        ctx.advect(len(n) - 1, -1, [-1.7])
+        want = ctx.get_coeffs()
+        mean, hi, scale = S.sl_get_planes(ctx.handle)
+        if slots:
+            assert hi.shape == (int(np.prod(n)), slots)
+            assert not hi[:, 0].any() and not hi[:, (k + 1) ** len(n):].any()
+        # decode the raw planes on the host and compare
+        x = hi.astype(np.uint32)
+        if storage == "mix_bf16":
+            vals = (x << 16).view(np.float32).astype(np.float64)
+        else:
+            vals = x.astype(np.uint16).view(np.float16).astype(np.float64)
+        coef = vals[:, 1:(k + 1) ** len(n)] if slots else vals.T
+        assert np.array_equal(coef * scale[:, None], want[:, 1:])
+        assert np.array_equal(mean, want[:, 0])
+        S.sl_set_planes(ctx.handle, mean, hi, scale)
+        ctx.synchronize()
+        assert np.array_equal(ctx.get_coeffs(), want)
