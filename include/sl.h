@@ -330,6 +330,9 @@ sl_status sl_batch_profile_query(sl_batch* batch, int64_t* launches, double* ms,
  *                      which needs n_0 divisible by it and 1..4 fibres per
  *                      thread (FP64 and FP32 stores)
  *   chunk              cells one thread walks along dimensions > 0 (1..n_dim)
+ *                      For cell records (sl_info.record_slots > 0): 1 plain,
+ *                      2 prefetching walk; along dimension 0 chunk 0 means one
+ *                      thread per cell, chunk > 0 a walk.
  *   pipeline           0: the walk keeps the previous cell in registers;
  *                      4 or 8: the walk streams its source rows through a
  *                      per-thread cp.async ring of that many rows in shared

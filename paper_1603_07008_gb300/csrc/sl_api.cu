@@ -242,7 +242,7 @@ SweepArgs make_args_parity(sl_ctx* c, int dim, int shift_dim, int parity)
     a.nfib = int(c->nfib);
     const auto& t = c->tune[dim];
     a.nfg = int(fibre_groups(c, t.ft));
-    a.chunk = dim == 0 ? 0 : t.chunk;
+    a.chunk = dim == 0 && !c->rec ? 0 : t.chunk;
     return a;
 }
 
@@ -956,7 +956,7 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
     out->fibres_per_thread = t.ft;
     out->unroll = t.unroll;
     out->pipeline = t.pipeline;
-    out->chunk = dim == 0 ? 0 : int64_t(t.chunk);
+    out->chunk = dim == 0 && !c->rec ? 0 : int64_t(t.chunk);
     return SL_OK;
 }
 
@@ -995,6 +995,12 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
             return fail(c, SL_EINVAL, "fibres_per_thread %d is not a provided split of the %lld fibres",
                         t->fibres_per_thread, (long long)c->nfib);
     }
+    if (c->rec) {
+        if (t->unroll != 1 && t->unroll != 2)
+            return fail(c, SL_EINVAL, "record sweeps take unroll 1 (plain) or 2 (prefetching walk)");
+        if (dim == 0 && t->chunk != 0 && (t->chunk < 1 || t->chunk > c->g.n[0]))
+            return fail(c, SL_EINVAL, "chunk along dimension 0 must be 0 (one thread per cell) or in [1, n_0]");
+    }
     if (dim > 0) {
         const int64_t N = c->g.n[dim];
         if (t->chunk < 1 || t->chunk > N) return fail(c, SL_EINVAL, "chunk must be in [1, n_dim]");
@@ -1014,9 +1020,9 @@ sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
     auto& d = c->tune[dim];
     d.block = t->block;
     d.ft = t->fibres_per_thread;
-    d.unroll = is_scaled(c) ? 1 : t->unroll;
+    d.unroll = is_scaled(c) && !c->rec ? 1 : t->unroll;
     d.pipeline = is_scaled(c) || dim == 0 ? 0 : t->pipeline;
-    d.chunk = dim == 0 ? 0 : uint32_t(t->chunk);
+    d.chunk = dim == 0 && !c->rec ? 0 : uint32_t(t->chunk);
     return SL_OK;
 }
 
@@ -1048,6 +1054,9 @@ sl_status sl_autotune(sl_ctx* c, int reps)
         std::vector<sl_ctx::Tune> cand;
         if (m == 0) {
             if (is_scaled(c)) {
+                if (c->rec)
+                    for (int u : {1, 2})
+                        for (int b : {64, 128}) cand.push_back({b, int(c->nfib), u, chunk_for(c, 0, 1), 0});
                 for (int f : scaled_fts(c)) {
                     if (f == c->nfib)
                         for (int b : {64, 128, 256})
@@ -1068,7 +1077,9 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             if (is_scaled(c)) {
                 for (int f : scaled_fts(c)) {
                     if (f == c->nfib)
-                        for (int b : {64, 128}) cand.push_back({b, f, 1, chunk_for(c, m, 1), 0});
+                        for (int b : {64, 128})
+                            for (int u : {1, 2})
+                                if (u == 1 || c->rec) cand.push_back({b, f, u, chunk_for(c, m, 1), 0});
                     else
                         cand.push_back({128, f, 1, chunk_for(c, m, 1), 0});
                 }

@@ -1047,8 +1047,8 @@ __global__ void __launch_bounds__(128) k_sweep_unit_rec(const SweepArgs a)
     uint4 ra[RS::NV], rb[RS::NV];
     rec_load<K, D>(a.src.hi, ca, ra);
     rec_load<K, D>(a.src.hi, cb, rb);
-    float out[RS::R];
     double om;
+    float out[RS::R];
     rec_combine<K, MODE, D, 0>(M, ra, __ldg(a.src.scale + ca), __ldg(a.src.mean + ca), rb,
                                __ldg(a.src.scale + cb), __ldg(a.src.mean + cb), out, om);
     uint4 ro[RS::NV];
@@ -1058,9 +1058,11 @@ __global__ void __launch_bounds__(128) k_sweep_unit_rec(const SweepArgs a)
     a.dst.mean[c] = om;
 }
 
-// Sweep along dimension M > 0 on cell records: one thread per line walking
-// its chunk, the previous source record kept in registers.
-template <int K, int MODE, int D, int M>
+// Sweep along dimension M on cell records: one thread per line walking its
+// chunk, the previous source record kept in registers (also used along
+// dimension 0, where the lines are contiguous runs of records).  With PF the
+// next source record is loaded before the current one is computed.
+template <int K, int MODE, int D, int M, bool PF>
 __global__ void __launch_bounds__(128) k_sweep_strided_rec(const SweepArgs a)
 {
     using RS = RecShape<K, D>;
@@ -1078,12 +1080,34 @@ __global__ void __launch_bounds__(128) k_sweep_strided_rec(const SweepArgs a)
     rec_load<K, D>(a.src.hi, cb, prev);
     float sp = __ldg(a.src.scale + cb);
     double mp = __ldg(a.src.mean + cb);
-    for (uint32_t i = L.i0; i < L.i1; ++i) {
+    uint4 cur[RS::NV];
+    float sc = 0.0f;
+    double mc = 0.0;
+    if constexpr (PF) {
         const uint32_t ca = L.base + uint32_t(ia) * a.inner;
-        uint4 cur[RS::NV];
         rec_load<K, D>(a.src.hi, ca, cur);
-        const float sc = __ldg(a.src.scale + ca);
-        const double mc = __ldg(a.src.mean + ca);
+        sc = __ldg(a.src.scale + ca);
+        mc = __ldg(a.src.mean + ca);
+    }
+    for (uint32_t i = L.i0; i < L.i1; ++i) {
+        uint4 nxt[RS::NV];
+        float sn = 0.0f;
+        double mn = 0.0;
+        if constexpr (PF) {
+            if (i + 1 < L.i1) {
+                int32_t in = ia + 1;
+                in -= in == N ? N : 0;
+                const uint32_t cn = L.base + uint32_t(in) * a.inner;
+                rec_load<K, D>(a.src.hi, cn, nxt);
+                sn = __ldg(a.src.scale + cn);
+                mn = __ldg(a.src.mean + cn);
+            }
+        } else {
+            const uint32_t ca = L.base + uint32_t(ia) * a.inner;
+            rec_load<K, D>(a.src.hi, ca, cur);
+            sc = __ldg(a.src.scale + ca);
+            mc = __ldg(a.src.mean + ca);
+        }
         float out[RS::R];
         double om;
         rec_combine<K, MODE, D, M>(Mt, cur, sc, mc, prev, sp, mp, out, om);
@@ -1097,6 +1121,12 @@ __global__ void __launch_bounds__(128) k_sweep_strided_rec(const SweepArgs a)
         for (int q = 0; q < RS::NV; ++q) prev[q] = cur[q];
         sp = sc;
         mp = mc;
+        if constexpr (PF) {
+#pragma unroll
+            for (int q = 0; q < RS::NV; ++q) cur[q] = nxt[q];
+            sc = sn;
+            mc = mn;
+        }
         ++ia;
         if (ia == N) ia = 0;
     }

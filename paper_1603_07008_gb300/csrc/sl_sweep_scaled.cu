@@ -71,35 +71,46 @@ cudaError_t launch_one(const SweepLaunch& L)
 
 // Cell-record layout (shapes whose records are nearly full): the sweep
 // dimension is a template parameter of the strided kernel.
+template <int K, int MODE, int D, int M>
+cudaError_t launch_rec_walk(const SweepLaunch& L, dim3 grid)
+{
+    switch (L.unroll) {
+    case 1: k_sweep_strided_rec<K, MODE, D, M, false><<<grid, L.block, 0, L.stream>>>(L.args); break;
+    case 2: k_sweep_strided_rec<K, MODE, D, M, true><<<grid, L.block, 0, L.stream>>>(L.args); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// Along dimension 0 the cells are either one thread each (chunk 0) or walked
+// like the other dimensions (chunk > 0).  unroll: 1 plain, 2 prefetching
+// walk.
 template <int K, int MODE, int D>
 cudaError_t launch_rec(const SweepLaunch& L)
 {
     const SweepArgs& a = L.args;
-    if (L.block > 128 || L.ndim != D || L.rec != RecShape<K, D>::R) return cudaErrorInvalidValue;
-    if (L.unit) {
+    if (L.block > 128 || L.ndim != D || L.rec != RecShape<K, D>::R || L.dim >= D) return cudaErrorInvalidValue;
+    if (L.unit && a.chunk == 0) {
         k_sweep_unit_rec<K, MODE, D><<<(a.cells + L.block - 1) / L.block, L.block, 0, L.stream>>>(a);
         return cudaGetLastError();
     }
     const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
     const dim3 grid((a.lines + L.block - 1) / L.block, nchunk);
     switch (L.dim) {
-    case 1: k_sweep_strided_rec<K, MODE, D, 1><<<grid, L.block, 0, L.stream>>>(a); break;
-    case 2:
-        if constexpr (D > 2) k_sweep_strided_rec<K, MODE, D, 2><<<grid, L.block, 0, L.stream>>>(a);
-        break;
+    case 0: return launch_rec_walk<K, MODE, D, 0>(L, grid);
+    case 1: return launch_rec_walk<K, MODE, D, 1>(L, grid);
+    case 2: return launch_rec_walk<K, MODE, D, 2>(L, grid);
     case 3:
-        if constexpr (D > 3) k_sweep_strided_rec<K, MODE, D, 3><<<grid, L.block, 0, L.stream>>>(a);
+        if constexpr (D > 3) return launch_rec_walk<K, MODE, D, 3>(L, grid);
         break;
     case 4:
-        if constexpr (D > 4) k_sweep_strided_rec<K, MODE, D, 4><<<grid, L.block, 0, L.stream>>>(a);
+        if constexpr (D > 4) return launch_rec_walk<K, MODE, D, 4>(L, grid);
         break;
     case 5:
-        if constexpr (D > 5) k_sweep_strided_rec<K, MODE, D, 5><<<grid, L.block, 0, L.stream>>>(a);
+        if constexpr (D > 5) return launch_rec_walk<K, MODE, D, 5>(L, grid);
         break;
-    default: return cudaErrorInvalidValue;
     }
-    if (L.dim >= D) return cudaErrorInvalidValue;
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 template <int MODE>

@@ -442,6 +442,7 @@ def test_scaled_launch_shapes_identical(storage, n, k):
             ctx.set_coeffs(u)
             ctx.advect(dim, -1, s)
             ref = ctx.get_coeffs()
+            shapes = []
             for f in splits:
                 for b in (32, 64, 128, 256):
                     if b == 256 and (dim > 0 or ctx.info["record_slots"]):
@@ -449,10 +450,17 @@ def test_scaled_launch_shapes_identical(storage, n, k):
                     sh = dict(block=b, fibres_per_thread=f)
                     if dim > 0:
                         sh["chunk"] = min(2, n[dim])
-                    ctx.set_tune(dim, **sh)
-                    ctx.set_coeffs(u)
-                    ctx.advect(dim, -1, s)
-                    assert np.array_equal(ctx.get_coeffs(), ref), (dim, f, b)
+                    shapes.append(sh)
+            if ctx.info["record_slots"]:
+                # record walks along every dimension, plain and prefetching
+                for un in (1, 2):
+                    for ch in sorted({1, min(2, n[dim]), n[dim]}):
+                        shapes.append(dict(block=64, fibres_per_thread=splits[0], unroll=un, chunk=ch))
+            for sh in shapes:
+                ctx.set_tune(dim, **sh)
+                ctx.set_coeffs(u)
+                ctx.advect(dim, -1, s)
+                assert np.array_equal(ctx.get_coeffs(), ref), (dim, sh)
 
 
 def test_set_tune_rejects_shapes_not_built():
