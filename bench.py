@@ -130,23 +130,77 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
-        for line in open(self.path):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
-            except ValueError:
-                continue
+        with open(self.path) as f:
+            lines = f.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
-        sm = [r[0] for r in rows]
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        return summarise_clocks(lines)
+
+
+def summarise_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi samples of ClockSampler.FIELDS (csv, no header, no units)."""
+    rows = []
+    for line in lines:
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+        except ValueError:
+            continue
+    if not rows:
+        return None
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+    sm = [r[0] for r in rows]
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+            "reasons": reasons, "samples": len(rows)}
+
+
+# DRAM traffic of the sweep launches (dram__bytes_read.sum + dram__bytes_write.sum),
+# taken from ncu captures of smaller cases of the same kernels and stored as a
+# ratio to the launch's algorithmic bytes (2 x state bytes), so that it scales
+# with the units a launch processes.  Each ratio is the launch-weighted mean over
+# one Strang step's sweeps, the captured unit-stride kernel standing for the
+# dimension-0 sweeps and the captured strided kernel for the others.  A ratio
+# holds only for the kernel sources it was taken on: if their hash differs, the
+# traffic is reported as null.
+TRAFFIC = {
+    ("4d", "mix_fp32"): {
+        "ratio": (2 * 0.98705 + 4 * 1.00223) / 6,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
+        "sha256": "c83b49b05af77433",
+        "capture": "48^4 cells, k=2; unit-stride 3.437 GB, strided 3.490 GB per launch "
+                   "against 3.482 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
+    ("6d", "mix_bf16"): {
+        "ratio": (2 * 1.00371 + 7 * 1.04164) / 9,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_scaled.cu"],
+        "sha256": "669cc3389538185a",
+        "capture": "16^6 cells, k=1, BF16 records; unit-stride 4.648 GB, strided 4.823 GB per "
+                   "launch against 4.631 GB algorithmic (profiles/sweep_6d_n16_records_bf16.md)"},
+    ("batch", "mix_fp32"): {
+        "ratio": (2 * 0.96357 + 1.05413) / 3,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
+        "sha256": "10719d23afe556fa",
+        "capture": "64 problems, default shapes; unit-stride 1.052 GB, strided 1.151 GB per "
+                   "launch against 1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
+}
+
+
+def sweep_traffic(workload, storage, bytes_per_launch):
+    """DRAM bytes per sweep launch at this size, or (None, why)."""
+    import hashlib
+    t = TRAFFIC.get((workload, storage))
+    if t is None:
+        return None, "no ncu capture of this workload's kernels"
+    m = hashlib.sha256()
+    for f in t["sources"]:
+        with open(os.path.join(ROOT, "paper_1603_07008_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    if m.hexdigest()[:16] != t["sha256"]:
+        return None, "kernel sources changed since the ncu capture"
+    return t["ratio"] * bytes_per_launch, ("scaled by units from an ncu capture of " +
+                                           t["capture"])
 
 
 def measured_peaks():
@@ -349,6 +403,7 @@ def run_ours(args):
     bytes_per_sweep = sweep_bytes / max(nl, 1)
     achieved_gbs = bytes_per_sweep / (avg_sweep_ms / 1000.0) / 1e9
     peak_gbs = float(peaks["hbm_gbs"])
+    traffic, traffic_note = sweep_traffic(args.workload, args.storage, bytes_per_sweep)
 
     fp64 = None
     if not args.no_fp64 and args.storage != "fp64":
@@ -395,7 +450,8 @@ def run_ours(args):
                        "parallelism": f"replicas x{world}", "tune": info["tune"]},
             "mass_drift": drift,
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
-                         "frac": achieved_gbs / peak_gbs, "traffic": None,
+                         "frac": achieved_gbs / peak_gbs, "traffic": traffic,
+                         "traffic_note": traffic_note,
                          "kernel": "sweep (all dims)", "peak_source": peak_src,
                          "bytes_per_launch": bytes_per_sweep, "avg_launch_ms": avg_sweep_ms,
                          "launches": nl, "per_dim": info.get("per_dim")},

@@ -1,0 +1,78 @@
+"""Host-side logic of bench.py on the CPU: the multi-rank reduction of the
+timed region (gloo, world size 2), the reference arm's rank-0-only rule, the
+clock-sample summary and the traffic bookkeeping."""
+import json
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, world, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w, r, local = bench.dist_env()
+        assert (w, r, local) == (world, rank, rank)
+        bench.barrier(w)
+        # rank r timed 10 + r ms and processed 100 (r + 1) units
+        ms, units = bench.aggregate(10.0 + rank, 100.0 * (rank + 1), w, torch.device("cpu"))
+        bench.barrier(w)
+        with open(os.path.join(out_dir, f"r{rank}.json"), "w") as f:
+            json.dump({"ms": ms, "units": units}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_aggregate_two_ranks_gloo(tmp_path):
+    world = 2
+    mp.start_processes(_rank_main, args=(world, _free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    for r in range(world):
+        got = json.loads((tmp_path / f"r{r}.json").read_text())
+        # every rank sees the slowest rank's time and the sum of all units
+        assert got == {"ms": 11.0, "units": 300.0}
+
+
+def test_aggregate_single_rank_is_identity():
+    assert bench.aggregate(3.5, 7.0, 1) == (3.5, 7.0)
+
+
+def test_reference_arm_only_on_rank_zero(monkeypatch, capsys):
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    args = bench.parse_args(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"])
+    bench.run_reference(args)
+    assert capsys.readouterr().out == ""
+
+
+def test_clock_summary():
+    rows = ["0, 1900, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "0, 1950, 2070, 1200.0, 0x4, Not Active, Not Active, Not Active, Active",
+            "0, 2000, 2070, 1100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+            "garbage line", "0, [N/A], 2070, 1, 0, a, b, c, d"]
+    s = bench.summarise_clocks(rows)
+    assert s == {"sm_mhz": 1950.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert bench.summarise_clocks([]) is None
+
+
+def test_traffic_bookkeeping():
+    t, why = bench.sweep_traffic("4d", "mix_fp32", 1.0e9)
+    if t is None:
+        assert "changed" in why          # kernels edited since the capture: reported as null
+    else:
+        assert 0.9e9 < t < 1.1e9
+    t, why = bench.sweep_traffic("2d", "fp64", 1.0e9)
+    assert t is None and "no ncu capture" in why
