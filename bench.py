@@ -310,6 +310,7 @@ class Arm:
             self.state_bytes = self.obj.info["state_bytes"]
             self.sweeps = 3
             self.dt = probs[0].dt
+            self.order = None
         else:
             p = self.p
             self.obj = S.Context(p.grid, p.k, storage, stream=stream)
@@ -318,6 +319,7 @@ class Arm:
                 self.obj.set_fields(p.field_list())
             apply_shapes(self.obj, shapes)
             self.dof = p.dof
+            self.order = p.k + 1
             self.state_bytes = self.obj.info["state_bytes"]
             self.sweeps = 1 if p.splitting == "advect" else 2 * len(p.grid.x_dims()) + len(p.grid.v_dims())
             self.dt = p.dt
@@ -385,7 +387,7 @@ def run_ours(args):
         arm.obj.profile_enable(False)
         m1 = arm.mass_total()
         info = {"state_bytes": arm.state_bytes, "dof": arm.dof, "sweeps": arm.sweeps,
-                "tune": arm.tunes()}
+                "tune": arm.tunes(), "order": arm.order}
         if dims:
             nd, msd = dims
             info["per_dim"] = [{"dim": d, "launches": nd[d], "ms_per_launch": msd[d] / max(nd[d], 1),
@@ -411,11 +413,25 @@ def run_ours(args):
         ms64_max, units64 = aggregate(ms64, units_local, world, dev)
         v64 = units64 / (ms64_max / 1000.0)
         nl64, sms64, sb64 = prof64
+        # The FP64 store's sweep is bound by the FP64 pipe, not by HBM: 2o FMAs
+        # (4o flops) per DoF update against 2 FP64 FMAs per clock per SM
+        # (1.25 TFLOP/s nominal at 152 SMs and 2.07 GHz).
+        alu = None
+        if info64["order"]:          # one degree for the whole state (not the mixed batch)
+            flops64 = 4.0 * info64["order"] * info64["dof"]
+            mhz = (clk64 or {}).get("sm_mhz") or 2070.0
+            alu_peak = 2.0 * 2.0 * 152 * mhz * 1e6 / 1e12
+            alu_ach = flops64 / (sms64 / max(nl64, 1) / 1000.0) / 1e12
+            alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
+                   "frac": alu_ach / alu_peak,
+                   "peak_source": f"derived: 2 FP64 FMA/clk/SM x 152 SMs x {mhz:.0f} MHz",
+                   "flops_per_launch": flops64}
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64_max / args.steps,
                 "sweep_ms": sms64 / max(nl64, 1),
                 "sweep_gbs": (sb64 / max(nl64, 1)) / (sms64 / max(nl64, 1) / 1000.0) / 1e9,
                 "mass_drift": drift64, "state_bytes": info64["state_bytes"], "clocks": clk64,
-                "per_dim": info64.get("per_dim")}
+                "per_dim": info64.get("per_dim"),
+                "roofline": alu}
 
     e2e = None
     if not args.no_e2e and args.workload == "4d":
