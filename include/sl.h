@@ -330,9 +330,14 @@ sl_status sl_batch_profile_query(sl_batch* batch, int64_t* launches, double* ms,
  *                      which needs n_0 divisible by it and 1..4 fibres per
  *                      thread (FP64 and FP32 stores)
  *   chunk              cells one thread walks along dimensions > 0 (1..n_dim)
- *                      For cell records (sl_info.record_slots > 0): 1 plain,
- *                      2 prefetching walk; along dimension 0 chunk 0 means one
- *                      thread per cell, chunk > 0 a walk.
+ *   Cell records (sl_info.record_slots = R > 0) take one of two forms:
+ *     one thread per cell: fibres_per_thread = o^(d-1), block <= 128,
+ *       unroll 1 (plain) or 2 (prefetching walk); along dimension 0 chunk 0
+ *       means one thread per target cell, chunk > 0 a walk;
+ *     lane groups (degree 1 in 5 or 6 dimensions): fibres_per_thread = 8,
+ *       G = R/16 lanes share a cell, each holding 16 slots; every dimension,
+ *       dimension 0 included, is walked (chunk >= 1), unroll 1, 2 or 4 cells
+ *       per walk step, block <= 256.
  *   pipeline           0: the walk keeps the previous cell in registers;
  *                      4 or 8: the walk streams its source rows through a
  *                      per-thread cp.async ring of that many rows in shared

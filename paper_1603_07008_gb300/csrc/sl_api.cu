@@ -122,13 +122,16 @@ bool is_scaled(const sl_ctx* c) { return c->mode == M_BF16 || c->mode == M_FP16;
 
 int64_t fibre_groups(const sl_ctx* c, int ft) { return is_scaled(c) ? 1 : (c->nfib + ft - 1) / ft; }
 
+bool rec_lanes_ok(const sl_ctx* c) { return c->rec > 0 && c->K == 1 && (c->ndim == 5 || c->ndim == 6); }
+bool rec_lanes(const sl_ctx* c, int ft) { return rec_lanes_ok(c) && ft == kRecLaneFt; }
+
 // Chunk length of the strided walk: long enough to amortise the extra load at
 // the start of a chunk, short enough to give a few waves of 2048 resident
 // threads on 152 SMs, and no more than 65535 grid rows.
-uint32_t chunk_for(const sl_ctx* c, int m, int ft)
+uint32_t chunk_for(const sl_ctx* c, int m, int ft, int lanes)
 {
     const int64_t N = c->g.n[m];
-    const int64_t lines = c->cells / N;
+    const int64_t lines = c->cells / N * lanes;
     const int64_t nfg = fibre_groups(c, ft);
     const int64_t want = int64_t(152) * 2048 * 2;
     int64_t nchunk = (want + lines * nfg - 1) / (lines * nfg);
@@ -165,7 +168,8 @@ std::vector<int> scaled_fts(const sl_ctx* c)
 {
     const int64_t nf = c->nfib;
     std::vector<int> v{int(nf)};
-    if (c->rec) return v;   // a record is always one thread's
+    if (rec_lanes_ok(c)) v.push_back(kRecLaneFt);
+    if (c->rec) return v;   // otherwise a record is one thread's
     if (c->K == 1 && nf == 32) v.insert(v.end(), {16, 8, 4});
     if (c->K == 1 && nf == 16) v.insert(v.end(), {8, 4});
     if (c->K == 2 && nf == 27) v.insert(v.end(), {9, 3});
@@ -188,6 +192,17 @@ int scaled_default_ft(const sl_ctx* c)
 void default_tune(sl_ctx* c, int m)
 {
     auto& t = c->tune[m];
+    t.pipeline = 0;
+    if (rec_lanes_ok(c) && c->ndim == 6) {
+        // 128-byte records: lane groups (measured ahead of one thread per
+        // cell, whose 16-byte pieces of 32 records per warp access keep the
+        // L1 data pipe busy); every dimension is walked
+        t.ft = kRecLaneFt;
+        t.block = 128;
+        t.unroll = m == 0 ? 2 : 1;
+        t.chunk = chunk_for(c, m, 1, c->rec / 16);
+        return;
+    }
     t.ft = is_scaled(c) ? scaled_default_ft(c) : 1;
     if (m == 0) {
         t.block = c->rec ? 128 : 256;
@@ -197,7 +212,7 @@ void default_tune(sl_ctx* c, int m)
     }
     t.block = 128;
     t.unroll = is_scaled(c) ? 1 : 2;
-    t.chunk = chunk_for(c, m, t.ft);
+    t.chunk = chunk_for(c, m, t.ft, 1);
 }
 
 SweepArgs make_args(sl_ctx* c, int dim, int shift_dim) { return make_args_parity(c, dim, shift_dim, c->cur); }
@@ -962,7 +977,8 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
 
 static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
 {
-    const int maxb = dim == 0 && !c->rec ? 256 : 128;
+    const bool lanes = rec_lanes(c, t->fibres_per_thread);
+    const int maxb = (dim == 0 && !c->rec) || lanes ? 256 : 128;
     if (t->block < 32 || t->block > maxb || t->block % 32)
         return fail(c, SL_EINVAL, "block must be a multiple of 32 in [32, %d]", maxb);
     if (!is_scaled(c)) {
@@ -995,12 +1011,19 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
             return fail(c, SL_EINVAL, "fibres_per_thread %d is not a provided split of the %lld fibres",
                         t->fibres_per_thread, (long long)c->nfib);
     }
-    if (c->rec) {
+    if (c->rec && lanes) {
+        if (t->unroll != 1 && t->unroll != 2 && t->unroll != 4)
+            return fail(c, SL_EINVAL, "lane-group record sweeps take unroll 1, 2 or 4");
+        if (dim == 0 && (t->chunk < 1 || t->chunk > c->g.n[0]))
+            return fail(c, SL_EINVAL, "lane-group record sweeps walk dimension 0 too: chunk in [1, n_0]");
+    } else if (c->rec) {
         if (t->unroll != 1 && t->unroll != 2)
             return fail(c, SL_EINVAL, "record sweeps take unroll 1 (plain) or 2 (prefetching walk)");
         if (dim == 0 && t->chunk != 0 && (t->chunk < 1 || t->chunk > c->g.n[0]))
             return fail(c, SL_EINVAL, "chunk along dimension 0 must be 0 (one thread per cell) or in [1, n_0]");
     }
+    if (c->rec && dim == 0 && t->chunk > 0 && (c->g.n[0] + t->chunk - 1) / t->chunk > 65535)
+        return fail(c, SL_EINVAL, "too many chunks for one launch");
     if (dim > 0) {
         const int64_t N = c->g.n[dim];
         if (t->chunk < 1 || t->chunk > N) return fail(c, SL_EINVAL, "chunk must be in [1, n_dim]");
@@ -1052,19 +1075,27 @@ sl_status sl_autotune(sl_ctx* c, int reps)
         if (result != SL_OK) break;
 
         std::vector<sl_ctx::Tune> cand;
-        if (m == 0) {
-            if (is_scaled(c)) {
-                if (c->rec)
+        if (is_scaled(c)) {
+            const uint32_t ch = chunk_for(c, m, 1, 1);
+            for (int f : scaled_fts(c)) {
+                if (rec_lanes(c, f)) {   // lane groups walk every dimension
+                    const uint32_t chl = chunk_for(c, m, 1, c->rec / 16);
+                    for (int u : {1, 2, 4})
+                        for (int b : {128, 256}) cand.push_back({b, f, u, chl, 0});
+                } else if (f == c->nfib && c->rec) {
+                    if (m == 0)
+                        for (int b : {64, 128}) cand.push_back({b, f, 1, 0, 0});
                     for (int u : {1, 2})
-                        for (int b : {64, 128}) cand.push_back({b, int(c->nfib), u, chunk_for(c, 0, 1), 0});
-                for (int f : scaled_fts(c)) {
-                    if (f == c->nfib)
-                        for (int b : {64, 128, 256})
-                            if (b <= 128 || !c->rec) cand.push_back({b, f, 1, 0, 0});
-                    else
-                        cand.push_back({128, f, 1, 0, 0});
+                        for (int b : {64, 128}) cand.push_back({b, f, u, ch, 0});
+                } else if (f == c->nfib) {
+                    for (int b : {64, 128, 256})
+                        if (m == 0 || b <= 128) cand.push_back({b, f, 1, m == 0 ? 0u : ch, 0});
+                } else {   // a cooperative split of the cell's fibres
+                    cand.push_back({128, f, 1, m == 0 ? 0u : ch, 0});
                 }
-            } else {
+            }
+        } else if (m == 0) {
+            {
                 for (int ft : {1, 2, 3, 4, 9})
                     if (ft <= c->nfib)
                         for (int b : {128, 256}) cand.push_back({b, ft, 1, 0, 0});
@@ -1074,24 +1105,15 @@ sl_status sl_autotune(sl_ctx* c, int reps)
                             for (int b : {128, 256}) cand.push_back({b, ft, v, 0, 0});
             }
         } else {
-            if (is_scaled(c)) {
-                for (int f : scaled_fts(c)) {
-                    if (f == c->nfib)
-                        for (int b : {64, 128})
-                            for (int u : {1, 2})
-                                if (u == 1 || c->rec) cand.push_back({b, f, u, chunk_for(c, m, 1), 0});
-                    else
-                        cand.push_back({128, f, 1, chunk_for(c, m, 1), 0});
-                }
-            } else {
+            {
                 const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
                 for (auto& x : fu)
-                    if (x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0]), 0});
+                    if (x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0], 1), 0});
                 const int fp[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {3, 4}};
                 for (auto& x : fp)
                     if (x[0] <= c->nfib)
                         for (int b : {64, 128})
-                            cand.push_back({b, x[0], 1, chunk_for(c, m, x[0]), x[1]});
+                            cand.push_back({b, x[0], 1, chunk_for(c, m, x[0], 1), x[1]});
             }
         }
         const sl_ctx::Tune keep = c->tune[m];

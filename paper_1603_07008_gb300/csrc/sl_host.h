@@ -81,7 +81,12 @@ sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what);
 sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c);
 bool is_scaled(const sl_ctx* c);
 int64_t fibre_groups(const sl_ctx* c, int ft);
-uint32_t chunk_for(const sl_ctx* c, int m, int ft);
+// lanes: threads per line (G of the lane-group record form, else 1)
+uint32_t chunk_for(const sl_ctx* c, int m, int ft, int lanes);
+// Cell records of degree 1 in 5 or 6 dimensions offer the lane-group form,
+// selected by fibres_per_thread == kRecLaneFt.
+bool rec_lanes_ok(const sl_ctx* c);
+bool rec_lanes(const sl_ctx* c, int ft);
 double cell_width(const sl_grid& g, int m);
 int64_t ipow(int64_t b, int e);
 // Sweep geometry along `dim`, reading copy `parity` and writing the other.

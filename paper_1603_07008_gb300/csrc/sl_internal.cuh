@@ -123,6 +123,10 @@ struct SweepLaunch {
 cudaError_t launch_sweep_f64(const SweepLaunch& L);      // M_FP64
 cudaError_t launch_sweep_f32(const SweepLaunch& L);      // M_F32
 cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
+// Cell records of degree 1 in 5 or 6 dimensions with G = R/16 lanes per cell,
+// 16 slots (8 fibres) each (selected by fibres_per_thread == kRecLaneFt).
+constexpr int kRecLaneFt = 8;
+cudaError_t launch_sweep_rec_lanes(const SweepLaunch& L);
 
 // Coefficients of the entries of A(alpha) and B(alpha) as polynomials in
 // alpha, exact rationals rounded once to FP64: a[j][l][p] alpha^p.

@@ -117,6 +117,7 @@ template <int MODE>
 cudaError_t launch_mode(const SweepLaunch& L)
 {
     if (L.rec) {
+        if (L.K == 1 && (L.ndim == 5 || L.ndim == 6) && L.ft == kRecLaneFt) return launch_sweep_rec_lanes(L);
         if (L.K == 1 && L.ndim == 6) return launch_rec<1, MODE, 6>(L);
         if (L.K == 1 && L.ndim == 5) return launch_rec<1, MODE, 5>(L);
         if (L.K == 3 && L.ndim == 3) return launch_rec<3, MODE, 3>(L);

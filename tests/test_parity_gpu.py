@@ -456,6 +456,12 @@ def test_scaled_launch_shapes_identical(storage, n, k):
                 for un in (1, 2):
                     for ch in sorted({1, min(2, n[dim]), n[dim]}):
                         shapes.append(dict(block=64, fibres_per_thread=splits[0], unroll=un, chunk=ch))
+                if k == 1 and len(n) in (5, 6):
+                    # lane groups: R/16 lanes share a cell, 1, 2 or 4 cells per walk step
+                    for un in (1, 2, 4):
+                        for ch in sorted({1, min(3, n[dim]), n[dim]}):
+                            for b in (32, 256):
+                                shapes.append(dict(block=b, fibres_per_thread=8, unroll=un, chunk=ch))
             for sh in shapes:
                 ctx.set_tune(dim, **sh)
                 ctx.set_coeffs(u)
@@ -464,6 +470,22 @@ def test_scaled_launch_shapes_identical(storage, n, k):
 
 
 def test_set_tune_rejects_shapes_not_built():
+    with S.Context(_grid((3, 2, 2, 3, 2, 2)), 1, "mix_bf16") as ctx:   # cell records, lane groups
+        assert ctx.info["record_slots"] == 64
+        ctx.set_tune(0, block=256, fibres_per_thread=8, unroll=4, chunk=3)
+        for dim, sh in [(0, dict(block=128, fibres_per_thread=8, unroll=1, chunk=0)),
+                        (0, dict(block=128, fibres_per_thread=8, unroll=3, chunk=3)),
+                        (1, dict(block=512, fibres_per_thread=8, unroll=1, chunk=2)),
+                        (1, dict(block=256, fibres_per_thread=32, unroll=1, chunk=2)),
+                        (1, dict(block=128, fibres_per_thread=4, unroll=1, chunk=2)),
+                        (1, dict(block=128, fibres_per_thread=8, unroll=1, chunk=3))]:
+            with pytest.raises(S.SlError) as e:
+                ctx.set_tune(dim, **sh)
+            assert e.value.status == S.SL_EINVAL
+    with S.Context(_grid((4, 3, 5)), 3, "mix_bf16") as ctx:   # records without lane groups
+        assert ctx.info["record_slots"] == 64
+        with pytest.raises(S.SlError):
+            ctx.set_tune(1, block=128, fibres_per_thread=8, unroll=1, chunk=2)
     with S.Context(_grid((4, 3, 3, 2)), 2, "mix_bf16") as ctx:
         for f in (1, 2, 5, 26):
             with pytest.raises(S.SlError) as e:
