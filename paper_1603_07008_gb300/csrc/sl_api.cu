@@ -203,7 +203,9 @@ void default_tune(sl_ctx* c, int m)
         t.chunk = chunk_for(c, m, 1, c->rec / 16);
         return;
     }
-    t.ft = is_scaled(c) ? scaled_default_ft(c) : 1;
+    // other records: one thread per cell (64-byte 5D records measured ahead of
+    // lane groups)
+    t.ft = c->rec ? int(c->nfib) : is_scaled(c) ? scaled_default_ft(c) : 1;
     if (m == 0) {
         t.block = c->rec ? 128 : 256;
         t.unroll = unit_vec_width(c) ? unit_vec_width(c) : 1;

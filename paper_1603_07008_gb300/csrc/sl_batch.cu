@@ -33,15 +33,35 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
     return cudaGetLastError();
 }
 
-// Persistent sweep over a work list: each block takes items blockIdx.x,
-// blockIdx.x + gridDim.x, ...; every thread reads the problem's sweep
-// geometry straight from the (read-only, L1-cached) argument array, so items
-// need no block barrier, and the problem's degree (0, 1 or 2) selects the
-// compiled variant (uniform across the block).  The loop is bounded by the
-// item count; no block waits on another.  Sweeps along dimension 0 and along
-// the other dimensions are separate kernels, so each has its own register
-// budget.
-template <int MODE, int FT>
+// Persistent sweeps over a work list.  Every thread reads its problem's sweep
+// geometry straight from the (read-only, L1-cached) argument array, and the
+// problem's degree K (0, 1 or 2) and fibres per thread ft (ceil(nfib / nfg),
+// at most FTM) select a compiled body, uniform across the block.  Sweeps
+// along dimension 0 and along the other dimensions are separate kernels, so
+// each has its own register budget.
+//
+// Along dimension 0 the items are short tiles of equal size, taken
+// round-robin (item blockIdx.x, blockIdx.x + gridDim.x, ...).  Along the
+// other dimensions the items (line tiles of uneven length) are sorted by
+// decreasing cost on the host and taken from a shared counter, one atomic per
+// item, so that the long ones start first and no block idles while work
+// remains.  Both loops are bounded by the item count; no block waits on
+// another.
+// One item along dimension 0: reps tiles of kBatchBlock consecutive cells.
+// Not inlined, so that each (K, FT) body gets its own register allocation
+// and reads the problem's geometry where it needs it.
+template <int K, int MODE, int FT>
+__device__ __noinline__ void unit_item(const SweepArgs* __restrict__ ap, uint32_t start, int fbase, int reps)
+{
+    const SweepArgs& a = *ap;
+    for (int r = 0; r < reps; ++r) {
+        const uint32_t c = start + threadIdx.x + uint32_t(r) * kBatchBlock;
+        if (c >= a.cells) break;
+        unit_cell<K, MODE, FT>(a, c, fbase);
+    }
+}
+
+template <int MODE, int FTM>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __restrict__ args,
                                                             const int32_t* __restrict__ kdeg,
                                                             const BatchItem* __restrict__ items,
@@ -49,64 +69,101 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __r
 {
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
-        const SweepArgs a = args[item.prob];
+        const SweepArgs* ap = args + item.prob;
         const int K = kdeg[item.prob];
-        const int fbase = int(item.grp) * FT;
-        // reps tiles of kBatchBlock consecutive cells
-        for (int r = 0; r < reps; ++r) {
-            const uint32_t c = item.start + threadIdx.x + uint32_t(r) * kBatchBlock;
-            if (c >= a.cells) break;
-            switch (K) {
-            case 0: unit_cell<0, MODE, FT>(a, c, fbase); break;
-            case 1: unit_cell<1, MODE, FT>(a, c, fbase); break;
-            default: unit_cell<2, MODE, FT>(a, c, fbase); break;
-            }
+        const int ft = (ap->nfib + ap->nfg - 1) / ap->nfg;
+        const int fbase = int(item.grp) * ft;
+        switch (K * 4 + ft) {
+        case 1: unit_item<0, MODE, 1>(ap, item.start, fbase, reps); break;
+        case 5: unit_item<1, MODE, 1>(ap, item.start, fbase, reps); break;
+        case 9: unit_item<2, MODE, 1>(ap, item.start, fbase, reps); break;
+        case 6:
+            if constexpr (FTM >= 2) unit_item<1, MODE, 2>(ap, item.start, fbase, reps);
+            break;
+        case 10:
+            if constexpr (FTM >= 2) unit_item<2, MODE, 2>(ap, item.start, fbase, reps);
+            break;
+        case 11:
+            if constexpr (FTM >= 3) unit_item<2, MODE, 3>(ap, item.start, fbase, reps);
+            break;
+        default: break;
         }
     }
 }
 
-template <int MODE, int FT, int U>
+// One item along dimension m > 0: kBatchBlock consecutive lines walking one
+// chunk of rows (not inlined, as unit_item).
+template <int K, int MODE, int FT, int U>
+__device__ __noinline__ void strided_item(const SweepArgs* __restrict__ ap, const BatchItem item)
+{
+    const SweepArgs& a = *ap;
+    const LineSetup L = line_setup(a, item.start + threadIdx.x, item.grp, item.chunk, FT);
+    if (L.active) strided_line<K, MODE, FT, U>(a, L);
+}
+
+// Next item of this block from the launch's counter, broadcast through
+// shared memory; the second barrier keeps the slot until every thread has
+// read it.
+__device__ __forceinline__ uint32_t next_item(uint32_t* ctr, uint32_t* slot)
+{
+    if (threadIdx.x == 0) *slot = atomicAdd(ctr, 1u);
+    __syncthreads();
+    const uint32_t it = *slot;
+    __syncthreads();
+    return it;
+}
+
+template <int MODE, int FTM, int U>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_strided(const SweepArgs* __restrict__ args,
                                                                const int32_t* __restrict__ kdeg,
                                                                const BatchItem* __restrict__ items,
-                                                               int nitems)
+                                                               int nitems, uint32_t* __restrict__ ctr)
 {
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    __shared__ uint32_t slot;
+    for (uint32_t it = next_item(ctr, &slot); it < uint32_t(nitems); it = next_item(ctr, &slot)) {
         const BatchItem item = items[it];
-        const SweepArgs a = args[item.prob];
+        const SweepArgs* ap = args + item.prob;
         const int K = kdeg[item.prob];
-        const LineSetup L = line_setup(a, item.start + threadIdx.x, item.grp, item.chunk, FT);
-        if (L.active) {
-            switch (K) {
-            case 0: strided_line<0, MODE, FT, U>(a, L); break;
-            case 1: strided_line<1, MODE, FT, U>(a, L); break;
-            default: strided_line<2, MODE, FT, U>(a, L); break;
-            }
+        const int ft = (ap->nfib + ap->nfg - 1) / ap->nfg;
+        switch (K * 4 + ft) {
+        case 1: strided_item<0, MODE, 1, U>(ap, item); break;
+        case 5: strided_item<1, MODE, 1, U>(ap, item); break;
+        case 9: strided_item<2, MODE, 1, U>(ap, item); break;
+        case 6:
+            if constexpr (FTM >= 2) strided_item<1, MODE, 2, U>(ap, item);
+            break;
+        case 10:
+            if constexpr (FTM >= 2) strided_item<2, MODE, 2, U>(ap, item);
+            break;
+        default: break;
         }
     }
 }
 
 namespace {
 
-template <int MODE, int FT, int U>
+template <int MODE, int FTM, int U>
 cudaError_t launch_b(const SweepArgs* a, const int32_t* k, const BatchItem* items, int nitems,
-                     int unit, int reps, int blocks, cudaStream_t st)
+                     int unit, int reps, int blocks, uint32_t* ctr, cudaStream_t st)
 {
     if (nitems <= 0) return cudaSuccess;
-    if (unit)
-        k_batch_unit<MODE, FT><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, reps);
-    else
-        k_batch_strided<MODE, FT, U><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems);
+    if (unit) {
+        k_batch_unit<MODE, FTM><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, reps);
+    } else {
+        cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+        k_batch_strided<MODE, FTM, U><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, ctr);
+    }
     return cudaGetLastError();
 }
 
-template <int MODE, int FT, int U>
+template <int MODE, int FTM, int U>
 int occ(int unit)
 {
     int n = 0;
-    cudaError_t e = unit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_unit<MODE, FT>,
+    cudaError_t e = unit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_unit<MODE, FTM>,
                                                                          kBatchBlock, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_strided<MODE, FT, U>,
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_strided<MODE, FTM, U>,
                                                                          kBatchBlock, 0);
     if (e != cudaSuccess) return 1;
     return n < 1 ? 1 : n;
@@ -114,24 +171,48 @@ int occ(int unit)
 
 }  // namespace
 
-#define SL_BATCH_SWITCH(CALL)                                                   \
-    switch (mode * 100 + ft * 10 + unroll) {                                    \
-    case M_FP64 * 100 + 11: { constexpr int MD = M_FP64, F = 1, UU = 1; CALL; } \
-    case M_FP64 * 100 + 14: { constexpr int MD = M_FP64, F = 1, UU = 4; CALL; } \
-    case M_FP64 * 100 + 21: { constexpr int MD = M_FP64, F = 2, UU = 1; CALL; } \
-    case M_FP64 * 100 + 24: { constexpr int MD = M_FP64, F = 2, UU = 4; CALL; } \
-    case M_F32 * 100 + 11: { constexpr int MD = M_F32, F = 1, UU = 1; CALL; }   \
-    case M_F32 * 100 + 14: { constexpr int MD = M_F32, F = 1, UU = 4; CALL; }   \
-    case M_F32 * 100 + 21: { constexpr int MD = M_F32, F = 2, UU = 1; CALL; }   \
-    case M_F32 * 100 + 24: { constexpr int MD = M_F32, F = 2, UU = 4; CALL; }   \
-    default: break;                                                             \
+// Compiled shapes: dimension 0 (unit) takes ft 1..3 with unroll 1; the other
+// dimensions ft 1..2 with unroll (cells per walk step) 1, 2 or 4.
+bool batch_shape_ok(int unit, int ft, int unroll)
+{
+    return unit ? (ft >= 1 && ft <= kBatchMaxFtUnit && unroll == 1)
+                : (ft >= 1 && ft <= kBatchMaxFtStrided && (unroll == 1 || unroll == 2 || unroll == 4));
+}
+
+#define SL_BATCH_SWITCH(CALL)                                                                \
+    if (unit) {                                                                              \
+        switch (mode * 10 + ft) {                                                            \
+        case M_FP64 * 10 + 1: { constexpr int MD = M_FP64, F = 1, UU = 1; CALL; }              \
+        case M_FP64 * 10 + 2: { constexpr int MD = M_FP64, F = 2, UU = 1; CALL; }              \
+        case M_FP64 * 10 + 3: { constexpr int MD = M_FP64, F = 3, UU = 1; CALL; }              \
+        case M_F32 * 10 + 1: { constexpr int MD = M_F32, F = 1, UU = 1; CALL; }                \
+        case M_F32 * 10 + 2: { constexpr int MD = M_F32, F = 2, UU = 1; CALL; }                \
+        case M_F32 * 10 + 3: { constexpr int MD = M_F32, F = 3, UU = 1; CALL; }                \
+        default: break;                                                                      \
+        }                                                                                    \
+    } else {                                                                                 \
+        switch (mode * 100 + ft * 10 + unroll) {                                             \
+        case M_FP64 * 100 + 11: { constexpr int MD = M_FP64, F = 1, UU = 1; CALL; }            \
+        case M_FP64 * 100 + 12: { constexpr int MD = M_FP64, F = 1, UU = 2; CALL; }            \
+        case M_FP64 * 100 + 14: { constexpr int MD = M_FP64, F = 1, UU = 4; CALL; }            \
+        case M_FP64 * 100 + 21: { constexpr int MD = M_FP64, F = 2, UU = 1; CALL; }            \
+        case M_FP64 * 100 + 22: { constexpr int MD = M_FP64, F = 2, UU = 2; CALL; }            \
+        case M_FP64 * 100 + 24: { constexpr int MD = M_FP64, F = 2, UU = 4; CALL; }            \
+        case M_F32 * 100 + 11: { constexpr int MD = M_F32, F = 1, UU = 1; CALL; }              \
+        case M_F32 * 100 + 12: { constexpr int MD = M_F32, F = 1, UU = 2; CALL; }              \
+        case M_F32 * 100 + 14: { constexpr int MD = M_F32, F = 1, UU = 4; CALL; }              \
+        case M_F32 * 100 + 21: { constexpr int MD = M_F32, F = 2, UU = 1; CALL; }              \
+        case M_F32 * 100 + 22: { constexpr int MD = M_F32, F = 2, UU = 2; CALL; }              \
+        case M_F32 * 100 + 24: { constexpr int MD = M_F32, F = 2, UU = 4; CALL; }              \
+        default: break;                                                                      \
+        }                                                                                    \
     }
 
 cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
                                const int32_t* d_kdeg, const BatchItem* d_items, int nitems,
-                               int unit, int reps, int blocks, cudaStream_t st)
+                               int unit, int reps, int blocks, uint32_t* d_ctr, cudaStream_t st)
 {
-    SL_BATCH_SWITCH(return (launch_b<MD, F, UU>(d_args, d_kdeg, d_items, nitems, unit, reps, blocks, st)))
+    SL_BATCH_SWITCH(return (launch_b<MD, F, UU>(d_args, d_kdeg, d_items, nitems, unit, reps, blocks, d_ctr, st)))
     return cudaErrorInvalidValue;
 }
 

@@ -3,8 +3,9 @@
 // A batch owns one single-problem context per problem (each with its own
 // ping-pong state, tables and fields).  All problems advance together: every
 // split substep is one table launch over all problems and one persistent
-// sweep launch over a work list of equal-sized tiles of all problems, so
-// uneven problem sizes balance across the GPU.
+// sweep launch over a work list of tiles of all problems, so uneven problem
+// sizes balance across the GPU (along dimensions > 0 the tiles are sorted by
+// decreasing cost and taken from a shared counter).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -36,6 +37,7 @@ struct sl_batch {
     PolyTab* d_tabs = nullptr;     // [degree 0..3]
     BatchMass* d_mass_desc = nullptr;
     double* d_mass = nullptr;      // [prob]
+    uint32_t* d_ctr = nullptr;     // [dim] work-list counters
     std::vector<double> h_mass;
     int maxcls[SL_MAX_DIM] = {0};
 
@@ -43,7 +45,7 @@ struct sl_batch {
     BatchItem* d_items[SL_MAX_DIM] = {nullptr};
     int nitems[SL_MAX_DIM] = {0};
     struct Tune {
-        int ft = 1;
+        int ft = 1;       // most fibres per thread (each problem takes min(ft, its fibres))
         int unroll = 1;   // cells per walk step (dimensions > 0)
         int rows = 64;    // rows per work item (dimensions > 0)
         int reps = 4;     // cell tiles per work item (dimension 0)
@@ -82,22 +84,17 @@ sl_status bcuda(sl_batch* b, cudaError_t e, const char* what)
         if (e_ != cudaSuccess) return bcuda((b), e_, #call); \
     } while (0)
 
-int min_fibres(const sl_batch* b)
-{
-    int64_t m = INT64_MAX;
-    for (auto* c : b->probs) m = std::min<int64_t>(m, c->nfib);
-    return int(m);
-}
 
 // Work items and sweep geometry of dimension m for the batch's current tune.
 sl_status rebuild_dim(sl_batch* b, int m)
 {
     const auto& t = b->tune[m];
     std::vector<BatchItem> items;
+    std::vector<int64_t> cost;   // values one item's threads update (dimensions > 0)
     std::vector<SweepArgs> args(2 * size_t(b->nprob));
     for (int p = 0; p < b->nprob; ++p) {
         sl_ctx* c = b->probs[p];
-        c->tune[m].ft = t.ft;
+        c->tune[m].ft = int(std::min<int64_t>(t.ft, c->nfib));
         c->tune[m].unroll = t.unroll;
         c->tune[m].pipeline = 0;
         const int64_t N = c->g.n[m];
@@ -114,10 +111,25 @@ sl_status rebuild_dim(sl_batch* b, int m)
         } else {
             const uint32_t tiles = (a.lines + kBatchBlock - 1) / kBatchBlock;
             const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
+            const int64_t ft = c->tune[m].ft;
             for (uint32_t g = 0; g < nfg; ++g)
                 for (uint32_t ch = 0; ch < nchunk; ++ch)
-                    for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * kBatchBlock, g, ch});
+                    for (uint32_t i = 0; i < tiles; ++i) {
+                        items.push_back({uint32_t(p), i * kBatchBlock, g, ch});
+                        const int64_t lines = std::min<int64_t>(kBatchBlock, int64_t(a.lines) - int64_t(i) * kBatchBlock);
+                        const int64_t rows = std::min<int64_t>(a.chunk, int64_t(a.N) - int64_t(ch) * a.chunk);
+                        const int64_t fib = std::min<int64_t>(ft, c->nfib - int64_t(g) * ft);
+                        cost.push_back(lines * rows * fib * c->O);
+                    }
         }
+    }
+    if (m > 0) {   // longest first (the blocks take them in order)
+        std::vector<size_t> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+        std::vector<BatchItem> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        items.swap(sorted);
     }
     SLB_CUDA(b, cudaMemcpyAsync(b->d_args + size_t(m) * 2 * b->nprob, args.data(),
                                 args.size() * sizeof(SweepArgs), cudaMemcpyHostToDevice, b->st));
@@ -156,7 +168,8 @@ sl_status batch_sweep(sl_batch* b, int m, double tau)
     const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
     SLB_CUDA(b, launch_batch_sweep(b->mode, t.ft, t.unroll,
                                    b->d_args + (size_t(m) * 2 + b->parity) * b->nprob, b->d_kdeg,
-                                   b->d_items[m], b->nitems[m], m == 0, t.reps, blocks, b->st));
+                                   b->d_items[m], b->nitems[m], m == 0, t.reps, blocks, b->d_ctr + m,
+                                   b->st));
     if (prof) {
         SLB_CUDA(b, cudaEventRecord(e1, b->st));
         b->ev.emplace_back(e0, e1);
@@ -279,6 +292,7 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
     const size_t o_tabs = take(sizeof(PolyTab) * 4);
     const size_t o_md = take(sizeof(BatchMass) * nprob);
     const size_t o_m = take(sizeof(double) * nprob);
+    const size_t o_ctr = take(sizeof(uint32_t) * SL_MAX_DIM);
     if (cudaMalloc(&b->mem, off) != cudaSuccess) return cleanup(fail(nullptr, SL_ENOMEM, "batch tables"));
     char* base = static_cast<char*>(b->mem);
     b->d_args = reinterpret_cast<SweepArgs*>(base + o_args);
@@ -287,6 +301,7 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
     b->d_tabs = reinterpret_cast<PolyTab*>(base + o_tabs);
     b->d_mass_desc = reinterpret_cast<BatchMass*>(base + o_md);
     b->d_mass = reinterpret_cast<double*>(base + o_m);
+    b->d_ctr = reinterpret_cast<uint32_t*>(base + o_ctr);
     b->h_mass.resize(nprob);
 
     std::vector<int32_t> kd(nprob);
@@ -332,11 +347,11 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
                         b->st) != cudaSuccess ||
         cudaStreamSynchronize(b->st) != cudaSuccess)
         return cleanup(fail(nullptr, SL_ECUDA, "uploading batch tables"));
-    // default shapes: the most fibres per thread every problem allows, four
-    // cells per walk step, 64-row work items, four cell tiles per item
-    const int ftmax = std::min(2, min_fibres(b));
+    // default shapes: the most fibres per thread compiled (each problem takes
+    // at most its own), four cells per walk step, 64-row work items, four
+    // cell tiles per item
     for (int m = 0; m < b->ndim; ++m) {
-        b->tune[m].ft = ftmax;
+        b->tune[m].ft = m == 0 ? kBatchMaxFtUnit : kBatchMaxFtStrided;
         b->tune[m].unroll = m == 0 ? 1 : 4;
         b->tune[m].rows = 64;
         b->tune[m].reps = 4;
@@ -495,7 +510,6 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
     if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
     if (b->capturing) return bfail(b, SL_EINVAL, "cannot autotune during a capture");
     reps = std::max(1, std::min(reps, 50));
-    const int ftmax = std::min(2, min_fibres(b));
     cudaEvent_t e0 = new_event(), e1 = new_event();
     if (!e0 || !e1) return bfail(b, SL_ECUDA, "cudaEventCreate failed");
     sl_status result = SL_OK;
@@ -503,13 +517,13 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
     b->prof = false;
     for (int m = 0; m < b->ndim && result == SL_OK; ++m) {
         std::vector<sl_batch::Tune> cand;
-        for (int ft = 1; ft <= ftmax; ++ft) {
-            if (m == 0) {
+        if (m == 0) {
+            for (int ft = 1; ft <= kBatchMaxFtUnit; ++ft)
                 for (int r : {1, 4, 8}) cand.push_back({ft, 1, 64, r});
-            } else {
-                for (int u : {1, 4})
-                    for (int rows : {32, 64, 128}) cand.push_back({ft, u, rows, 4});
-            }
+        } else {
+            for (int ft = 1; ft <= kBatchMaxFtStrided; ++ft)
+                for (int u : {2, 4})
+                    for (int rows : {32, 64, 128, 1 << 30}) cand.push_back({ft, u, rows, 4});
         }
         sl_batch::Tune best = b->tune[m];
         float best_ms = 1e30f;
@@ -527,7 +541,7 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
                 const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
                 e = launch_batch_sweep(b->mode, t.ft, t.unroll, b->d_args + (size_t(m) * 2 + par) * b->nprob,
                                        b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, t.reps, blocks,
-                                       b->st);
+                                       b->d_ctr + m, b->st);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);

@@ -190,7 +190,9 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
 // `kBatchBlock` consecutive lines walking one chunk of rows (other
 // dimensions), starting at `start` of problem `prob`, for fibre group `grp`.
 constexpr int kBatchBlock = 128;
-constexpr int kBatchMaxK = 2;   // degrees compiled into the batched sweep
+constexpr int kBatchMaxK = 2;          // degrees compiled into the batched sweep
+constexpr int kBatchMaxFtUnit = 3;     // fibres per thread compiled along dimension 0
+constexpr int kBatchMaxFtStrided = 2;  // ... and along the other dimensions
 struct BatchItem {
     uint32_t prob;
     uint32_t start;
@@ -221,10 +223,14 @@ struct BatchMass {
 
 cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int nprob, int maxclass,
                             double tau, cudaStream_t st);
-// unit = 1: sweep along dimension 0, each item covering reps * kBatchBlock cells.
+// unit = 1: sweep along dimension 0, each item covering reps * kBatchBlock
+// cells.  ft is the most fibres per thread (each problem's own is
+// ceil(nfib / nfg) of its arguments).  Along the other dimensions the blocks
+// take items from *d_ctr, which the launch first sets to zero.
 cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
                                const int32_t* d_kdeg, const BatchItem* d_items, int nitems,
-                               int unit, int reps, int blocks, cudaStream_t st);
+                               int unit, int reps, int blocks, uint32_t* d_ctr, cudaStream_t st);
+bool batch_shape_ok(int unit, int ft, int unroll);
 // Resident blocks per SM of the batched sweep kernel for (mode, ft, unroll).
 int batch_sweep_occupancy(int mode, int ft, int unroll, int unit);
 cudaError_t launch_batch_mass(const BatchMass* d_desc, int nprob, int parity, double* d_out,
