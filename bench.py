@@ -339,9 +339,8 @@ class Arm:
         return float(np.sum(m)) if self.workload == "batch" else m
 
     def tunes(self):
-        if self.workload == "batch":
-            return None
-        return [self.obj.get_tune(d) for d in range(self.p.grid.ndim)]
+        nd = self.p[0].grid.ndim if self.workload == "batch" else self.p.grid.ndim
+        return [self.obj.get_tune(d) for d in range(nd)]
 
 
 def run_ours(args):

@@ -310,6 +310,10 @@ sl_status sl_batch_autotune(sl_batch* batch, int reps);
  * bytes = 2 x (sum of the problems' state bytes) per launch. */
 sl_status sl_batch_profile_enable(sl_batch* batch, int enable);
 sl_status sl_batch_profile_query(sl_batch* batch, int64_t* launches, double* ms, double* bytes);
+/* Per sweep dimension m (launches[SL_MAX_DIM], ms[SL_MAX_DIM]): the launches
+ * and milliseconds of the last sl_batch_profile_query's window. */
+sl_status sl_batch_profile_dims(const sl_batch* batch, int64_t* launches, double* ms);
+
 
 /* ---------------------------------------------------------------- launch shapes */
 
@@ -361,6 +365,12 @@ sl_status sl_set_tune(sl_ctx* ctx, int dim, const sl_tune* tune);
  * times on the current state (out of place, so the state is unchanged) and
  * keep the fastest.  Synchronises.  Must not be called during a capture. */
 sl_status sl_autotune(sl_ctx* ctx, int reps);
+
+/* The batch's work-list shape along dimension dim: block = threads per
+ * block, fibres_per_thread = the most fibres per thread (each problem takes
+ * at most its own), unroll = cells per walk step, chunk = rows per work item
+ * (dim > 0) or cells per work item (dim 0); pipeline is 0. */
+sl_status sl_batch_get_tune(const sl_batch* batch, int dim, sl_tune* out);
 
 /* ---------------------------------------------------------------- profiling */
 

@@ -30,7 +30,8 @@ __all__ = [
     "sl_batch_create", "sl_batch_destroy", "sl_batch_last_error", "sl_batch_info", "sl_batch_project",
     "sl_batch_set_coeffs", "sl_batch_get_coeffs", "sl_batch_set_fields", "sl_batch_step",
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
-    "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query",
+    "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
+    "sl_batch_get_tune",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -149,6 +150,8 @@ def lib():
             "sl_batch_autotune": (st, [_vp, ctypes.c_int]),
             "sl_batch_profile_enable": (st, [_vp, ctypes.c_int]),
             "sl_batch_profile_query": (st, [_vp, _i64p, _dp, _dp]),
+            "sl_batch_profile_dims": (st, [_vp, _i64p, _dp]),
+            "sl_batch_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
         }
         for name, (res, args) in sig.items():
@@ -546,6 +549,20 @@ def sl_batch_profile_query(b):
     return n.value, ms.value, by.value
 
 
+def sl_batch_profile_dims(b):
+    n = (ctypes.c_int64 * MAX_DIM)()
+    ms = (ctypes.c_double * MAX_DIM)()
+    _bcheck(lib().sl_batch_profile_dims(b, n, ms), b)
+    return list(n), list(ms)
+
+
+def sl_batch_get_tune(b, dim: int):
+    t = sl_tune()
+    _bcheck(lib().sl_batch_get_tune(b, int(dim), ctypes.byref(t)), b)
+    return dict(block=t.block, fibres_per_thread=t.fibres_per_thread, unroll=t.unroll,
+                pipeline=t.pipeline, chunk=t.chunk)
+
+
 class Batch:
     """Owns one sl_batch handle for a list of problems (objects with .grid, .k)."""
 
@@ -609,3 +626,9 @@ class Batch:
 
     def profile_query(self):
         return sl_batch_profile_query(self.handle)
+
+    def profile_dims(self):
+        return sl_batch_profile_dims(self.handle)
+
+    def get_tune(self, dim):
+        return sl_batch_get_tune(self.handle, dim)

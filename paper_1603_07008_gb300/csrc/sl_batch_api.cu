@@ -58,7 +58,10 @@ struct sl_batch {
 
     bool prof = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+    std::vector<int> ev_dim;
     int64_t prof_launches = 0;
+    int64_t last_dim_launches[SL_MAX_DIM] = {0};
+    double last_dim_ms[SL_MAX_DIM] = {0.0};
 };
 
 namespace {
@@ -173,6 +176,7 @@ sl_status batch_sweep(sl_batch* b, int m, double tau)
     if (prof) {
         SLB_CUDA(b, cudaEventRecord(e1, b->st));
         b->ev.emplace_back(e0, e1);
+        b->ev_dim.push_back(m);
         b->prof_launches++;
     }
     b->parity ^= 1;
@@ -576,18 +580,48 @@ sl_status sl_batch_profile_query(sl_batch* b, int64_t* launches, double* ms, dou
     if (!b) return fail(nullptr, SL_EINVAL, "batch is NULL");
     SLB_CUDA(b, cudaStreamSynchronize(b->st));
     double tot = 0.0;
-    for (auto& pr : b->ev) {
+    for (int m = 0; m < SL_MAX_DIM; ++m) {
+        b->last_dim_launches[m] = 0;
+        b->last_dim_ms[m] = 0.0;
+    }
+    for (size_t q = 0; q < b->ev.size(); ++q) {
         float t = 0.0f;
-        SLB_CUDA(b, cudaEventElapsedTime(&t, pr.first, pr.second));
+        SLB_CUDA(b, cudaEventElapsedTime(&t, b->ev[q].first, b->ev[q].second));
         tot += t;
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+        b->last_dim_launches[b->ev_dim[q]]++;
+        b->last_dim_ms[b->ev_dim[q]] += t;
+        cudaEventDestroy(b->ev[q].first);
+        cudaEventDestroy(b->ev[q].second);
     }
     b->ev.clear();
+    b->ev_dim.clear();
     if (launches) *launches = b->prof_launches;
     if (ms) *ms = tot;
     if (bytes) *bytes = 2.0 * double(b->state_bytes) * double(b->prof_launches);
     b->prof_launches = 0;
+    return SL_OK;
+}
+
+sl_status sl_batch_profile_dims(const sl_batch* b, int64_t* launches, double* ms)
+{
+    if (!b || !launches || !ms) return fail(nullptr, SL_EINVAL, "NULL argument");
+    for (int m = 0; m < SL_MAX_DIM; ++m) {
+        launches[m] = b->last_dim_launches[m];
+        ms[m] = b->last_dim_ms[m];
+    }
+    return SL_OK;
+}
+
+sl_status sl_batch_get_tune(const sl_batch* b, int dim, sl_tune* out)
+{
+    if (!b || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (dim < 0 || dim >= b->ndim) return fail(nullptr, SL_EINVAL, "dim out of range");
+    const auto& t = b->tune[dim];
+    out->block = kBatchBlock;
+    out->fibres_per_thread = t.ft;
+    out->unroll = t.unroll;
+    out->pipeline = 0;
+    out->chunk = dim == 0 ? int64_t(t.reps) * kBatchBlock : int64_t(t.rows);
     return SL_OK;
 }
 

@@ -78,6 +78,25 @@ def test_batch_graph_and_autotune_keep_results():
         assert np.array_equal(a, c)
 
 
+def test_batch_profile_and_tune_readback():
+    probs = _problems(SIZES, DEGS, "mix_fp32")
+    with S.Batch([p.grid for p in probs], [p.k for p in probs], "mix_fp32") as b:
+        for i, p in enumerate(probs):
+            b.project(i, p.nq, p.weights, p.params)
+        b.set_fields([p.field_list()[0] for p in probs])
+        t0, t1 = b.get_tune(0), b.get_tune(1)
+        assert t0["block"] == 128 and 1 <= t0["fibres_per_thread"] <= 3 and t0["chunk"] % 128 == 0
+        assert 1 <= t1["fibres_per_thread"] <= 2 and t1["unroll"] in (1, 2, 4) and t1["chunk"] >= 1
+        b.profile_enable(True)
+        b.step("strang", 0.1, 2)          # x/2, v, x/2 per step
+        n, ms, by = b.profile_query()
+        nd, msd = b.profile_dims()
+        assert n == 6 and nd[:2] == [4, 2] and sum(nd) == 6
+        assert abs(sum(msd) - ms) <= 1e-6 * max(ms, 1.0)
+        with pytest.raises(S.SlError):
+            b.get_tune(2)
+
+
 def test_batch_mass_matches_single_problem_mass():
     probs = _problems(SIZES, DEGS, "fp64")
     with S.Batch([p.grid for p in probs], [p.k for p in probs], "fp64") as b:
