@@ -257,6 +257,16 @@ sl_status sl_mass(sl_ctx* ctx, double* out);
 sl_status sl_mass_noalloc(const double* d_mean, int64_t cells, double cell_volume, double* d_out,
                           void* cuda_stream);
 
+/* Self-test of the device-side binary32 <-> binary64 conversions the mean
+ * row of the low-precision stores uses (integer-pipe forms of the IEEE 754
+ * conversions).  For host arrays of n elements (1 <= n <= 2^26):
+ * f_out[2i] = fl32(d_in[i]) and f_out[2i+1] = fl32(-d_in[i]), rounded to
+ * nearest with ties to even (f_out holds 2n floats); d_out[i] = f_in[i]
+ * (exact).  Synchronous, on the default stream.  Errors: SL_EINVAL,
+ * SL_ENOMEM, SL_ECUDA; sl_last_error does not cover this call. */
+sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
+                                  double* d_out);
+
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later
  * sl_set_fields is not seen by the graph until it is captured again. */

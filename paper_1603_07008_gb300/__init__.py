@@ -31,7 +31,7 @@ __all__ = [
     "sl_batch_set_coeffs", "sl_batch_get_coeffs", "sl_batch_set_fields", "sl_batch_step",
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
-    "sl_batch_get_tune",
+    "sl_batch_get_tune", "sl_selftest_conversions",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -153,6 +153,8 @@ def lib():
             "sl_batch_profile_dims": (st, [_vp, _i64p, _dp]),
             "sl_batch_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
+            "sl_selftest_conversions": (st, [_dp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
+                                             ctypes.POINTER(ctypes.c_float), _dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -362,6 +364,22 @@ def sl_set_tune(ctx, dim: int, block: int, fibres_per_thread: int = 1, unroll: i
 
 def sl_autotune(ctx, reps: int = 3):
     _check(lib().sl_autotune(ctx, int(reps)), ctx)
+
+
+def sl_selftest_conversions(d_in, f_in):
+    """(fl32(d), fl32(-d), double(f)) from the library's device conversions."""
+    d = np.ascontiguousarray(d_in, dtype=np.float64)
+    f = np.ascontiguousarray(f_in, dtype=np.float32)
+    if d.size != f.size:
+        raise ValueError("d_in and f_in differ in length")
+    fo = np.empty(2 * d.size, dtype=np.float32)
+    do = np.empty(d.size, dtype=np.float64)
+    st = lib().sl_selftest_conversions(d.ctypes.data_as(_dp), f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       d.size, fo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                       do.ctypes.data_as(_dp))
+    if st != SL_OK:
+        raise SlError(st, "sl_selftest_conversions failed")
+    return fo[0::2], fo[1::2], do
 
 
 def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, stream=None):

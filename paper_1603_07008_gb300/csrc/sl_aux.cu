@@ -2,6 +2,7 @@
 // construction of A(alpha), B(alpha) per shift class, the FP64 mass
 // reduction, encoding/decoding of the split store, and the initial
 // projection eq. (cj).
+#include "../../include/sl.h"
 #include "sl_ab.cuh"
 #include "sl_sweep.cuh"
 
@@ -321,3 +322,43 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
 }
 
 }  // namespace sl
+
+// ---------------------------------------------------------------- conversion self-test
+
+namespace sl {
+
+__global__ void k_conv_check(const double* __restrict__ din, const float* __restrict__ fin, uint32_t n,
+                             float* __restrict__ fout, double* __restrict__ dout)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    fout[2 * i] = d2f_rn(din[i], false);
+    fout[2 * i + 1] = d2f_rn(din[i], true);
+    dout[i] = f2d_exact(fin[i]);
+}
+
+}  // namespace sl
+
+extern "C" sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
+                                             double* d_out)
+{
+    if (!d_in || !f_in || !f_out || !d_out || n < 1 || n > (int64_t(1) << 26)) return SL_EINVAL;
+    const size_t N = size_t(n);
+    char* mem = nullptr;
+    const size_t bytes = N * (8 + 4 + 8 + 8);
+    if (cudaMalloc(&mem, bytes) != cudaSuccess) return SL_ENOMEM;
+    double* din = reinterpret_cast<double*>(mem);
+    double* dout = din + N;
+    float* fout = reinterpret_cast<float*>(dout + N);
+    float* fin = fout + 2 * N;
+    cudaError_t e = cudaMemcpy(din, d_in, N * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fin, f_in, N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        sl::k_conv_check<<<unsigned((N + 255) / 256), 256>>>(din, fin, uint32_t(N), fout, dout);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(f_out, fout, N * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(d_out, dout, N * 8, cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    return e == cudaSuccess ? SL_OK : SL_ECUDA;
+}

@@ -98,6 +98,67 @@ __device__ __forceinline__ void pow2_scale(float mx, float& s, float& inv)
     inv = __uint_as_float((253u - E) << 23);
 }
 
+// Conversions between IEEE 754 binary32 and binary64 done on the integer
+// pipe.  GB300's FP64 pipe (which also executes the F2F conversions) runs at
+// a small fraction of the FP32 rate, and the mean row of the low-precision
+// stores would otherwise spend three of its seven FP64-pipe instructions on
+// conversions.  Both functions return exactly what the conversion instruction
+// returns (float to double is exact; double to float rounds to nearest, ties
+// to even); inputs outside the ranges handled here (subnormal results,
+// infinities, NaN) take the conversion instruction.
+//
+// binary32 -> binary64: sign kept, exponent rebiased by 1023 - 127 = 896,
+// the 23 fraction bits placed at the top of the 52-bit fraction.
+__device__ __forceinline__ double f2d_exact(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __hiloint2double(int(u), 0);   // +-0
+    if (e == 0u || e == 255u) return double(x);                         // subnormal, inf, NaN
+    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double(int(hi), int(u << 29));
+}
+
+// binary64 -> binary32 of (neg ? -x : x), rounded to nearest even: the top
+// 23 of the 52 fraction bits are kept and the other 29 decide the rounding;
+// a carry out of the fraction moves into the exponent, which is the correct
+// result, up to overflow to infinity.  Results below the binary32 normal
+// range (other than zero) take the conversion instruction.
+__device__ __forceinline__ float d2f_rn(double x, bool neg)
+{
+    uint32_t hi = uint32_t(__double2hiint(x));
+    const uint32_t lo = uint32_t(__double2loint(x));
+    if (neg) hi ^= 0x80000000u;
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);   // +-0
+    if (e < 897u || e > 1150u) return float(__hiloint2double(int(hi), int(lo)));
+    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t r = lo & 0x1fffffffu;
+    uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
+    f += (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+// New mean of a cell in the low-precision stores (conservation form, see
+// combine) from the source means ma (cell i - sigma), mb (i - sigma - 1) and
+// their per-cell FP32 sums ga = G(a), gb = G(b); dm = fl32(ma - mb) for the
+// l = 0 term of the other rows.  Four FP64-pipe instructions with the
+// integer-pipe conversions; HW uses the conversion instructions instead (the
+// same results; shorter code, for kernels bound by instruction latency rather
+// than by the FP64 pipe).
+template <bool HW = false>
+__device__ __forceinline__ double mean_row_lp(double alpha, double ma, double mb, float ga, float gb, float& dm)
+{
+    const double t = mb - ma;
+    if constexpr (HW) {
+        dm = float(-t);
+        return fma(alpha, t, ma) + (double(ga) - double(gb));
+    } else {
+        dm = d2f_rn(t, true);
+        return fma(alpha, t, ma) + (f2d_exact(ga) - f2d_exact(gb));
+    }
+}
+
 template <int K, int MODE, int FT>
 struct CellVals {
     typename St<MODE>::R v[FT][K + 1];   // v[0][0] of the mean's group is unused: the mean is in m
@@ -169,7 +230,8 @@ struct Mats {
 
 // New values of one target cell from its source cells a (= i - sigma) and
 // b (= i - sigma - 1).  With MEAN, fibre 0 of the group is the mean's fibre.
-template <int K, int MODE, int FT, bool MEAN>
+// HW: conversions of the mean row by instruction (see mean_row_lp).
+template <int K, int MODE, int FT, bool MEAN, bool HW = false>
 __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K, MODE, FT>& a,
                                         const CellVals<K, MODE, FT>& b,
                                         CellVals<K, MODE, FT>& out)
@@ -210,9 +272,8 @@ __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K
                     ga = fmaf(M.a[0][l], a.v[0][l], ga);
                     gb = fmaf(M.a[0][l], b.v[0][l], gb);
                 }
-                const double t = b.m - a.m;
-                out.m = fma(M.alpha, t, a.m) + (double(ga) - double(gb));
-                const float dm = float(-t);
+                float dm;
+                out.m = mean_row_lp<HW>(M.alpha, a.m, b.m, ga, gb, dm);
 #pragma unroll
                 for (int j = 1; j < O; ++j) {
                     R acc = M.a[j][0] * dm;
@@ -394,7 +455,7 @@ __device__ __forceinline__ uint32_t shift_class(const SweepArgs& a, uint32_t inn
 
 // ---------------------------------------------------------------- unit stride
 
-template <int K, int MODE, int FT, bool MEAN>
+template <int K, int MODE, int FT, bool MEAN, bool HW = false>
 __device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32_t ca, uint32_t cb,
                                           uint32_t cls, int fbase)
 {
@@ -411,12 +472,12 @@ __device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32
     CellVals<K, MODE, FT> va, vb, out;
     load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, ca, jb, 1, va);
     load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, cb, jb, 1, vb);
-    combine<K, MODE, FT, MEAN>(M, va, vb, out);
+    combine<K, MODE, FT, MEAN, HW>(M, va, vb, out);
     store_cell<K, MODE, FT, MEAN>(a.dst, a.pstride, c, jb, 1, out);
 }
 
 // Target cell c of a sweep along dimension 0, fibres fbase .. fbase+FT-1.
-template <int K, int MODE, int FT>
+template <int K, int MODE, int FT, bool HW = false>
 __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fbase)
 {
     const uint32_t line = a.fdN.div(c);
@@ -430,9 +491,9 @@ __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fb
     const uint32_t ca = c - i + uint32_t(ia);
     const uint32_t cb = c - i + uint32_t(ib);
     if (St<MODE>::scaled || fbase == 0)
-        unit_body<K, MODE, FT, true>(a, c, ca, cb, cls, fbase);
+        unit_body<K, MODE, FT, true, HW>(a, c, ca, cb, cls, fbase);
     else
-        unit_body<K, MODE, FT, false>(a, c, ca, cb, cls, fbase);
+        unit_body<K, MODE, FT, false, HW>(a, c, ca, cb, cls, fbase);
 }
 
 // Sweep along dimension 0: one thread per target cell (and fibre group

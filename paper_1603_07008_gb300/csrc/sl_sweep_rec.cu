@@ -95,9 +95,8 @@ __device__ __forceinline__ void lg_combine(const Mats<1, MODE>& T, const LgRow& 
             float ga = 0.0f, gb = 0.0f;
             ga = fmaf(T.a[0][1], a1, ga);
             gb = fmaf(T.a[0][1], b1, gb);
-            const double t = rb.m - ra.m;
-            om = fma(T.alpha, t, ra.m) + (double(ga) - double(gb));
-            const float dm = float(-t);
+            float dm;
+            om = mean_row_lp(T.alpha, ra.m, rb.m, ga, gb, dm);
             float acc = T.a[1][0] * dm;
             acc = fmaf(T.a[1][1], a1, acc);
             acc = fmaf(T.b[1][1], b1, acc);

@@ -1,0 +1,70 @@
+"""The device-side binary32 <-> binary64 conversions of the mean row (integer
+pipe forms) against IEEE 754 round-to-nearest-even conversions on the host,
+bit for bit, on random values and the edge cases of both formats."""
+import numpy as np
+import pytest
+
+import paper_1603_07008_gb300 as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _bits32(x):
+    return np.asarray(x, dtype=np.float32).view(np.uint32)
+
+
+def _bits64(x):
+    return np.asarray(x, dtype=np.float64).view(np.uint64)
+
+
+def _doubles():
+    rng = np.random.default_rng(7)
+    f32 = np.finfo(np.float32)
+    base = [0.0, -0.0, 1.0, -1.0, 1.5, np.pi, 1e-3, 0.37, 2.0 ** -126, 2.0 ** -127, 2.0 ** -149,
+            2.0 ** -150, 1e-45, 1e-300, 5e-324, float(f32.max), -float(f32.max), 3.5e38, 1e300,
+            np.inf, -np.inf, np.nan]
+    # exact ties between two binary32 values: mantissa bit 28 of the 29 dropped bits set, rest zero
+    ties = []
+    for m in (0, 1, 2, 3, 0x7FFFFF):
+        for e in (-100, -1, 0, 1, 60, 127):
+            x = np.float64((1.0 + m * 2.0 ** -23 + 2.0 ** -24) * 2.0 ** e)
+            ties += [x, -x, np.nextafter(x, np.inf), np.nextafter(x, -np.inf)]
+    # largest finite double that rounds to FLT_MAX, and the one above (overflow to inf)
+    ties += [float(f32.max) * (1 + 2.0 ** -25), float(f32.max) * (1 + 2.0 ** -24)]
+    rnd = rng.standard_normal(20000) * np.exp2(rng.integers(-140, 130, 20000))
+    bits = rng.integers(0, 2 ** 63, 20000, dtype=np.int64).astype(np.uint64).view(np.float64)
+    return np.concatenate([base, ties, rnd, bits[np.isfinite(bits)]]).astype(np.float64)
+
+
+def _floats(n):
+    rng = np.random.default_rng(8)
+    f32 = np.finfo(np.float32)
+    base = np.array([0.0, -0.0, 1.0, -2.5, f32.max, -f32.max, f32.tiny, f32.tiny / 2, 1e-45, -1e-45,
+                     np.inf, -np.inf, np.nan], dtype=np.float32)
+    rnd = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32).view(np.float32)
+    out = np.concatenate([base, rnd])[:n]
+    return np.resize(out, n)
+
+
+def test_conversions_match_ieee_round_to_nearest_even():
+    d = _doubles()
+    f = _floats(d.size)
+    with np.errstate(over="ignore"):
+        want_pos = d.astype(np.float32)
+        want_neg = (-d).astype(np.float32)
+    got_pos, got_neg, got_d = S.sl_selftest_conversions(d, f)
+    nan_p = np.isnan(want_pos)
+    assert np.array_equal(np.isnan(got_pos), nan_p) and np.array_equal(np.isnan(got_neg), np.isnan(want_neg))
+    assert np.array_equal(_bits32(got_pos[~nan_p]), _bits32(want_pos[~nan_p]))
+    assert np.array_equal(_bits32(got_neg[~nan_p]), _bits32(want_neg[~nan_p]))
+    want_d = f.astype(np.float64)
+    nan_d = np.isnan(want_d)
+    assert np.array_equal(np.isnan(got_d), nan_d)
+    assert np.array_equal(_bits64(got_d[~nan_d]), _bits64(want_d[~nan_d]))
+
+
+def test_conversion_selftest_rejects_bad_sizes():
+    with pytest.raises(ValueError):
+        S.sl_selftest_conversions(np.zeros(3), np.zeros(2, np.float32))
+    st = S.lib().sl_selftest_conversions(None, None, 0, None, None)
+    assert st == S.SL_EINVAL
