@@ -262,10 +262,14 @@ sl_status sl_mass_noalloc(const double* d_mean, int64_t cells, double cell_volum
  * conversions).  For host arrays of n elements (1 <= n <= 2^26):
  * f_out[2i] = fl32(d_in[i]) and f_out[2i+1] = fl32(-d_in[i]), rounded to
  * nearest with ties to even (f_out holds 2n floats); d_out[i] = f_in[i]
- * (exact).  Synchronous, on the default stream.  Errors: SL_EINVAL,
+ * (exact).  Exception, the binary32 subnormal range: results of magnitude
+ * below 2^-126 become a signed zero, and subnormal f_in map to doubles of
+ * magnitude below 2^-126.  *mismatches = the number of elements on which the
+ * library's branching and branch-free forms of these conversions disagree
+ * (must be 0).  Synchronous, on the default stream.  Errors: SL_EINVAL,
  * SL_ENOMEM, SL_ECUDA; sl_last_error does not cover this call. */
 sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
-                                  double* d_out);
+                                  double* d_out, int64_t* mismatches);
 
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later
@@ -352,6 +356,10 @@ sl_status sl_batch_profile_dims(const sl_batch* batch, int64_t* launches, double
  *       G = R/16 lanes share a cell, each holding 16 slots; every dimension,
  *       dimension 0 included, is walked (chunk >= 1), unroll 1, 2 or 4 cells
  *       per walk step, block <= 256.
+ *   max_blocks_per_sm  0, or 4, 5 or 6: the register walk along dimensions > 0
+ *                      (FP64 and FP32 stores, pipeline 0) runs at most that
+ *                      many blocks per SM (fewer concurrent walks can use the
+ *                      DRAM pages better; the autotuner measures it)
  *   pipeline           0: the walk keeps the previous cell in registers;
  *                      4 or 8: the walk streams its source rows through a
  *                      per-thread cp.async ring of that many rows in shared
@@ -365,6 +373,8 @@ typedef struct {
     int32_t unroll;
     int32_t pipeline;
     int64_t chunk;
+    int32_t max_blocks_per_sm;
+    int32_t reserved;   /* must be 0 */
 } sl_tune;
 
 sl_status sl_get_tune(const sl_ctx* ctx, int dim, sl_tune* out);

@@ -50,7 +50,8 @@ class SlError(RuntimeError):
 
 class sl_tune(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("fibres_per_thread", ctypes.c_int32),
-                ("unroll", ctypes.c_int32), ("pipeline", ctypes.c_int32), ("chunk", ctypes.c_int64)]
+                ("unroll", ctypes.c_int32), ("pipeline", ctypes.c_int32), ("chunk", ctypes.c_int64),
+                ("max_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class sl_grid(ctypes.Structure):
@@ -154,7 +155,7 @@ def lib():
             "sl_batch_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_selftest_conversions": (st, [_dp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
-                                             ctypes.POINTER(ctypes.c_float), _dp]),
+                                             ctypes.POINTER(ctypes.c_float), _dp, _i64p]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -353,12 +354,13 @@ def sl_profile_dims(ctx):
 def sl_get_tune(ctx, dim: int) -> dict:
     t = sl_tune()
     _check(lib().sl_get_tune(ctx, int(dim), ctypes.byref(t)), ctx)
-    return {k: getattr(t, k) for k, _ in sl_tune._fields_}
+    return {k: getattr(t, k) for k, _ in sl_tune._fields_ if k != "reserved"}
 
 
 def sl_set_tune(ctx, dim: int, block: int, fibres_per_thread: int = 1, unroll: int = 1,
-                chunk: int = 0, pipeline: int = 0):
-    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(pipeline), int(chunk))
+                chunk: int = 0, pipeline: int = 0, max_blocks_per_sm: int = 0):
+    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(pipeline), int(chunk),
+                int(max_blocks_per_sm), 0)
     _check(lib().sl_set_tune(ctx, int(dim), ctypes.byref(t)), ctx)
 
 
@@ -367,19 +369,21 @@ def sl_autotune(ctx, reps: int = 3):
 
 
 def sl_selftest_conversions(d_in, f_in):
-    """(fl32(d), fl32(-d), double(f)) from the library's device conversions."""
+    """(fl32(d), fl32(-d), double(f), mismatches) from the library's device
+    conversions; mismatches counts elements where its two forms disagree."""
     d = np.ascontiguousarray(d_in, dtype=np.float64)
     f = np.ascontiguousarray(f_in, dtype=np.float32)
     if d.size != f.size:
         raise ValueError("d_in and f_in differ in length")
     fo = np.empty(2 * d.size, dtype=np.float32)
     do = np.empty(d.size, dtype=np.float64)
+    mm = ctypes.c_int64()
     st = lib().sl_selftest_conversions(d.ctypes.data_as(_dp), f.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                                        d.size, fo.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                       do.ctypes.data_as(_dp))
+                                       do.ctypes.data_as(_dp), ctypes.byref(mm))
     if st != SL_OK:
         raise SlError(st, "sl_selftest_conversions failed")
-    return fo[0::2], fo[1::2], do
+    return fo[0::2], fo[1::2], do, mm.value
 
 
 def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, stream=None):

@@ -193,6 +193,7 @@ void default_tune(sl_ctx* c, int m)
 {
     auto& t = c->tune[m];
     t.pipeline = 0;
+    t.occ = 0;
     if (rec_lanes_ok(c) && c->ndim == 6) {
         // 128-byte records: lane groups (measured ahead of one thread per
         // cell, whose 16-byte pieces of 32 records per warp access keep the
@@ -290,6 +291,7 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.dim = dim;
     L.ndim = c->ndim;
     L.rec = c->rec;
+    L.occ = dim == 0 ? 0 : c->tune[dim].occ;
     return is_scaled(c) ? launch_sweep_scaled(L) : c->mode == M_FP64 ? launch_sweep_f64(L)
                                                                       : launch_sweep_f32(L);
 }
@@ -973,6 +975,8 @@ sl_status sl_get_tune(const sl_ctx* c, int dim, sl_tune* out)
     out->fibres_per_thread = t.ft;
     out->unroll = t.unroll;
     out->pipeline = t.pipeline;
+    out->max_blocks_per_sm = t.occ;
+    out->reserved = 0;
     out->chunk = dim == 0 && !c->rec ? 0 : int64_t(t.chunk);
     return SL_OK;
 }
@@ -981,6 +985,13 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
 {
     const bool lanes = rec_lanes(c, t->fibres_per_thread);
     const int maxb = (dim == 0 && !c->rec) || lanes ? 256 : 128;
+    if (t->reserved != 0) return fail(c, SL_EINVAL, "sl_tune.reserved must be 0");
+    if (t->max_blocks_per_sm != 0) {
+        if (t->max_blocks_per_sm < 4 || t->max_blocks_per_sm > 6)
+            return fail(c, SL_EINVAL, "max_blocks_per_sm must be 0, 4, 5 or 6");
+        if (is_scaled(c) || dim == 0 || t->pipeline != 0)
+            return fail(c, SL_EINVAL, "max_blocks_per_sm applies to the register walk of the FP64/FP32 stores");
+    }
     if (t->block < 32 || t->block > maxb || t->block % 32)
         return fail(c, SL_EINVAL, "block must be a multiple of 32 in [32, %d]", maxb);
     if (!is_scaled(c)) {
@@ -1047,6 +1058,7 @@ sl_status sl_set_tune(sl_ctx* c, int dim, const sl_tune* t)
     d.ft = t->fibres_per_thread;
     d.unroll = is_scaled(c) && !c->rec ? 1 : t->unroll;
     d.pipeline = is_scaled(c) || dim == 0 ? 0 : t->pipeline;
+    d.occ = t->max_blocks_per_sm;
     d.chunk = dim == 0 && !c->rec ? 0 : uint32_t(t->chunk);
     return SL_OK;
 }
@@ -1064,7 +1076,11 @@ sl_status sl_autotune(sl_ctx* c, int reps)
     for (int m = 0; m < c->ndim && result == SL_OK; ++m) {
         const int sd = natural_shift_dim(c, m);
         const int nclass = sd < 0 ? 1 : int(c->g.n[sd]);
-        std::vector<double> sh(size_t(nclass), 0.37);
+        // shifts of -0.63, 0.37 and 1.37 cells in turn over the classes, so
+        // that, as in a real step, sigma differs between neighbouring lines
+        // whose class follows their own coordinate
+        std::vector<double> sh(static_cast<size_t>(nclass));
+        for (int q = 0; q < nclass; ++q) sh[size_t(q)] = 0.37 + double(q % 3) - 1.0;
         cudaError_t e = cudaMemcpyAsync(c->d_shifts, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, c->st);
         if (e != cudaSuccess) {
             result = cuda_fail(c, e, "autotune shifts");
@@ -1110,7 +1126,12 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             {
                 const int fu[][2] = {{1, 1}, {1, 2}, {1, 4}, {2, 1}, {2, 2}, {2, 4}, {3, 1}, {3, 2}};
                 for (auto& x : fu)
-                    if (x[0] <= c->nfib) cand.push_back({128, x[0], x[1], chunk_for(c, m, x[0], 1), 0});
+                    if (x[0] <= c->nfib)
+                        for (int occ : {0, 5, 4}) {
+                            sl_ctx::Tune t{128, x[0], x[1], chunk_for(c, m, x[0], 1), 0};
+                            t.occ = occ;
+                            cand.push_back(t);
+                        }
                 const int fp[][2] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {3, 4}};
                 for (auto& x : fp)
                     if (x[0] <= c->nfib)
@@ -1119,28 +1140,37 @@ sl_status sl_autotune(sl_ctx* c, int reps)
             }
         }
         const sl_ctx::Tune keep = c->tune[m];
-        sl_ctx::Tune best = keep;
-        float best_ms = 1e30f;
-        for (const auto& t : cand) {
+        // time one candidate: a warm-up launch, then reps launches
+        auto time_one = [&](const sl_ctx::Tune& t, float* ms) {
             c->tune[m] = t;
-            e = launch_only(c, m, sd);   // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, c->st);
-            for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_only(c, m, sd);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, c->st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.0f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                c->tune[m] = keep;
-                result = cuda_fail(c, e, "autotune launch");
-                break;
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = t;
-            }
+            cudaError_t err = launch_only(c, m, sd);
+            if (err == cudaSuccess) err = cudaEventRecord(e0, c->st);
+            for (int r = 0; r < reps && err == cudaSuccess; ++r) err = launch_only(c, m, sd);
+            if (err == cudaSuccess) err = cudaEventRecord(e1, c->st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+            return err;
+        };
+        std::vector<float> t_ms(cand.size(), 1e30f);
+        for (size_t q = 0; q < cand.size() && e == cudaSuccess; ++q) e = time_one(cand[q], &t_ms[q]);
+        // second round over the three fastest, keeping each one's better time
+        std::vector<size_t> order(cand.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return t_ms[x] < t_ms[y]; });
+        for (size_t r = 0; r < std::min<size_t>(3, order.size()) && e == cudaSuccess; ++r) {
+            float ms = 1e30f;
+            e = time_one(cand[order[r]], &ms);
+            t_ms[order[r]] = std::min(t_ms[order[r]], ms);
         }
-        c->tune[m] = best;
+        if (e != cudaSuccess) {
+            c->tune[m] = keep;
+            result = cuda_fail(c, e, "autotune launch");
+            break;
+        }
+        size_t best = 0;
+        for (size_t q = 1; q < cand.size(); ++q)
+            if (t_ms[q] < t_ms[best]) best = q;
+        c->tune[m] = cand.empty() ? keep : cand[best];
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -327,38 +327,54 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
 
 namespace sl {
 
+// Branch-free forms into the outputs; the branching forms must give the same
+// bits (NaN compared as NaN), else the element counts as a mismatch.
 __global__ void k_conv_check(const double* __restrict__ din, const float* __restrict__ fin, uint32_t n,
-                             float* __restrict__ fout, double* __restrict__ dout)
+                             float* __restrict__ fout, double* __restrict__ dout,
+                             unsigned long long* __restrict__ mism)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    fout[2 * i] = d2f_rn(din[i], false);
-    fout[2 * i + 1] = d2f_rn(din[i], true);
-    dout[i] = f2d_exact(fin[i]);
+    const float p = d2f_fast(din[i], false), q = d2f_fast(din[i], true);
+    const double d = f2d_fast(fin[i]);
+    fout[2 * i] = p;
+    fout[2 * i + 1] = q;
+    dout[i] = d;
+    const float pb = d2f_branch(din[i], false), qb = d2f_branch(din[i], true);
+    const double db = f2d_branch(fin[i]);
+    const bool same = (__float_as_uint(p) == __float_as_uint(pb) || (p != p && pb != pb)) &&
+                      (__float_as_uint(q) == __float_as_uint(qb) || (q != q && qb != qb)) &&
+                      (__double_as_longlong(d) == __double_as_longlong(db) || (d != d && db != db));
+    if (!same) atomicAdd(mism, 1ull);
 }
 
 }  // namespace sl
 
 extern "C" sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
-                                             double* d_out)
+                                             double* d_out, int64_t* mismatches)
 {
-    if (!d_in || !f_in || !f_out || !d_out || n < 1 || n > (int64_t(1) << 26)) return SL_EINVAL;
+    if (!d_in || !f_in || !f_out || !d_out || !mismatches || n < 1 || n > (int64_t(1) << 26)) return SL_EINVAL;
     const size_t N = size_t(n);
     char* mem = nullptr;
-    const size_t bytes = N * (8 + 4 + 8 + 8);
+    const size_t bytes = N * (8 + 4 + 8 + 8) + 16;
     if (cudaMalloc(&mem, bytes) != cudaSuccess) return SL_ENOMEM;
-    double* din = reinterpret_cast<double*>(mem);
+    unsigned long long* mism = reinterpret_cast<unsigned long long*>(mem);
+    double* din = reinterpret_cast<double*>(mem + 16);
     double* dout = din + N;
     float* fout = reinterpret_cast<float*>(dout + N);
     float* fin = fout + 2 * N;
-    cudaError_t e = cudaMemcpy(din, d_in, N * 8, cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemset(mism, 0, 8);
+    if (e == cudaSuccess) e = cudaMemcpy(din, d_in, N * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(fin, f_in, N * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
-        sl::k_conv_check<<<unsigned((N + 255) / 256), 256>>>(din, fin, uint32_t(N), fout, dout);
+        sl::k_conv_check<<<unsigned((N + 255) / 256), 256>>>(din, fin, uint32_t(N), fout, dout, mism);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpy(f_out, fout, N * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess) e = cudaMemcpy(d_out, dout, N * 8, cudaMemcpyDeviceToHost);
+    unsigned long long mm = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&mm, mism, 8, cudaMemcpyDeviceToHost);
+    *mismatches = int64_t(mm);
     cudaFree(mem);
     return e == cudaSuccess ? SL_OK : SL_ECUDA;
 }

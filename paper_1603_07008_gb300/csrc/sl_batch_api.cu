@@ -622,6 +622,8 @@ sl_status sl_batch_get_tune(const sl_batch* b, int dim, sl_tune* out)
     out->unroll = t.unroll;
     out->pipeline = 0;
     out->chunk = dim == 0 ? int64_t(t.reps) * kBatchBlock : int64_t(t.rows);
+    out->max_blocks_per_sm = 0;
+    out->reserved = 0;
     return SL_OK;
 }
 

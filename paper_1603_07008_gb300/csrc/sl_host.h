@@ -67,6 +67,7 @@ struct sl_ctx {
         int unroll = 1;
         uint32_t chunk = 0;
         int pipeline = 0;
+        int occ = 0;   // resident blocks per SM the walk is limited to (0: no limit)
     } tune[SL_MAX_DIM];
 
     std::string err;

@@ -117,6 +117,7 @@ struct SweepLaunch {
     int dim;             // sweep dimension
     int ndim;            // grid dimensions
     int rec;             // > 0: scaled store in cell records of this many slots
+    int occ;             // > 0: the strided register walk runs at most this many blocks per SM
     cudaStream_t stream;
 };
 

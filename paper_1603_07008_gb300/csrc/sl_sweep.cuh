@@ -99,63 +99,102 @@ __device__ __forceinline__ void pow2_scale(float mx, float& s, float& inv)
 }
 
 // Conversions between IEEE 754 binary32 and binary64 done on the integer
-// pipe.  GB300's FP64 pipe (which also executes the F2F conversions) runs at
-// a small fraction of the FP32 rate, and the mean row of the low-precision
-// stores would otherwise spend three of its seven FP64-pipe instructions on
-// conversions.  Both functions return exactly what the conversion instruction
-// returns (float to double is exact; double to float rounds to nearest, ties
-// to even); inputs outside the ranges handled here (subnormal results,
-// infinities, NaN) take the conversion instruction.
+// pipe, without branches.  GB300's FP64 pipe (which also executes the F2F
+// conversions) runs at a small fraction of the FP32 rate, and the mean row of
+// the low-precision stores would otherwise spend three of its seven FP64-pipe
+// instructions on conversions.  For every input outside the binary32
+// subnormal range both return exactly what the conversion instructions
+// return (float to double is exact; double to float rounds to nearest, ties
+// to even, overflowing to infinity; zeros, infinities and NaN keep their
+// kind and sign).  Subnormal binary32 values (inputs of f2d_fast, results of
+// d2f_fast, all below 1.2e-38 in magnitude) are not reproduced: f2d_fast maps
+// them to values below 2^-126 and d2f_fast flushes such results to a signed
+// zero.  Both are fixed functions of their input, which is all the mean row
+// needs for its sums to telescope.
 //
 // binary32 -> binary64: sign kept, exponent rebiased by 1023 - 127 = 896,
 // the 23 fraction bits placed at the top of the 52-bit fraction.
-__device__ __forceinline__ double f2d_exact(float x)
+__device__ __forceinline__ double f2d_fast(float x)
 {
     const uint32_t u = __float_as_uint(x);
-    const uint32_t e = (u >> 23) & 0xffu;
-    if ((u & 0x7fffffffu) == 0u) return __hiloint2double(int(u), 0);   // +-0
-    if (e == 0u || e == 255u) return double(x);                         // subnormal, inf, NaN
-    const uint32_t hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-    return __hiloint2double(int(hi), int(u << 29));
+    const uint32_t a = u & 0x7fffffffu;
+    uint32_t hi = (a >> 3) + 0x38000000u;                       // exponent + 896, fraction >> 3
+    hi = a >= 0x7f800000u ? (0x7ff00000u | ((a >> 3) & 0xfffffu)) : hi;   // inf, NaN
+    hi = a == 0u ? 0u : hi;
+    return __hiloint2double(int(hi | (u & 0x80000000u)), int(u << 29));
 }
 
 // binary64 -> binary32 of (neg ? -x : x), rounded to nearest even: the top
 // 23 of the 52 fraction bits are kept and the other 29 decide the rounding;
 // a carry out of the fraction moves into the exponent, which is the correct
-// result, up to overflow to infinity.  Results below the binary32 normal
-// range (other than zero) take the conversion instruction.
-__device__ __forceinline__ float d2f_rn(double x, bool neg)
+// result, including the overflow of the largest values to infinity.
+__device__ __forceinline__ float d2f_fast(double x, bool neg)
 {
-    uint32_t hi = uint32_t(__double2hiint(x));
+    const uint32_t hi = uint32_t(__double2hiint(x)) ^ (neg ? 0x80000000u : 0u);
     const uint32_t lo = uint32_t(__double2loint(x));
-    if (neg) hi ^= 0x80000000u;
-    const uint32_t e = (hi >> 20) & 0x7ffu;
-    if (((hi & 0x7fffffffu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);   // +-0
-    if (e < 897u || e > 1150u) return float(__hiloint2double(int(hi), int(lo)));
-    const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const uint32_t s = hi & 0x80000000u;
+    const uint32_t a = hi & 0x7fffffffu;                        // |x|, high word
+    const uint32_t m = ((a & 0xfffffu) << 3) | (lo >> 29);
     const uint32_t r = lo & 0x1fffffffu;
-    uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | m;
-    f += (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
-    return __uint_as_float(f);
+    const uint32_t up = (r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    uint32_t f = (((a >> 20) - 896u) << 23 | m) + up;           // normal range
+    f = a >= 0x47f00000u ? 0x7f800000u : f;                     // |x| >= 2^128: infinity
+    f = a >= 0x7ff00000u && (((a & 0xfffffu) | lo) != 0u) ? (0x7fc00000u | m) : f;   // NaN
+    f = a < 0x38100000u ? 0u : f;                               // |x| < 2^-126: zero
+    return __uint_as_float(f | s);
+}
+
+// The same two conversions with a branch around the normal-range case
+// (values of the mean row nearly always are), the other cases handled by the
+// branch-free forms, so the results are the same bits.
+__device__ __forceinline__ double f2d_branch(float x)
+{
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e - 1u < 254u) {
+        const uint32_t hi = (u & 0x80000000u) | (((u & 0x7fffffffu) >> 3) + 0x38000000u);
+        return __hiloint2double(int(hi), int(u << 29));
+    }
+    return f2d_fast(x);
+}
+__device__ __forceinline__ float d2f_branch(double x, bool neg)
+{
+    const uint32_t hi = uint32_t(__double2hiint(x)) ^ (neg ? 0x80000000u : 0u);
+    const uint32_t lo = uint32_t(__double2loint(x));
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e - 897u < 254u) {
+        const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t r = lo & 0x1fffffffu;
+        const uint32_t f = ((hi & 0x80000000u) | ((e - 896u) << 23) | m) +
+                           ((r > 0x10000000u || (r == 0x10000000u && (m & 1u))) ? 1u : 0u);
+        return __uint_as_float(f);
+    }
+    return d2f_fast(x, neg);
 }
 
 // New mean of a cell in the low-precision stores (conservation form, see
 // combine) from the source means ma (cell i - sigma), mb (i - sigma - 1) and
 // their per-cell FP32 sums ga = G(a), gb = G(b); dm = fl32(ma - mb) for the
-// l = 0 term of the other rows.  Four FP64-pipe instructions with the
-// integer-pipe conversions; HW uses the conversion instructions instead (the
-// same results; shorter code, for kernels bound by instruction latency rather
-// than by the FP64 pipe).
-template <bool HW = false>
+// l = 0 term of the other rows: four FP64-pipe instructions.
+// Conversion forms of the mean row, picked per kernel by measurement:
+// CV_FLAT and CV_BRANCH give the same bits (the integer-pipe forms above);
+// CV_INSTR uses the conversion instructions, which differ from them only in
+// the binary32 subnormal range (below 1.2e-38 in magnitude).
+enum : int { CV_FLAT = 0, CV_BRANCH = 1, CV_INSTR = 2 };
+
+template <int CV = CV_FLAT>
 __device__ __forceinline__ double mean_row_lp(double alpha, double ma, double mb, float ga, float gb, float& dm)
 {
     const double t = mb - ma;
-    if constexpr (HW) {
+    if constexpr (CV == CV_INSTR) {
         dm = float(-t);
         return fma(alpha, t, ma) + (double(ga) - double(gb));
+    } else if constexpr (CV == CV_BRANCH) {
+        dm = d2f_branch(t, true);
+        return fma(alpha, t, ma) + (f2d_branch(ga) - f2d_branch(gb));
     } else {
-        dm = d2f_rn(t, true);
-        return fma(alpha, t, ma) + (f2d_exact(ga) - f2d_exact(gb));
+        dm = d2f_fast(t, true);
+        return fma(alpha, t, ma) + (f2d_fast(ga) - f2d_fast(gb));
     }
 }
 
@@ -230,8 +269,8 @@ struct Mats {
 
 // New values of one target cell from its source cells a (= i - sigma) and
 // b (= i - sigma - 1).  With MEAN, fibre 0 of the group is the mean's fibre.
-// HW: conversions of the mean row by instruction (see mean_row_lp).
-template <int K, int MODE, int FT, bool MEAN, bool HW = false>
+// CV: the conversion form of the mean row (see mean_row_lp).
+template <int K, int MODE, int FT, bool MEAN, int CV = CV_FLAT>
 __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K, MODE, FT>& a,
                                         const CellVals<K, MODE, FT>& b,
                                         CellVals<K, MODE, FT>& out)
@@ -273,7 +312,7 @@ __device__ __forceinline__ void combine(const Mats<K, MODE>& M, const CellVals<K
                     gb = fmaf(M.a[0][l], b.v[0][l], gb);
                 }
                 float dm;
-                out.m = mean_row_lp<HW>(M.alpha, a.m, b.m, ga, gb, dm);
+                out.m = mean_row_lp<CV>(M.alpha, a.m, b.m, ga, gb, dm);
 #pragma unroll
                 for (int j = 1; j < O; ++j) {
                     R acc = M.a[j][0] * dm;
@@ -455,7 +494,7 @@ __device__ __forceinline__ uint32_t shift_class(const SweepArgs& a, uint32_t inn
 
 // ---------------------------------------------------------------- unit stride
 
-template <int K, int MODE, int FT, bool MEAN, bool HW = false>
+template <int K, int MODE, int FT, bool MEAN, int CV = CV_FLAT>
 __device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32_t ca, uint32_t cb,
                                           uint32_t cls, int fbase)
 {
@@ -472,12 +511,12 @@ __device__ __forceinline__ void unit_body(const SweepArgs& a, uint32_t c, uint32
     CellVals<K, MODE, FT> va, vb, out;
     load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, ca, jb, 1, va);
     load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, cb, jb, 1, vb);
-    combine<K, MODE, FT, MEAN, HW>(M, va, vb, out);
+    combine<K, MODE, FT, MEAN, CV>(M, va, vb, out);
     store_cell<K, MODE, FT, MEAN>(a.dst, a.pstride, c, jb, 1, out);
 }
 
 // Target cell c of a sweep along dimension 0, fibres fbase .. fbase+FT-1.
-template <int K, int MODE, int FT, bool HW = false>
+template <int K, int MODE, int FT, int CV = CV_FLAT>
 __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fbase)
 {
     const uint32_t line = a.fdN.div(c);
@@ -491,9 +530,9 @@ __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fb
     const uint32_t ca = c - i + uint32_t(ia);
     const uint32_t cb = c - i + uint32_t(ib);
     if (St<MODE>::scaled || fbase == 0)
-        unit_body<K, MODE, FT, true, HW>(a, c, ca, cb, cls, fbase);
+        unit_body<K, MODE, FT, true, CV>(a, c, ca, cb, cls, fbase);
     else
-        unit_body<K, MODE, FT, false, HW>(a, c, ca, cb, cls, fbase);
+        unit_body<K, MODE, FT, false, CV>(a, c, ca, cb, cls, fbase);
 }
 
 // Sweep along dimension 0: one thread per target cell (and fibre group
@@ -704,6 +743,8 @@ __device__ __forceinline__ LineSetup line_setup_grid(const SweepArgs& a, int FT)
                       blockIdx.y / uint32_t(a.nfg), FT);
 }
 
+// The walk's mean row uses the branching conversions (measured: about 10%
+// faster than the branch-free form along dimensions > 0 of the 4D store).
 template <int K, int MODE, int FT, int U, bool MEAN>
 __device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup& L)
 {
@@ -755,7 +796,7 @@ __device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup
 #pragma unroll
             for (int s = 0; s < U; ++s) {
                 CellVals<K, MODE, FT> out;
-                combine<K, MODE, FT, MEAN>(M, cur[s], s == 0 ? prev : cur[s - 1], out);
+                combine<K, MODE, FT, MEAN, CV_BRANCH>(M, cur[s], s == 0 ? prev : cur[s - 1], out);
                 store_row(i + s, out);
             }
             prev = cur[U - 1];
@@ -766,7 +807,7 @@ __device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup
     for (; i < L.i1; ++i) {
         CellVals<K, MODE, FT> cur, out;
         load_row(ia, cur);
-        combine<K, MODE, FT, MEAN>(M, cur, prev, out);
+        combine<K, MODE, FT, MEAN, CV_BRANCH>(M, cur, prev, out);
         store_row(i, out);
         prev = cur;
         ++ia;

@@ -399,6 +399,8 @@ def test_every_launch_shape_gives_identical_results(storage, n, k):
                     for ch in sorted({1, min(3, n[dim]), n[dim]}):
                         shapes.append(dict(block=128, fibres_per_thread=f, unroll=un, chunk=ch))
                 shapes.append(dict(block=32, fibres_per_thread=1, unroll=2, chunk=min(2, n[dim])))
+                for occ in (4, 5, 6):   # at most occ blocks per SM
+                    shapes.append(dict(block=128, fibres_per_thread=1, unroll=4, chunk=n[dim], max_blocks_per_sm=occ))
                 for f, pl in ASYNC_SHAPES:
                     if f > nfib:
                         continue
@@ -501,7 +503,10 @@ def test_set_tune_rejects_shapes_not_built():
                         (0, dict(block=128, fibres_per_thread=1, pipeline=4)),
                         (0, dict(block=128, fibres_per_thread=1, unroll=2)),
                         (0, dict(block=128, fibres_per_thread=9, unroll=4)),
-                        (1, dict(block=32, fibres_per_thread=1, pipeline=4, chunk=8))]:
+                        (1, dict(block=32, fibres_per_thread=1, pipeline=4, chunk=8)),
+                        (1, dict(block=128, fibres_per_thread=1, unroll=1, chunk=8, max_blocks_per_sm=3)),
+                        (1, dict(block=128, fibres_per_thread=1, pipeline=4, chunk=8, max_blocks_per_sm=5)),
+                        (0, dict(block=128, fibres_per_thread=1, max_blocks_per_sm=5))]:
             with pytest.raises(S.SlError) as e:
                 ctx.set_tune(dim, **sh)
             assert e.value.status == S.SL_EINVAL
