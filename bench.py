@@ -167,23 +167,23 @@ def summarise_clocks(lines):
 # traffic is reported as null.
 TRAFFIC = {
     ("4d", "mix_fp32"): {
-        "ratio": (2 * 0.98705 + 4 * 1.00223) / 6,
+        "ratio": (2 * 0.98515 + 2 * 1.00207 + 2 * 1.00708) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "c83b49b05af77433",
-        "capture": "48^4 cells, k=2; unit-stride 3.437 GB, strided 3.490 GB per launch "
-                   "against 3.482 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
+        "sha256": "afeca8afb9a93709",
+        "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
+                   "1 fibres) against 3.482 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
     ("6d", "mix_bf16"): {
-        "ratio": (2 * 1.00371 + 7 * 1.04164) / 9,
-        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_scaled.cu"],
-        "sha256": "669cc3389538185a",
-        "capture": "16^6 cells, k=1, BF16 records; unit-stride 4.648 GB, strided 4.823 GB per "
-                   "launch against 4.631 GB algorithmic (profiles/sweep_6d_n16_records_bf16.md)"},
+        "ratio": (2 * 1.03766 + 7 * 1.03630) / 9,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
+        "sha256": "b54a83cf889798c0",
+        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.805 / 4.799 GB per launch (dimensions 0, "
+                   "1) against 4.631 GB algorithmic (profiles/sweep_6d_n16_lane_records_bf16.md)"},
     ("batch", "mix_fp32"): {
-        "ratio": (2 * 0.96357 + 1.05413) / 3,
+        "ratio": (2 * 0.96474 + 1.04158) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
-        "sha256": "10719d23afe556fa",
-        "capture": "64 problems, default shapes; unit-stride 1.052 GB, strided 1.151 GB per "
-                   "launch against 1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
+        "sha256": "cd1019a0fedd9362",
+        "capture": "64 problems, default shapes; 1.053 / 1.137 GB per launch (dimensions 0, 1) against "
+                   "1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
 }
 
 

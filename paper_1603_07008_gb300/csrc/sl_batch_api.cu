@@ -351,14 +351,15 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
                         b->st) != cudaSuccess ||
         cudaStreamSynchronize(b->st) != cudaSuccess)
         return cleanup(fail(nullptr, SL_ECUDA, "uploading batch tables"));
-    // default shapes: the most fibres per thread compiled (each problem takes
-    // at most its own), four cells per walk step, 64-row work items, four
-    // cell tiles per item
+    // default shapes (the autotuner's usual picks on 2D x-v batches): whole
+    // cells along dimension 0 (each problem takes at most its own fibres) in
+    // items of eight cell tiles; one fibre per thread, four cells per walk
+    // step and 64-row items along the other dimensions
     for (int m = 0; m < b->ndim; ++m) {
-        b->tune[m].ft = m == 0 ? kBatchMaxFtUnit : kBatchMaxFtStrided;
+        b->tune[m].ft = m == 0 ? kBatchMaxFtUnit : 1;
         b->tune[m].unroll = m == 0 ? 1 : 4;
         b->tune[m].rows = 64;
-        b->tune[m].reps = 4;
+        b->tune[m].reps = m == 0 ? 8 : 4;
         sl_status s = rebuild_dim(b, m);
         if (s != SL_OK) {
             fail(nullptr, s, "%s", b->err.c_str());
