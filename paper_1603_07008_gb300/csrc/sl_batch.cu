@@ -49,10 +49,7 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
 // another.
 // One item along dimension 0: reps tiles of kBatchBlock consecutive cells.
 // Not inlined, so that each (K, FT) body gets its own register allocation
-// and reads the problem's geometry where it needs it.  The per-cell form is
-// bound by instruction latency, not by the FP64 pipe, so its mean row
-// converts by instruction (measured faster here; the results differ from the
-// other forms' only for intermediates in the binary32 subnormal range).
+// and reads the problem's geometry where it needs it.
 template <int K, int MODE, int FT>
 __device__ __noinline__ void unit_item(const SweepArgs* __restrict__ ap, uint32_t start, int fbase, int reps)
 {
@@ -60,7 +57,7 @@ __device__ __noinline__ void unit_item(const SweepArgs* __restrict__ ap, uint32_
     for (int r = 0; r < reps; ++r) {
         const uint32_t c = start + threadIdx.x + uint32_t(r) * kBatchBlock;
         if (c >= a.cells) break;
-        unit_cell<K, MODE, FT, CV_INSTR>(a, c, fbase);
+        unit_cell<K, MODE, FT>(a, c, fbase);
     }
 }
 

@@ -176,20 +176,15 @@ __device__ __forceinline__ float d2f_branch(double x, bool neg)
 // combine) from the source means ma (cell i - sigma), mb (i - sigma - 1) and
 // their per-cell FP32 sums ga = G(a), gb = G(b); dm = fl32(ma - mb) for the
 // l = 0 term of the other rows: four FP64-pipe instructions.
-// Conversion forms of the mean row, picked per kernel by measurement:
-// CV_FLAT and CV_BRANCH give the same bits (the integer-pipe forms above);
-// CV_INSTR uses the conversion instructions, which differ from them only in
-// the binary32 subnormal range (below 1.2e-38 in magnitude).
-enum : int { CV_FLAT = 0, CV_BRANCH = 1, CV_INSTR = 2 };
+// Conversion forms of the mean row, picked per kernel by measurement; both
+// give the same bits (the integer-pipe forms above).
+enum : int { CV_FLAT = 0, CV_BRANCH = 1 };
 
 template <int CV = CV_FLAT>
 __device__ __forceinline__ double mean_row_lp(double alpha, double ma, double mb, float ga, float gb, float& dm)
 {
     const double t = mb - ma;
-    if constexpr (CV == CV_INSTR) {
-        dm = float(-t);
-        return fma(alpha, t, ma) + (double(ga) - double(gb));
-    } else if constexpr (CV == CV_BRANCH) {
+    if constexpr (CV == CV_BRANCH) {
         dm = d2f_branch(t, true);
         return fma(alpha, t, ma) + (f2d_branch(ga) - f2d_branch(gb));
     } else {
