@@ -90,6 +90,10 @@ def lib():
             L.or_apply_cell.restype = ctypes.c_int
             L.or_apply_cell.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp, _dp]
+            L.or_set_mutation.restype = None
+            L.or_set_mutation.argtypes = [ctypes.c_int]
+            L.or_get_mutation.restype = ctypes.c_int
+            L.or_get_mutation.argtypes = []
             _lib = L
     return _lib
 
@@ -114,6 +118,22 @@ def _check(rc: int, what: str):
 # --------------------------------------------------------------------------
 # scalar pieces
 # --------------------------------------------------------------------------
+
+class planted_mistake:
+    """Context manager for the test of the pins: inside it the C oracle runs
+    with planted mistake m (see MUTATION m in sl_oracle.c); 0 is the oracle."""
+
+    def __init__(self, m: int):
+        self.m = int(m)
+
+    def __enter__(self):
+        lib().or_set_mutation(self.m)
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_mutation(0)
+        return False
+
 
 def legendre(j: int, x: float) -> float:
     return lib().or_legendre(j, float(x))

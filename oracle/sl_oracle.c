@@ -47,6 +47,15 @@
 #define OR_MAXK 3
 #define OR_MAXQ 64
 
+/* Planted mistakes for the test that checks the pins (tests/): with
+ * or_mutation = m > 0 one plausible error of the kind a reader could make
+ * (a wrong sign, index, factor or operand order) replaces the correct
+ * statement at the place marked MUTATION m, so that the test can show that
+ * some pin fails for each of them.  0, the default, is the oracle itself. */
+static int or_mutation = 0;
+void or_set_mutation(int m) { or_mutation = m; }
+int or_get_mutation(void) { return or_mutation; }
+
 /* ------------------------------------------------------------------ */
 /* Legendre polynomials and Gauss-Legendre quadrature                  */
 /* ------------------------------------------------------------------ */
@@ -57,7 +66,7 @@ double or_legendre(int j, double x)
     if (j == 0) return 1.0;
     double pm1 = 1.0, p = x;
     for (int n = 1; n < j; ++n) {
-        double pn1 = ((2.0 * n + 1.0) * x * p - n * pm1) / (n + 1.0);
+        double pn1 = ((2.0 * n + 1.0) * x * p - n * pm1) / (or_mutation == 1 ? (double)n : n + 1.0);   /* MUTATION 1 */
         pm1 = p;
         p = pn1;
     }
@@ -97,7 +106,8 @@ int or_gauss_legendre(int n, double* x, double* w)
         dp = n * (z * p1 - p0) / (z * z - 1.0);
         /* the guess for i runs from the largest root down */
         x[n - 1 - i] = z;
-        w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        w[n - 1 - i] = or_mutation == 2 ? 2.0 / ((1.0 - z * z) * fabs(dp))                /* MUTATION 2 */
+                                        : 2.0 / ((1.0 - z * z) * dp * dp);
     }
     return 0;
 }
@@ -109,10 +119,10 @@ int or_gauss_legendre(int n, double* x, double* w)
 /* s = sigma + alpha with sigma = floor(s), alpha in [0,1). */
 void or_shift_split(double s, int64_t* sigma, double* alpha)
 {
-    double f = floor(s);
+    double f = or_mutation == 3 ? trunc(s) : floor(s);   /* MUTATION 3 */
     double a = s - f;
     int64_t sg = (int64_t)f;
-    if (a >= 1.0) { sg += 1; a = 0.0; }
+    if (a >= 1.0 && or_mutation != 19) { sg += 1; a = 0.0; }   /* MUTATION 19 */
     *sigma = sg;
     *alpha = a;
 }
@@ -129,7 +139,7 @@ int or_ab_matrices(int k, double alpha, double* A, double* B)
 {
     if (k < 0 || k > OR_MAXK || !(alpha >= 0.0) || !(alpha < 1.0)) return -1;
     const int o = k + 1;
-    if (alpha == 0.0) {
+    if (alpha == 0.0 && or_mutation != 16) {   /* MUTATION 16 */
         for (int j = 0; j < o; ++j)
             for (int l = 0; l < o; ++l) {
                 A[j * o + l] = (j == l) ? 1.0 : 0.0;
@@ -146,12 +156,14 @@ int or_ab_matrices(int k, double alpha, double* A, double* B)
             for (int q = 0; q < nq; ++q) {
                 /* [-1,1] -> [2a-1, 1]: xi = (1-a) t + a, dxi = (1-a) dt */
                 double xi = (1.0 - alpha) * t[q] + alpha;
-                sa += (1.0 - alpha) * w[q] * or_legendre(j, xi) * or_legendre(l, xi - 2.0 * alpha);
+                sa += (1.0 - alpha) * w[q] * or_legendre(j, xi) *
+                      or_legendre(l, or_mutation == 4 ? xi + 2.0 * alpha : xi - 2.0 * alpha);   /* MUTATION 4 */
                 /* [-1,1] -> [-1, 2a-1]: eta = a t + a - 1, deta = a dt */
                 double eta = alpha * t[q] + alpha - 1.0;
-                sb += alpha * w[q] * or_legendre(j, eta) * or_legendre(l, eta + 2.0 - 2.0 * alpha);
+                sb += alpha * w[q] * or_legendre(j, eta) *
+                      or_legendre(l, or_mutation == 5 ? eta - 2.0 + 2.0 * alpha : eta + 2.0 - 2.0 * alpha);   /* MUTATION 5 */
             }
-            A[j * o + l] = 0.5 * (2.0 * j + 1.0) * sa;
+            A[j * o + l] = (or_mutation == 6 ? 1.0 : 0.5) * (2.0 * j + 1.0) * sa;   /* MUTATION 6 */
             B[j * o + l] = 0.5 * (2.0 * j + 1.0) * sb;
         }
     }
@@ -231,8 +243,8 @@ int or_sweep(int ndim, const int64_t* n, int k, int dim, int shift_dim,
         int64_t cls = shift_dim < 0 ? 0 : idx[shift_dim];
         const double* A = AB + 2 * o * o * cls;
         const double* B = A + o * o;
-        int64_t ia = pmod(idx[dim] - sig[cls], n[dim]);
-        int64_t ib = pmod(ia - 1, n[dim]);
+        int64_t ia = pmod(or_mutation == 10 ? idx[dim] + sig[cls] : idx[dim] - sig[cls], n[dim]);   /* MUTATION 10 */
+        int64_t ib = pmod(or_mutation == 9 ? ia + 1 : ia - 1, n[dim]);                               /* MUTATION 9 */
         int64_t ca = c + (ia - idx[dim]) * cstride;
         int64_t cb = c + (ib - idx[dim]) * cstride;
         for (int64_t J = 0; J < ncoef; ++J) {
@@ -240,8 +252,11 @@ int or_sweep(int ndim, const int64_t* n, int k, int dim, int shift_dim,
             int64_t Jbase = J - jm * ostride;
             double acc = 0.0;
             for (int l = 0; l < o; ++l) {
-                acc += A[jm * o + l] * u[ca * ncoef + Jbase + l * ostride];
-                acc += B[jm * o + l] * u[cb * ncoef + Jbase + l * ostride];
+                const int e = or_mutation == 7 ? l * o + jm : jm * o + l;          /* MUTATION 7 */
+                const double* Aa = or_mutation == 8 ? B : A;                       /* MUTATION 8 */
+                const double* Bb = or_mutation == 8 ? A : B;
+                acc += Aa[e] * u[ca * ncoef + Jbase + l * ostride];
+                if (or_mutation != 11) acc += Bb[e] * u[cb * ncoef + Jbase + l * ostride];   /* MUTATION 11 */
             }
             out[c * ncoef + J] = acc;
         }
@@ -281,7 +296,7 @@ int or_bruteforce_sweep(int ndim, const int64_t* n, int k, int dim, int shift_di
          * crosses an integer. */
         double y0 = (double)idx[dim] - s;
         double yb = floor(y0 + 1.0);            /* integer in (y0, y0+1] */
-        double xib = 2.0 * (yb - y0) - 1.0;     /* local coordinate of the break */
+        double xib = 2.0 * (yb - y0) - (or_mutation == 17 ? 0.0 : 1.0);   /* local coordinate of the break; MUTATION 17 */
         if (xib > 1.0) xib = 1.0;
         if (xib < -1.0) xib = -1.0;
         for (int64_t J = 0; J < ncoef; ++J) {
@@ -334,8 +349,9 @@ static void factor_project(const double* prm, double lo, double h, int64_t i, in
     for (int j = 0; j <= k; ++j) {
         double acc = 0.0;
         for (int q = 0; q < nq; ++q)
-            acc += w[q] * factor_eval(prm, xc + 0.5 * h * t[q]) * or_legendre(j, t[q]);
-        cj[j] = 0.5 * (2.0 * j + 1.0) * acc;
+            acc += w[q] * factor_eval(prm, xc + (or_mutation == 14 ? h : 0.5 * h) * t[q]) *   /* MUTATION 14 */
+                   or_legendre(j, t[q]);
+        cj[j] = (or_mutation == 13 ? 1.0 : 0.5) * (2.0 * j + 1.0) * acc;   /* MUTATION 13 */
     }
 }
 
@@ -375,7 +391,7 @@ int or_project(int ndim, const int64_t* n, const double* lo, const double* hi, i
                 factor_project(params + (tt * ndim + m) * 4, lo[m], h[m], idx[m], k, nq, t, w, p[m]);
             for (int64_t J = 0; J < ncoef; ++J) {
                 int64_t r = J;
-                for (int m = 0; m < ndim; ++m) { jidx[m] = (int)(r % o); r /= o; }
+                for (int m = 0; m < ndim; ++m) { jidx[or_mutation == 15 ? ndim - 1 - m : m] = (int)(r % o); r /= o; }   /* MUTATION 15 */
                 double prod = weight[tt];
                 for (int m = 0; m < ndim; ++m) prod *= p[m][jidx[m]];
                 dst[J] += prod;
@@ -404,7 +420,7 @@ double or_mass(int ndim, const int64_t* n, const double* lo, const double* hi, i
     }
     double s = 0.0;
     for (int64_t c = 0; c < cells; ++c) s += u[c * ncoef];
-    return vol * s;
+    return or_mutation == 12 ? s : vol * s;   /* MUTATION 12 */
 }
 
 /* ------------------------------------------------------------------ */
@@ -425,8 +441,8 @@ int or_apply_cell(int ndim, int k, int dim, const double* A, const double* B,
         int64_t Jbase = J - jm * ostride;
         double acc = 0.0;
         for (int l = 0; l < o; ++l) {
-            acc += A[jm * o + l] * ua[Jbase + l * ostride];
-            acc += B[jm * o + l] * ub[Jbase + l * ostride];
+            acc += A[jm * o + l] * (or_mutation == 18 ? ub : ua)[Jbase + l * ostride];   /* MUTATION 18 */
+            acc += B[jm * o + l] * (or_mutation == 18 ? ua : ub)[Jbase + l * ostride];
         }
         out[J] = acc;
     }

@@ -269,6 +269,27 @@ def test_projection_of_polynomials_is_exact():
     assert np.max(np.abs(one[:, 0] - 2.5)) < 1e-15 and np.max(np.abs(one[:, 1:])) < 1e-15
 
 
+def test_projection_tensor_order_in_several_dimensions():
+    """In d dimensions coefficient J = sum_m j_m o^m belongs to P_{j_0}(xi_0)
+    P_{j_1}(xi_1) ...: the product of a linear function of x_m (the factor
+    sin(eps x)/eps) and constants in the other dimensions has c_0 = x_c, the
+    coefficient with j_m = 1 equal to h_m / 2, and no other."""
+    eps = 1e-5
+    for ndim in (2, 3):
+        n = (3, 4, 2)[:ndim]
+        g = W.Grid(n=n, lo=(-1.0, 0.5, 2.0)[:ndim], hi=(2.0, 1.5, 3.0)[:ndim], pair=(-1,) * ndim)
+        k, o = 2, 3
+        for m in range(ndim):
+            prm = [[0.0, 0.0, 0.0, 0.0] for _ in range(ndim)]
+            prm[m] = [0.0, 0.0, eps, -math.pi / 2]
+            c = O.project(g, k, 5, np.array([1.0 / eps]), np.array([prm]))
+            h = (g.hi[m] - g.lo[m]) / g.n[m]
+            J1 = o ** m
+            assert np.max(np.abs(c[:, J1] - h / 2)) < 1e-9, (ndim, m)
+            others = [J for J in range(o ** ndim) if J not in (0, J1)]
+            assert np.max(np.abs(c[:, others])) < 1e-9, (ndim, m)
+
+
 def test_projection_matches_adaptive_quadrature():
     scipy_integrate = pytest.importorskip("scipy.integrate")
     p = W.config1()
