@@ -582,3 +582,36 @@ def test_record_layout_raw_planes(storage, n, k, slots):
         S.sl_set_planes(ctx.handle, mean, hi, scale)
         ctx.synchronize()
         assert np.array_equal(ctx.get_coeffs(), want)
+
+
+@pytest.mark.parametrize("storage", ["fp64", "mix_fp32", "mix_bf16"])
+def test_shift_edge_cases_match_oracle(storage):
+    """Shifts at the edges of the split s = sigma + alpha, one per line:
+    tiny negative shifts whose fractional part rounds to 1 (sigma + 1,
+    alpha = 0: an exact copy), integers of both signs, shifts of many periods,
+    alpha just below 1 and just above 0."""
+    n = (10, 12)
+    k = 2
+    N = n[0]
+    edge = [-1e-20, -2.0 ** -60, 1.0 - 2.0 ** -53, 3.0, -7.0, 1e6 + 0.37, -1e6 - 0.37, 0.5, 2.0 ** -40,
+            N - 1e-15, -N + 1e-15, 2.5 * N]
+    s = np.array(edge, dtype=float)
+    u = _rand(n, k, 91)
+    with S.Context(_grid(n), k, storage) as ctx:
+        ctx.set_coeffs(u)
+        stored = ctx.get_coeffs()
+        ctx.advect(0, 1, s)
+        got = ctx.get_coeffs()
+    ref = O.sweep(stored, n, k, 0, 1, s)
+    ncoef = (k + 1) ** 2
+    G = got.reshape(n[1], n[0], ncoef)
+    R = ref.reshape(n[1], n[0], ncoef)
+    for line, sh in enumerate(edge):
+        sig, alpha = O.shift_split(sh)
+        if alpha == 0.0:   # exact copy: the stored values, rolled, bit for bit
+            assert np.array_equal(G[line], np.roll(stored.reshape(n[1], n[0], ncoef)[line], sig, axis=0)), sh
+        elif storage == "fp64":
+            assert O.rel_max(G[line], R[line]) <= FP64_TOL, sh
+        else:
+            tol = 1e-6 if storage == "mix_fp32" else 1e-2
+            assert np.sqrt(np.sum((G[line] - R[line]) ** 2)) <= tol * np.sqrt(np.sum(R[line] ** 2)), sh
