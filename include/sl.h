@@ -391,6 +391,14 @@ sl_status sl_autotune(sl_ctx* ctx, int reps);
  * at most its own), unroll = cells per walk step, chunk = rows per work item
  * (dim > 0) or cells per work item (dim 0); pipeline is 0. */
 sl_status sl_batch_get_tune(const sl_batch* batch, int dim, sl_tune* out);
+/* Set the batch's work-list shape along dimension dim, in the terms of
+ * sl_batch_get_tune: block must be 128 and pipeline and max_blocks_per_sm
+ * 0; dimension 0 takes fibres_per_thread 1..3 with unroll (cells per thread)
+ * 1 or 2, or 1..2 with 4, and chunk a multiple of 128 x unroll up to
+ * 8 x 128 x unroll cells per item; the other dimensions take
+ * fibres_per_thread 1..2, unroll 1, 2 or 4 and chunk >= 1 rows per item.
+ * Errors: SL_EINVAL for a shape this build does not provide. */
+sl_status sl_batch_set_tune(sl_batch* batch, int dim, const sl_tune* tune);
 
 /* ---------------------------------------------------------------- profiling */
 

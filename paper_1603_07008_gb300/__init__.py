@@ -31,7 +31,7 @@ __all__ = [
     "sl_batch_set_coeffs", "sl_batch_get_coeffs", "sl_batch_set_fields", "sl_batch_step",
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
-    "sl_batch_get_tune", "sl_selftest_conversions",
+    "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -153,6 +153,7 @@ def lib():
             "sl_batch_profile_query": (st, [_vp, _i64p, _dp, _dp]),
             "sl_batch_profile_dims": (st, [_vp, _i64p, _dp]),
             "sl_batch_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
+            "sl_batch_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_selftest_conversions": (st, [_dp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                              ctypes.POINTER(ctypes.c_float), _dp, _i64p]),
@@ -585,6 +586,13 @@ def sl_batch_get_tune(b, dim: int):
                 pipeline=t.pipeline, chunk=t.chunk)
 
 
+def sl_batch_set_tune(b, dim: int, fibres_per_thread: int, unroll: int, chunk: int, block: int = 128,
+                      pipeline: int = 0, max_blocks_per_sm: int = 0):
+    t = sl_tune(int(block), int(fibres_per_thread), int(unroll), int(pipeline), int(chunk),
+                int(max_blocks_per_sm), 0)
+    _bcheck(lib().sl_batch_set_tune(b, int(dim), ctypes.byref(t)), b)
+
+
 class Batch:
     """Owns one sl_batch handle for a list of problems (objects with .grid, .k)."""
 
@@ -654,3 +662,6 @@ class Batch:
 
     def get_tune(self, dim):
         return sl_batch_get_tune(self.handle, dim)
+
+    def set_tune(self, dim, **kw):
+        sl_batch_set_tune(self.handle, dim, **kw)

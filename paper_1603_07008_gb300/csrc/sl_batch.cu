@@ -61,7 +61,74 @@ __device__ __noinline__ void unit_item(const SweepArgs* __restrict__ ap, uint32_
     }
 }
 
-template <int MODE, int FTM>
+// PC consecutive target cells c .. c + PC - 1 of one line per thread: the
+// line, shift class and matrices are set up once, and the PC + 1 source
+// cells i - sigma - 1 .. i - sigma + PC - 1 are each loaded once (the source
+// i - sigma of one target is the i - sigma - 1 of the next).  A run that
+// crosses a line end takes the one-cell form for each cell.
+template <int K, int MODE, int FT, bool MEAN, int PC>
+__device__ __forceinline__ void unit_run_body(const SweepArgs& a, uint32_t c, uint32_t ls, uint32_t i,
+                                              uint32_t cls, int fbase)
+{
+    constexpr int O = K + 1;
+    int jb[FT];
+    group_bases<FT>(fbase, a.nfib, O, 1, jb);
+    const int32_t N = int32_t(a.N);
+    const int32_t sig = __ldg(a.tab.sigma + cls);
+    int32_t ib = int32_t(i) - sig - 1;
+    ib += ib < 0 ? N : 0;
+    ib += ib < 0 ? N : 0;
+    Mats<K, MODE> M;
+    M.template load<MEAN>(a.tab, cls);
+    CellVals<K, MODE, FT> v[PC + 1];
+#pragma unroll
+    for (int q = 0; q <= PC; ++q) {
+        int32_t x = ib + q;
+        x -= x >= N ? N : 0;
+        load_cell<K, MODE, FT, MEAN>(a.src, a.pstride, ls + uint32_t(x), jb, 1, v[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < PC; ++q) {
+        CellVals<K, MODE, FT> out;
+        combine<K, MODE, FT, MEAN>(M, v[q + 1], v[q], out);
+        store_cell<K, MODE, FT, MEAN>(a.dst, a.pstride, c + q, jb, 1, out);
+    }
+}
+
+template <int K, int MODE, int FT, int PC>
+__device__ __noinline__ void unit_item_runs(const SweepArgs* __restrict__ ap, uint32_t start, int fbase, int reps)
+{
+    const SweepArgs& a = *ap;
+    for (int r = 0; r < reps; ++r) {
+        const uint32_t c = start + PC * (threadIdx.x + uint32_t(r) * kBatchBlock);
+        if (c >= a.cells) break;
+        const uint32_t line = a.fdN.div(c);
+        const uint32_t ls = line * a.N;
+        const uint32_t i = c - ls;
+        if (i + PC <= a.N) {
+            const uint32_t cls = shift_class(a, 0, line);
+            if (fbase == 0)
+                unit_run_body<K, MODE, FT, true, PC>(a, c, ls, i, cls, fbase);
+            else
+                unit_run_body<K, MODE, FT, false, PC>(a, c, ls, i, cls, fbase);
+        } else {
+            for (int q = 0; q < PC; ++q)
+                if (c + q < a.cells) unit_cell<K, MODE, FT>(a, c + q, fbase);
+        }
+    }
+}
+
+// PC cells per thread: 1 (unit_item) or runs of 2 or 4 consecutive ones (unit_item_runs).
+template <int K, int MODE, int FT, int PC>
+__device__ __forceinline__ void unit_items(const SweepArgs* __restrict__ ap, uint32_t start, int fbase, int reps)
+{
+    if constexpr (PC == 2 || PC == 4)
+        unit_item_runs<K, MODE, FT, PC>(ap, start, fbase, reps);
+    else
+        unit_item<K, MODE, FT>(ap, start, fbase, reps);
+}
+
+template <int MODE, int FTM, int PC>
 __global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __restrict__ args,
                                                             const int32_t* __restrict__ kdeg,
                                                             const BatchItem* __restrict__ items,
@@ -74,17 +141,17 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __r
         const int ft = (ap->nfib + ap->nfg - 1) / ap->nfg;
         const int fbase = int(item.grp) * ft;
         switch (K * 4 + ft) {
-        case 1: unit_item<0, MODE, 1>(ap, item.start, fbase, reps); break;
-        case 5: unit_item<1, MODE, 1>(ap, item.start, fbase, reps); break;
-        case 9: unit_item<2, MODE, 1>(ap, item.start, fbase, reps); break;
+        case 1: unit_items<0, MODE, 1, PC>(ap, item.start, fbase, reps); break;
+        case 5: unit_items<1, MODE, 1, PC>(ap, item.start, fbase, reps); break;
+        case 9: unit_items<2, MODE, 1, PC>(ap, item.start, fbase, reps); break;
         case 6:
-            if constexpr (FTM >= 2) unit_item<1, MODE, 2>(ap, item.start, fbase, reps);
+            if constexpr (FTM >= 2) unit_items<1, MODE, 2, PC>(ap, item.start, fbase, reps);
             break;
         case 10:
-            if constexpr (FTM >= 2) unit_item<2, MODE, 2>(ap, item.start, fbase, reps);
+            if constexpr (FTM >= 2) unit_items<2, MODE, 2, PC>(ap, item.start, fbase, reps);
             break;
         case 11:
-            if constexpr (FTM >= 3) unit_item<2, MODE, 3>(ap, item.start, fbase, reps);
+            if constexpr (FTM >= 3) unit_items<2, MODE, 3, PC>(ap, item.start, fbase, reps);
             break;
         default: break;
         }
@@ -148,7 +215,7 @@ cudaError_t launch_b(const SweepArgs* a, const int32_t* k, const BatchItem* item
 {
     if (nitems <= 0) return cudaSuccess;
     if (unit) {
-        k_batch_unit<MODE, FTM><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, reps);
+        k_batch_unit<MODE, FTM, U><<<blocks, kBatchBlock, 0, st>>>(a, k, items, nitems, reps);
     } else {
         cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st);
         if (e != cudaSuccess) return e;
@@ -161,7 +228,7 @@ template <int MODE, int FTM, int U>
 int occ(int unit)
 {
     int n = 0;
-    cudaError_t e = unit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_unit<MODE, FTM>,
+    cudaError_t e = unit ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_unit<MODE, FTM, U>,
                                                                          kBatchBlock, 0)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_batch_strided<MODE, FTM, U>,
                                                                          kBatchBlock, 0);
@@ -171,23 +238,34 @@ int occ(int unit)
 
 }  // namespace
 
-// Compiled shapes: dimension 0 (unit) takes ft 1..3 with unroll 1; the other
-// dimensions ft 1..2 with unroll (cells per walk step) 1, 2 or 4.
+// Compiled shapes: dimension 0 (unit) takes ft 1..3 with unroll (cells per
+// thread) 1 or 2, and ft 1..2 with 4; the other dimensions ft 1..2 with
+// unroll (cells per walk step) 1, 2 or 4.
 bool batch_shape_ok(int unit, int ft, int unroll)
 {
-    return unit ? (ft >= 1 && ft <= kBatchMaxFtUnit && unroll == 1)
+    return unit ? (ft >= 1 && ft <= kBatchMaxFtUnit && (unroll == 1 || unroll == 2 || (unroll == 4 && ft <= 2)))
                 : (ft >= 1 && ft <= kBatchMaxFtStrided && (unroll == 1 || unroll == 2 || unroll == 4));
 }
 
 #define SL_BATCH_SWITCH(CALL)                                                                \
     if (unit) {                                                                              \
-        switch (mode * 10 + ft) {                                                            \
-        case M_FP64 * 10 + 1: { constexpr int MD = M_FP64, F = 1, UU = 1; CALL; }              \
-        case M_FP64 * 10 + 2: { constexpr int MD = M_FP64, F = 2, UU = 1; CALL; }              \
-        case M_FP64 * 10 + 3: { constexpr int MD = M_FP64, F = 3, UU = 1; CALL; }              \
-        case M_F32 * 10 + 1: { constexpr int MD = M_F32, F = 1, UU = 1; CALL; }                \
-        case M_F32 * 10 + 2: { constexpr int MD = M_F32, F = 2, UU = 1; CALL; }                \
-        case M_F32 * 10 + 3: { constexpr int MD = M_F32, F = 3, UU = 1; CALL; }                \
+        switch (mode * 100 + ft * 10 + unroll) {                                             \
+        case M_FP64 * 100 + 11: { constexpr int MD = M_FP64, F = 1, UU = 1; CALL; }            \
+        case M_FP64 * 100 + 21: { constexpr int MD = M_FP64, F = 2, UU = 1; CALL; }            \
+        case M_FP64 * 100 + 31: { constexpr int MD = M_FP64, F = 3, UU = 1; CALL; }            \
+        case M_FP64 * 100 + 12: { constexpr int MD = M_FP64, F = 1, UU = 2; CALL; }            \
+        case M_FP64 * 100 + 22: { constexpr int MD = M_FP64, F = 2, UU = 2; CALL; }            \
+        case M_FP64 * 100 + 32: { constexpr int MD = M_FP64, F = 3, UU = 2; CALL; }            \
+        case M_F32 * 100 + 11: { constexpr int MD = M_F32, F = 1, UU = 1; CALL; }              \
+        case M_F32 * 100 + 21: { constexpr int MD = M_F32, F = 2, UU = 1; CALL; }              \
+        case M_F32 * 100 + 31: { constexpr int MD = M_F32, F = 3, UU = 1; CALL; }              \
+        case M_F32 * 100 + 12: { constexpr int MD = M_F32, F = 1, UU = 2; CALL; }              \
+        case M_F32 * 100 + 22: { constexpr int MD = M_F32, F = 2, UU = 2; CALL; }              \
+        case M_F32 * 100 + 32: { constexpr int MD = M_F32, F = 3, UU = 2; CALL; }              \
+        case M_FP64 * 100 + 14: { constexpr int MD = M_FP64, F = 1, UU = 4; CALL; }            \
+        case M_FP64 * 100 + 24: { constexpr int MD = M_FP64, F = 2, UU = 4; CALL; }            \
+        case M_F32 * 100 + 14: { constexpr int MD = M_F32, F = 1, UU = 4; CALL; }              \
+        case M_F32 * 100 + 24: { constexpr int MD = M_F32, F = 2, UU = 4; CALL; }              \
         default: break;                                                                      \
         }                                                                                    \
     } else {                                                                                 \

@@ -46,7 +46,7 @@ struct sl_batch {
     int nitems[SL_MAX_DIM] = {0};
     struct Tune {
         int ft = 1;       // most fibres per thread (each problem takes min(ft, its fibres))
-        int unroll = 1;   // cells per walk step (dimensions > 0)
+        int unroll = 1;   // cells per walk step (dimensions > 0), cells per thread (dimension 0)
         int rows = 64;    // rows per work item (dimensions > 0)
         int reps = 4;     // cell tiles per work item (dimension 0)
     } tune[SL_MAX_DIM];
@@ -107,7 +107,7 @@ sl_status rebuild_dim(sl_batch* b, int m)
         const SweepArgs& a = args[p];
         const uint32_t nfg = uint32_t(a.nfg);
         if (m == 0) {
-            const uint32_t span = uint32_t(kBatchBlock * t.reps);
+            const uint32_t span = uint32_t(kBatchBlock * t.reps * t.unroll);   // unroll: cells per thread
             const uint32_t tiles = (a.cells + span - 1) / span;
             for (uint32_t g = 0; g < nfg; ++g)
                 for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * span, g, 0});
@@ -524,42 +524,61 @@ sl_status sl_batch_autotune(sl_batch* b, int reps)
         std::vector<sl_batch::Tune> cand;
         if (m == 0) {
             for (int ft = 1; ft <= kBatchMaxFtUnit; ++ft)
-                for (int r : {1, 4, 8}) cand.push_back({ft, 1, 64, r});
+                for (int u : {1, 2, 4})
+                    if (batch_shape_ok(1, ft, u))
+                        for (int r : {1, 4, 8}) cand.push_back({ft, u, 64, r});
         } else {
             for (int ft = 1; ft <= kBatchMaxFtStrided; ++ft)
                 for (int u : {2, 4})
                     for (int rows : {32, 64, 128, 1 << 30}) cand.push_back({ft, u, rows, 4});
         }
-        sl_batch::Tune best = b->tune[m];
-        float best_ms = 1e30f;
-        for (const auto& t : cand) {
-            b->tune[m] = t;
-            result = rebuild_dim(b, m);
-            if (result != SL_OK) break;
-            // out of place and the parity is restored, so the state is unchanged
-            const int par = b->parity;
-            cudaError_t e = cudaSuccess;
-            float ms = 0.0f;
-            for (int r = -1; r < reps && e == cudaSuccess; ++r) {
-                if (r == 0) e = cudaEventRecord(e0, b->st);
-                if (e != cudaSuccess) break;
-                const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
-                e = launch_batch_sweep(b->mode, t.ft, t.unroll, b->d_args + (size_t(m) * 2 + par) * b->nprob,
-                                       b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, t.reps, blocks,
-                                       b->d_ctr + m, b->st);
-            }
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                result = bcuda(b, e, "batch autotune");
-                break;
-            }
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = t;
-            }
+        // tables of a split substep of 0.05 time units, so that sigma varies
+        // between lines as in a real step (they are rebuilt by every sweep)
+        cudaError_t e = launch_batch_ab(b->d_ab + size_t(m) * b->nprob, b->d_tabs, b->nprob, b->maxcls[m], 0.05,
+                                        b->st);
+        if (e != cudaSuccess) {
+            result = bcuda(b, e, "batch autotune tables");
+            break;
         }
+        // time one candidate: a warm-up launch, then reps launches (out of
+        // place with the parity restored, so the state is unchanged)
+        auto time_one = [&](const sl_batch::Tune& t, float* ms) -> cudaError_t {
+            b->tune[m] = t;
+            if (rebuild_dim(b, m) != SL_OK) return cudaErrorUnknown;
+            const int par = b->parity;
+            cudaError_t err = cudaSuccess;
+            for (int r = -1; r < reps && err == cudaSuccess; ++r) {
+                if (r == 0) err = cudaEventRecord(e0, b->st);
+                if (err != cudaSuccess) break;
+                const int blocks = b->sms * batch_sweep_occupancy(b->mode, t.ft, t.unroll, m == 0);
+                err = launch_batch_sweep(b->mode, t.ft, t.unroll, b->d_args + (size_t(m) * 2 + par) * b->nprob,
+                                         b->d_kdeg, b->d_items[m], b->nitems[m], m == 0, t.reps, blocks,
+                                         b->d_ctr + m, b->st);
+            }
+            if (err == cudaSuccess) err = cudaEventRecord(e1, b->st);
+            if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+            if (err == cudaSuccess) err = cudaEventElapsedTime(ms, e0, e1);
+            return err;
+        };
+        std::vector<float> t_ms(cand.size(), 1e30f);
+        for (size_t q = 0; q < cand.size() && e == cudaSuccess; ++q) e = time_one(cand[q], &t_ms[q]);
+        // second round over the three fastest, keeping each one's better time
+        std::vector<size_t> order(cand.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = q;
+        std::sort(order.begin(), order.end(), [&](size_t x, size_t y) { return t_ms[x] < t_ms[y]; });
+        for (size_t r = 0; r < std::min<size_t>(3, order.size()) && e == cudaSuccess; ++r) {
+            float ms = 1e30f;
+            e = time_one(cand[order[r]], &ms);
+            t_ms[order[r]] = std::min(t_ms[order[r]], ms);
+        }
+        if (e != cudaSuccess) {
+            result = e == cudaErrorUnknown ? SL_ECUDA : bcuda(b, e, "batch autotune");
+            break;
+        }
+        size_t bi = 0;
+        for (size_t q = 1; q < cand.size(); ++q)
+            if (t_ms[q] < t_ms[bi]) bi = q;
+        const sl_batch::Tune best = cand[bi];
         b->tune[m] = best;
         if (result == SL_OK) result = rebuild_dim(b, m);
     }
@@ -613,6 +632,37 @@ sl_status sl_batch_profile_dims(const sl_batch* b, int64_t* launches, double* ms
     return SL_OK;
 }
 
+sl_status sl_batch_set_tune(sl_batch* b, int dim, const sl_tune* t)
+{
+    if (!b || !t) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (b->capturing) return bfail(b, SL_EINVAL, "cannot change shapes during a capture");
+    if (dim < 0 || dim >= b->ndim) return bfail(b, SL_EINVAL, "dim out of range");
+    if (t->block != kBatchBlock || t->pipeline != 0 || t->max_blocks_per_sm != 0 || t->reserved != 0)
+        return bfail(b, SL_EINVAL, "batches run 128 threads per block, no pipeline and no blocks-per-SM cap");
+    if (!batch_shape_ok(dim == 0, t->fibres_per_thread, t->unroll))
+        return bfail(b, SL_EINVAL, "(fibres_per_thread, unroll) not provided");
+    sl_batch::Tune n = b->tune[dim];
+    n.ft = t->fibres_per_thread;
+    n.unroll = t->unroll;
+    if (dim == 0) {
+        const int64_t per = int64_t(kBatchBlock) * t->unroll;
+        if (t->chunk < per || t->chunk % per != 0 || t->chunk / per > 8)
+            return bfail(b, SL_EINVAL, "chunk along dimension 0 must be 1..8 x 128 x unroll cells");
+        n.reps = int(t->chunk / per);
+    } else {
+        if (t->chunk < 1 || t->chunk > (int64_t(1) << 30)) return bfail(b, SL_EINVAL, "chunk must be >= 1 rows");
+        n.rows = int(t->chunk);
+    }
+    const sl_batch::Tune keep = b->tune[dim];
+    b->tune[dim] = n;
+    sl_status s = rebuild_dim(b, dim);
+    if (s != SL_OK) {
+        b->tune[dim] = keep;
+        rebuild_dim(b, dim);
+    }
+    return s;
+}
+
 sl_status sl_batch_get_tune(const sl_batch* b, int dim, sl_tune* out)
 {
     if (!b || !out) return fail(nullptr, SL_EINVAL, "NULL argument");
@@ -622,7 +672,7 @@ sl_status sl_batch_get_tune(const sl_batch* b, int dim, sl_tune* out)
     out->fibres_per_thread = t.ft;
     out->unroll = t.unroll;
     out->pipeline = 0;
-    out->chunk = dim == 0 ? int64_t(t.reps) * kBatchBlock : int64_t(t.rows);
+    out->chunk = dim == 0 ? int64_t(t.reps) * kBatchBlock * t.unroll : int64_t(t.rows);
     out->max_blocks_per_sm = 0;
     out->reserved = 0;
     return SL_OK;

@@ -146,3 +146,42 @@ def test_config4_full_size_batch():
         ref = O.step(O.project(p.grid, p.k, p.nq, p.weights, p.params), p.grid, p.k, "strang",
                      0.1, 2, p.field_list())
         assert O.rel_l2(got[i], ref, p.k, 2) <= 1e-5
+
+
+def test_batch_every_shape_gives_identical_results():
+    """Every work-list shape (fibres per thread, cells per thread or per walk
+    step, item size) changes only the work distribution."""
+    probs = _problems(SIZES, DEGS, "mix_fp32")
+    shapes0 = [dict(fibres_per_thread=f, unroll=u, chunk=128 * u * r)
+               for f, u in [(1, 1), (2, 1), (3, 1), (1, 2), (3, 2), (1, 4), (2, 4)] for r in (1, 3)]
+    shapes1 = [dict(fibres_per_thread=f, unroll=u, chunk=ch) for f in (1, 2) for u in (1, 2, 4) for ch in (1, 7, 1 << 30)]
+    with S.Batch([p.grid for p in probs], [p.k for p in probs], "mix_fp32") as b:
+        for i, p in enumerate(probs):
+            b.project(i, p.nq, p.weights, p.params)
+        b.set_fields([p.field_list()[0] for p in probs])
+        init = [b.get_coeffs(i) for i in range(len(probs))]
+
+        def run():
+            for i in range(len(probs)):
+                b.set_coeffs(i, init[i])
+            b.step("strang", 0.1, 2)
+            return [b.get_coeffs(i) for i in range(len(probs))]
+
+        ref = run()
+        for dim, shapes in ((0, shapes0), (1, shapes1)):
+            keep = b.get_tune(dim)
+            for sh in shapes:
+                b.set_tune(dim, **sh)
+                t = b.get_tune(dim)
+                assert (t["fibres_per_thread"], t["unroll"], t["chunk"]) == (sh["fibres_per_thread"], sh["unroll"], sh["chunk"])
+                got = run()
+                for a, c in zip(got, ref):
+                    assert np.array_equal(a, c), (dim, sh)
+            b.set_tune(dim, **keep)
+        for dim, sh in [(0, dict(fibres_per_thread=3, unroll=4, chunk=512)), (0, dict(fibres_per_thread=1, unroll=1, chunk=100)),
+                        (0, dict(fibres_per_thread=1, unroll=1, chunk=128 * 9)), (1, dict(fibres_per_thread=3, unroll=1, chunk=8)),
+                        (1, dict(fibres_per_thread=1, unroll=3, chunk=8)), (1, dict(fibres_per_thread=1, unroll=1, chunk=0)),
+                        (1, dict(fibres_per_thread=1, unroll=1, chunk=8, block=64)), (2, dict(fibres_per_thread=1, unroll=1, chunk=8))]:
+            with pytest.raises(S.SlError) as e:
+                b.set_tune(dim, **sh)
+            assert e.value.status == S.SL_EINVAL
