@@ -271,6 +271,22 @@ sl_status sl_mass_noalloc(const double* d_mean, int64_t cells, double cell_volum
 sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
                                   double* d_out, int64_t* mismatches);
 
+/* Self-consistent field (NEXT to the sweep: the Vlasov-Poisson system of
+ * Sec. II in 1+1 dimensions).  For a grid with one x dimension paired with
+ * one v dimension, enable = 1 makes sl_step and sl_graph_capture compute the
+ * field of the v-sweep from the state before every v-sweep, instead of
+ * taking the samples of sl_set_fields: d_x E = rho - rho_bar with
+ * rho_i = h_v sum_j c_{i,j;0} (the x-cell average of int f dv) and rho_bar
+ * its mean, E at the x-cell centres = sum_{j<i} q_j + q_i / 2 with
+ * q = (rho - rho_bar) h_x, minus its mean (int E dx = 0).  Allocates a
+ * scratch of (ceil(n_v / 256) + 1) n_x + 1 doubles on first use (not during
+ * a capture).  Errors: SL_EINVAL (other grids), SL_ENOMEM. */
+sl_status sl_set_poisson(sl_ctx* ctx, int enable);
+/* The field of the current state at the x-cell centres (host array of n_x
+ * doubles), and the field energy (1/2) sum_i E_i^2 h_x.  Synchronise. */
+sl_status sl_get_field(sl_ctx* ctx, double* field);
+sl_status sl_field_energy(sl_ctx* ctx, double* energy);
+
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later
  * sl_set_fields is not seen by the graph until it is captured again. */

@@ -29,6 +29,10 @@ Functions and the paper passages they follow:
   project / project_cells    -- eq. (cj)
   mass                       -- c0 is the cell mean (Sec. II-A, III-A)
   step                       -- split time step (Sec. II)
+  poisson_field, vp_step     -- self-consistent field of the Vlasov equation of
+                                Sec. II in 1+1 dimensions (reading: d_x E =
+                                rho - rho_bar, rho = int f dv) and the split
+                                step that recomputes it before every v-sweep
 """
 from __future__ import annotations
 
@@ -281,6 +285,63 @@ def step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, fi
     for _ in range(nsteps):
         for dim, sd, s in sched:
             u = sweep(u, grid.n, k, dim, sd, s)
+    return u
+
+
+def _vp_dims(grid):
+    if len(grid.n) == 2:
+        for m in (0, 1):
+            if grid.pair[m] == 1 - m and grid.pair[1 - m] < 0:
+                return m, 1 - m
+    raise ValueError("the self-consistent field needs one x and one v dimension")
+
+
+def poisson_field(u: np.ndarray, grid, k: int) -> np.ndarray:
+    """E at the x-cell centres for d_x E = rho - rho_bar on the periodic
+    x-domain, int E dx = 0.  rho_i = h_v sum_j c_{i,j;0} is the x-cell average
+    of int f dv; E is the field of that piecewise-constant density at the
+    cell centres: sum_{j<i} q_j + q_i / 2 with q = (rho - rho_bar) h_x, minus
+    its mean.  Sums run one after the other in index order."""
+    x, v = _vp_dims(grid)
+    nx, nv = grid.n[x], grid.n[v]
+    hx = (grid.hi[x] - grid.lo[x]) / nx
+    hv = (grid.hi[v] - grid.lo[v]) / nv
+    c0 = u[:, 0].reshape(grid.n[1], grid.n[0])      # [index along dim 1][index along dim 0]
+    rho = np.zeros(nx)
+    for i in range(nx):
+        s = 0.0
+        for j in range(nv):
+            s += c0[j, i] if x == 0 else c0[i, j]
+        rho[i] = hv * s
+    rho_bar = sum(rho) / nx
+    q = (rho - rho_bar) * hx
+    E = np.empty(nx)
+    run = 0.0
+    for i in range(nx):
+        E[i] = run + 0.5 * q[i]
+        run += q[i]
+    return E - sum(E) / nx
+
+
+def field_energy(E: np.ndarray, grid) -> float:
+    """(1/2) sum_i E_i^2 h_x."""
+    x, _ = _vp_dims(grid)
+    return 0.5 * (grid.hi[x] - grid.lo[x]) / grid.n[x] * float(np.sum(np.asarray(E) ** 2))
+
+
+def vp_step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, energies=None) -> np.ndarray:
+    """Split steps with the field recomputed from the state before every
+    v-sweep; appends the field energy of the state after every step to
+    `energies` if given."""
+    x, v = _vp_dims(grid)
+    for _ in range(nsteps):
+        for dim, tau in ([(x, 0.5 * dt), (v, dt), (x, 0.5 * dt)] if splitting == "strang"
+                         else [(x, dt), (v, dt)]):
+            fields = [poisson_field(u, grid, k)] if dim == v else [np.zeros(grid.n[x])]
+            sd, s = line_shifts(grid, dim, tau, fields)
+            u = sweep(u, grid.n, k, dim, sd, s)
+        if energies is not None:
+            energies.append(field_energy(poisson_field(u, grid, k), grid))
     return u
 
 

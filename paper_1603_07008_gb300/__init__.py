@@ -31,7 +31,8 @@ __all__ = [
     "sl_batch_set_coeffs", "sl_batch_get_coeffs", "sl_batch_set_fields", "sl_batch_step",
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
-    "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions",
+    "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
+    "sl_field_energy",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -155,6 +156,9 @@ def lib():
             "sl_batch_get_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_batch_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
+            "sl_set_poisson": (st, [_vp, ctypes.c_int]),
+            "sl_get_field": (st, [_vp, _dp]),
+            "sl_field_energy": (st, [_vp, _dp]),
             "sl_selftest_conversions": (st, [_dp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
                                              ctypes.POINTER(ctypes.c_float), _dp, _i64p]),
         }
@@ -387,6 +391,22 @@ def sl_selftest_conversions(d_in, f_in):
     return fo[0::2], fo[1::2], do, mm.value
 
 
+def sl_set_poisson(ctx, enable=True):
+    _check(lib().sl_set_poisson(ctx, 1 if enable else 0), ctx)
+
+
+def sl_get_field(ctx, nx: int) -> np.ndarray:
+    out = np.empty(int(nx), dtype=np.float64)
+    _check(lib().sl_get_field(ctx, out.ctypes.data_as(_dp)), ctx)
+    return out
+
+
+def sl_field_energy(ctx) -> float:
+    w = ctypes.c_double()
+    _check(lib().sl_field_energy(ctx, ctypes.byref(w)), ctx)
+    return w.value
+
+
 def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, stream=None):
     """Allocation-free mass reduction on raw device addresses (integers):
     enqueues d_out[0] = cell_volume * sum(d_mean[:cells]) on `stream`."""
@@ -476,6 +496,16 @@ class Context:
 
     def profile_dims(self):
         return sl_profile_dims(self.handle)
+
+    def set_poisson(self, enable=True):
+        sl_set_poisson(self.handle, enable)
+
+    def field(self):
+        nx = [n for n, pr in zip(self.grid.n, self.grid.pair) if pr >= 0][0]
+        return sl_get_field(self.handle, nx)
+
+    def field_energy(self):
+        return sl_field_energy(self.handle)
 
 
 # ---------------------------------------------------------------------------

@@ -357,6 +357,18 @@ int64_t field_offset(const sl_ctx* c, int xdim)
     return off;
 }
 
+// Field of the current state at the x-cell centres into E (and the field
+// energy into *energy) on the context's stream.
+cudaError_t vp_field(sl_ctx* c, double* E, double* energy)
+{
+    const int x = c->vp_x, v = c->vp_v;
+    const uint32_t nx = uint32_t(c->g.n[x]), nv = uint32_t(c->g.n[v]);
+    const uint32_t sx = x == 0 ? 1u : uint32_t(c->g.n[0]);
+    const uint32_t sv = v == 0 ? 1u : uint32_t(c->g.n[0]);
+    return launch_vp_field(c->planes[c->cur].mean, nx, nv, sx, sv, cell_width(c->g, x), cell_width(c->g, v),
+                           c->d_vp, E, energy, c->st);
+}
+
 sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     const std::vector<SubStep> plan = plan_of(c, sp);
@@ -380,6 +392,10 @@ sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
                 int xm = -1;
                 for (int m = 0; m < c->ndim; ++m)
                     if (c->g.pair[m] == ss.dim) xm = m;
+                if (c->poisson) {   // the field of the current state
+                    cudaError_t e = vp_field(c, c->d_fields + field_offset(c, xm), nullptr);
+                    if (e != cudaSuccess) return cuda_fail(c, e, "self-consistent field");
+                }
                 src.kind = 2;
                 src.data = c->d_fields + field_offset(c, xm);
                 src.tau = tau;
@@ -619,6 +635,7 @@ void sl_destroy(sl_ctx* c)
     for (auto e : c->ev_free) cudaEventDestroy(e);
     if (c->d_stage) cudaFree(c->d_stage);
     if (c->d_proj) cudaFree(c->d_proj);
+    if (c->d_vp) cudaFree(c->d_vp);
     if (c->h_mass) cudaFreeHost(c->h_mass);
     if (c->mem) cudaFree(c->mem);
     delete c;
@@ -861,6 +878,88 @@ sl_status sl_set_fields(sl_ctx* c, const double* fields, int64_t count)
     return SL_OK;
 }
 
+// The grid's one x dimension and its v dimension, or -1 if the grid is not
+// 1+1-dimensional with that one pair.
+static bool vp_dims(const sl_ctx* c, int* x, int* v)
+{
+    if (c->ndim != 2) return false;
+    for (int m = 0; m < 2; ++m)
+        if (c->g.pair[m] == 1 - m && c->g.pair[1 - m] < 0) {
+            *x = m;
+            *v = 1 - m;
+            return true;
+        }
+    return false;
+}
+
+static sl_status vp_alloc(sl_ctx* c)
+{
+    if (c->d_vp) return SL_OK;
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot allocate during a capture");
+    const size_t nx = size_t(c->g.n[c->vp_x]);
+    const size_t n = size_t(vp_chunks(uint32_t(c->g.n[c->vp_v]))) * nx + nx + 1;
+    cudaError_t e = cudaMalloc(&c->d_vp, n * sizeof(double));
+    if (e != cudaSuccess) {
+        c->d_vp = nullptr;
+        return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(double), cudaGetErrorString(e));
+    }
+    return SL_OK;
+}
+
+sl_status sl_set_poisson(sl_ctx* c, int enable)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (!enable) {
+        c->poisson = false;
+        return SL_OK;
+    }
+    int x = -1, v = -1;
+    if (!vp_dims(c, &x, &v)) return fail(c, SL_EINVAL, "the self-consistent field needs one x and one v dimension");
+    c->vp_x = x;
+    c->vp_v = v;
+    sl_status s = vp_alloc(c);
+    if (s != SL_OK) return s;
+    c->poisson = true;
+    return SL_OK;
+}
+
+sl_status sl_field_energy(sl_ctx* c, double* energy)
+{
+    if (!c || !energy) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot read the field energy during a capture");
+    int x = -1, v = -1;
+    if (!vp_dims(c, &x, &v)) return fail(c, SL_EINVAL, "the self-consistent field needs one x and one v dimension");
+    c->vp_x = x;
+    c->vp_v = v;
+    sl_status s = vp_alloc(c);
+    if (s != SL_OK) return s;
+    const size_t nx = size_t(c->g.n[x]);
+    double* E = c->d_vp + size_t(vp_chunks(uint32_t(c->g.n[v]))) * nx;
+    SL_CUDA(c, vp_field(c, E, E + nx));
+    SL_CUDA(c, cudaMemcpyAsync(c->h_mass, E + nx, 8, cudaMemcpyDeviceToHost, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    *energy = c->h_mass[0];
+    return SL_OK;
+}
+
+sl_status sl_get_field(sl_ctx* c, double* field)
+{
+    if (!c || !field) return fail(nullptr, SL_EINVAL, "NULL argument");
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot read the field during a capture");
+    int x = -1, v = -1;
+    if (!vp_dims(c, &x, &v)) return fail(c, SL_EINVAL, "the self-consistent field needs one x and one v dimension");
+    c->vp_x = x;
+    c->vp_v = v;
+    sl_status s = vp_alloc(c);
+    if (s != SL_OK) return s;
+    const size_t nx = size_t(c->g.n[x]);
+    double* E = c->d_vp + size_t(vp_chunks(uint32_t(c->g.n[v]))) * nx;
+    SL_CUDA(c, vp_field(c, E, nullptr));
+    SL_CUDA(c, cudaMemcpyAsync(field, E, nx * 8, cudaMemcpyDeviceToHost, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return SL_OK;
+}
+
 static sl_status check_step_args(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
@@ -870,7 +969,8 @@ static sl_status check_step_args(sl_ctx* c, sl_splitting sp, double dt, int nste
     bool any = false;
     for (int m = 0; m < c->ndim; ++m) any |= c->g.pair[m] >= 0;
     if (!any) return fail(c, SL_EINVAL, "grid has no x/v pairs to split");
-    if (c->nfields > 0 && !c->fields_set) return fail(c, SL_EINVAL, "fields not set (sl_set_fields)");
+    if (c->nfields > 0 && !c->fields_set && !c->poisson)
+        return fail(c, SL_EINVAL, "fields not set (sl_set_fields or sl_set_poisson)");
     return SL_OK;
 }
 

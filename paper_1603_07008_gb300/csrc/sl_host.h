@@ -36,6 +36,11 @@ struct sl_ctx {
     double* d_fields = nullptr;
     int64_t nfields = 0;
     bool fields_set = false;
+    // self-consistent field (one x and one v dimension): the field of the
+    // v-sweep is computed from the state before every v-sweep
+    bool poisson = false;
+    int vp_x = -1, vp_v = -1;
+    double* d_vp = nullptr;     // [chunks][n_x] partial sums, E scratch [n_x], energy [1]
     double* d_partials = nullptr;
     double* d_mass = nullptr;
     int mass_nblk = 1;
@@ -79,6 +84,7 @@ namespace host {
 sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...);
 sl_status fail_to(std::string* err, sl_status s, const char* fmt, ...);
 sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what);
+cudaError_t vp_field(sl_ctx* c, double* E, double* energy);
 sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c);
 bool is_scaled(const sl_ctx* c);
 int64_t fibre_groups(const sl_ctx* c, int ft);

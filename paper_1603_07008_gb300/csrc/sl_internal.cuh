@@ -129,6 +129,16 @@ cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
 constexpr int kRecLaneFt = 8;
 cudaError_t launch_sweep_rec_lanes(const SweepLaunch& L);
 
+// Self-consistent field of a grid with one x and one v dimension: the
+// density partial sums over chunks of kVpChunk v-rows, then E at the x-cell
+// centres (and, if energy != nullptr, (1/2) sum E^2 h_x).  The cell with
+// x-index i and v-index j is i * sx + j * sv.  partial holds
+// vp_chunks(nv) * nx doubles.
+constexpr uint32_t kVpChunk = 256;
+int vp_chunks(uint32_t nv);
+cudaError_t launch_vp_field(const double* mean, uint32_t nx, uint32_t nv, uint32_t sx, uint32_t sv, double hx,
+                            double hv, double* partial, double* E, double* energy, cudaStream_t st);
+
 // Coefficients of the entries of A(alpha) and B(alpha) as polynomials in
 // alpha, exact rationals rounded once to FP64: a[j][l][p] alpha^p.
 struct PolyTab {

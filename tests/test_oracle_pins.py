@@ -341,3 +341,53 @@ def test_schedule_structure():
     assert np.allclose(sched[0][2], v * 0.05 / h_x, rtol=1e-15, atol=0)
     E = p.field_list()[0]
     assert np.allclose(sched[2][2], E * 0.1 / h_v, rtol=1e-15, atol=0)
+
+
+# ---------------------------------------------------------------- self-consistent field (Vlasov-Poisson)
+
+def _landau_grid(nx, nv):
+    p = W.config2(n=8, steps=1)
+    return p, W.Grid(n=(nx, nv), lo=p.grid.lo, hi=p.grid.hi, pair=p.grid.pair)
+
+
+def test_poisson_field_of_a_cosine_density_converges_at_second_order():
+    """f0 = M(v)(1 + a cos(k x)) has rho = e (1 + a cos(k x)) with
+    e = erf(6 / sqrt 2) on v in [-6, 6]; d_x E = rho - rho_bar gives
+    E = e (a / k) sin(k x).  The cell-centre field converges at order 2."""
+    errs = []
+    for nx in (16, 32, 64):
+        p, g = _landau_grid(nx, 64)
+        u = O.project(g, 2, p.nq, p.weights, p.params)
+        E = O.poisson_field(u, g, 2)
+        h = 4 * math.pi / nx
+        xc = (np.arange(nx) + 0.5) * h
+        ex = math.erf(6 / math.sqrt(2)) * (0.01 / 0.5) * np.sin(0.5 * xc)
+        errs.append(np.max(np.abs(E - ex)) / np.max(np.abs(ex)))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert min(orders) > 1.9 and errs[-1] < 2e-3, (errs, orders)
+    # a density constant in x has no field; the sign: E grows where rho > rho_bar
+    p, g = _landau_grid(8, 16)
+    u = np.zeros((g.cells, 9))
+    u[:, 0] = 0.7
+    assert np.all(O.poisson_field(u, g, 2) == 0.0)
+    u[0, 0] += 1.0        # extra density in cell 0 (v-row 0)
+    E = O.poisson_field(u, g, 2)
+    assert E[1] - E[0] > 0 and abs(np.mean(E)) < 1e-15
+
+
+def test_linear_landau_damping_rate():
+    """The self-consistent split step damps the field energy of
+    f0 = M(v)(1 + 0.01 cos(x / 2)) at twice the linear Landau rate
+    gamma = -0.1533 (wave number 1/2), and it oscillates at omega = 1.4156:
+    textbook linear theory, independent of the paper."""
+    p, g = _landau_grid(64, 128)
+    u = O.project(g, 2, p.nq, p.weights, p.params)
+    en = [O.field_energy(O.poisson_field(u, g, 2), g)]
+    O.vp_step(u, g, 2, "strang", 0.1, 200, en)
+    t = np.arange(len(en)) * 0.1
+    le = np.log(np.array(en))
+    peaks = [i for i in range(1, len(le) - 1) if le[i] > le[i - 1] and le[i] >= le[i + 1] and t[i] < 20]
+    gamma = np.polyfit(t[peaks], le[peaks], 1)[0] / 2
+    assert abs(gamma + 0.1533) < 0.003, gamma
+    omega = math.pi / np.mean(np.diff(t[peaks]))
+    assert abs(omega - 1.4156) < 0.05, omega
