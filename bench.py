@@ -50,7 +50,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="4d", choices=["4d", "2d", "batch", "6d", "1d"],
+    ap.add_argument("--workload", default="4d", choices=["4d", "2d", "batch", "6d", "1d", "vp"],
                     help="4d: 64^4 k=2 (default); 2d: 512^2 k=2; batch: 256 uneven 2D problems; "
                          "6d: 20^6 k=1; 1d: N=1024 k=2")
     ap.add_argument("--n", type=int, default=None, help="cells per dimension (4d/2d/6d)")
@@ -275,14 +275,14 @@ def apply_shapes(ctx, shapes):
 
 
 DEFAULT_STORE = {"4d": "mix_fp32", "2d": "mix_fp32", "batch": "mix_fp32", "6d": "mix_bf16",
-                 "1d": "fp64"}
-DEFAULT_N = {"4d": 64, "2d": 512, "6d": 20, "1d": 1024}
+                 "1d": "fp64", "vp": "mix_fp32"}
+DEFAULT_N = {"4d": 64, "2d": 512, "6d": 20, "1d": 1024, "vp": 4096}
 
 
 def make_problem(W, workload, n, storage, nprob=256):
     if workload == "4d":
         return W.config3(n=n, steps=1, storage=storage)
-    if workload == "2d":
+    if workload in ("2d", "vp"):
         return W.config2(n=n, steps=1, storage=storage)
     if workload == "6d":
         return W.config5(n=n, steps=1, storage=storage)
@@ -315,7 +315,9 @@ class Arm:
             p = self.p
             self.obj = S.Context(p.grid, p.k, storage, stream=stream)
             self.obj.project(p.nq, p.weights, p.params)
-            if p.splitting != "advect":
+            if self.workload == "vp":      # field from the state before every v-sweep
+                self.obj.set_poisson(True)
+            elif p.splitting != "advect":
                 self.obj.set_fields(p.field_list())
             apply_shapes(self.obj, shapes)
             self.dof = p.dof
@@ -447,6 +449,7 @@ def run_ours(args):
     if rank == 0:
         wl = {"4d": f"4d_xxvv_{args.n}^4_k2_{args.storage}_strang",
               "2d": f"2d_xv_{args.n}^2_k2_{args.storage}_strang",
+              "vp": f"2d_xv_{args.n}^2_k2_{args.storage}_strang_self_consistent_field",
               "6d": f"6d_xxxvvv_{args.n}^6_k1_{args.storage}_strang",
               "1d": f"1d_n{args.n}_k2_{args.storage}_advect",
               "batch": f"batch256_2d_xv_k1k2_{args.storage}_strang"}[args.workload]
