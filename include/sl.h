@@ -292,6 +292,12 @@ sl_status sl_field_energy(sl_ctx* ctx, double* energy);
  * sl_set_fields is not seen by the graph until it is captured again. */
 sl_status sl_graph_capture(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
 sl_status sl_graph_launch(sl_ctx* ctx);
+/* Capture nsteps sweeps of sl_advect(ctx, dim, shift_dim, shifts, nshift),
+ * each with its table build, into a CUDA graph (replacing a previous graph)
+ * that sl_graph_launch replays.  The graph keeps its own device copy of the
+ * shifts.  Same argument checks as sl_advect; nsteps >= 1. */
+sl_status sl_graph_capture_advect(sl_ctx* ctx, int dim, int shift_dim, const double* shifts, int64_t nshift,
+                                  int nsteps);
 
 /* Wait for all work of the context's stream. */
 sl_status sl_synchronize(sl_ctx* ctx);

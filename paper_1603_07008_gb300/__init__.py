@@ -32,7 +32,7 @@ __all__ = [
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
     "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
-    "sl_field_energy",
+    "sl_field_energy", "sl_graph_capture_advect",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -157,6 +157,7 @@ def lib():
             "sl_batch_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
+            "sl_graph_capture_advect": (st, [_vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int]),
             "sl_get_field": (st, [_vp, _dp]),
             "sl_field_energy": (st, [_vp, _dp]),
             "sl_selftest_conversions": (st, [_dp, ctypes.POINTER(ctypes.c_float), ctypes.c_int64,
@@ -391,6 +392,12 @@ def sl_selftest_conversions(d_in, f_in):
     return fo[0::2], fo[1::2], do, mm.value
 
 
+def sl_graph_capture_advect(ctx, dim: int, shift_dim: int, shifts, nsteps: int):
+    s = np.ascontiguousarray(np.atleast_1d(shifts), dtype=np.float64)
+    _check(lib().sl_graph_capture_advect(ctx, int(dim), int(shift_dim), s.ctypes.data_as(_dp), s.size,
+                                         int(nsteps)), ctx)
+
+
 def sl_set_poisson(ctx, enable=True):
     _check(lib().sl_set_poisson(ctx, 1 if enable else 0), ctx)
 
@@ -496,6 +503,9 @@ class Context:
 
     def profile_dims(self):
         return sl_profile_dims(self.handle)
+
+    def graph_capture_advect(self, dim, shift_dim, shifts, nsteps):
+        sl_graph_capture_advect(self.handle, dim, shift_dim, shifts, nsteps)
 
     def set_poisson(self, enable=True):
         sl_set_poisson(self.handle, enable)

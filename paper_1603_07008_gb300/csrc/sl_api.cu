@@ -463,6 +463,54 @@ int natural_shift_dim(const sl_ctx* c, int m)
 // ABI
 // ======================================================================
 
+namespace {
+
+// Capture `sweeps` sweeps issued by `enqueue` into one graph, or into two when
+// `sweeps` is odd (the graph for each copy of the ping-pong state it may start
+// from).
+template <typename F>
+sl_status capture_graphs(sl_ctx* c, int sweeps, F enqueue)
+{
+    if (!c->st) return fail(c, SL_EINVAL, "graph capture needs a non-default stream");
+    drop_graph(c);
+    const int start = c->cur;
+    const int flip = sweeps & 1;
+    const int ngraphs = flip ? 2 : 1;
+    for (int gi = 0; gi < ngraphs; ++gi) {
+        c->cur = start ^ gi;
+        cudaGraph_t graph = nullptr;
+        SL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        c->capturing = true;
+        sl_status s = enqueue();
+        c->capturing = false;
+        cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+        if (s != SL_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            c->cur = start;
+            drop_graph(c);
+            return s;
+        }
+        if (e != cudaSuccess) {
+            c->cur = start;
+            drop_graph(c);
+            return cuda_fail(c, e, "cudaStreamEndCapture");
+        }
+        e = cudaGraphInstantiate(&c->gexec[gi], graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            c->cur = start;
+            drop_graph(c);
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+    }
+    c->cur = start;
+    c->graph_start = start;
+    c->graph_flip = flip;
+    return SL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sl_last_error(const sl_ctx* ctx)
@@ -636,6 +684,7 @@ void sl_destroy(sl_ctx* c)
     if (c->d_stage) cudaFree(c->d_stage);
     if (c->d_proj) cudaFree(c->d_proj);
     if (c->d_vp) cudaFree(c->d_vp);
+    if (c->d_gshifts) cudaFree(c->d_gshifts);
     if (c->h_mass) cudaFreeHost(c->h_mass);
     if (c->mem) cudaFree(c->mem);
     delete c;
@@ -999,43 +1048,48 @@ sl_status sl_graph_capture(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     sl_status s = check_step_args(c, sp, dt, nsteps);
     if (s != SL_OK) return s;
-    if (!c->st) return fail(c, SL_EINVAL, "graph capture needs a non-default stream");
-    drop_graph(c);
-    const int start = c->cur;
     const int sweeps = int(plan_of(c, sp).size()) * nsteps;
-    const int flip = sweeps & 1;
-    const int ngraphs = flip ? 2 : 1;
-    for (int gi = 0; gi < ngraphs; ++gi) {
-        c->cur = start ^ gi;
-        cudaGraph_t graph = nullptr;
-        SL_CUDA(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
-        c->capturing = true;
-        s = enqueue_steps(c, sp, dt, nsteps);
-        c->capturing = false;
-        cudaError_t e = cudaStreamEndCapture(c->st, &graph);
-        if (s != SL_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            c->cur = start;
-            drop_graph(c);
-            return s;
-        }
-        if (e != cudaSuccess) {
-            c->cur = start;
-            drop_graph(c);
-            return cuda_fail(c, e, "cudaStreamEndCapture");
-        }
-        e = cudaGraphInstantiate(&c->gexec[gi], graph, 0);
-        cudaGraphDestroy(graph);
-        if (e != cudaSuccess) {
-            c->cur = start;
-            drop_graph(c);
-            return cuda_fail(c, e, "cudaGraphInstantiate");
-        }
+    return capture_graphs(c, sweeps, [&]() { return enqueue_steps(c, sp, dt, nsteps); });
+}
+
+sl_status sl_graph_capture_advect(sl_ctx* c, int dim, int shift_dim, const double* shifts, int64_t nshift,
+                                  int nsteps)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (dim < 0 || dim >= c->ndim) return fail(c, SL_EINVAL, "dim %d out of range", dim);
+    if (shift_dim < -1 || shift_dim >= c->ndim || shift_dim == dim)
+        return fail(c, SL_EINVAL, "shift_dim %d invalid for dim %d", shift_dim, dim);
+    const int64_t expect = shift_dim < 0 ? 1 : c->g.n[shift_dim];
+    if (nshift != expect) return fail(c, SL_EINVAL, "nshift = %lld, expected %lld", (long long)nshift, (long long)expect);
+    if (!shifts) return fail(c, SL_EINVAL, "shifts is NULL");
+    if (nsteps < 1) return fail(c, SL_EINVAL, "nsteps < 1");
+    for (int64_t i = 0; i < nshift; ++i)
+        if (!std::isfinite(shifts[i]) || std::fabs(shifts[i]) > 1e15)
+            return fail(c, SL_ENAN, "shift %lld is not finite or too large", (long long)i);
+    if (c->capturing) return fail(c, SL_EINVAL, "already capturing");
+    // the graph's own copy of the shifts, so later calls cannot change what it reads
+    if (c->gshifts_n < nshift) {
+        if (c->d_gshifts) cudaFree(c->d_gshifts);
+        c->d_gshifts = nullptr;
+        c->gshifts_n = 0;
+        cudaError_t e = cudaMalloc(&c->d_gshifts, size_t(nshift) * 8);
+        if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+        c->gshifts_n = nshift;
     }
-    c->cur = start;
-    c->graph_start = start;
-    c->graph_flip = flip;
-    return SL_OK;
+    SL_CUDA(c, cudaMemcpyAsync(c->d_gshifts, shifts, size_t(nshift) * 8, cudaMemcpyHostToDevice, c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
+    return capture_graphs(c, nsteps, [&]() -> sl_status {
+        for (int q = 0; q < nsteps; ++q) {
+            ShiftSource src{};
+            src.kind = 0;
+            src.data = c->d_gshifts;
+            sl_status r = build_table(c, dim, int(nshift), src);
+            if (r != SL_OK) return r;
+            r = run_sweep(c, dim, shift_dim);
+            if (r != SL_OK) return r;
+        }
+        return SL_OK;
+    });
 }
 
 sl_status sl_graph_launch(sl_ctx* c)

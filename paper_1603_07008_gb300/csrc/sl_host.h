@@ -54,6 +54,8 @@ struct sl_ctx {
     sl::PolyTab poly{};
 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    double* d_gshifts = nullptr;   // shifts owned by a captured advect graph
+    int64_t gshifts_n = 0;
     int graph_start = -1;       // copy index the first graph starts from
     int graph_flip = 0;         // sweeps per graph mod 2
     bool capturing = false;

@@ -75,25 +75,24 @@ __global__ void __launch_bounds__(kVpThreads) k_vp_field(const double* __restric
         local += r;
     }
     const double rho_bar = block_sum(local, red) / double(nx);
-    // q_i = (rho_i - rho_bar) h_x; segment sums, their exclusive prefix by thread 0
+    // q_i = (rho_i - rho_bar) h_x and the sum over the thread's segment
     double ssum = 0.0;
     for (uint32_t i = b0; i < b1; ++i) {
         const double q = (E[i] - rho_bar) * hx;
         E[i] = q;
         ssum += q;
     }
+    // inclusive scan of the segment sums (Hillis-Steele, a fixed order of
+    // additions), then the exclusive prefix of this thread's segment
     seg[threadIdx.x] = ssum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int t = 0; t < kVpThreads; ++t) {
-            const double v = seg[t];
-            seg[t] = acc;
-            acc += v;
-        }
+    for (int off = 1; off < kVpThreads; off <<= 1) {
+        const double add = int(threadIdx.x) >= off ? seg[threadIdx.x - off] : 0.0;
+        __syncthreads();
+        seg[threadIdx.x] += add;
+        __syncthreads();
     }
-    __syncthreads();
-    double run = seg[threadIdx.x];
+    double run = threadIdx.x > 0 ? seg[threadIdx.x - 1] : 0.0;
     double esum = 0.0;
     for (uint32_t i = b0; i < b1; ++i) {
         const double q = E[i];

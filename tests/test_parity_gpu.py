@@ -615,3 +615,29 @@ def test_shift_edge_cases_match_oracle(storage):
         else:
             tol = 1e-6 if storage == "mix_fp32" else 1e-2
             assert np.sqrt(np.sum((G[line] - R[line]) ** 2)) <= tol * np.sqrt(np.sum(R[line] ** 2)), sh
+
+
+def test_advect_graph_replay_matches_advect_calls():
+    """A captured sequence of sweeps with fixed per-line shifts replays the
+    same sweeps as the calls, and keeps its own copy of the shifts."""
+    import torch
+    n, k = (33, 5), 2
+    rng = np.random.default_rng(17)
+    u = _rand(n, k, 5)
+    s = rng.uniform(-3, 3, size=n[1])
+    st = torch.cuda.Stream()
+    with S.Context(_grid(n), k, "mix_fp32", stream=st) as a, S.Context(_grid(n), k, "mix_fp32", stream=st) as b:
+        a.set_coeffs(u)
+        b.set_coeffs(u)
+        for _ in range(5):
+            a.advect(0, 1, s)
+        b.graph_capture_advect(0, 1, s, 5)      # 5 sweeps: odd, two graphs
+        b.advect(1, -1, [0.0])                  # an identity sweep (and other shifts) in between
+        b.graph_launch()
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+        for _ in range(5):
+            a.advect(0, 1, s)
+        b.graph_launch()
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+        with pytest.raises(S.SlError):
+            b.graph_capture_advect(0, 1, s[:3], 2)
