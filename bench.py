@@ -169,20 +169,20 @@ TRAFFIC = {
     ("4d", "mix_fp32"): {
         "ratio": (2 * 0.98515 + 2 * 1.00207 + 2 * 1.00708) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "afeca8afb9a93709",
+        "sha256": "1550dbf35d426332",
         "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
                    "1 fibres) against 3.482 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
     ("6d", "mix_bf16"): {
         "ratio": (2 * 1.03766 + 7 * 1.03630) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "b54a83cf889798c0",
+        "sha256": "113203572ce969a6",
         "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.805 / 4.799 GB per launch (dimensions 0, "
                    "1) against 4.631 GB algorithmic (profiles/sweep_6d_n16_lane_records_bf16.md)"},
     ("batch", "mix_fp32"): {
-        "ratio": (2 * 0.96474 + 1.04158) / 3,
+        "ratio": (2 * 0.95846 + 1.04159) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
-        "sha256": "cd1019a0fedd9362",
-        "capture": "64 problems, default shapes; 1.053 / 1.137 GB per launch (dimensions 0, 1) against "
+        "sha256": "f1f558c2dbb9934a",
+        "capture": "64 problems, default shapes; 1.046 / 1.137 GB per launch (dimensions 0, 1) against "
                    "1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
 }
 

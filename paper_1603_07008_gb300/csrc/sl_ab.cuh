@@ -25,10 +25,12 @@ __device__ __forceinline__ double shift_of(const ShiftSource& src, int c)
 // moves to the next integer), sigma reduced into [0, N).  The entries of A and
 // B are the exact polynomials of the projection integrals, stored centred at
 // alpha = 1/2 and evaluated by Horner's rule; alpha = 0 is the exact identity.
-// Writes class c's record (padded to 16 bytes) in FP64 and FP32.
-__device__ __forceinline__ void ab_class(int K, double s, uint32_t N, const PolyTab& tab, int c,
-                                         int32_t* __restrict__ sigma, double* __restrict__ alpha,
-                                         double* __restrict__ ab64, float* __restrict__ ab32)
+// Writes class c's record (padded to 16 bytes) in FP64 and FP32.  The degree
+// is a template parameter so that the loops unroll.
+template <int K>
+__device__ __forceinline__ void ab_class_k(double s, uint32_t N, const PolyTab& tab, int c,
+                                           int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                                           double* __restrict__ ab64, float* __restrict__ ab32)
 {
     const double f = floor(s);
     double a = s - f;
@@ -42,12 +44,14 @@ __device__ __forceinline__ void ab_class(int K, double s, uint32_t N, const Poly
     sigma[c] = int32_t(r);
     alpha[c] = a;
 
-    const int O = K + 1;
-    const int deg = 2 * K + 1;
+    constexpr int O = K + 1;
+    constexpr int deg = 2 * K + 1;
     const double t = a - 0.5;
     double* m64 = ab64 + size_t(c) * ab_stride64(O);
     float* m32 = ab32 + size_t(c) * ab_stride32(O);
+#pragma unroll
     for (int j = 0; j < O; ++j) {
+#pragma unroll
         for (int l = 0; l < O; ++l) {
             double va, vb;
             if (a == 0.0) {
@@ -56,6 +60,7 @@ __device__ __forceinline__ void ab_class(int K, double s, uint32_t N, const Poly
             } else {
                 va = tab.a[j][l][deg];
                 vb = tab.b[j][l][deg];
+#pragma unroll
                 for (int p = deg - 1; p >= 0; --p) {
                     va = fma(va, t, tab.a[j][l][p]);
                     vb = fma(vb, t, tab.b[j][l][p]);
@@ -66,6 +71,18 @@ __device__ __forceinline__ void ab_class(int K, double s, uint32_t N, const Poly
             m32[j * O + l] = __double2float_rn(va);
             m32[O * O + j * O + l] = __double2float_rn(vb);
         }
+    }
+}
+
+__device__ __forceinline__ void ab_class(int K, double s, uint32_t N, const PolyTab& tab, int c,
+                                         int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                                         double* __restrict__ ab64, float* __restrict__ ab32)
+{
+    switch (K) {
+    case 0: ab_class_k<0>(s, N, tab, c, sigma, alpha, ab64, ab32); break;
+    case 1: ab_class_k<1>(s, N, tab, c, sigma, alpha, ab64, ab32); break;
+    case 2: ab_class_k<2>(s, N, tab, c, sigma, alpha, ab64, ab32); break;
+    default: ab_class_k<3>(s, N, tab, c, sigma, alpha, ab64, ab32); break;
     }
 }
 

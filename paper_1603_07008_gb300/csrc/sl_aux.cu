@@ -11,22 +11,32 @@ namespace sl {
 // ---------------------------------------------------------------- A, B
 
 // One thread per shift class; the arithmetic is in sl_ab.cuh.
-__global__ void k_ab_build(int K, int nclass, uint32_t N, ShiftSource src, PolyTab tab,
-                           int32_t* __restrict__ sigma, double* __restrict__ alpha,
-                           double* __restrict__ ab64, float* __restrict__ ab32)
+// One thread per shift class, in blocks of one warp so that the classes of a
+// line family (a few hundred to a few thousand) spread over many SMs: the
+// evaluation is a chain of dependent FP64 multiply-adds.
+template <int K>
+__global__ void __launch_bounds__(32) k_ab_build(int nclass, uint32_t N, ShiftSource src, PolyTab tab,
+                                                 int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                                                 double* __restrict__ ab64, float* __restrict__ ab32)
 {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= nclass) return;
-    ab_class(K, shift_of(src, c), N, tab, c, sigma, alpha, ab64, ab32);
+    ab_class_k<K>(shift_of(src, c), N, tab, c, sigma, alpha, ab64, ab32);
 }
 
 cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,
                             const PolyTab& tab, int32_t* sigma, double* alpha, double* ab64,
                             float* ab32, cudaStream_t st)
 {
-    const int block = 128;
-    k_ab_build<<<(nclass + block - 1) / block, block, 0, st>>>(K, nclass, N, src, tab, sigma,
-                                                              alpha, ab64, ab32);
+    const int block = 32;
+    const int grid = (nclass + block - 1) / block;
+    switch (K) {
+    case 0: k_ab_build<0><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 1: k_ab_build<1><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 2: k_ab_build<2><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 3: k_ab_build<3><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

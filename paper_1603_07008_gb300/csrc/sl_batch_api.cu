@@ -352,14 +352,14 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
         cudaStreamSynchronize(b->st) != cudaSuccess)
         return cleanup(fail(nullptr, SL_ECUDA, "uploading batch tables"));
     // default shapes (the autotuner's usual picks on 2D x-v batches): whole
-    // cells along dimension 0 (each problem takes at most its own fibres) in
-    // items of eight cell tiles; one fibre per thread, four cells per walk
-    // step and 64-row items along the other dimensions
+    // cells (each problem takes at most its own fibres), two consecutive cells
+    // per thread and items of four tiles along dimension 0; one fibre per
+    // thread, four cells per walk step and 64-row items along the others
     for (int m = 0; m < b->ndim; ++m) {
         b->tune[m].ft = m == 0 ? kBatchMaxFtUnit : 1;
-        b->tune[m].unroll = m == 0 ? 1 : 4;
+        b->tune[m].unroll = m == 0 ? 2 : 4;
         b->tune[m].rows = 64;
-        b->tune[m].reps = m == 0 ? 8 : 4;
+        b->tune[m].reps = 4;
         sl_status s = rebuild_dim(b, m);
         if (s != SL_OK) {
             fail(nullptr, s, "%s", b->err.c_str());
