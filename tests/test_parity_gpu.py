@@ -641,3 +641,30 @@ def test_advect_graph_replay_matches_advect_calls():
         assert np.array_equal(a.get_coeffs(), b.get_coeffs())
         with pytest.raises(S.SlError):
             b.graph_capture_advect(0, 1, s[:3], 2)
+
+
+def test_largest_grid_sampled_after_one_step():
+    """The largest grid the library takes in 2D: 46340^2 = 2,147,395,600 cells
+    (just below the 2^31 - 1 limit; k = 1, mixed FP32, 86 GB for the two
+    copies of the state).  One Strang step against the oracle on the
+    dependency cones of sampled cells, including the first and last cells,
+    so that 32-bit cell indices and 64-bit plane offsets are exercised at
+    their ends; mass conserved."""
+    n = 46340
+    p = W.config2(n=n, steps=1)
+    g = p.grid
+    assert g.cells < 2 ** 31 - 1
+    rng = np.random.default_rng(7)
+    cells = np.concatenate([[0, n - 1, g.cells - n, g.cells - 1], rng.integers(0, g.cells, 8)]).astype(np.int64)
+    sched = O.schedule(g, "strang", p.dt, p.field_list())
+    ref = O.sample_after(g, 1, p.nq, p.weights, p.params, sched, cells)
+    with S.Context(g, 1, "mix_fp32") as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, 1)
+        got = ctx.get_cells(cells)
+        m1 = ctx.mass()
+    for i in range(len(cells)):
+        assert O.rel_l2(got[i:i + 1], ref[i:i + 1], 1, 2) <= 1e-5, cells[i]
+    assert abs(m1 - m0) / abs(m0) <= MASS_TOL
