@@ -1041,6 +1041,21 @@ __device__ __forceinline__ uint32_t enc16(float v)
         return __half_as_ushort(__float2half_rn(v));
 }
 
+// Two values to a packed pair of 16-bit codes (lo in the low half), rounded
+// to nearest even: one paired conversion instead of two conversions, a
+// shift and an or (the same bits as enc16 on each).
+template <int MODE>
+__device__ __forceinline__ uint32_t enc16x2(float lo, float hi)
+{
+    if constexpr (MODE == M_BF16) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&p);
+    } else {
+        const __half2 p = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<const uint32_t*>(&p);
+    }
+}
+
 template <int MODE, int NV>
 __device__ __forceinline__ float rec_get(const uint4 (&r)[NV], int J)
 {
@@ -1097,9 +1112,10 @@ __device__ __forceinline__ float rec_pack(float (&out)[RecShape<K, D>::R], uint4
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
             const int J0 = 8 * q + 2 * h, J1 = J0 + 1;
-            const uint32_t lo = (J0 >= 1 && J0 < RS::NC) ? enc16<MODE>(out[J0] * inv) : 0u;
-            const uint32_t hi = (J1 >= 1 && J1 < RS::NC) ? enc16<MODE>(out[J1] * inv) : 0u;
-            w[h] = lo | (hi << 16);
+            // slot 0 and padding slots encode +0, whose code is 0
+            const float lo = (J0 >= 1 && J0 < RS::NC) ? out[J0] * inv : 0.0f;
+            const float hi = (J1 >= 1 && J1 < RS::NC) ? out[J1] * inv : 0.0f;
+            w[h] = enc16x2<MODE>(lo, hi);
         }
         ro[q] = make_uint4(w[0], w[1], w[2], w[3]);
     }

@@ -124,7 +124,7 @@ __device__ __forceinline__ void lg_store(const SweepArgs& a, uint32_t c, int h, 
     pow2_scale(mx, sc, inv);
     uint32_t w[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) w[k] = enc16<MODE>(out[2 * k] * inv) | (enc16<MODE>(out[2 * k + 1] * inv) << 16);
+    for (int k = 0; k < 8; ++k) w[k] = enc16x2<MODE>(out[2 * k] * inv, out[2 * k + 1] * inv);
     if (h == 0) w[0] &= 0xffff0000u;   // slot 0 (the mean's) stays zero
     uint4* p = static_cast<uint4*>(a.dst.hi) + size_t(c) * (R / 8);
     p[c0] = make_uint4(w[0], w[1], w[2], w[3]);

@@ -185,3 +185,19 @@ def test_batch_every_shape_gives_identical_results():
             with pytest.raises(S.SlError) as e:
                 b.set_tune(dim, **sh)
             assert e.value.status == S.SL_EINVAL
+
+
+def test_batch_lie_matches_single_problems():
+    probs = _problems(SIZES, DEGS, "mix_fp32")
+    with S.Batch([p.grid for p in probs], [p.k for p in probs], "mix_fp32") as b:
+        for i, p in enumerate(probs):
+            b.project(i, p.nq, p.weights, p.params)
+        b.set_fields([p.field_list()[0] for p in probs])
+        b.step("lie", 0.1, 3)
+        got = [b.get_coeffs(i) for i in range(len(probs))]
+    for i, p in enumerate(probs):
+        with S.Context(p.grid, p.k, "mix_fp32") as c:
+            c.project(p.nq, p.weights, p.params)
+            c.set_fields(p.field_list())
+            c.step("lie", 0.1, 3)
+            assert np.array_equal(got[i], c.get_coeffs()), i

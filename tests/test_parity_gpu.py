@@ -668,3 +668,25 @@ def test_largest_grid_sampled_after_one_step():
     for i in range(len(cells)):
         assert O.rel_l2(got[i:i + 1], ref[i:i + 1], 1, 2) <= 1e-5, cells[i]
     assert abs(m1 - m0) / abs(m0) <= MASS_TOL
+
+
+@pytest.mark.parametrize("cfg", ["2d", "4d"])
+@pytest.mark.parametrize("storage", ["fp64", "mix_fp32"])
+def test_lie_splitting_matches_oracle(cfg, storage):
+    """Lie splitting (x-dims then v-dims, each with dt) against the oracle."""
+    p = W.config2(n=40, steps=5) if cfg == "2d" else W.config3(n=8, steps=2)
+    u = O.project(p.grid, p.k, p.nq, p.weights, p.params)
+    with S.Context(p.grid, p.k, storage) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        stored = ctx.get_coeffs()
+        m0 = ctx.mass()
+        ctx.step("lie", p.dt, p.steps)
+        got = ctx.get_coeffs()
+        drift = abs(ctx.mass() - m0) / abs(m0)
+    ref = O.step(stored if storage != "fp64" else u, p.grid, p.k, "lie", p.dt, p.steps, p.field_list())
+    if storage == "fp64":
+        assert O.rel_max(got, ref) <= FP64_TOL
+    else:
+        assert O.rel_l2(got, ref, p.k, p.grid.ndim) <= 1e-5
+    assert drift <= MASS_TOL
