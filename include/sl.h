@@ -133,6 +133,34 @@ typedef struct {
 sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
                     sl_ctx** out);
 
+/* Layout of one copy of the state for (grid, degree, storage): plane_stride
+ * (elements between coefficient planes, cells rounded up to 64),
+ * record_slots (0: planar), and the bytes of its three arrays: the FP64 mean
+ * plane [plane_stride], the higher coefficients ([o^d - 1][plane_stride]
+ * planes, or [cells][record_slots] records, in the storage's element type)
+ * and the FP32 scale plane [plane_stride] (0 bytes for the unscaled stores).
+ * Errors as sl_create's argument checks. */
+typedef struct {
+    int64_t plane_stride;
+    int32_t record_slots;
+    int32_t reserved;
+    int64_t mean_bytes;
+    int64_t hi_bytes;
+    int64_t scale_bytes;
+} sl_layout;
+sl_status sl_plane_layout(const sl_grid* grid, int degree, sl_storage storage, sl_layout* out);
+
+/* As sl_create, but the two copies of the state live in caller-owned device
+ * memory (e.g. framework tensors): planes = {mean_0, hi_0, scale_0, mean_1,
+ * hi_1, scale_1}, each 256-byte aligned and of the sizes sl_plane_layout
+ * gives (the scale pointers may be NULL for the unscaled stores).  The
+ * context neither initialises nor frees them; the caller keeps them alive
+ * until sl_destroy.  Which copy holds the current state changes with every
+ * sweep (sl_get_planes reads the current one).  Errors: as sl_create, and
+ * SL_EINVAL for a NULL or misaligned plane pointer. */
+sl_status sl_create_external(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
+                             void* const* planes, sl_ctx** out);
+
 /* Free the context and its device memory (after synchronising its stream).
  * NULL is ignored. */
 void sl_destroy(sl_ctx* ctx);

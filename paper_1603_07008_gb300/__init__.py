@@ -32,7 +32,7 @@ __all__ = [
     "sl_batch_mass", "sl_batch_graph_capture", "sl_batch_graph_launch", "sl_batch_synchronize",
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
     "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
-    "sl_field_energy", "sl_graph_capture_advect",
+    "sl_field_energy", "sl_graph_capture_advect", "sl_create_external", "sl_plane_layout",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -53,6 +53,11 @@ class sl_tune(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("fibres_per_thread", ctypes.c_int32),
                 ("unroll", ctypes.c_int32), ("pipeline", ctypes.c_int32), ("chunk", ctypes.c_int64),
                 ("max_blocks_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class sl_layout(ctypes.Structure):
+    _fields_ = [("plane_stride", ctypes.c_int64), ("record_slots", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("mean_bytes", ctypes.c_int64), ("hi_bytes", ctypes.c_int64), ("scale_bytes", ctypes.c_int64)]
 
 
 class sl_grid(ctypes.Structure):
@@ -157,6 +162,10 @@ def lib():
             "sl_batch_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
+            "sl_create_external": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int, _vp,
+                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
+            "sl_plane_layout": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(sl_layout)]),
             "sl_graph_capture_advect": (st, [_vp, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int64, ctypes.c_int]),
             "sl_get_field": (st, [_vp, _dp]),
             "sl_field_energy": (st, [_vp, _dp]),
@@ -398,6 +407,27 @@ def sl_graph_capture_advect(ctx, dim: int, shift_dim: int, shifts, nsteps: int):
                                          int(nsteps)), ctx)
 
 
+def sl_plane_layout(grid, degree: int, storage) -> dict:
+    """Layout of one copy of the state (see sl.h)."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    g = make_grid(grid)
+    lay = sl_layout()
+    _check(lib().sl_plane_layout(ctypes.byref(g), int(degree), st, ctypes.byref(lay)))
+    return {k: getattr(lay, k) for k, _ in sl_layout._fields_ if k != "reserved"}
+
+
+def sl_create_external(grid, degree: int, storage, planes, stream=None):
+    """Context over six caller-owned device addresses (integers or 0):
+    mean_0, hi_0, scale_0, mean_1, hi_1, scale_1."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    g = make_grid(grid)
+    arr = (_vp * 6)(*[_vp(int(p)) if p else _vp() for p in planes])
+    h = _vp()
+    _check(lib().sl_create_external(ctypes.byref(g), int(degree), st, _stream_handle(stream), arr,
+                                    ctypes.byref(h)))
+    return h
+
+
 def sl_set_poisson(ctx, enable=True):
     _check(lib().sl_set_poisson(ctx, 1 if enable else 0), ctx)
 
@@ -429,11 +459,16 @@ def sl_mass_noalloc(d_mean: int, cells: int, cell_volume: float, d_out: int, str
 class Context:
     """Owns one sl_ctx handle; methods forward to the functions above."""
 
-    def __init__(self, grid, degree: int, storage, stream=None):
+    def __init__(self, grid, degree: int, storage, stream=None, planes=None):
+        """planes: six device addresses for sl_create_external (the caller
+        keeps that memory alive), or None for library-owned state."""
         self.grid = grid
         self.degree = degree
         self.storage = storage
-        self.handle = sl_create(grid, degree, storage, stream)
+        if planes is None:
+            self.handle = sl_create(grid, degree, storage, stream)
+        else:
+            self.handle = sl_create_external(grid, degree, storage, planes, stream)
         self.info = sl_get_info(self.handle)
 
     def close(self):

@@ -559,13 +559,43 @@ sl_status sl_ab_host(int degree, double alpha, double* A, double* B)
     return SL_OK;
 }
 
-sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
-                    sl_ctx** out)
+// One copy of the state: bytes of the mean plane, the higher coefficients
+// (planes or cell records) and the scale plane (0 for the unscaled stores).
+static void copy_bytes(int64_t cells, int64_t ncoef, int rec, int elem, bool scaled, int64_t pstride,
+                       size_t* mean, size_t* hi, size_t* scale)
+{
+    *mean = size_t(pstride) * 8;
+    *hi = rec ? size_t(cells) * size_t(rec) * size_t(elem) : size_t(pstride) * size_t(ncoef - 1) * size_t(elem);
+    *scale = scaled ? size_t(pstride) * 4 : 0;
+}
+
+static int record_slots_of(const sl_grid* grid, int degree, sl_storage storage, int64_t ncoef)
+{
+    // cell records for the scaled shapes that fill them (at most one padding
+    // slot besides slot 0): 6D and 5D with k = 1, 3D with k = 3
+    if ((storage == SL_MIX_BF16 || storage == SL_MIX_FP16) &&
+        ((degree == 1 && (grid->ndim == 6 || grid->ndim == 5)) || (degree == 3 && grid->ndim == 3)))
+        return int((ncoef + 7) / 8 * 8);
+    return 0;
+}
+
+// planes == nullptr: the context allocates both copies of the state;
+// otherwise planes = {mean0, hi0, scale0, mean1, hi1, scale1}, caller-owned.
+static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
+                            void* const* planes, sl_ctx** out)
 {
     if (!out) return fail(nullptr, SL_EINVAL, "out is NULL");
     *out = nullptr;
     sl_status s = check_grid(grid, degree, storage, nullptr);
     if (s != SL_OK) return s;
+    const bool scaled = storage == SL_MIX_BF16 || storage == SL_MIX_FP16;
+    if (planes)
+        for (int q = 0; q < 6; ++q) {
+            const bool need = (q % 3) != 2 || scaled;
+            if (need && !planes[q]) return fail(nullptr, SL_EINVAL, "plane pointer %d is NULL", q);
+            if (planes[q] && reinterpret_cast<uintptr_t>(planes[q]) % 256 != 0)
+                return fail(nullptr, SL_EINVAL, "plane pointer %d is not 256-byte aligned", q);
+        }
 
     sl_ctx* c = new (std::nothrow) sl_ctx();
     if (!c) return fail(nullptr, SL_ENOMEM, "host allocation failed");
@@ -585,31 +615,28 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
     c->nfib = ipow(c->O, c->ndim - 1);
     c->pstride = int64_t(align_up(size_t(c->cells), 64));
     c->elem = elem_size(storage);
-    // cell records for the scaled shapes that fill them (at most one padding
-    // slot besides slot 0): 6D and 5D with k = 1, 3D with k = 3
-    if ((storage == SL_MIX_BF16 || storage == SL_MIX_FP16) &&
-        ((degree == 1 && (grid->ndim == 6 || grid->ndim == 5)) || (degree == 3 && grid->ndim == 3)))
-        c->rec = int((c->ncoef + 7) / 8 * 8);
+    c->rec = record_slots_of(grid, degree, storage, c->ncoef);
     c->state_bytes = state_bytes_of(c->cells, c->ncoef, storage);
+    c->external = planes != nullptr;
     for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
     build_poly_table(degree, &c->poly);
     for (int m = 0; m < c->ndim; ++m) default_tune(c, m);
 
-    const bool scaled = storage == SL_MIX_BF16 || storage == SL_MIX_FP16;
-    // layout of the single allocation
+    // layout of the single allocation (the state only when the context owns it)
     const size_t A = 256;
     size_t off = 0;
-    size_t o_state[2][3];
-    for (int b = 0; b < 2; ++b) {
-        o_state[b][0] = off;
-        off = align_up(off + size_t(c->pstride) * 8, A);
-        o_state[b][1] = off;
-        off = align_up(off + (c->rec ? size_t(c->cells) * c->rec * c->elem
-                                     : size_t(c->pstride) * size_t(c->ncoef - 1) * c->elem),
-                       A);
-        o_state[b][2] = off;
-        if (scaled) off = align_up(off + size_t(c->pstride) * 4, A);
-    }
+    size_t o_state[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    size_t b_mean, b_hi, b_scale;
+    copy_bytes(c->cells, c->ncoef, c->rec, c->elem, scaled, c->pstride, &b_mean, &b_hi, &b_scale);
+    if (!planes)
+        for (int b = 0; b < 2; ++b) {
+            o_state[b][0] = off;
+            off = align_up(off + b_mean, A);
+            o_state[b][1] = off;
+            off = align_up(off + b_hi, A);
+            o_state[b][2] = off;
+            off = align_up(off + b_scale, A);
+        }
     const size_t o_sigma = off;
     off = align_up(off + size_t(c->maxcls) * 4, A);
     const size_t o_alpha = off;
@@ -640,9 +667,15 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
     }
     char* base = static_cast<char*>(c->mem);
     for (int b = 0; b < 2; ++b) {
-        c->planes[b].mean = reinterpret_cast<double*>(base + o_state[b][0]);
-        c->planes[b].hi = base + o_state[b][1];
-        c->planes[b].scale = scaled ? reinterpret_cast<float*>(base + o_state[b][2]) : nullptr;
+        if (planes) {
+            c->planes[b].mean = static_cast<double*>(planes[3 * b]);
+            c->planes[b].hi = planes[3 * b + 1];
+            c->planes[b].scale = scaled ? static_cast<float*>(planes[3 * b + 2]) : nullptr;
+        } else {
+            c->planes[b].mean = reinterpret_cast<double*>(base + o_state[b][0]);
+            c->planes[b].hi = base + o_state[b][1];
+            c->planes[b].scale = scaled ? reinterpret_cast<float*>(base + o_state[b][2]) : nullptr;
+        }
     }
     c->d_sigma = reinterpret_cast<int32_t*>(base + o_sigma);
     c->d_alpha = reinterpret_cast<double*>(base + o_alpha);
@@ -658,7 +691,8 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
         delete c;
         return fail(nullptr, SL_ENOMEM, "cudaMallocHost: %s", cudaGetErrorString(e));
     }
-    // state starts at zero (the scale plane at zero decodes to zero too)
+    // an owned state starts at zero (the scale plane at zero decodes to zero
+    // too); a caller's planes keep their contents
     e = cudaMemsetAsync(c->mem, 0, c->mem_bytes, c->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
@@ -668,6 +702,40 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
         return fail(nullptr, SL_ECUDA, "initialising the state: %s", cudaGetErrorString(e));
     }
     *out = c;
+    return SL_OK;
+}
+
+sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream, sl_ctx** out)
+{
+    return create_ctx(grid, degree, storage, cuda_stream, nullptr, out);
+}
+
+sl_status sl_create_external(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
+                             void* const* planes, sl_ctx** out)
+{
+    if (!planes) return fail(nullptr, SL_EINVAL, "planes is NULL");
+    return create_ctx(grid, degree, storage, cuda_stream, planes, out);
+}
+
+sl_status sl_plane_layout(const sl_grid* grid, int degree, sl_storage storage, sl_layout* out)
+{
+    if (!out) return fail(nullptr, SL_EINVAL, "out is NULL");
+    sl_status s = check_grid(grid, degree, storage, nullptr);
+    if (s != SL_OK) return s;
+    int64_t cells = 1;
+    for (int m = 0; m < grid->ndim; ++m) cells *= grid->n[m];
+    const int64_t ncoef = ipow(degree + 1, grid->ndim);
+    const int64_t pstride = int64_t(align_up(size_t(cells), 64));
+    const int rec = record_slots_of(grid, degree, storage, ncoef);
+    size_t bm, bh, bs;
+    copy_bytes(cells, ncoef, rec, elem_size(storage), storage == SL_MIX_BF16 || storage == SL_MIX_FP16, pstride,
+               &bm, &bh, &bs);
+    out->plane_stride = pstride;
+    out->record_slots = rec;
+    out->reserved = 0;
+    out->mean_bytes = int64_t(bm);
+    out->hi_bytes = int64_t(bh);
+    out->scale_bytes = int64_t(bs);
     return SL_OK;
 }
 
@@ -686,7 +754,7 @@ void sl_destroy(sl_ctx* c)
     if (c->d_vp) cudaFree(c->d_vp);
     if (c->d_gshifts) cudaFree(c->d_gshifts);
     if (c->h_mass) cudaFreeHost(c->h_mass);
-    if (c->mem) cudaFree(c->mem);
+    if (c->mem) cudaFree(c->mem);   // a caller's planes (sl_create_external) are not freed
     delete c;
 }
 

@@ -25,6 +25,7 @@ struct sl_ctx {
     void* mem = nullptr;
     size_t mem_bytes = 0;
     sl::Planes planes[2]{};
+    bool external = false;      // planes owned by the caller (sl_create_external)
     int cur = 0;
 
     int maxcls = 1;

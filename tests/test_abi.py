@@ -126,3 +126,31 @@ def test_create_rejects_bad_degree_and_scaled_size():
     with pytest.raises(S.SlError) as e:
         S.sl_create(_grid((2, 2, 2, 2, 2)), 2, "mix_bf16")   # 3^5 = 243 > 128
     assert e.value.status == S.SL_ENOTSUP
+
+
+def test_plane_layout_matches_state_bytes():
+    for n, k, st in [((10, 7), 2, "mix_fp32"), ((3, 2, 2, 3, 2, 2), 1, "mix_bf16"), ((5, 3), 1, "fp64"),
+                     ((4, 3, 5), 3, "mix_fp16")]:
+        g = W.Grid(n=n, lo=(0.0,) * len(n), hi=(1.0,) * len(n), pair=(-1,) * len(n))
+        lay = S.sl_plane_layout(g, k, st)
+        cells = int(np.prod(n))
+        assert lay["plane_stride"] == -(-cells // 64) * 64
+        assert lay["mean_bytes"] == lay["plane_stride"] * 8
+        if lay["record_slots"]:
+            assert lay["hi_bytes"] == cells * lay["record_slots"] * 2
+        else:
+            elem = {"mix_fp32": 4, "fp64": 8, "mix_bf16": 2, "mix_fp16": 2}[st]
+            assert lay["hi_bytes"] == lay["plane_stride"] * ((k + 1) ** len(n) - 1) * elem
+        assert lay["scale_bytes"] == (lay["plane_stride"] * 4 if st in ("mix_bf16", "mix_fp16") else 0)
+    with pytest.raises(S.SlError):
+        S.sl_plane_layout(W.Grid(n=(0,), lo=(0.0,), hi=(1.0,), pair=(-1,)), 1, "fp64")
+
+
+def test_create_external_rejects_bad_planes_before_device_work():
+    g = W.Grid(n=(8,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    with pytest.raises(S.SlError) as e:
+        S.sl_create_external(g, 1, "fp64", [0, 0, 0, 0, 0, 0])
+    assert e.value.status == S.SL_EINVAL
+    with pytest.raises(S.SlError) as e:
+        S.sl_create_external(g, 1, "fp64", [256, 512 + 8, 0, 1024, 2048, 0])   # misaligned hi_0
+    assert e.value.status == S.SL_EINVAL

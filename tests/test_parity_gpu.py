@@ -690,3 +690,36 @@ def test_lie_splitting_matches_oracle(cfg, storage):
     else:
         assert O.rel_l2(got, ref, p.k, p.grid.ndim) <= 1e-5
     assert drift <= MASS_TOL
+
+
+@pytest.mark.parametrize("storage,n,k", [("mix_fp32", (9, 6), 2), ("fp64", (7, 5, 3), 1),
+                                         ("mix_bf16", (3, 2, 2, 3, 2, 2), 1), ("mix_fp16", (5, 4, 3), 2)])
+def test_external_planes_give_the_same_results(storage, n, k):
+    """A context over caller-owned planes (torch tensors) computes exactly
+    what a context with library-owned state computes, and the current state
+    is in the caller's memory."""
+    import torch
+    g = _grid(n)
+    lay = S.sl_plane_layout(g, k, storage)
+    bufs = []
+    for _ in range(2):
+        for key in ("mean_bytes", "hi_bytes", "scale_bytes"):
+            nb = lay[key]
+            # torch's allocator hands out 512-byte aligned blocks
+            bufs.append(torch.zeros(max(nb, 1), dtype=torch.uint8, device="cuda") if nb else None)
+    ptrs = [b.data_ptr() if b is not None else 0 for b in bufs]
+    assert all(p % 256 == 0 for p in ptrs)
+    u = _rand(n, k, 3)
+    rng = np.random.default_rng(2)
+    with S.Context(g, k, storage) as a, S.Context(g, k, storage, planes=ptrs) as b:
+        for c in (a, b):
+            c.set_coeffs(u)
+        for dim in range(len(n)):
+            s = _shifts(rng, n, dim, -1)
+            a.advect(dim, -1, s)
+            b.advect(dim, -1, s)
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+        cur = len(n) % 2                       # copy holding the state after len(n) sweeps
+        mean = bufs[3 * cur].view(torch.float64)[: int(np.prod(n))].cpu().numpy()
+        assert np.array_equal(mean, b.get_coeffs()[:, 0])
+    del bufs
