@@ -50,9 +50,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="4d", choices=["4d", "2d", "batch", "6d", "1d", "vp"],
+    ap.add_argument("--workload", default="4d", choices=["4d", "2d", "batch", "6d", "1d", "vp", "paper1d"],
                     help="4d: 64^4 k=2 (default); 2d: 512^2 k=2; batch: 256 uneven 2D problems; "
-                         "6d: 20^6 k=1; 1d: N=1024 k=2")
+                         "6d: 20^6 k=1; 1d: N=1024 k=2; paper1d: the 1D stores of Tables III-VI "
+                         "(order 2 and 4, every # double) on N = 2^27 cells")
     ap.add_argument("--n", type=int, default=None, help="cells per dimension (4d/2d/6d)")
     ap.add_argument("--storage", default=None, help="store of the timed arm (default per workload)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison arm")
@@ -492,6 +493,117 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# The stores of Tables III-VI (Sec. III): (degree, store), "# double" per store.
+PAPER1D_ROWS = [(1, "fp64"), (1, "mix_fp32"), (1, "fp32"),
+                (3, "fp64"), (3, "mix_fp32_d3"), (3, "mix_fp32_d2"), (3, "mix_fp32"), (3, "fp32")]
+PAPER1D_NDOUBLE = {"fp32": 0, "mix_fp32": 1, "mix_fp32_d2": 2, "mix_fp32_d3": 3}
+
+
+def run_paper1d(args):
+    """The GB300 counterpart of Tables III-VI: the 1D advection (constant
+    velocity, CFL 0.37: sigma = 0, alpha = 0.37) of orders 2 and 4 with every
+    store, on N = 2^27 cells (2.1 to 4.3 GB per state copy, far above L2).
+    Per store: sweep GB/s (algorithmic bytes: read + write of the state),
+    DoF updates/s, speedup over the FP64 store and memory reduction, as the
+    paper's columns; the headline value is order 4 with c_0 in FP64."""
+    import torch
+    import paper_1603_07008_gb300 as S
+    from paper_1603_07008_gb300 import workloads as W
+
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.Stream(device=dev)
+    n = args.n or (1 << 27)
+    peaks, peak_src = measured_peaks()
+    peak_gbs = float(peaks["hbm_gbs"])
+    g = W.Grid(n=(n,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    shift = 0.37
+    rows, fp64_rate = [], {}
+    clk_all = None
+    for k, store in PAPER1D_ROWS:
+        ctx = S.Context(g, k, store, stream=stream)
+        # 1 + cos(2 pi 8 x + 0.3): the oscillatory profile of Table II
+        ctx.project(k + 2, [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]])
+        ctx.autotune(3)
+        m0 = ctx.mass()
+        for _ in range(args.warmup):
+            ctx.advect(0, -1, [shift])
+        ctx.synchronize()
+        ctx.profile_query()
+        ctx.profile_enable(True)
+        barrier(world)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.advect(0, -1, [shift])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = e0.elapsed_time(e1)
+        nl, sms, sbytes = ctx.profile_query()
+        ctx.profile_enable(False)
+        drift = abs(ctx.mass() - m0) / abs(m0)
+        info = ctx.info
+        tune = ctx.get_tune(0)
+        ctx.close()
+        ms_max, units = aggregate(ms, float(args.steps * info["dof"]), world, dev)
+        sweep_ms = sms / max(nl, 1)
+        gbs = (sbytes / max(nl, 1)) / (sweep_ms / 1000.0) / 1e9
+        rate = units / (ms_max / 1000.0)
+        if store == "fp64":
+            fp64_rate[k] = (rate, info["state_bytes"])
+        r64, b64 = fp64_rate[k]
+        rows.append({"order": k + 1, "store": store,
+                     "n_double": k + 1 if store == "fp64" else PAPER1D_NDOUBLE[store],
+                     "sweep_gbs": gbs, "frac_of_hbm": gbs / peak_gbs, "sweep_ms": sweep_ms,
+                     "dof_per_s": rate, "speedup_vs_fp64": rate / r64,
+                     "memorydown": b64 / info["state_bytes"], "mass_drift": drift,
+                     "state_bytes": info["state_bytes"], "tune": tune, "clocks": clk})
+        if k == 3 and store == "mix_fp32":
+            head = rows[-1]
+            head_launch = (nl, sms, sbytes)
+            clk_all = clk
+    if rank == 0:
+        nl, sms, sbytes = head_launch
+        avg = sms / max(nl, 1)
+        out = {
+            "metric": METRIC, "value": head["dof_per_s"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["sweep_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"1d_n{n}_k3_mix_fp32_advect_cfl0.37 (with every store of orders 2, 4)",
+                       "dof": n * 4, "sweeps_per_step": 1, "state_bytes": head["state_bytes"],
+                       "l2": f"state {head['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
+                       "parallelism": f"replicas x{world}"},
+            "mass_drift": head["mass_drift"],
+            "roofline": {"bound": "hbm", "achieved": head["sweep_gbs"], "peak": peak_gbs, "unit": "GB/s",
+                         "frac": head["sweep_gbs"] / peak_gbs, "traffic": None,
+                         "traffic_note": "no ncu capture of this workload's kernels",
+                         "kernel": "sweep along dimension 0", "peak_source": peak_src,
+                         "bytes_per_launch": sbytes / max(nl, 1), "avg_launch_ms": avg, "launches": nl},
+            "table": rows,
+            "speedup_mixed_vs_fp64": head["speedup_vs_fp64"],
+            "e2e": None,
+            "gpu_launches": args.steps * 2 * len(PAPER1D_ROWS),
+            "clocks": clk_all,
+            "cpu_baseline": None,
+        }
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
 def run_e2e(S, W, p, args, stream, world, dev):
     """Through the public API with host buffers: every step uploads the state
     from pinned host memory (sl_set_planes), runs one Strang step (sl_step) and
@@ -531,6 +643,8 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "paper1d":
+        run_paper1d(args)
     else:
         run_ours(args)
 

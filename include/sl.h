@@ -78,11 +78,27 @@ typedef enum {
     SL_ENOTSUP = -6    /* valid request this build does not support (e.g. scaled mode with o^d > 128) */
 } sl_status;
 
+/* Storage of the Legendre coefficients c_{j_0..j_{d-1}} of a cell (Sec. III-A,
+ * "# double" = how many coefficients per dimension are kept in FP64):
+ *   SL_FP64         every coefficient in FP64 (# double = o)
+ *   SL_MIX_FP32     the cell mean c_{0..0} in FP64, the others in FP32 (# double = 1)
+ *   SL_MIX_BF16/16  the cell mean in FP64, the others BF16 / FP16 times a
+ *                   per-cell FP32 power-of-two scale
+ *   SL_FP32         every coefficient in FP32, FP32 arithmetic (# double = 0;
+ *                   mass is conserved only to FP32 rounding, Table II)
+ *   SL_MIX_FP32_D2  the coefficients whose every index j_m < 2 in FP64, the
+ *                   others in FP32 (# double = 2; in 1D c_0, c_1); degree >= 2
+ *   SL_MIX_FP32_D3  every index j_m < 3 in FP64 (# double = 3); degree 3
+ * In the stores of # double = q >= 1 the rows of FP64 coefficients are computed
+ * in FP64, the others in FP32. */
 typedef enum {
     SL_FP64 = 0,
     SL_MIX_FP32 = 1,
     SL_MIX_BF16 = 2,
-    SL_MIX_FP16 = 3
+    SL_MIX_FP16 = 3,
+    SL_FP32 = 4,
+    SL_MIX_FP32_D2 = 5,
+    SL_MIX_FP32_D3 = 6
 } sl_storage;
 
 typedef enum {
@@ -139,6 +155,10 @@ sl_status sl_create(const sl_grid* grid, int degree, sl_storage storage, void* c
  * plane [plane_stride], the higher coefficients ([o^d - 1][plane_stride]
  * planes, or [cells][record_slots] records, in the storage's element type)
  * and the FP32 scale plane [plane_stride] (0 bytes for the unscaled stores).
+ * The stores of # double = 0, 2, 3 (SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3)
+ * have n_lo = q^d FP64 planes [n_lo][plane_stride] in place of the mean plane
+ * (none for SL_FP32) and n_hi = o^d - q^d FP32 planes, both in increasing
+ * coefficient order J = sum_m j_m o^m (the FP64 plane of the cell mean first).
  * Errors as sl_create's argument checks. */
 typedef struct {
     int64_t plane_stride;
@@ -174,7 +194,9 @@ sl_status sl_get_info(const sl_ctx* ctx, sl_info* out);
 
 /* Bytes of one state (the algorithmic byte model) without creating a
  * context: cells * (8 + (o^d - 1) * elem (+ 4 for the per-cell scale)),
- * elem = 8 / 4 / 2 / 2 for SL_FP64 / SL_MIX_FP32 / SL_MIX_BF16 / SL_MIX_FP16.
+ * elem = 8 / 4 / 2 / 2 for SL_FP64 / SL_MIX_FP32 / SL_MIX_BF16 / SL_MIX_FP16,
+ * and cells * (8 n_lo + 4 n_hi) for the stores of # double = q (see
+ * sl_plane_layout).
  * Sec. III-A gives the memory reduction this model implies (1.6x for
  * 1D order 4 with c_0 in FP64).  Host only. */
 sl_status sl_state_bytes(const sl_grid* grid, int degree, sl_storage storage, int64_t* bytes);
@@ -204,7 +226,10 @@ sl_status sl_get_cells(sl_ctx* ctx, const int64_t* cells, int64_t ncells, double
 
 /* Raw planes in the store's own layout (for checkpoints and for callers that
  * keep the state on the host between steps):
- *   mean  [cells]            FP64 cell means c_{0..0}
+ *   mean  [cells]            FP64 cell means c_{0..0} ([n_lo][cells] FP64
+ *                            planes for SL_MIX_FP32_D2/D3; unused, may be NULL,
+ *                            for SL_FP32; hi is then [n_hi][cells] FP32,
+ *                            see sl_plane_layout)
  *   hi    [o^d - 1][cells]   coefficient J >= 1 at hi[(J-1)*cells + cell], in
  *                            the store's element type (FP64, FP32, or the
  *                            BF16 / FP16 bit patterns); with cell records

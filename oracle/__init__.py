@@ -33,6 +33,12 @@ Functions and the paper passages they follow:
                                 Sec. II in 1+1 dimensions (reading: d_x E =
                                 rho - rho_bar, rho = int f dv) and the split
                                 step that recomputes it before every v-sweep
+  fp64_coefficients,         -- which coefficients a store of "# double" = q
+  storage_bytes,                keeps in FP64 (Sec. III-A, Tables II-VI;
+  round_storage,                reading for d > 1: every index j_m < q), its
+  stored_sweeps                 bytes per cell, the state as that store holds
+                                it, and sweeps with the state rounded to the
+                                store after each (FP64 arithmetic)
 """
 from __future__ import annotations
 
@@ -285,6 +291,53 @@ def step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, fi
     for _ in range(nsteps):
         for dim, sd, s in sched:
             u = sweep(u, grid.n, k, dim, sd, s)
+    return u
+
+
+# --------------------------------------------------------------------------
+# split storage: "# double" of Sec. III-A (Table II and Tables III-VI)
+# --------------------------------------------------------------------------
+
+def fp64_coefficients(k: int, ndim: int, ndouble: int) -> np.ndarray:
+    """Boolean mask over the o^d coefficients J = sum_m j_m o^m of a cell:
+    True for those a store of "# double" = ndouble keeps in FP64.  Sec. III-A
+    counts, in one dimension, the coefficients c_0 .. c_{q-1} stored in double
+    precision (q = 1: only the cell mean).  Reading for d dimensions: the
+    tensor-product coefficients with every per-dimension index j_m < q."""
+    o = k + 1
+    if not 0 <= ndouble <= o:
+        raise ValueError(f"# double must be in 0..{o}")
+    mask = np.ones(o ** ndim, dtype=bool)
+    for J in range(o ** ndim):
+        r = J
+        for _ in range(ndim):
+            mask[J] &= (r % o) < ndouble
+            r //= o
+    return mask
+
+
+def storage_bytes(k: int, ndim: int, ndouble: int) -> int:
+    """Bytes per cell of that store: 8 per FP64 and 4 per FP32 coefficient."""
+    n64 = int(fp64_coefficients(k, ndim, ndouble).sum())
+    return 8 * n64 + 4 * ((k + 1) ** ndim - n64)
+
+
+def round_storage(u: np.ndarray, k: int, ndim: int, ndouble: int) -> np.ndarray:
+    """The state [cells, o^d] as that store holds it: FP64 coefficients as
+    they are, the others rounded to FP32 (round to nearest, ties to even)."""
+    mask = fp64_coefficients(k, ndim, ndouble)
+    v = np.array(u, dtype=np.float64, copy=True)
+    v[:, ~mask] = v[:, ~mask].astype(np.float32).astype(np.float64)
+    return v
+
+
+def stored_sweeps(u: np.ndarray, n: Sequence[int], k: int, ndouble: int, sweeps) -> np.ndarray:
+    """Apply sweeps (dim, shift_dim, shifts) in turn, each in FP64, rounding
+    the state to the store of "# double" = ndouble after every sweep: what a
+    store of that precision holds when its arithmetic is exact."""
+    u = round_storage(u, k, len(n), ndouble)
+    for dim, sd, s in sweeps:
+        u = round_storage(sweep(u, n, k, dim, sd, s), k, len(n), ndouble)
     return u
 
 

@@ -20,7 +20,8 @@ import numpy as np
 
 __all__ = [
     "SL_OK", "SL_EINVAL", "SL_ENOMEM", "SL_ECUDA", "SL_ETIMEOUT", "SL_ENAN", "SL_ENOTSUP",
-    "SL_FP64", "SL_MIX_FP32", "SL_MIX_BF16", "SL_MIX_FP16", "SL_LIE", "SL_STRANG", "STORAGE",
+    "SL_FP64", "SL_MIX_FP32", "SL_MIX_BF16", "SL_MIX_FP16", "SL_FP32", "SL_MIX_FP32_D2", "SL_MIX_FP32_D3",
+    "N_DOUBLE", "plane_counts", "SL_LIE", "SL_STRANG", "STORAGE",
     "SlError", "sl_grid", "make_grid", "lib", "library_path", "Context",
     "sl_create", "sl_destroy", "sl_last_error", "sl_get_info", "sl_state_bytes", "sl_ab_host",
     "sl_set_coeffs", "sl_get_coeffs", "sl_get_cells", "sl_set_planes", "sl_get_planes", "sl_project", "sl_advect",
@@ -37,8 +38,13 @@ __all__ = [
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SL_FP64, SL_MIX_FP32, SL_MIX_BF16, SL_MIX_FP16 = 0, 1, 2, 3
+SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3 = 4, 5, 6
 SL_LIE, SL_STRANG = 0, 1
-STORAGE = {"fp64": SL_FP64, "mix_fp32": SL_MIX_FP32, "mix_bf16": SL_MIX_BF16, "mix_fp16": SL_MIX_FP16}
+STORAGE = {"fp64": SL_FP64, "mix_fp32": SL_MIX_FP32, "mix_bf16": SL_MIX_BF16, "mix_fp16": SL_MIX_FP16,
+           "fp32": SL_FP32, "mix_fp32_d2": SL_MIX_FP32_D2, "mix_fp32_d3": SL_MIX_FP32_D3}
+# Coefficients per dimension kept in FP64 ("# double" of Sec. III-A) of the
+# stores that keep a block of them (the mixed stores keep the mean: 1).
+N_DOUBLE = {SL_FP32: 0, SL_MIX_FP32: 1, SL_MIX_FP32_D2: 2, SL_MIX_FP32_D3: 3}
 SPLITTING = {"lie": SL_LIE, "strang": SL_STRANG}
 MAX_DIM = 6
 
@@ -265,18 +271,39 @@ def sl_get_cells(ctx, cells) -> np.ndarray:
 
 
 _ELEM = {SL_FP64: np.float64, SL_MIX_FP32: np.float32, SL_MIX_BF16: np.uint16,
-         SL_MIX_FP16: np.uint16}
+         SL_MIX_FP16: np.uint16, SL_FP32: np.float32, SL_MIX_FP32_D2: np.float32, SL_MIX_FP32_D3: np.float32}
+
+
+def plane_counts(ndim: int, degree: int, storage) -> Tuple[int, int]:
+    """(FP64 planes, low-precision planes) of one copy of the state: q^d and
+    o^d - q^d for the stores of # double = q (0, 2, 3), else 1 and o^d - 1."""
+    st = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    nc = (degree + 1) ** ndim
+    nlo = N_DOUBLE[st] ** ndim if st in (SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3) else 1
+    return nlo, nc - nlo
 
 
 def plane_arrays(ctx):
-    """Host numpy arrays (mean, hi, scale) shaped for sl_get_planes / sl_set_planes."""
+    """Host numpy arrays (mean, hi, scale) shaped for sl_get_planes / sl_set_planes:
+    mean is [cells] (one FP64 plane), [n_lo, cells] (several) or None (SL_FP32)."""
     info = sl_get_info(ctx)
     st = info["storage"]
-    mean = np.empty(info["cells"], dtype=np.float64)
+    if st in (SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3):
+        # state bytes = cells (8 n_lo + 4 n_hi), n_lo + n_hi = o^d
+        nlo = (info["state_bytes"] // info["cells"] - 4 * info["ncoef"]) // 4
+    else:
+        nlo = 1
+    nhi = info["ncoef"] - nlo
+    if nlo == 0:
+        mean = None
+    elif nlo == 1:
+        mean = np.empty(info["cells"], dtype=np.float64)
+    else:
+        mean = np.empty((nlo, info["cells"]), dtype=np.float64)
     if info["record_slots"]:
         hi = np.empty((info["cells"], info["record_slots"]), dtype=_ELEM[st])
     else:
-        hi = np.empty((info["ncoef"] - 1, info["cells"]), dtype=_ELEM[st])
+        hi = np.empty((nhi, info["cells"]), dtype=_ELEM[st])
     scale = np.empty(info["cells"], dtype=np.float32) if st in (SL_MIX_BF16, SL_MIX_FP16) else None
     return mean, hi, scale
 
@@ -285,19 +312,23 @@ def sl_set_planes(ctx, mean, hi, scale=None):
     """Enqueue the copy of raw planes (host arrays or raw host addresses).
     The memory must stay valid until the context's stream passes the copy."""
     fp = ctypes.POINTER(ctypes.c_float)
-    m = mean if isinstance(mean, int) else _ptr(mean)
-    m = ctypes.cast(m, _dp) if isinstance(mean, int) else m
+    if mean is None:
+        m = None
+    else:
+        m = mean if isinstance(mean, int) else _ptr(mean)
+        m = ctypes.cast(m, _dp) if isinstance(mean, int) else m
     h = hi if isinstance(hi, int) else hi.ctypes.data
     s = None if scale is None else (ctypes.cast(scale, fp) if isinstance(scale, int) else scale.ctypes.data_as(fp))
     _check(lib().sl_set_planes(ctx, m, ctypes.c_void_p(h), s), ctx)
 
 
 def sl_get_planes(ctx, mean=None, hi=None, scale=None):
-    if mean is None:
+    if hi is None:
         mean, hi, scale = plane_arrays(ctx)
     fp = ctypes.POINTER(ctypes.c_float)
     s = None if scale is None else scale.ctypes.data_as(fp)
-    _check(lib().sl_get_planes(ctx, _ptr(mean), ctypes.c_void_p(hi.ctypes.data), s), ctx)
+    m = None if mean is None else _ptr(mean)
+    _check(lib().sl_get_planes(ctx, m, ctypes.c_void_p(hi.ctypes.data), s), ctx)
     return mean, hi, scale
 
 

@@ -61,7 +61,10 @@ size_t elem_size(int mode)
 {
     switch (mode) {
     case M_FP64: return 8;
-    case M_F32: return 4;
+    case M_F32:
+    case M_F32ALL:
+    case M_SPLIT2:
+    case M_SPLIT3: return 4;
     default: return 2;
     }
 }
@@ -80,8 +83,11 @@ sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c)
         return fail(c, SL_EINVAL, "ndim must be in 1..%d (got %d)", SL_MAX_DIM, g->ndim);
     if (degree < 0 || degree > SL_MAX_DEGREE)
         return fail(c, SL_EINVAL, "degree must be in 0..%d (got %d)", SL_MAX_DEGREE, degree);
-    if (storage < SL_FP64 || storage > SL_MIX_FP16)
+    if (storage < SL_FP64 || storage > SL_MIX_FP32_D3)
         return fail(c, SL_EINVAL, "unknown storage mode %d", storage);
+    if (split_q(storage) > degree)
+        return fail(c, SL_EINVAL, "# double = %d needs degree >= %d (got %d); degree + 1 is SL_FP64",
+                    split_q(storage), split_q(storage), degree);
     double cells = 1.0;
     for (int m = 0; m < g->ndim; ++m) {
         if (g->n[m] < 1) return fail(c, SL_EINVAL, "n[%d] must be >= 1 (got %lld)", m, (long long)g->n[m]);
@@ -107,9 +113,17 @@ sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c)
     return SL_OK;
 }
 
-int64_t state_bytes_of(int64_t cells, int64_t ncoef, int mode)
+void plane_counts(int ndim, int degree, int storage, int64_t* nlo, int64_t* nhi)
 {
-    int64_t b = cells * (8 + (ncoef - 1) * int64_t(elem_size(mode)));
+    const int64_t nc = ipow(degree + 1, ndim);
+    const int q = split_q(storage);
+    *nlo = q < 0 ? 1 : ipow(q, ndim);
+    *nhi = nc - *nlo;
+}
+
+int64_t state_bytes_of(int64_t cells, int64_t nlo, int64_t nhi, int mode)
+{
+    int64_t b = cells * (8 * nlo + nhi * int64_t(elem_size(mode)));
     if (mode == M_BF16 || mode == M_FP16) b += cells * 4;
     return b;
 }
@@ -119,6 +133,14 @@ double cell_width(const sl_grid& g, int m) { return (g.hi[m] - g.lo[m]) / double
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 bool is_scaled(const sl_ctx* c) { return c->mode == M_BF16 || c->mode == M_FP16; }
+bool is_split(const sl_ctx* c) { return c->mode == M_SPLIT2 || c->mode == M_SPLIT3; }
+
+void* hi_block(const sl_ctx* c, int parity)
+{
+    // the all-FP32 store's kernels address coefficient J at hi + (J-1)*pstride
+    if (c->mode == M_F32ALL) return static_cast<float*>(c->planes[parity].hi) - c->pstride;
+    return c->planes[parity].hi;
+}
 
 int64_t fibre_groups(const sl_ctx* c, int ft) { return is_scaled(c) ? 1 : (c->nfib + ft - 1) / ft; }
 
@@ -157,7 +179,7 @@ bool strided_ok(int ft, int u)
 // store or the extent does not allow it).
 int unit_vec_width(const sl_ctx* c)
 {
-    if (is_scaled(c)) return 0;
+    if (is_scaled(c) || is_split(c)) return 0;
     const int v = int(16 / c->elem);
     return c->g.n[0] % v == 0 ? v : 0;
 }
@@ -207,6 +229,12 @@ void default_tune(sl_ctx* c, int m)
     // other records: one thread per cell (64-byte 5D records measured ahead of
     // lane groups)
     t.ft = c->rec ? int(c->nfib) : is_scaled(c) ? scaled_default_ft(c) : 1;
+    if (is_split(c)) {   // one fibre per thread; no vector form
+        t.block = m == 0 ? 256 : 128;
+        t.unroll = m == 0 ? 1 : 2;
+        t.chunk = m == 0 ? 0 : chunk_for(c, m, 1, 1);
+        return;
+    }
     if (m == 0) {
         t.block = c->rec ? 128 : 256;
         t.unroll = unit_vec_width(c) ? unit_vec_width(c) : 1;
@@ -261,6 +289,7 @@ SweepArgs make_args_parity(sl_ctx* c, int dim, int shift_dim, int parity)
     const auto& t = c->tune[dim];
     a.nfg = int(fibre_groups(c, t.ft));
     a.chunk = dim == 0 && !c->rec ? 0 : t.chunk;
+    a.cmap = c->d_cmap;
     return a;
 }
 
@@ -292,8 +321,13 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.ndim = c->ndim;
     L.rec = c->rec;
     L.occ = dim == 0 ? 0 : c->tune[dim].occ;
-    return is_scaled(c) ? launch_sweep_scaled(L) : c->mode == M_FP64 ? launch_sweep_f64(L)
-                                                                      : launch_sweep_f32(L);
+    if (is_scaled(c)) return launch_sweep_scaled(L);
+    switch (c->mode) {
+    case M_FP64: return launch_sweep_f64(L);
+    case M_F32: return launch_sweep_f32(L);
+    case M_F32ALL: return launch_sweep_f32all(L);
+    default: return launch_sweep_split(L);
+    }
 }
 
 // One sweep along dim using the shift table already built on the stream.
@@ -435,6 +469,8 @@ CodecArgs codec_of(const sl_ctx* c)
     a.ncoef = int(c->ncoef);
     a.mode = c->mode;
     a.rec = c->rec;
+    a.cmap = c->d_cmap;
+    if (is_split_family(c->mode)) a.p.hi = hi_block(c, c->cur);
     return a;
 }
 
@@ -526,7 +562,9 @@ sl_status sl_state_bytes(const sl_grid* grid, int degree, sl_storage storage, in
     if (!bytes) return fail(nullptr, SL_EINVAL, "bytes is NULL");
     int64_t cells = 1;
     for (int m = 0; m < grid->ndim; ++m) cells *= grid->n[m];
-    *bytes = state_bytes_of(cells, ipow(degree + 1, grid->ndim), storage);
+    int64_t nlo, nhi;
+    plane_counts(grid->ndim, degree, storage, &nlo, &nhi);
+    *bytes = state_bytes_of(cells, nlo, nhi, storage);
     return SL_OK;
 }
 
@@ -561,12 +599,32 @@ sl_status sl_ab_host(int degree, double alpha, double* A, double* B)
 
 // One copy of the state: bytes of the mean plane, the higher coefficients
 // (planes or cell records) and the scale plane (0 for the unscaled stores).
-static void copy_bytes(int64_t cells, int64_t ncoef, int rec, int elem, bool scaled, int64_t pstride,
+static void copy_bytes(int64_t cells, int64_t nlo, int64_t nhi, int rec, int elem, bool scaled, int64_t pstride,
                        size_t* mean, size_t* hi, size_t* scale)
 {
-    *mean = size_t(pstride) * 8;
-    *hi = rec ? size_t(cells) * size_t(rec) * size_t(elem) : size_t(pstride) * size_t(ncoef - 1) * size_t(elem);
+    *mean = size_t(pstride) * size_t(nlo) * 8;
+    *hi = rec ? size_t(cells) * size_t(rec) * size_t(elem) : size_t(pstride) * size_t(nhi) * size_t(elem);
     *scale = scaled ? size_t(pstride) * 4 : 0;
+}
+
+// Coefficient map of the stores of # double = q (sl::Planes): FP64 plane
+// -1 - e or FP32 plane e for every coefficient J, each block in increasing J.
+// The all-FP32 store (q = 0) maps J to FP32 plane J.
+static std::vector<int32_t> coefficient_map(int ndim, int O, int q)
+{
+    const int64_t nc = ipow(O, ndim);
+    std::vector<int32_t> map(size_t(nc), 0);
+    int32_t nlo = 0, nhi = 0;
+    for (int64_t J = 0; J < nc; ++J) {
+        bool lo = true;
+        int64_t r = J;
+        for (int m = 0; m < ndim; ++m) {
+            lo = lo && (r % O) < q;
+            r /= O;
+        }
+        map[size_t(J)] = lo ? -1 - nlo++ : nhi++;
+    }
+    return map;
 }
 
 static int record_slots_of(const sl_grid* grid, int degree, sl_storage storage, int64_t ncoef)
@@ -591,7 +649,7 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     const bool scaled = storage == SL_MIX_BF16 || storage == SL_MIX_FP16;
     if (planes)
         for (int q = 0; q < 6; ++q) {
-            const bool need = (q % 3) != 2 || scaled;
+            const bool need = (q % 3 == 0 && storage != SL_FP32) || q % 3 == 1 || scaled;
             if (need && !planes[q]) return fail(nullptr, SL_EINVAL, "plane pointer %d is NULL", q);
             if (planes[q] && reinterpret_cast<uintptr_t>(planes[q]) % 256 != 0)
                 return fail(nullptr, SL_EINVAL, "plane pointer %d is not 256-byte aligned", q);
@@ -616,7 +674,8 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     c->pstride = int64_t(align_up(size_t(c->cells), 64));
     c->elem = elem_size(storage);
     c->rec = record_slots_of(grid, degree, storage, c->ncoef);
-    c->state_bytes = state_bytes_of(c->cells, c->ncoef, storage);
+    plane_counts(c->ndim, degree, storage, &c->nlo, &c->nhi);
+    c->state_bytes = state_bytes_of(c->cells, c->nlo, c->nhi, storage);
     c->external = planes != nullptr;
     for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
     build_poly_table(degree, &c->poly);
@@ -627,7 +686,7 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     size_t off = 0;
     size_t o_state[2][3] = {{0, 0, 0}, {0, 0, 0}};
     size_t b_mean, b_hi, b_scale;
-    copy_bytes(c->cells, c->ncoef, c->rec, c->elem, scaled, c->pstride, &b_mean, &b_hi, &b_scale);
+    copy_bytes(c->cells, c->nlo, c->nhi, c->rec, c->elem, scaled, c->pstride, &b_mean, &b_hi, &b_scale);
     if (!planes)
         for (int b = 0; b < 2; ++b) {
             o_state[b][0] = off;
@@ -658,6 +717,9 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     off = align_up(off + size_t(c->mass_nblk) * 8, A);
     const size_t o_mass = off;
     off = align_up(off + 8, A);
+    const bool mapped = is_split_family(c->mode);
+    const size_t o_cmap = off;
+    if (mapped) off = align_up(off + size_t(c->ncoef) * 4, A);
     c->mem_bytes = off;
 
     cudaError_t e = cudaMalloc(&c->mem, c->mem_bytes);
@@ -676,7 +738,12 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
             c->planes[b].hi = base + o_state[b][1];
             c->planes[b].scale = scaled ? reinterpret_cast<float*>(base + o_state[b][2]) : nullptr;
         }
+        if (c->mode == M_F32ALL) {   // see sl::Planes
+            c->planes[b].mean = nullptr;
+            c->planes[b].hi = static_cast<float*>(c->planes[b].hi) + c->pstride;
+        }
     }
+    if (mapped) c->d_cmap = reinterpret_cast<int32_t*>(base + o_cmap);
     c->d_sigma = reinterpret_cast<int32_t*>(base + o_sigma);
     c->d_alpha = reinterpret_cast<double*>(base + o_alpha);
     c->d_ab64 = reinterpret_cast<double*>(base + o_ab64);
@@ -694,6 +761,11 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     // an owned state starts at zero (the scale plane at zero decodes to zero
     // too); a caller's planes keep their contents
     e = cudaMemsetAsync(c->mem, 0, c->mem_bytes, c->st);
+    std::vector<int32_t> cmap;
+    if (mapped && e == cudaSuccess) {
+        cmap = coefficient_map(c->ndim, c->O, split_q(c->mode));
+        e = cudaMemcpyAsync(c->d_cmap, cmap.data(), cmap.size() * 4, cudaMemcpyHostToDevice, c->st);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
     if (e != cudaSuccess) {
         cudaFreeHost(c->h_mass);
@@ -727,8 +799,10 @@ sl_status sl_plane_layout(const sl_grid* grid, int degree, sl_storage storage, s
     const int64_t ncoef = ipow(degree + 1, grid->ndim);
     const int64_t pstride = int64_t(align_up(size_t(cells), 64));
     const int rec = record_slots_of(grid, degree, storage, ncoef);
+    int64_t nlo, nhi;
+    plane_counts(grid->ndim, degree, storage, &nlo, &nhi);
     size_t bm, bh, bs;
-    copy_bytes(cells, ncoef, rec, elem_size(storage), storage == SL_MIX_BF16 || storage == SL_MIX_FP16, pstride,
+    copy_bytes(cells, nlo, nhi, rec, elem_size(storage), storage == SL_MIX_BF16 || storage == SL_MIX_FP16, pstride,
                &bm, &bh, &bs);
     out->plane_stride = pstride;
     out->record_slots = rec;
@@ -841,7 +915,7 @@ static sl_status planes_args(sl_ctx* c, const void* mean, const void* hi, const 
 {
     if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
     const bool scaled = c->mode == M_BF16 || c->mode == M_FP16;
-    if (!mean || (c->ncoef > 1 && !hi)) return fail(c, SL_EINVAL, "NULL plane");
+    if ((c->nlo > 0 && !mean) || (c->nhi > 0 && !hi)) return fail(c, SL_EINVAL, "NULL plane");
     if (scaled && !scale) return fail(c, SL_EINVAL, "scaled store needs the scale plane");
     if (c->capturing) return fail(c, SL_EINVAL, "plane copies cannot be captured");
     return SL_OK;
@@ -852,13 +926,16 @@ sl_status sl_set_planes(sl_ctx* c, const double* mean, const void* hi, const flo
     sl_status s = planes_args(c, mean, hi, scale);
     if (s != SL_OK) return s;
     const Planes& p = c->planes[c->cur];
-    SL_CUDA(c, cudaMemcpyAsync(p.mean, mean, size_t(c->cells) * 8, cudaMemcpyHostToDevice, c->st));
+    void* hb = hi_block(c, c->cur);
+    if (c->nlo > 0)
+        SL_CUDA(c, cudaMemcpy2DAsync(p.mean, size_t(c->pstride) * 8, mean, size_t(c->cells) * 8,
+                                     size_t(c->cells) * 8, size_t(c->nlo), cudaMemcpyHostToDevice, c->st));
     if (c->rec)
-        SL_CUDA(c, cudaMemcpyAsync(p.hi, hi, size_t(c->cells) * c->rec * c->elem, cudaMemcpyHostToDevice,
+        SL_CUDA(c, cudaMemcpyAsync(hb, hi, size_t(c->cells) * c->rec * c->elem, cudaMemcpyHostToDevice,
                                    c->st));
-    else if (c->ncoef > 1)
-        SL_CUDA(c, cudaMemcpy2DAsync(p.hi, size_t(c->pstride) * c->elem, hi, size_t(c->cells) * c->elem,
-                                     size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
+    else if (c->nhi > 0)
+        SL_CUDA(c, cudaMemcpy2DAsync(hb, size_t(c->pstride) * c->elem, hi, size_t(c->cells) * c->elem,
+                                     size_t(c->cells) * c->elem, size_t(c->nhi),
                                      cudaMemcpyHostToDevice, c->st));
     if (p.scale)
         SL_CUDA(c, cudaMemcpyAsync(p.scale, scale, size_t(c->cells) * 4, cudaMemcpyHostToDevice, c->st));
@@ -870,13 +947,16 @@ sl_status sl_get_planes(sl_ctx* c, double* mean, void* hi, float* scale)
     sl_status s = planes_args(c, mean, hi, scale);
     if (s != SL_OK) return s;
     const Planes& p = c->planes[c->cur];
-    SL_CUDA(c, cudaMemcpyAsync(mean, p.mean, size_t(c->cells) * 8, cudaMemcpyDeviceToHost, c->st));
+    const void* hb = hi_block(c, c->cur);
+    if (c->nlo > 0)
+        SL_CUDA(c, cudaMemcpy2DAsync(mean, size_t(c->cells) * 8, p.mean, size_t(c->pstride) * 8,
+                                     size_t(c->cells) * 8, size_t(c->nlo), cudaMemcpyDeviceToHost, c->st));
     if (c->rec)
-        SL_CUDA(c, cudaMemcpyAsync(hi, p.hi, size_t(c->cells) * c->rec * c->elem, cudaMemcpyDeviceToHost,
+        SL_CUDA(c, cudaMemcpyAsync(hi, hb, size_t(c->cells) * c->rec * c->elem, cudaMemcpyDeviceToHost,
                                    c->st));
-    else if (c->ncoef > 1)
-        SL_CUDA(c, cudaMemcpy2DAsync(hi, size_t(c->cells) * c->elem, p.hi, size_t(c->pstride) * c->elem,
-                                     size_t(c->cells) * c->elem, size_t(c->ncoef - 1),
+    else if (c->nhi > 0)
+        SL_CUDA(c, cudaMemcpy2DAsync(hi, size_t(c->cells) * c->elem, hb, size_t(c->pstride) * c->elem,
+                                     size_t(c->cells) * c->elem, size_t(c->nhi),
                                      cudaMemcpyDeviceToHost, c->st));
     if (p.scale)
         SL_CUDA(c, cudaMemcpyAsync(scale, p.scale, size_t(c->cells) * 4, cudaMemcpyDeviceToHost, c->st));
@@ -1011,6 +1091,8 @@ static bool vp_dims(const sl_ctx* c, int* x, int* v)
 
 static sl_status vp_alloc(sl_ctx* c)
 {
+    if (c->mode == M_F32ALL)
+        return fail(c, SL_ENOTSUP, "the self-consistent field reads the FP64 mean plane, which SL_FP32 lacks");
     if (c->d_vp) return SL_OK;
     if (c->capturing) return fail(c, SL_EINVAL, "cannot allocate during a capture");
     const size_t nx = size_t(c->g.n[c->vp_x]);
@@ -1104,8 +1186,12 @@ sl_status sl_mass(sl_ctx* c, double* out)
     if (!out) return fail(c, SL_EINVAL, "out is NULL");
     double vol = 1.0;
     for (int m = 0; m < c->ndim; ++m) vol *= cell_width(c->g, m);
-    SL_CUDA(c, launch_mass(c->planes[c->cur].mean, uint32_t(c->cells), c->d_partials, c->mass_nblk,
-                           vol, c->d_mass, c->st));
+    if (c->mode == M_F32ALL)   // the mean is FP32 plane 0
+        SL_CUDA(c, launch_mass_f32(static_cast<const float*>(hi_block(c, c->cur)), uint32_t(c->cells),
+                                   c->d_partials, c->mass_nblk, vol, c->d_mass, c->st));
+    else
+        SL_CUDA(c, launch_mass(c->planes[c->cur].mean, uint32_t(c->cells), c->d_partials, c->mass_nblk,
+                               vol, c->d_mass, c->st));
     SL_CUDA(c, cudaMemcpyAsync(c->h_mass, c->d_mass, 8, cudaMemcpyDeviceToHost, c->st));
     SL_CUDA(c, cudaStreamSynchronize(c->st));
     *out = *c->h_mass;
@@ -1208,6 +1294,13 @@ static sl_status check_tune(sl_ctx* c, int dim, const sl_tune* t)
     const bool lanes = rec_lanes(c, t->fibres_per_thread);
     const int maxb = (dim == 0 && !c->rec) || lanes ? 256 : 128;
     if (t->reserved != 0) return fail(c, SL_EINVAL, "sl_tune.reserved must be 0");
+    if (is_split(c)) {
+        if (t->fibres_per_thread != 1) return fail(c, SL_EINVAL, "the # double = 2, 3 stores take one fibre per thread");
+        if (t->pipeline != 0 || t->max_blocks_per_sm != 0)
+            return fail(c, SL_EINVAL, "the # double = 2, 3 stores have no pipeline or block limit");
+        if (dim == 0 && t->unroll != 1) return fail(c, SL_EINVAL, "unroll along dimension 0 must be 1");
+        if (dim > 0 && t->unroll != 1 && t->unroll != 2) return fail(c, SL_EINVAL, "unroll must be 1 or 2");
+    }
     if (t->max_blocks_per_sm != 0) {
         if (t->max_blocks_per_sm < 4 || t->max_blocks_per_sm > 6)
             return fail(c, SL_EINVAL, "max_blocks_per_sm must be 0, 4, 5 or 6");
@@ -1334,6 +1427,12 @@ sl_status sl_autotune(sl_ctx* c, int reps)
                     cand.push_back({128, f, 1, m == 0 ? 0u : ch, 0});
                 }
             }
+        } else if (is_split(c)) {
+            if (m == 0)
+                for (int b : {128, 256}) cand.push_back({b, 1, 1, 0, 0});
+            else
+                for (int u : {1, 2})
+                    for (int b : {64, 128}) cand.push_back({b, 1, u, chunk_for(c, m, 1, 1), 0});
         } else if (m == 0) {
             {
                 for (int ft : {1, 2, 3, 4, 9})

@@ -73,14 +73,15 @@ __device__ __forceinline__ double block_sum(double v)
 // Fixed-shape reduction: the grid size depends only on the cell count, each
 // thread sums a fixed strided subset, warps reduce by shuffles, blocks write
 // partials, and one block sums the partials in a fixed order.
-__global__ void __launch_bounds__(kMassThreads) k_mass_partial(const double* __restrict__ mean,
+template <typename T>
+__global__ void __launch_bounds__(kMassThreads) k_mass_partial(const T* __restrict__ mean,
                                                                uint32_t cells,
                                                                double* __restrict__ partials)
 {
     double s = 0.0;
     for (uint32_t c = blockIdx.x * kMassThreads + threadIdx.x; c < cells;
          c += gridDim.x * kMassThreads)
-        s += mean[c];
+        s += double(mean[c]);
     s = block_sum(s);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -98,17 +99,47 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double* __res
 cudaError_t launch_mass(const double* mean, uint32_t cells, double* partials, int nblocks,
                         double vol, double* out, cudaStream_t st)
 {
-    k_mass_partial<<<nblocks, kMassThreads, 0, st>>>(mean, cells, partials);
+    k_mass_partial<double><<<nblocks, kMassThreads, 0, st>>>(mean, cells, partials);
+    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, vol, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_f32(const float* mean, uint32_t cells, double* partials, int nblocks,
+                            double vol, double* out, cudaStream_t st)
+{
+    k_mass_partial<float><<<nblocks, kMassThreads, 0, st>>>(mean, cells, partials);
     k_mass_final<<<1, kMassThreads, 0, st>>>(partials, nblocks, vol, out);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- codec
 
+// Coefficient J of a cell in the stores placed by the coefficient map (the
+// general split stores and the all-FP32 store): FP64 plane -1 - e or FP32
+// plane e of the map entry e, FP32 values rounded to nearest even.
+__device__ __forceinline__ void put_mapped(const CodecArgs& c, int J, uint32_t cell, double v)
+{
+    const int e = c.cmap[J];
+    if (e < 0)
+        c.p.mean[int64_t(-1 - e) * c.pstride + cell] = v;
+    else
+        static_cast<float*>(c.p.hi)[int64_t(e) * c.pstride + cell] = __double2float_rn(v);
+}
+__device__ __forceinline__ double get_mapped(const CodecArgs& c, int J, uint32_t cell)
+{
+    const int e = c.cmap[J];
+    if (e < 0) return c.p.mean[int64_t(-1 - e) * c.pstride + cell];
+    return double(static_cast<const float*>(c.p.hi)[int64_t(e) * c.pstride + cell]);
+}
+
 template <int MODE>
 __device__ void encode_cell(const CodecArgs& c, const double* v, uint32_t cell)
 {
     using T = typename St<MODE>::T;
+    if constexpr (MODE == M_SPLIT2) {
+        for (int J = 0; J < c.ncoef; ++J) put_mapped(c, J, cell, v[J]);
+        return;
+    }
     c.p.mean[cell] = v[0];
     if constexpr (MODE == M_FP64) {
         for (int J = 1; J < c.ncoef; ++J) *coef_ptr<T>(c, J, cell) = v[J];
@@ -135,6 +166,10 @@ template <int MODE>
 __device__ void decode_cell(const CodecArgs& c, uint32_t cell, double* out)
 {
     using T = typename St<MODE>::T;
+    if constexpr (MODE == M_SPLIT2) {
+        for (int J = 0; J < c.ncoef; ++J) out[J] = get_mapped(c, J, cell);
+        return;
+    }
     out[0] = c.p.mean[cell];
     double s = 1.0;
     if constexpr (St<MODE>::scaled) s = double(c.p.scale[cell]);
@@ -185,6 +220,9 @@ __global__ void k_gather(CodecArgs c, const int64_t* __restrict__ cells, uint32_
     case M_F32: { constexpr int MD = M_F32; CALL; } break;   \
     case M_BF16: { constexpr int MD = M_BF16; CALL; } break; \
     case M_FP16: { constexpr int MD = M_FP16; CALL; } break; \
+    case M_F32ALL:                                     \
+    case M_SPLIT2:                                     \
+    case M_SPLIT3: { constexpr int MD = M_SPLIT2; CALL; } break; \
     default: return cudaErrorInvalidValue;             \
     }
 
@@ -290,6 +328,10 @@ __global__ void k_project_cells(ProjectArgs pa, const double* __restrict__ w,
     for (int m = 0; m < pa.ndim; ++m) {
         im[m] = r % pa.n[m];
         r /= pa.n[m];
+    }
+    if constexpr (MODE == M_SPLIT2) {
+        for (int J = 0; J < c.ncoef; ++J) put_mapped(c, J, cell, project_coef(pa, w, tab, nmax, im, J));
+        return;
     }
     c.p.mean[cell] = project_coef(pa, w, tab, nmax, im, 0);
     if constexpr (!St<MODE>::scaled) {

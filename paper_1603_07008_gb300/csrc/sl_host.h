@@ -19,7 +19,9 @@ struct sl_ctx {
     cudaStream_t st = nullptr;
     int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
     int rec = 0;                // > 0: scaled store in cell records of rec 16-bit slots
-    size_t elem = 8;
+    size_t elem = 8;            // bytes of a low-precision (hi) element
+    int64_t nlo = 1, nhi = 0;   // FP64 planes (the mean's block) and hi planes of one copy
+    int32_t* d_cmap = nullptr;  // coefficient map of the stores that use one (see sl::Planes)
     int64_t state_bytes = 0;
 
     void* mem = nullptr;
@@ -90,6 +92,11 @@ sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what);
 cudaError_t vp_field(sl_ctx* c, double* E, double* energy);
 sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c);
 bool is_scaled(const sl_ctx* c);
+bool is_split(const sl_ctx* c);   // the general split stores (# double = 2, 3)
+// FP64 and hi planes per copy of (ndim, degree, storage).
+void plane_counts(int ndim, int degree, int storage, int64_t* nlo, int64_t* nhi);
+// Start of a copy's hi block (its first plane), whatever the kernels' convention.
+void* hi_block(const sl_ctx* c, int parity);
 int64_t fibre_groups(const sl_ctx* c, int ft);
 // lanes: threads per line (G of the lane-group record form, else 1)
 uint32_t chunk_for(const sl_ctx* c, int m, int ft, int lanes);

@@ -9,8 +9,23 @@
 
 namespace sl {
 
-// Storage modes, numerically equal to sl_storage.
-enum Mode : int { M_FP64 = 0, M_F32 = 1, M_BF16 = 2, M_FP16 = 3 };
+// Storage modes, numerically equal to sl_storage.  M_F32ALL keeps every
+// coefficient in FP32 ("# double" = 0 of Sec. III-A); M_SPLIT2 / M_SPLIT3 keep
+// the coefficients whose every per-dimension index is below 2 / 3 in FP64 and
+// the rest in FP32 ("# double" = 2, 3).
+enum Mode : int { M_FP64 = 0, M_F32 = 1, M_BF16 = 2, M_FP16 = 3, M_F32ALL = 4, M_SPLIT2 = 5, M_SPLIT3 = 6 };
+
+// FP64 indices per dimension ("# double") of a store of the split family
+// below (-1 for the other stores).
+__host__ __device__ constexpr int split_q(int mode)
+{
+    return mode == M_F32ALL ? 0 : mode == M_SPLIT2 ? 2 : mode == M_SPLIT3 ? 3 : -1;
+}
+// Stores whose coefficient planes are placed by a coefficient map (below).
+__host__ __device__ constexpr bool is_split_family(int mode)
+{
+    return mode == M_F32ALL || mode == M_SPLIT2 || mode == M_SPLIT3;
+}
 
 constexpr int kMaxDim = 6;
 constexpr int kMaxK = 3;
@@ -50,6 +65,13 @@ struct FastDiv {
 // One split copy of the state: FP64 mean plane, low-precision planes for the
 // other o^d - 1 coefficients (coefficient J >= 1 lives at hi + (J-1)*pstride),
 // and the per-cell FP32 scale plane of the scaled modes.
+// The general split stores (M_SPLIT2, M_SPLIT3) hold a block of FP64 planes at
+// `mean` (plane 0 is the cell mean) and a block of FP32 planes at `hi`, the
+// plane of coefficient J given by the coefficient map: map[J] = e >= 0 for FP32
+// plane e, map[J] = -1 - e for FP64 plane e.  The all-FP32 store (M_F32ALL)
+// has no FP64 plane (mean = nullptr); its o^d FP32 planes start one plane
+// before `hi`, so that coefficient J is at hi + (J-1)*pstride for every J >= 0
+// as in the mixed stores.
 struct Planes {
     double* mean;
     void* hi;
@@ -90,6 +112,7 @@ struct SweepArgs {
     int nfib;            // o^(d-1) fibres per cell
     int nfg;             // fibre groups (gridDim.y = nfg * nchunk for the strided kernel)
     uint32_t chunk;      // cells per thread along the line (strided kernel)
+    const int32_t* cmap; // coefficient map of the general split stores (see Planes)
 };
 
 // Coefficient plane pointer helpers.
@@ -123,6 +146,8 @@ struct SweepLaunch {
 
 cudaError_t launch_sweep_f64(const SweepLaunch& L);      // M_FP64
 cudaError_t launch_sweep_f32(const SweepLaunch& L);      // M_F32
+cudaError_t launch_sweep_f32all(const SweepLaunch& L);   // M_F32ALL
+cudaError_t launch_sweep_split(const SweepLaunch& L);    // M_SPLIT2, M_SPLIT3
 cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
 // Cell records of degree 1 in 5 or 6 dimensions with G = R/16 lanes per cell,
 // 16 slots (8 fibres) each (selected by fibres_per_thread == kRecLaneFt).
@@ -160,6 +185,9 @@ cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& sr
 
 cudaError_t launch_mass(const double* mean, uint32_t cells, double* partials, int nblocks,
                         double vol, double* out, cudaStream_t st);
+// The same reduction over an FP32 mean plane (the all-FP32 store).
+cudaError_t launch_mass_f32(const float* mean, uint32_t cells, double* partials, int nblocks,
+                            double vol, double* out, cudaStream_t st);
 int mass_blocks(uint32_t cells);
 
 struct CodecArgs {
@@ -168,6 +196,8 @@ struct CodecArgs {
     int ncoef;
     int mode;
     int rec;             // > 0: higher coefficients in cell records of rec slots (slot J = coefficient J)
+    const int32_t* cmap; // general split and all-FP32 stores: coefficient map, with p.hi the
+                         // start of the FP32 block (see Planes)
 };
 
 // Address of coefficient J >= 1 of a cell, planar or in records.

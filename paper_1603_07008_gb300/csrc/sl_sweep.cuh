@@ -23,7 +23,8 @@
 //
 // A thread's fibre group either contains the fibre of the cell mean (group 0)
 // or not; the two cases are separate instantiations of the kernel body, so
-// the mean's special handling costs nothing elsewhere.  The last group of a
+// the mean's special handling costs nothing elsewhere.  The all-FP32 store
+// (M_F32ALL) has no FP64 mean: every group is computed as an FP32 group.  The last group of a
 // cell may be partial; its missing fibres repeat the last valid one, whose
 // values are then computed and stored twice by the same thread.
 //
@@ -51,24 +52,45 @@ struct St<M_FP64> {
     using T = double;
     using R = double;
     static constexpr bool scaled = false;
+    static constexpr bool mean64 = true;   // the cell mean has its own FP64 plane
 };
 template <>
 struct St<M_F32> {
     using T = float;
     using R = float;
     static constexpr bool scaled = false;
+    static constexpr bool mean64 = true;
+};
+// every coefficient, the mean included, in FP32 planes with FP32 arithmetic
+template <>
+struct St<M_F32ALL> {
+    using T = float;
+    using R = float;
+    static constexpr bool scaled = false;
+    static constexpr bool mean64 = false;
+};
+// the general split stores, whose planes the coefficient map places (only
+// the codec instantiates this; their sweeps are in sl_sweep_split.cu)
+template <>
+struct St<M_SPLIT2> {
+    using T = float;
+    using R = float;
+    static constexpr bool scaled = false;
+    static constexpr bool mean64 = true;
 };
 template <>
 struct St<M_BF16> {
     using T = __nv_bfloat16;
     using R = float;
     static constexpr bool scaled = true;
+    static constexpr bool mean64 = true;
 };
 template <>
 struct St<M_FP16> {
     using T = __half;
     using R = float;
     static constexpr bool scaled = true;
+    static constexpr bool mean64 = true;
 };
 
 __device__ __forceinline__ double ld_raw(const double* p) { return __ldg(p); }
@@ -524,7 +546,7 @@ __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fb
     ib += ib < 0 ? int32_t(a.N) : 0;
     const uint32_t ca = c - i + uint32_t(ia);
     const uint32_t cb = c - i + uint32_t(ib);
-    if (St<MODE>::scaled || fbase == 0)
+    if (St<MODE>::scaled || (St<MODE>::mean64 && fbase == 0))
         unit_body<K, MODE, FT, true, CV>(a, c, ca, cb, cls, fbase);
     else
         unit_body<K, MODE, FT, false, CV>(a, c, ca, cb, cls, fbase);
@@ -694,7 +716,7 @@ __global__ void __launch_bounds__(256) k_sweep_unit_vec(const SweepArgs a)
     const uint32_t line = a.fdN.div(c0);
     const uint32_t i0 = c0 - line * a.N;
     const uint32_t cls = shift_class(a, 0, line);
-    if (fbase == 0)
+    if (St<MODE>::mean64 && fbase == 0)
         unit_vec_body<K, MODE, FT, true>(a, c0, i0, cls, fbase);
     else
         unit_vec_body<K, MODE, FT, false>(a, c0, i0, cls, fbase);
@@ -813,7 +835,7 @@ __device__ __forceinline__ void strided_body(const SweepArgs& a, const LineSetup
 template <int K, int MODE, int FT, int U>
 __device__ __forceinline__ void strided_line(const SweepArgs& a, const LineSetup& L)
 {
-    if (St<MODE>::scaled || L.fbase == 0)
+    if (St<MODE>::scaled || (St<MODE>::mean64 && L.fbase == 0))
         strided_body<K, MODE, FT, U, true>(a, L);
     else
         strided_body<K, MODE, FT, U, false>(a, L);
@@ -1371,7 +1393,7 @@ __global__ void __launch_bounds__(B) k_sweep_strided_async(const SweepArgs a)
     static_assert(!St<MODE>::scaled, "cp.async ring needs 4- or 8-byte elements");
     const LineSetup L = line_setup_grid(a, FT);
     if (!L.active) return;
-    if (L.fbase == 0)
+    if (St<MODE>::mean64 && L.fbase == 0)
         async_body<K, MODE, FT, P, B, true>(a, L);
     else
         async_body<K, MODE, FT, P, B, false>(a, L);

@@ -82,24 +82,26 @@ def test_state_bytes_model():
 
 def test_memory_reduction_matches_paper():
     """The paper's memorydown figures (Tables III-VI, Sec. III-A) follow from
-    the byte model: FP64 bytes over (8 + 4 (o^d - 1)) for c_0 in FP64."""
+    the byte model of every store: FP64 bytes over 8 n_lo + 4 n_hi, for
+    "# double" = 0, 1, 2 (c_0 .. c_{q-1} in FP64 in one dimension)."""
     rows = []
     for line in open(os.path.join(ROOT, "tests", "golden", "memory_reduction.txt")):
         if line.strip() and not line.startswith("#"):
             d, o, nd, red, _ = line.split()
             rows.append((int(d), int(o), int(nd), float(red)))
     checked = 0
+    store = {0: "fp32", 1: "mix_fp32", 2: "mix_fp32_d2", 3: "mix_fp32_d3"}
     for d, o, nd, red in rows:
         g = _grid((8,) * d)
         if nd == o ** d:
             continue   # all-FP64 reference row
-        assert nd == 1
-        r = S.sl_state_bytes(g, o - 1, "fp64") / S.sl_state_bytes(g, o - 1, "mix_fp32")
+        assert d == 1 or nd == 1
+        r = S.sl_state_bytes(g, o - 1, "fp64") / S.sl_state_bytes(g, o - 1, store[nd])
         digits = len(str(red).split(".")[1])
         # the paper truncates 2D (128/68 = 1.88) to 1.8; allow one unit in its last digit
         assert abs(r - red) <= 10 ** -digits * 1.0 + 1e-12, (d, o, r, red)
         checked += 1
-    assert checked == 5
+    assert checked == 10
 
 
 @pytest.mark.parametrize("bad,code", [

@@ -6,6 +6,7 @@ oracle in turn, and at least one pin of tests/test_oracle_pins.py must then
 fail; with none planted every pin used here passes.  CPU only."""
 from fractions import Fraction
 
+import numpy as np
 import pytest
 
 import oracle as O
@@ -78,3 +79,51 @@ def test_each_planted_mistake_fails_a_pin(m):
         failed = _failing_pins()
     assert failed, f"no pin catches mutation {m}: {MUTATIONS[m]}"
     assert O.lib().or_get_mutation() == 0
+
+
+# Planted mistakes in the host-side split-storage mask ("# double",
+# Sec. III-A): each replaces oracle.fp64_coefficients, and the pins of the
+# split stores must catch it.
+def _mask_from(test):
+    def mask(k, ndim, ndouble):
+        o = k + 1
+        m = np.zeros(o ** ndim, dtype=bool)
+        for J in range(o ** ndim):
+            digits = [(J // o ** d) % o for d in range(ndim)]
+            m[J] = test(digits, ndouble)
+        return m
+    return mask
+
+
+MASK_MUTATIONS = {
+    "index bound j_m <= q": _mask_from(lambda j, q: all(x <= q for x in j)),
+    "only dimension 0 tested": _mask_from(lambda j, q: j[0] < q),
+    "any index below q instead of every": _mask_from(lambda j, q: any(x < q for x in j)),
+    "sum of the indices below q": _mask_from(lambda j, q: sum(j) < q),
+}
+SPLIT_PINS = {
+    "memorydown": P.test_storage_bytes_reproduce_the_printed_memory_reductions,
+    "mask_structure": lambda: [P.test_fp64_coefficients_structure(k, d) for (k, d) in [(1, 1), (3, 1), (2, 2)]],
+    "round_storage": P.test_round_storage_and_stored_sweeps,
+}
+
+
+def test_split_pins_pass_and_the_unmutated_mask_is_the_reading():
+    for pin in SPLIT_PINS.values():
+        pin()
+    for k, d in [(1, 1), (2, 2), (3, 3)]:
+        for q in range(k + 2):
+            assert np.array_equal(_mask_from(lambda j, q: all(x < q for x in j))(k, d, q),
+                                  O.fp64_coefficients(k, d, q))
+
+
+@pytest.mark.parametrize("name", sorted(MASK_MUTATIONS))
+def test_each_planted_mask_mistake_fails_a_split_pin(name, monkeypatch):
+    monkeypatch.setattr(O, "fp64_coefficients", MASK_MUTATIONS[name])
+    failed = []
+    for pin_name, pin in SPLIT_PINS.items():
+        try:
+            pin()
+        except Exception:
+            failed.append(pin_name)
+    assert failed, f"no pin catches the mask mistake: {name}"

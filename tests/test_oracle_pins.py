@@ -10,6 +10,7 @@ of the projection (Sec. II-A), and a brute-force projection that never forms
 the update matrices.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -391,3 +392,66 @@ def test_linear_landau_damping_rate():
     assert abs(gamma + 0.1533) < 0.003, gamma
     omega = math.pi / np.mean(np.diff(t[peaks]))
     assert abs(omega - 1.4156) < 0.05, omega
+
+
+# ---------------------------------------------------------------- split storage ("# double", Sec. III-A)
+
+def _golden_memorydown():
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "memory_reduction.txt")):
+        if line.strip() and not line.startswith("#"):
+            d, o, nd, red, src = line.split()
+            rows.append((int(d), int(o), int(nd), float(red), src))
+    return rows
+
+
+def test_storage_bytes_reproduce_the_printed_memory_reductions():
+    """The memorydown columns of Tables III-VI (one dimension, "# double" =
+    0..o) and the 2D / 3D figures of Sec. III-A (c_0 only) follow from which
+    coefficients the oracle keeps in FP64."""
+    rows = _golden_memorydown()
+    for d, o, nd, red, src in rows:
+        q = o if nd == o ** d else nd
+        assert d == 1 or q in (1, o), src
+        r = O.storage_bytes(o - 1, d, o) / O.storage_bytes(o - 1, d, q)
+        digits = len(str(red).split(".")[1])
+        assert abs(r - red) <= 10 ** -digits + 1e-12, (d, o, nd, r, red, src)
+    assert len(rows) == 12
+
+
+@pytest.mark.parametrize("k,ndim", [(1, 1), (3, 1), (2, 2), (3, 3), (1, 6)])
+def test_fp64_coefficients_structure(k, ndim):
+    o = k + 1
+    for q in range(o + 1):
+        m = O.fp64_coefficients(k, ndim, q)
+        assert m.sum() == q ** ndim
+        # tensor structure: J is FP64 iff each of its digits is
+        one = np.arange(o) < q
+        full = one
+        for _ in range(ndim - 1):
+            full = np.logical_and.outer(one, full).reshape(-1)
+        assert np.array_equal(m, full)
+    assert not O.fp64_coefficients(k, ndim, 0).any()
+    assert np.flatnonzero(O.fp64_coefficients(k, ndim, 1)).tolist() == [0]
+    assert O.fp64_coefficients(k, ndim, o).all()
+
+
+def test_round_storage_and_stored_sweeps():
+    rng = np.random.default_rng(5)
+    n, k = (6, 5), 2
+    u = rng.standard_normal((30, 9))
+    assert np.array_equal(O.round_storage(u, k, 2, 3), u)
+    assert np.array_equal(O.round_storage(u, k, 2, 0), u.astype(np.float32).astype(np.float64))
+    r = O.round_storage(u, k, 2, 2)
+    assert np.array_equal(O.round_storage(r, k, 2, 2), r)
+    m = O.fp64_coefficients(k, 2, 2)
+    assert np.array_equal(r[:, m], u[:, m]) and not np.array_equal(r[:, ~m], u[:, ~m])
+    # with every coefficient in FP64 the stored sweeps are the plain sweeps
+    sw = [(0, 1, rng.uniform(-2, 2, n[1])), (1, -1, [0.37])]
+    plain = O.sweep(O.sweep(u, n, k, *sw[0]), n, k, *sw[1])
+    assert np.array_equal(O.stored_sweeps(u, n, k, 3, sw), plain)
+    # an integer shift moves the stored values unchanged
+    for q in (0, 1, 2):
+        got = O.stored_sweeps(u, n, k, q, [(1, -1, [2.0])])
+        want = np.roll(O.round_storage(u, k, 2, q).reshape(5, 6, 9), 2, axis=0).reshape(30, 9)
+        assert np.array_equal(got, want)
