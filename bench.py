@@ -64,6 +64,7 @@ def parse_args(argv=None):
                          "instead of the autotuner, or 'default' for the library's defaults "
                          "(e.g. to profile one fixed kernel)")
     ap.add_argument("--nprob", type=int, default=256, help="problems of the batched workload")
+    ap.add_argument("--order", type=int, default=None, help="paper1d: only the rows of this order (2 or 4)")
     return ap.parse_args(argv)
 
 
@@ -526,11 +527,16 @@ def run_paper1d(args):
     shift = 0.37
     rows, fp64_rate = [], {}
     clk_all = None
-    for k, store in PAPER1D_ROWS:
+    # --storage: that store's rows only (e.g. to profile one kernel)
+    todo = [r for r in PAPER1D_ROWS if args.storage in (None, r[1]) and args.order in (None, r[0] + 1)]
+    if not todo:
+        raise SystemExit(f"no paper1d row with store {args.storage!r}")
+    head = head_launch = None
+    for k, store in todo:
         ctx = S.Context(g, k, store, stream=stream)
         # 1 + cos(2 pi 8 x + 0.3): the oscillatory profile of Table II
         ctx.project(k + 2, [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]])
-        ctx.autotune(3)
+        apply_shapes(ctx, args.shapes)
         m0 = ctx.mass()
         for _ in range(args.warmup):
             ctx.advect(0, -1, [shift])
@@ -562,14 +568,14 @@ def run_paper1d(args):
         rate = units / (ms_max / 1000.0)
         if store == "fp64":
             fp64_rate[k] = (rate, info["state_bytes"])
-        r64, b64 = fp64_rate[k]
+        r64, b64 = fp64_rate.get(k, (None, None))
         rows.append({"order": k + 1, "store": store,
                      "n_double": k + 1 if store == "fp64" else PAPER1D_NDOUBLE[store],
                      "sweep_gbs": gbs, "frac_of_hbm": gbs / peak_gbs, "sweep_ms": sweep_ms,
-                     "dof_per_s": rate, "speedup_vs_fp64": rate / r64,
-                     "memorydown": b64 / info["state_bytes"], "mass_drift": drift,
+                     "dof_per_s": rate, "speedup_vs_fp64": rate / r64 if r64 else None,
+                     "memorydown": b64 / info["state_bytes"] if b64 else None, "mass_drift": drift,
                      "state_bytes": info["state_bytes"], "tune": tune, "clocks": clk})
-        if k == 3 and store == "mix_fp32":
+        if head is None or (k == 3 and store == "mix_fp32"):
             head = rows[-1]
             head_launch = (nl, sms, sbytes)
             clk_all = clk
@@ -579,10 +585,12 @@ def run_paper1d(args):
         out = {
             "metric": METRIC, "value": head["dof_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["sweep_ms"],
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32"}.get(head["store"], "f32+f64"),
             "data": "synthetic",
-            "config": {"workload": f"1d_n{n}_k3_mix_fp32_advect_cfl0.37 (with every store of orders 2, 4)",
-                       "dof": n * 4, "sweeps_per_step": 1, "state_bytes": head["state_bytes"],
+            "config": {"workload": f"1d_n{n}_k{head['order'] - 1}_{head['store']}_advect_cfl0.37"
+                                   + (" (with every store of orders 2, 4)" if len(todo) > 1 else ""),
+                       "dof": n * head["order"], "sweeps_per_step": 1, "state_bytes": head["state_bytes"],
                        "l2": f"state {head['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "mass_drift": head["mass_drift"],
@@ -594,7 +602,7 @@ def run_paper1d(args):
             "table": rows,
             "speedup_mixed_vs_fp64": head["speedup_vs_fp64"],
             "e2e": None,
-            "gpu_launches": args.steps * 2 * len(PAPER1D_ROWS),
+            "gpu_launches": args.steps * 2 * len(todo),
             "clocks": clk_all,
             "cpu_baseline": None,
         }
