@@ -33,6 +33,9 @@ Functions and the paper passages they follow:
                                 Sec. II in 1+1 dimensions (reading: d_x E =
                                 rho - rho_bar, rho = int f dv) and the split
                                 step that recomputes it before every v-sweep
+  sweep_nodal,               -- x-sweep with the velocity at the Gauss nodes of
+  bruteforce_nodal              every v-cell (reading of v d_x f with v varying
+                                inside a v-cell), and the same without A, B
   fp64_coefficients,         -- which coefficients a store of "# double" = q
   storage_bytes,                keeps in FP64 (Sec. III-A, Tables II-VI;
   round_storage,                reading for d > 1: every index j_m < q), its
@@ -92,6 +95,13 @@ def lib():
             L.or_bruteforce_sweep.restype = ctypes.c_int
             L.or_bruteforce_sweep.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+            L.or_sweep_nodal.restype = ctypes.c_int
+            L.or_sweep_nodal.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp]
+            L.or_bruteforce_nodal.restype = ctypes.c_int
+            L.or_bruteforce_nodal.argtypes = [ctypes.c_int, _i64p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              _dp, _dp]
             L.or_project.restype = ctypes.c_int
             L.or_project.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, ctypes.c_int,
                                      ctypes.c_int, _dp, _dp, _i64p, ctypes.c_int64, _dp]
@@ -200,6 +210,37 @@ def bruteforce_sweep(u: np.ndarray, n: Sequence[int], k: int, dim: int, shift_di
     return out
 
 
+def _nodal_args(grid, dim: int, tau: float):
+    vdim = grid.pair[dim]
+    if vdim < 0:
+        raise ValueError(f"dimension {dim} has no paired v-dimension")
+    h = [(grid.hi[m] - grid.lo[m]) / grid.n[m] for m in range(len(grid.n))]
+    return vdim, float(grid.lo[vdim]), h[vdim], float(tau) / h[dim]
+
+
+def sweep_nodal(u: np.ndarray, grid, k: int, dim: int, tau: float) -> np.ndarray:
+    """x-sweep along `dim` over time tau with the velocity of the paired
+    v-dimension taken at the o Gauss-Legendre nodes of every v-cell (see
+    or_sweep_nodal)."""
+    n_ = _i64(grid.n)
+    u_ = _f64(u)
+    vdim, vlo, hv, toh = _nodal_args(grid, dim, tau)
+    out = np.empty_like(u_)
+    _check(lib().or_sweep_nodal(len(n_), _p(n_, _i64p), k, dim, vdim, vlo, hv, toh, _p(u_), _p(out)),
+           "sweep_nodal")
+    return out
+
+
+def bruteforce_nodal(u: np.ndarray, grid, k: int, dim: int, tau: float, nq: int = 12) -> np.ndarray:
+    n_ = _i64(grid.n)
+    u_ = _f64(u)
+    vdim, vlo, hv, toh = _nodal_args(grid, dim, tau)
+    out = np.empty_like(u_)
+    _check(lib().or_bruteforce_nodal(len(n_), _p(n_, _i64p), k, dim, vdim, vlo, hv, toh, nq, _p(u_),
+                                     _p(out)), "bruteforce_nodal")
+    return out
+
+
 def project(grid, k: int, nq: int, weights, params) -> np.ndarray:
     """Coefficients of all cells, eq. (cj), of u0 = sum_t w_t prod_m g_{t,m}."""
     return project_cells(grid, k, nq, weights, params, None)
@@ -286,12 +327,26 @@ def schedule(grid, splitting: str, dt: float, fields) -> List[Tuple[int, int, np
     return out
 
 
-def step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, fields) -> np.ndarray:
+def step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, fields,
+         nodal_v: bool = False) -> np.ndarray:
+    """nsteps split steps; nodal_v: the x-sweeps take the velocity at the
+    Gauss nodes of every v-cell (sweep_nodal) instead of its centre."""
     sched = schedule(grid, splitting, dt, fields)
+    taus = _plan_taus(grid, splitting, dt)
     for _ in range(nsteps):
-        for dim, sd, s in sched:
-            u = sweep(u, grid.n, k, dim, sd, s)
+        for (dim, sd, s), tau in zip(sched, taus):
+            if nodal_v and grid.pair[dim] >= 0:
+                u = sweep_nodal(u, grid, k, dim, tau)
+            else:
+                u = sweep(u, grid.n, k, dim, sd, s)
     return u
+
+
+def _plan_taus(grid, splitting: str, dt: float) -> List[float]:
+    xd = [m for m in range(len(grid.n)) if grid.pair[m] >= 0]
+    if splitting == "strang":
+        return [0.5 * dt] * len(xd) + [dt] * len(xd) + [0.5 * dt] * len(xd)
+    return [dt] * (2 * len(xd))
 
 
 # --------------------------------------------------------------------------

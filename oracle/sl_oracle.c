@@ -328,6 +328,164 @@ int or_bruteforce_sweep(int ndim, const int64_t* n, int k, int dim, int shift_di
 }
 
 /* ------------------------------------------------------------------ */
+/* Nodal-in-velocity x-sweep                                           */
+/* ------------------------------------------------------------------ */
+
+/* The x-sweep along `dim` with the velocity taken at the o Gauss-Legendre
+ * nodes eta_q of every cell of the paired v-dimension `vdim`, instead of one
+ * velocity per v-cell (reading of the multi-dimensional term v d_x f, whose
+ * velocity varies inside a v-cell).  For every target cell and every fibre of
+ * coefficients that varies in (j_dim, j_vdim) only:
+ *   1. values at the nodes: U_q(l) = sum_jv c_{l,jv} P_jv(eta_q);
+ *   2. the update rule of Sec. II-A at node q, with the shift in cells
+ *      s_{j,q} = (vlo + (j + 1/2 + eta_q / 2) hv) * tau_over_h, j the v-cell;
+ *   3. back to coefficients with the o-point Gauss rule (eq. (cj) along v):
+ *      c'_{jx,jv} = (2 jv + 1) / 2 * sum_q w_q P_jv(eta_q) U'_q(jx).
+ * Same layout as or_sweep.  Returns 0, or -1 for bad arguments. */
+static double node_shift(double vlo, double hv, double tau_over_h, int64_t j, double eta)
+{
+    const double half = or_mutation == 20 ? 1.0 : 0.5;      /* MUTATION 20 */
+    return (vlo + ((double)j + 0.5 + half * eta) * hv) * tau_over_h;
+}
+
+int or_sweep_nodal(int ndim, const int64_t* n, int k, int dim, int vdim, double vlo, double hv,
+                   double tau_over_h, const double* u, double* out)
+{
+    if (check_grid(ndim, n, k)) return -1;
+    if (ndim < 2 || dim < 0 || dim >= ndim || vdim < 0 || vdim >= ndim || vdim == dim) return -1;
+    if (!isfinite(vlo) || !isfinite(hv) || !isfinite(tau_over_h) || !(hv > 0.0)) return -1;
+    const int o = k + 1;
+    const int64_t ncoef = ipow(o, ndim);
+    const int64_t ostride = ipow(o, dim), vstride = ipow(o, vdim);
+    int64_t cells = 1, cstride = 1;
+    for (int m = 0; m < ndim; ++m) cells *= n[m];
+    for (int m = 0; m < dim; ++m) cstride *= n[m];
+    double eta[OR_MAXK + 1], w[OR_MAXK + 1];
+    or_gauss_legendre(o, eta, w);
+
+    /* per (v-cell, node): sigma and the matrices */
+    const int64_t nclass = n[vdim] * o;
+    int64_t* sig = (int64_t*)malloc(sizeof(int64_t) * nclass);
+    double* AB = (double*)malloc(sizeof(double) * 2 * o * o * nclass);
+    if (!sig || !AB) { free(sig); free(AB); return -2; }
+    for (int64_t j = 0; j < n[vdim]; ++j)
+        for (int q = 0; q < o; ++q) {
+            const int64_t cls = j * o + q;
+            double alpha;
+            or_shift_split(node_shift(vlo, hv, tau_over_h, j, eta[q]), &sig[cls], &alpha);
+            or_ab_matrices(k, alpha, AB + 2 * o * o * cls, AB + 2 * o * o * cls + o * o);
+        }
+
+    int64_t idx[OR_MAXDIM];
+    for (int64_t c = 0; c < cells; ++c) {
+        cell_index(ndim, n, c, idx);
+        for (int64_t J = 0; J < ncoef; ++J) out[c * ncoef + J] = 0.0;
+        for (int q = 0; q < o; ++q) {
+            const int64_t cls = idx[vdim] * o + q;
+            const double* A = AB + 2 * o * o * cls;
+            const double* B = A + o * o;
+            const int64_t ia = pmod(idx[dim] - sig[cls], n[dim]);
+            const int64_t ib = pmod(ia - 1, n[dim]);
+            const int64_t ca = c + (ia - idx[dim]) * cstride;
+            const int64_t cb = c + (ib - idx[dim]) * cstride;
+            const int qe = or_mutation == 22 ? o - 1 - q : q;     /* MUTATION 22 */
+            for (int64_t base = 0; base < ncoef; ++base) {
+                if ((base / ostride) % o != 0 || (base / vstride) % o != 0) continue;
+                double Ua[OR_MAXK + 1], Ub[OR_MAXK + 1];
+                for (int l = 0; l < o; ++l) {
+                    Ua[l] = 0.0;
+                    Ub[l] = 0.0;
+                    for (int jv = 0; jv < o; ++jv) {
+                        const double p = or_legendre(jv, eta[qe]);
+                        Ua[l] += u[ca * ncoef + base + l * ostride + jv * vstride] * p;
+                        Ub[l] += u[cb * ncoef + base + l * ostride + jv * vstride] * p;
+                    }
+                }
+                for (int jx = 0; jx < o; ++jx) {
+                    double up = 0.0;
+                    for (int l = 0; l < o; ++l) up += A[jx * o + l] * Ua[l] + B[jx * o + l] * Ub[l];
+                    for (int jv = 0; jv < o; ++jv) {
+                        const double norm = or_mutation == 21 ? (2.0 * jv + 1.0) : 0.5 * (2.0 * jv + 1.0);   /* MUTATION 21 */
+                        out[c * ncoef + base + jx * ostride + jv * vstride] +=
+                            norm * w[q] * or_legendre(jv, eta[q]) * up;
+                    }
+                }
+            }
+        }
+    }
+    free(sig);
+    free(AB);
+    return 0;
+}
+
+/* The same sweep without A or B: at each node the translated piecewise
+ * polynomial in x (values U_q of step 1) is projected onto P_jx by an
+ * nq-point Gauss rule on each side of the source-cell boundary, as in
+ * or_bruteforce_sweep; steps 1 and 3 as in or_sweep_nodal. */
+int or_bruteforce_nodal(int ndim, const int64_t* n, int k, int dim, int vdim, double vlo, double hv,
+                        double tau_over_h, int nq, const double* u, double* out)
+{
+    if (check_grid(ndim, n, k)) return -1;
+    if (ndim < 2 || dim < 0 || dim >= ndim || vdim < 0 || vdim >= ndim || vdim == dim) return -1;
+    if (nq < 1 || nq > OR_MAXQ || !(hv > 0.0)) return -1;
+    const int o = k + 1;
+    const int64_t ncoef = ipow(o, ndim);
+    const int64_t ostride = ipow(o, dim), vstride = ipow(o, vdim);
+    int64_t cells = 1, cstride = 1;
+    for (int m = 0; m < ndim; ++m) cells *= n[m];
+    for (int m = 0; m < dim; ++m) cstride *= n[m];
+    const int64_t N = n[dim];
+    double eta[OR_MAXK + 1], w[OR_MAXK + 1], t[OR_MAXQ], tw[OR_MAXQ];
+    or_gauss_legendre(o, eta, w);
+    or_gauss_legendre(nq, t, tw);
+
+    int64_t idx[OR_MAXDIM];
+    for (int64_t c = 0; c < cells; ++c) {
+        cell_index(ndim, n, c, idx);
+        for (int64_t J = 0; J < ncoef; ++J) out[c * ncoef + J] = 0.0;
+        for (int q = 0; q < o; ++q) {
+            const double s = (vlo + ((double)idx[vdim] + 0.5 + 0.5 * eta[q]) * hv) * tau_over_h;
+            const double y0 = (double)idx[dim] - s;
+            const double yb = floor(y0 + 1.0);
+            double xib = 2.0 * (yb - y0) - 1.0;
+            if (xib > 1.0) xib = 1.0;
+            if (xib < -1.0) xib = -1.0;
+            for (int64_t base = 0; base < ncoef; ++base) {
+                if ((base / ostride) % o != 0 || (base / vstride) % o != 0) continue;
+                for (int jx = 0; jx < o; ++jx) {
+                    double acc = 0.0;
+                    for (int part = 0; part < 2; ++part) {
+                        const double a = part == 0 ? -1.0 : xib;
+                        const double b = part == 0 ? xib : 1.0;
+                        const double half = 0.5 * (b - a);
+                        if (half <= 0.0) continue;
+                        for (int r = 0; r < nq; ++r) {
+                            const double xi = half * t[r] + 0.5 * (a + b);
+                            const double y = y0 + 0.5 * (xi + 1.0);
+                            const double fy = floor(y);
+                            const int64_t src = pmod((int64_t)fy, N);
+                            const double xs = 2.0 * (y - fy) - 1.0;
+                            const int64_t cs = c + (src - idx[dim]) * cstride;
+                            double val = 0.0;
+                            for (int l = 0; l < o; ++l)
+                                for (int jv = 0; jv < o; ++jv)
+                                    val += u[cs * ncoef + base + l * ostride + jv * vstride] *
+                                           or_legendre(l, xs) * or_legendre(jv, eta[q]);
+                            acc += half * tw[r] * val * or_legendre(jx, xi);
+                        }
+                    }
+                    const double up = 0.5 * (2.0 * jx + 1.0) * acc;
+                    for (int jv = 0; jv < o; ++jv)
+                        out[c * ncoef + base + jx * ostride + jv * vstride] +=
+                            0.5 * (2.0 * jv + 1.0) * w[q] * or_legendre(jv, eta[q]) * up;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
 /* Initial projection, eq. (cj)                                        */
 /* ------------------------------------------------------------------ */
 

@@ -33,6 +33,9 @@ PINS = {
     "projection_quadrature": P.test_projection_matches_adaptive_quadrature,
     "maxwellian_mass": P.test_mass_of_maxwellian_workload_closed_form,
     "sample_after": P.test_sample_after_matches_full_grid,
+    "nodal_bruteforce": lambda: P.test_nodal_sweep_agrees_with_bruteforce((5, 4), 1),
+    "nodal_round_trip_mass": P.test_nodal_round_trip_and_mass,
+    "nodal_free_streaming": lambda: P.test_nodal_sweep_converges_to_free_streaming(1),
 }
 
 MUTATIONS = {
@@ -55,6 +58,9 @@ MUTATIONS = {
     17: "brute-force sweep puts the break point one half cell off",
     18: "per-cell update swaps its source cells",
     19: "shift split keeps alpha = 1 instead of moving to the next cell",
+    20: "nodal sweep: node velocity at eta instead of eta / 2 from the v-cell centre",
+    21: "nodal sweep: back-transform without the 1/2 of (2 jv + 1) / 2",
+    22: "nodal sweep: values taken at the mirrored node",
 }
 
 

@@ -455,3 +455,88 @@ def test_round_storage_and_stored_sweeps():
         got = O.stored_sweeps(u, n, k, q, [(1, -1, [2.0])])
         want = np.roll(O.round_storage(u, k, 2, q).reshape(5, 6, 9), 2, axis=0).reshape(30, 9)
         assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- nodal-in-velocity x-sweep
+
+def _xv(n, lo=(0.0, -1.0), hi=(1.0, 1.0)):
+    return W.Grid(n=tuple(n), lo=lo, hi=hi, pair=(1, -1))
+
+
+@pytest.mark.parametrize("n,k", [((5, 4), 1), ((6, 3), 2), ((4, 3), 3)])
+def test_nodal_sweep_agrees_with_bruteforce(n, k):
+    """Per node, the update rule equals translating the node's values and
+    projecting them back by quadrature (no A, B), for shifts of several cells
+    either way."""
+    rng = np.random.default_rng(11)
+    u = rng.standard_normal((n[0] * n[1], (k + 1) ** 2))
+    g = _xv(n, lo=(0.0, -3.0), hi=(1.0, 2.0))
+    for tau in (0.37, -0.91, 1.3):
+        a = O.sweep_nodal(u, g, k, 0, tau)
+        b = O.bruteforce_nodal(u, g, k, 0, tau)
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+
+
+def test_nodal_sweep_in_three_dimensions_acts_fibre_by_fibre():
+    """With a third, unpaired dimension the sweep acts on each of its
+    coefficient indices separately: a state that depends on that index only
+    through a factor gives the 2D result times the factor."""
+    rng = np.random.default_rng(12)
+    k, o = 1, 2
+    n2 = (4, 3)
+    u2 = rng.standard_normal((12, o * o))
+    f = rng.standard_normal((2, o))            # the third dimension: 2 cells, o coefficients
+    u3 = np.einsum("cj,dk->dckj", u2, f).reshape(2 * 12, o * o * o)   # J = j0 + o j1 + o^2 j2
+    g2 = _xv(n2)
+    g3 = W.Grid(n=(4, 3, 2), lo=(0.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), pair=(1, -1, -1))
+    a2 = O.sweep_nodal(u2, g2, k, 0, 0.41)
+    a3 = O.sweep_nodal(u3, g3, k, 0, 0.41)
+    want = np.einsum("cj,dk->dckj", a2, f).reshape(2 * 12, o * o * o)
+    assert np.max(np.abs(a3 - want)) <= 1e-14 * np.max(np.abs(want))
+
+
+def test_nodal_round_trip_and_mass():
+    """tau = 0: values at the o Gauss nodes and back reproduce every
+    polynomial of degree k in v (the o-point rule is exact to degree 2o - 1);
+    and the sweep conserves the mass (sum of cell means)."""
+    rng = np.random.default_rng(13)
+    for k in (1, 2, 3):
+        g = _xv((5, 4))
+        u = rng.standard_normal((20, (k + 1) ** 2))
+        assert np.max(np.abs(O.sweep_nodal(u, g, k, 0, 0.0) - u)) <= 1e-14 * np.max(np.abs(u))
+        a = O.sweep_nodal(u, g, k, 0, 0.73)
+        assert abs(O.mass(a, g, k) - O.mass(u, g, k)) <= 1e-14 * np.sum(np.abs(u[:, 0]))
+
+
+def _free_streaming_terms(T):
+    """f(x, v, T) = e^{-v^2} (1 + cos(2 pi (x - v T)) / 2), a sum of three
+    separable products: the exact solution of d_t f + v d_x f = 0."""
+    w = np.array([1.0, 0.5, 0.5])
+    p = np.array([[[0, 0, 0, 0], [1, 0, 0, 0]],
+                  [[0, 0, 2 * math.pi, 0], [1, 0, 2 * math.pi * T, 0]],
+                  [[0, 0, 2 * math.pi, -math.pi / 2], [1, 0, 2 * math.pi * T, -math.pi / 2]]], dtype=float)
+    return w, p
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_nodal_sweep_converges_to_free_streaming(k):
+    """Free streaming d_t f + v d_x f = 0 over T = 1/2 in 8 x-sweeps: the
+    nodal-in-v sweep converges at order k + 1 under refinement in x and v,
+    while one velocity per v-cell (the centre) stays first order."""
+    T, steps = 0.5, 8
+    errs, errc = [], []
+    for N in (16, 32):
+        g = _xv((N, N))
+        u0 = O.project(g, k, k + 3, *_free_streaming_terms(0.0))
+        ue = O.project(g, k, k + 3, *_free_streaming_terms(T))
+        un, uc = u0, u0
+        v = -1.0 + (np.arange(N) + 0.5) * (2.0 / N)
+        for _ in range(steps):
+            un = O.sweep_nodal(un, g, k, 0, T / steps)
+            uc = O.sweep(uc, g.n, k, 0, 1, v * (T / steps) * N)
+        errs.append(O.rel_l2(un, ue, k, 2))
+        errc.append(O.rel_l2(uc, ue, k, 2))
+    order = math.log2(errs[0] / errs[1])
+    assert order >= k + 0.8, (errs, order)
+    assert errs[1] < errc[1] / 10, (errs, errc)
+    assert math.log2(errc[0] / errc[1]) < 1.2
