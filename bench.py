@@ -169,22 +169,22 @@ def summarise_clocks(lines):
 # traffic is reported as null.
 TRAFFIC = {
     ("4d", "mix_fp32"): {
-        "ratio": (2 * 0.98515 + 2 * 1.00207 + 2 * 1.00708) / 6,
+        "ratio": (2 * 0.98532 + 2 * 1.00212 + 2 * 1.00721) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "1550dbf35d426332",
+        "sha256": "c25b789ce3578fbd",
         "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
-                   "1 fibres) against 3.482 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
+                   "1 fibres) against 3.483 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
     ("6d", "mix_bf16"): {
-        "ratio": (2 * 1.03766 + 7 * 1.03630) / 9,
+        "ratio": (2 * 1.03611 + 7 * 1.03695) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "113203572ce969a6",
-        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.805 / 4.799 GB per launch (dimensions 0, "
+        "sha256": "24af3214783b5368",
+        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.798 / 4.802 GB per launch (dimensions 0, "
                    "1) against 4.631 GB algorithmic (profiles/sweep_6d_n16_lane_records_bf16.md)"},
     ("batch", "mix_fp32"): {
-        "ratio": (2 * 0.95846 + 1.04159) / 3,
+        "ratio": (2 * 0.95830 + 1.04223) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
-        "sha256": "f1f558c2dbb9934a",
-        "capture": "64 problems, default shapes; 1.046 / 1.137 GB per launch (dimensions 0, 1) against "
+        "sha256": "2f4bcda6db02243b",
+        "capture": "64 problems, default shapes; 1.046 / 1.138 GB per launch (dimensions 0, 1) against "
                    "1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
 }
 

@@ -340,6 +340,26 @@ sl_status sl_set_poisson(sl_ctx* ctx, int enable);
 sl_status sl_get_field(sl_ctx* ctx, double* field);
 sl_status sl_field_energy(sl_ctx* ctx, double* energy);
 
+/* Nodal-in-velocity x-sweeps (NEXT to the sweep: in several dimensions the
+ * velocity of the x-advection v d_x f varies inside a v-cell).  enable = 1
+ * makes sl_step and sl_graph_capture sweep every x-dimension m with the
+ * velocity taken at the o Gauss-Legendre nodes eta_q of each cell of its v-
+ * dimension p = pair[m], instead of at the cell centre:
+ *   U_q(l)    = sum_jv c_{l,jv} P_jv(eta_q)                  (values at node q)
+ *   U'_q      = the update rule of Sec. II-A for U_q with the shift
+ *               (lo_p + (j + 1/2 + eta_q / 2) h_p) tau / h_m, j the v-cell
+ *   c'_{jx,jv} = (2 jv + 1) / 2 sum_q w_q P_jv(eta_q) U'_q(jx)  (eq. (cj) along v)
+ * for every fibre of coefficients varying in (j_m, j_p).  The mean stays
+ * conserved to FP64 rounding in the mixed store.  Stores SL_FP64 and
+ * SL_MIX_FP32 (SL_ENOTSUP otherwise).  Allocates the node velocities and
+ * tables on first use (not during a capture).  Errors: SL_EINVAL (no x-
+ * dimension with a pair), SL_ENOTSUP, SL_ENOMEM. */
+sl_status sl_set_nodal_velocity(sl_ctx* ctx, int enable);
+/* One nodal-in-velocity x-sweep along the x-dimension dim over time tau
+ * (shifts v tau / h_dim at the nodes, as above).  Errors: SL_EINVAL (dim not an
+ * x-dimension), SL_ENAN (tau not finite), as sl_set_nodal_velocity. */
+sl_status sl_advect_nodal(sl_ctx* ctx, int dim, double tau);
+
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later
  * sl_set_fields is not seen by the graph until it is captured again. */

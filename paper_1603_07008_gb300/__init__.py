@@ -34,6 +34,7 @@ __all__ = [
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
     "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
     "sl_field_energy", "sl_graph_capture_advect", "sl_create_external", "sl_plane_layout",
+    "sl_set_nodal_velocity", "sl_advect_nodal",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -168,6 +169,8 @@ def lib():
             "sl_batch_set_tune": (st, [_vp, ctypes.c_int, ctypes.POINTER(sl_tune)]),
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
+            "sl_set_nodal_velocity": (st, [_vp, ctypes.c_int]),
+            "sl_advect_nodal": (st, [_vp, ctypes.c_int, ctypes.c_double]),
             "sl_create_external": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
             "sl_plane_layout": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int,
@@ -463,6 +466,14 @@ def sl_set_poisson(ctx, enable=True):
     _check(lib().sl_set_poisson(ctx, 1 if enable else 0), ctx)
 
 
+def sl_set_nodal_velocity(ctx, enable=True):
+    _check(lib().sl_set_nodal_velocity(ctx, 1 if enable else 0), ctx)
+
+
+def sl_advect_nodal(ctx, dim: int, tau: float):
+    _check(lib().sl_advect_nodal(ctx, int(dim), float(tau)), ctx)
+
+
 def sl_get_field(ctx, nx: int) -> np.ndarray:
     out = np.empty(int(nx), dtype=np.float64)
     _check(lib().sl_get_field(ctx, out.ctypes.data_as(_dp)), ctx)
@@ -575,6 +586,12 @@ class Context:
 
     def set_poisson(self, enable=True):
         sl_set_poisson(self.handle, enable)
+
+    def set_nodal_velocity(self, enable=True):
+        sl_set_nodal_velocity(self.handle, enable)
+
+    def advect_nodal(self, dim, tau):
+        sl_advect_nodal(self.handle, dim, tau)
 
     def field(self):
         nx = [n for n, pr in zip(self.grid.n, self.grid.pair) if pr >= 0][0]

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "sl_host.h"
+#include "sl_nodal.h"
 
 using namespace sl;
 using namespace sl::host;
@@ -330,8 +331,42 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     }
 }
 
+// The nodal-in-velocity x-sweep along dim from the current copy, with the
+// node table already built on the stream.
+cudaError_t launch_nodal_only(sl_ctx* c, int dim)
+{
+    const int p = c->g.pair[dim];
+    NodalArgs a{};
+    a.src = c->planes[c->cur];
+    a.dst = c->planes[c->cur ^ 1];
+    a.tab.sigma = c->d_nsig;
+    a.tab.alpha = c->d_nalpha;
+    a.tab.ab64 = c->d_nab64;
+    a.tab.ab32 = c->d_nab32;
+    a.cells = uint32_t(c->cells);
+    a.N = uint32_t(c->g.n[dim]);
+    a.NV = uint32_t(c->g.n[p]);
+    int64_t ix = 1, iv = 1;
+    for (int q = 0; q < dim; ++q) ix *= c->g.n[q];
+    for (int q = 0; q < p; ++q) iv *= c->g.n[q];
+    a.inner_x = uint32_t(ix);
+    a.fdInnerX.set(uint32_t(ix));
+    a.fdNX.set(a.N);
+    a.fdInnerV.set(uint32_t(iv));
+    a.fdNV.set(a.NV);
+    a.pstride = c->pstride;
+    a.ostride = int(ipow(c->O, dim));
+    a.vstride = int(ipow(c->O, p));
+    a.ndim = c->ndim;
+    a.xdim = dim;
+    a.vdim = p;
+    double eta[kMaxO], w[kMaxO];
+    nodal_setup(c->K, eta, w, &a);
+    return launch_sweep_nodal(c->K, c->mode, a, int(ipow(c->O, c->ndim - 2)), c->st);
+}
+
 // One sweep along dim using the shift table already built on the stream.
-sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
+sl_status run_sweep(sl_ctx* c, int dim, int shift_dim, bool nodal = false)
 {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = c->prof && !c->capturing;
@@ -341,7 +376,7 @@ sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
         if (!e0 || !e1) return fail(c, SL_ECUDA, "cudaEventCreate failed");
         SL_CUDA(c, cudaEventRecord(e0, c->st));
     }
-    cudaError_t e = launch_only(c, dim, shift_dim);
+    cudaError_t e = nodal ? launch_nodal_only(c, dim) : launch_only(c, dim, shift_dim);
     if (e != cudaSuccess) return cuda_fail(c, e, "sweep kernel launch");
     if (prof) {
         SL_CUDA(c, cudaEventRecord(e1, c->st));
@@ -350,6 +385,22 @@ sl_status run_sweep(sl_ctx* c, int dim, int shift_dim)
         c->prof_launches++;
     }
     c->cur ^= 1;
+    return SL_OK;
+}
+
+// Node table of the x-sweep along dim over time tau: class j * o + q has
+// the velocity of node q of v-cell j.
+sl_status nodal_table(sl_ctx* c, int dim, double tau)
+{
+    const int p = c->g.pair[dim];
+    ShiftSource src{};
+    src.kind = 2;
+    src.data = static_cast<const double*>(c->d_nodal) + c->nodal_vel_off[dim];
+    src.tau = tau;
+    src.h = cell_width(c->g, dim);
+    cudaError_t e = launch_ab_build(c->K, int(c->g.n[p] * c->O), uint32_t(c->g.n[dim]), src, c->poly, c->d_nsig,
+                                    c->d_nalpha, c->d_nab64, c->d_nab32, c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "node table launch");
     return SL_OK;
 }
 
@@ -411,6 +462,13 @@ sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
             const double tau = ss.frac * dt;
             ShiftSource src{};
             int shift_dim, nclass;
+            if (c->g.pair[ss.dim] >= 0 && c->nodal) {
+                // x-sweep with the velocity at the Gauss nodes of every v-cell
+                sl_status r = nodal_table(c, ss.dim, tau);
+                if (r == SL_OK) r = run_sweep(c, ss.dim, -1, true);
+                if (r != SL_OK) return r;
+                continue;
+            }
             if (c->g.pair[ss.dim] >= 0) {
                 // x-sweep: velocity = cell centre of the paired v-dimension
                 const int p = c->g.pair[ss.dim];
@@ -826,6 +884,7 @@ void sl_destroy(sl_ctx* c)
     if (c->d_stage) cudaFree(c->d_stage);
     if (c->d_proj) cudaFree(c->d_proj);
     if (c->d_vp) cudaFree(c->d_vp);
+    if (c->d_nodal) cudaFree(c->d_nodal);
     if (c->d_gshifts) cudaFree(c->d_gshifts);
     if (c->h_mass) cudaFreeHost(c->h_mass);
     if (c->mem) cudaFree(c->mem);   // a caller's planes (sl_create_external) are not freed
@@ -1120,6 +1179,83 @@ sl_status sl_set_poisson(sl_ctx* c, int enable)
     if (s != SL_OK) return s;
     c->poisson = true;
     return SL_OK;
+}
+
+// Node velocities of every x-dimension and the node tables, allocated once.
+static sl_status nodal_alloc(sl_ctx* c)
+{
+    if (c->d_nodal) return SL_OK;
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot allocate during a capture");
+    if (c->mode != M_FP64 && c->mode != M_F32)
+        return fail(c, SL_ENOTSUP, "the nodal-in-velocity x-sweep takes the FP64 and mixed FP32 stores");
+    NodalArgs tmp{};
+    double eta[kMaxO], w[kMaxO];
+    nodal_setup(c->K, eta, w, &tmp);
+    std::vector<double> vel;
+    int maxcls = 1;
+    for (int m = 0; m < c->ndim; ++m) {
+        const int p = c->g.pair[m];
+        if (p < 0) continue;
+        c->nodal_vel_off[m] = int64_t(vel.size());
+        const double hv = cell_width(c->g, p);
+        for (int64_t j = 0; j < c->g.n[p]; ++j)
+            for (int q = 0; q < c->O; ++q) vel.push_back(c->g.lo[p] + (double(j) + 0.5 + 0.5 * eta[q]) * hv);
+        maxcls = std::max(maxcls, int(c->g.n[p] * c->O));
+    }
+    if (vel.empty()) return fail(c, SL_EINVAL, "the nodal-in-velocity x-sweep needs an x-dimension with a pair");
+    const size_t A = 256;
+    size_t off = align_up(vel.size() * 8, A);
+    const size_t o_sig = off;
+    off = align_up(off + size_t(maxcls) * 4, A);
+    const size_t o_alpha = off;
+    off = align_up(off + size_t(maxcls) * 8, A);
+    const size_t o_ab64 = off;
+    off = align_up(off + size_t(maxcls) * ab_stride64(c->O) * 8, A);
+    const size_t o_ab32 = off;
+    off = align_up(off + size_t(maxcls) * ab_stride32(c->O) * 4, A);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, off);
+    if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
+    e = cudaMemcpy(mem, vel.data(), vel.size() * 8, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(mem);
+        return cuda_fail(c, e, "node velocities");
+    }
+    char* b = static_cast<char*>(mem);
+    c->d_nodal = mem;
+    c->nodal_maxcls = maxcls;
+    c->d_nsig = reinterpret_cast<int32_t*>(b + o_sig);
+    c->d_nalpha = reinterpret_cast<double*>(b + o_alpha);
+    c->d_nab64 = reinterpret_cast<double*>(b + o_ab64);
+    c->d_nab32 = reinterpret_cast<float*>(b + o_ab32);
+    return SL_OK;
+}
+
+sl_status sl_set_nodal_velocity(sl_ctx* c, int enable)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (!enable) {
+        c->nodal = false;
+        return SL_OK;
+    }
+    if (c->ndim < 2) return fail(c, SL_EINVAL, "the nodal-in-velocity x-sweep needs an x-dimension with a pair");
+    sl_status s = nodal_alloc(c);
+    if (s != SL_OK) return s;
+    c->nodal = true;
+    return SL_OK;
+}
+
+sl_status sl_advect_nodal(sl_ctx* c, int dim, double tau)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (dim < 0 || dim >= c->ndim || c->g.pair[dim] < 0)
+        return fail(c, SL_EINVAL, "dim must be an x-dimension (pair[dim] >= 0)");
+    if (!std::isfinite(tau)) return fail(c, SL_ENAN, "tau is not finite");
+    sl_status s = nodal_alloc(c);
+    if (s != SL_OK) return s;
+    s = nodal_table(c, dim, tau);
+    if (s != SL_OK) return s;
+    return run_sweep(c, dim, -1, true);
 }
 
 sl_status sl_field_energy(sl_ctx* c, double* energy)

@@ -44,6 +44,15 @@ struct sl_ctx {
     bool poisson = false;
     int vp_x = -1, vp_v = -1;
     double* d_vp = nullptr;     // [chunks][n_x] partial sums, E scratch [n_x], energy [1]
+    // x-sweeps with the velocity at the Gauss nodes of every v-cell
+    bool nodal = false;
+    void* d_nodal = nullptr;    // node velocities per x-dimension, then the node tables
+    int64_t nodal_vel_off[SL_MAX_DIM] = {0};
+    int nodal_maxcls = 0;
+    int32_t* d_nsig = nullptr;
+    double* d_nalpha = nullptr;
+    double* d_nab64 = nullptr;
+    float* d_nab32 = nullptr;
     double* d_partials = nullptr;
     double* d_mass = nullptr;
     int mass_nblk = 1;

@@ -1,0 +1,407 @@
+// sl_nodal.cu -- the x-sweep with the velocity taken at the Gauss-Legendre
+// nodes of every v-cell ("nodal in v").
+//
+// In several dimensions the x-advection v d_x f (Sec. II, splitting) has a
+// velocity that varies inside a v-cell.  The plain sweep takes one velocity
+// per v-cell (its centre).  Here, for the x-dimension m paired with the
+// v-dimension p, the coefficients of a cell are evaluated at the o nodes
+// eta_q of the v-cell, U_q(l) = sum_jv c_{l,jv} P_jv(eta_q); each node is
+// swept along x with its own shift s_{j,q} = v(eta_q) tau / h_m (the update
+// rule of Sec. II-A), v(eta) = lo_p + (j + 1/2 + eta / 2) h_p; and the new
+// coefficients are the o-point Gauss rule of the new nodal values,
+// c'_{jx,jv} = (2 jv + 1) / 2 sum_q w_q P_jv(eta_q) U'_q(jx) (eq. (cj) along v).
+//
+// One thread per target cell and fibre of coefficients varying in (j_m, j_p)
+// (blockIdx.y), for any x-dimension: consecutive threads take consecutive
+// cells, so every plane access is coalesced; the source cells of a node are
+// the target's line shifted by sigma_q, and the nodes' source cells, equal
+// for most cells (the node shifts of one v-cell differ by h_p tau / h_m),
+// are loaded once per distinct sigma.
+//
+// Stores: FP64, and the mixed FP32 store.  In the mixed store the fibre of
+// the cell mean keeps everything that reaches the mean in FP64: the node
+// value of row 0, U_q(0) = c_{0,0} + sum_{jv>=1} c_{0,jv} P_jv(eta_q), row 0
+// of each node in the conservation form of the plain sweep (with the per-cell
+// FP32 sums G_q(c) = sum_{l>=1} fl32(A_0l U_q(l))), and c'_{0,0} =
+// sum_q w'_q U'_q(0), where the weights w'_q = w_q / 2 are rounded so that
+// they sum to exactly one.  The node values enter c'_{0,jv} (jv >= 1) as FP32
+// differences U'_q(0) - c'_{0,0} (the Gauss rule maps a constant to zero for
+// jv >= 1).  Everything else is FP32.
+#include "sl_sweep.cuh"
+#include "sl_nodal.h"
+
+#include <cmath>
+
+namespace sl {
+
+namespace {
+
+// Base coefficient index of 2D fibre g: its digits along the dimensions other
+// than x and v, in increasing dimension order.
+__device__ __forceinline__ int nodal_fibre_base(const NodalArgs& a, int g)
+{
+    int base = 0, stride = 1;
+    for (int m = 0; m < a.ndim; ++m) {
+        if (m != a.xdim && m != a.vdim) {
+            base += (g % a.O) * stride;
+            g /= a.O;
+        }
+        stride *= a.O;
+    }
+    return base;
+}
+
+template <typename T>
+__device__ __forceinline__ const T* coef_plane(const Planes& p, int64_t ps, int J)
+{
+    return static_cast<const T*>(p.hi) + int64_t(J - 1) * ps;
+}
+
+// FP64 store, or an FP32 fibre of the mixed store (no FP64 entry): the whole
+// computation in the store's type R.
+template <int K, typename R>
+__device__ __forceinline__ void nodal_plain(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0, uint32_t j,
+                                            int base)
+{
+    constexpr int O = K + 1;
+    const bool has_mean = sizeof(R) == 8 && base == 0;   // the FP64 store's J = 0 is the mean plane
+    R acc[O][O];
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) acc[x][v] = R(0);
+    R va[O][O], vb[O][O];
+    int32_t last = -1;
+    const int32_t N = int32_t(a.N);
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        const uint32_t cls = j * O + q;
+        const int32_t sig = __ldg(a.tab.sigma + cls);
+        if (sig != last) {
+            int32_t ia = int32_t(i) - sig;
+            ia += ia < 0 ? N : 0;
+            int32_t ib = ia - 1;
+            ib += ib < 0 ? N : 0;
+            const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+#pragma unroll
+            for (int l = 0; l < O; ++l)
+#pragma unroll
+                for (int v = 0; v < O; ++v) {
+                    const int J = base + l * a.ostride + v * a.vstride;
+                    if (has_mean && J == 0) {
+                        va[l][v] = R(__ldg(a.src.mean + ca));
+                        vb[l][v] = R(__ldg(a.src.mean + cb));
+                    } else {
+                        const R* p = coef_plane<R>(a.src, a.pstride, J);
+                        va[l][v] = __ldg(p + ca);
+                        vb[l][v] = __ldg(p + cb);
+                    }
+                }
+            last = sig;
+        }
+        R A[O][O], B[O][O];
+        if constexpr (sizeof(R) == 8) {
+            const double* m = a.tab.ab64 + size_t(cls) * ab_stride64(O);
+#pragma unroll
+            for (int x = 0; x < O; ++x)
+#pragma unroll
+                for (int l = 0; l < O; ++l) {
+                    A[x][l] = __ldg(m + x * O + l);
+                    B[x][l] = __ldg(m + O * O + x * O + l);
+                }
+        } else {
+            const float* m = a.tab.ab32 + size_t(cls) * ab_stride32(O);
+#pragma unroll
+            for (int x = 0; x < O; ++x)
+#pragma unroll
+                for (int l = 0; l < O; ++l) {
+                    A[x][l] = __ldg(m + x * O + l);
+                    B[x][l] = __ldg(m + O * O + x * O + l);
+                }
+        }
+        R ua[O], ub[O];
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            R sa = R(0), sb = R(0);
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                const R e = sizeof(R) == 8 ? R(a.eval64[q][v]) : R(a.eval32[q][v]);
+                sa = fma(va[l][v], e, sa);
+                sb = fma(vb[l][v], e, sb);
+            }
+            ua[l] = sa;
+            ub[l] = sb;
+        }
+        R up[O];
+        if constexpr (sizeof(R) == 8) {
+            // row 0 in the conservation form; the l = 0 term of the other
+            // rows from the difference of the sources
+            const double t = ub[0] - ua[0];
+            double r = fma(__ldg(a.tab.alpha + cls), t, ua[0]);
+#pragma unroll
+            for (int l = 1; l < O; ++l) r = fma(A[0][l], ua[l] - ub[l], r);
+            up[0] = r;
+#pragma unroll
+            for (int x = 1; x < O; ++x) {
+                double s = -A[x][0] * t;
+#pragma unroll
+                for (int l = 1; l < O; ++l) {
+                    s = fma(A[x][l], ua[l], s);
+                    s = fma(B[x][l], ub[l], s);
+                }
+                up[x] = s;
+            }
+        } else {
+#pragma unroll
+            for (int x = 0; x < O; ++x) {
+                R s = R(0);
+#pragma unroll
+                for (int l = 0; l < O; ++l) {
+                    s = fma(A[x][l], ua[l], s);
+                    s = fma(B[x][l], ub[l], s);
+                }
+                up[x] = s;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < O; ++x)
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                const R bw = sizeof(R) == 8 ? R(a.back64[v][q]) : R(a.back32[v][q]);
+                acc[x][v] = fma(bw, up[x], acc[x][v]);
+            }
+    }
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) {
+            const int J = base + x * a.ostride + v * a.vstride;
+            if (has_mean && J == 0)
+                a.dst.mean[c] = double(acc[x][v]);
+            else
+                static_cast<R*>(a.dst.hi)[int64_t(J - 1) * a.pstride + c] = acc[x][v];
+        }
+}
+
+// The fibre of the cell mean in the mixed store (see the file comment).
+template <int K>
+__device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
+                                                 uint32_t j)
+{
+    constexpr int O = K + 1;
+    float acc[O][O];   // rows jx >= 1
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) acc[x][v] = 0.0f;
+    double up0[O];
+    float va[O][O], vb[O][O];   // [l][jv], entry (0, 0) unused
+    double ma = 0.0, mb = 0.0;
+    int32_t last = -1;
+    const int32_t N = int32_t(a.N);
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        const uint32_t cls = j * O + q;
+        const int32_t sig = __ldg(a.tab.sigma + cls);
+        if (sig != last) {
+            int32_t ia = int32_t(i) - sig;
+            ia += ia < 0 ? N : 0;
+            int32_t ib = ia - 1;
+            ib += ib < 0 ? N : 0;
+            const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+            ma = __ldg(a.src.mean + ca);
+            mb = __ldg(a.src.mean + cb);
+#pragma unroll
+            for (int l = 0; l < O; ++l)
+#pragma unroll
+                for (int v = 0; v < O; ++v) {
+                    if (l == 0 && v == 0) continue;
+                    const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
+                    va[l][v] = __ldg(p + ca);
+                    vb[l][v] = __ldg(p + cb);
+                }
+            last = sig;
+        }
+        const float* m32 = a.tab.ab32 + size_t(cls) * ab_stride32(O);
+        float A[O][O], B[O][O];
+#pragma unroll
+        for (int x = 0; x < O; ++x)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                A[x][l] = __ldg(m32 + x * O + l);
+                B[x][l] = __ldg(m32 + O * O + x * O + l);
+            }
+        // node values: row 0 in FP64, the others in FP32
+        double ua0 = ma, ub0 = mb;
+#pragma unroll
+        for (int v = 1; v < O; ++v) {
+            ua0 = fma(f2d_fast(va[0][v]), a.eval64[q][v], ua0);
+            ub0 = fma(f2d_fast(vb[0][v]), a.eval64[q][v], ub0);
+        }
+        float ua[O], ub[O];
+#pragma unroll
+        for (int l = 1; l < O; ++l) {
+            float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                sa = fmaf(va[l][v], a.eval32[q][v], sa);
+                sb = fmaf(vb[l][v], a.eval32[q][v], sb);
+            }
+            ua[l] = sa;
+            ub[l] = sb;
+        }
+        // row 0: conservation form with the per-cell FP32 sums
+        float ga = 0.0f, gb = 0.0f;
+#pragma unroll
+        for (int l = 1; l < O; ++l) {
+            ga = fmaf(A[0][l], ua[l], ga);
+            gb = fmaf(A[0][l], ub[l], gb);
+        }
+        const double t = ub0 - ua0;
+        up0[q] = fma(__ldg(a.tab.alpha + cls), t, ua0) + (f2d_fast(ga) - f2d_fast(gb));
+        // rows jx >= 1 in FP32, the l = 0 term from fl32(ua0 - ub0)
+        const float dm = d2f_fast(t, true);
+#pragma unroll
+        for (int x = 1; x < O; ++x) {
+            float s = A[x][0] * dm;
+#pragma unroll
+            for (int l = 1; l < O; ++l) {
+                s = fmaf(A[x][l], ua[l], s);
+                s = fmaf(B[x][l], ub[l], s);
+            }
+#pragma unroll
+            for (int v = 0; v < O; ++v) acc[x][v] = fmaf(a.back32[v][q], s, acc[x][v]);
+        }
+    }
+    double m = 0.0;
+#pragma unroll
+    for (int q = 0; q < O; ++q) m = fma(a.wmean[q], up0[q], m);
+    a.dst.mean[c] = m;
+#pragma unroll
+    for (int v = 1; v < O; ++v) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < O; ++q) s = fmaf(a.back32[v][q], d2f_fast(up0[q] - m, false), s);
+        acc[0][v] = s;
+    }
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) {
+            if (x == 0 && v == 0) continue;
+            static_cast<float*>(a.dst.hi)[int64_t(x * a.ostride + v * a.vstride - 1) * a.pstride + c] = acc[x][v];
+        }
+}
+
+template <int K, int MODE>
+__global__ void __launch_bounds__(256) k_sweep_nodal(const NodalArgs a)
+{
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= a.cells) return;
+    const int base = nodal_fibre_base(a, int(blockIdx.y));
+    const uint32_t ox = a.fdInnerX.div(c);
+    const uint32_t i = ox - a.fdNX.div(ox) * a.N;        // coordinate along x
+    const uint32_t ov = a.fdInnerV.div(c);
+    const uint32_t j = ov - a.fdNV.div(ov) * a.NV;       // v-cell
+    const uint32_t line0 = c - i * a.inner_x;
+    if constexpr (MODE == M_FP64) {
+        nodal_plain<K, double>(a, c, i, line0, j, base);
+    } else {
+        if (base == 0)
+            nodal_mean_fibre<K>(a, c, i, line0, j);
+        else
+            nodal_plain<K, float>(a, c, i, line0, j, base);
+    }
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_o from
+// the Chebyshev-like start cos(pi (q + 3/4) / (o + 1/2)), ascending.
+void gauss_nodes(int o, double* eta, double* w)
+{
+    for (int q = 0; q < o; ++q) {
+        double x = std::cos(M_PI * (q + 0.75) / (o + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int n = 1; n < o; ++n) {
+                const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            if (o == 1) p1 = x, p0 = 1.0;
+            dp = o * (x * p1 - p0) / (x * x - 1.0);
+            const double dx = p1 / dp;
+            x -= dx;
+            if (std::fabs(dx) < 1e-17) break;
+        }
+        eta[o - 1 - q] = x;
+        w[o - 1 - q] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+}
+
+double legendre_host(int j, double x)
+{
+    double p0 = 1.0, p1 = x;
+    if (j == 0) return 1.0;
+    for (int n = 1; n < j; ++n) {
+        const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+        p0 = p1;
+        p1 = p2;
+    }
+    return p1;
+}
+
+}  // namespace
+
+void nodal_setup(int K, double* eta, double* weights, NodalArgs* a)
+{
+    const int o = K + 1;
+    gauss_nodes(o, eta, weights);
+    a->O = o;
+    for (int q = 0; q < o; ++q)
+        for (int v = 0; v < o; ++v) {
+            const double p = legendre_host(v, eta[q]);
+            a->eval64[q][v] = p;
+            a->eval32[q][v] = float(p);
+            const double b = 0.5 * (2.0 * v + 1.0) * weights[q] * p;
+            a->back64[v][q] = b;
+            a->back32[v][q] = float(b);
+        }
+    // w'_q = w_q / 2 on the grid of 2^-52, the last one completing the sum to
+    // exactly 1 (every partial sum is a multiple of 2^-52 below 2, so exact)
+    double sum = 0.0;
+    for (int q = 0; q + 1 < o; ++q) {
+        a->wmean[q] = std::ldexp(std::nearbyint(std::ldexp(0.5 * weights[q], 52)), -52);
+        sum += a->wmean[q];
+    }
+    a->wmean[o - 1] = 1.0 - sum;
+    for (int q = 0; q < o; ++q) a->back64[0][q] = a->wmean[q];
+}
+
+cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st)
+{
+    const int block = 256;
+    const dim3 grid((a.cells + block - 1) / block, uint32_t(nfib2));
+    if (mode == M_FP64) {
+        switch (K) {
+        case 0: k_sweep_nodal<0, M_FP64><<<grid, block, 0, st>>>(a); break;
+        case 1: k_sweep_nodal<1, M_FP64><<<grid, block, 0, st>>>(a); break;
+        case 2: k_sweep_nodal<2, M_FP64><<<grid, block, 0, st>>>(a); break;
+        case 3: k_sweep_nodal<3, M_FP64><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else if (mode == M_F32) {
+        switch (K) {
+        case 0: k_sweep_nodal<0, M_F32><<<grid, block, 0, st>>>(a); break;
+        case 1: k_sweep_nodal<1, M_F32><<<grid, block, 0, st>>>(a); break;
+        case 2: k_sweep_nodal<2, M_F32><<<grid, block, 0, st>>>(a); break;
+        case 3: k_sweep_nodal<3, M_F32><<<grid, block, 0, st>>>(a); break;
+        default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sl

@@ -1,0 +1,36 @@
+// sl_nodal.h -- arguments of the nodal-in-velocity x-sweep (sl_nodal.cu).
+// Not part of the public ABI (include/sl.h is).
+#pragma once
+
+#include "sl_internal.cuh"
+
+namespace sl {
+
+// One nodal x-sweep along xdim (paired with vdim) from src to dst.  tab holds
+// the classes j * o + q (v-cell j, node q).  The node tables are filled by
+// nodal_setup.
+struct NodalArgs {
+    Planes src, dst;
+    ShiftTable tab;
+    uint32_t cells;
+    uint32_t N, NV;            // extents of the x- and v-dimensions
+    uint32_t inner_x;          // cells between neighbours along x
+    FastDiv fdInnerX, fdNX;    // cell -> x coordinate: (cell / inner_x) % N
+    FastDiv fdInnerV, fdNV;    // cell -> v-cell:       (cell / inner_v) % NV
+    int64_t pstride;
+    int ostride, vstride;      // o^xdim, o^vdim
+    int ndim, xdim, vdim, O;
+    double eval64[kMaxO][kMaxO];   // P_jv(eta_q) at [q][jv]
+    double back64[kMaxO][kMaxO];   // (2 jv + 1) / 2 w_q P_jv(eta_q) at [jv][q]; row 0 = wmean
+    double wmean[kMaxO];           // w_q / 2 rounded to sum to exactly 1
+    float eval32[kMaxO][kMaxO];
+    float back32[kMaxO][kMaxO];
+};
+
+// Gauss-Legendre nodes eta[o] (ascending) and weights[o] of degree K's o = K + 1
+// points, and the node tables of a.
+void nodal_setup(int K, double* eta, double* weights, NodalArgs* a);
+// grid: cells x nfib2 (= o^(d-2) fibres of coefficients varying in (j_x, j_v)).
+cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st);
+
+}  // namespace sl

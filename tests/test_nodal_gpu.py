@@ -1,0 +1,185 @@
+"""Parity of the nodal-in-velocity x-sweep (sl_advect_nodal, and sl_step after
+sl_set_nodal_velocity) with the oracle's sweep_nodal, through the C ABI.
+
+Tolerances: FP64 store max-relative <= 1e-12; mixed FP32 store relative
+function-space L2 <= 1e-6 for one sweep against the oracle applied to the
+stored (rounded) input and <= 1e-5 after split steps against the FP64 oracle;
+mass drift <= 1e-13 after 1000 steps in both stores.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_1603_07008_gb300 as S
+from paper_1603_07008_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# (extents, pair, v-box): x-dimension 0 or 1, with and without unpaired dimensions
+XV = [((7, 5), (1, -1)), ((5, 6), (-1, 0)), ((4, 3, 5), (2, -1, -1)), ((3, 4, 2, 3), (2, 3, -1, -1)),
+      ((6, 2, 4), (-1, 2, -1))]
+
+
+def _grid(n, pair):
+    d = len(n)
+    lo = tuple(-3.0 if pair.count(m) else 0.0 for m in range(d))    # v-dimensions span [-3, 2)
+    hi = tuple(2.0 if pair.count(m) else 1.0 for m in range(d))
+    return W.Grid(n=tuple(n), lo=lo, hi=hi, pair=tuple(pair))
+
+
+def _rand(n, k, seed):
+    return W.random_coefficients(int(np.prod(n)), k, len(n), seed)
+
+
+def _xdims(pair):
+    return [m for m, p in enumerate(pair) if p >= 0]
+
+
+@pytest.mark.parametrize("n,pair", XV)
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_fp64_nodal_sweeps_match_oracle(n, pair, k):
+    if (k + 1) ** len(n) > 512:
+        pytest.skip("coefficient count covered by smaller shapes")
+    g = _grid(n, pair)
+    u = _rand(n, k, 31)
+    with S.Context(g, k, "fp64") as ctx:
+        for dim in _xdims(pair):
+            for tau in (0.37, -1.3, 2.9):
+                ctx.set_coeffs(u)
+                ctx.advect_nodal(dim, tau)
+                got = ctx.get_coeffs()
+                ref = O.sweep_nodal(u, g, k, dim, tau)
+                assert O.rel_max(got, ref) <= 1e-12, (dim, tau)
+
+
+@pytest.mark.parametrize("n,pair", XV)
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_mixed_nodal_sweeps_match_oracle(n, pair, k):
+    if (k + 1) ** len(n) > 512:
+        pytest.skip("coefficient count covered by smaller shapes")
+    g = _grid(n, pair)
+    u = _rand(n, k, 32)
+    stored = O.round_storage(u, k, len(n), 1)
+    with S.Context(g, k, "mix_fp32") as ctx:
+        for dim in _xdims(pair):
+            for tau in (0.37, -1.3):
+                ctx.set_coeffs(u)
+                ctx.advect_nodal(dim, tau)
+                got = ctx.get_coeffs()
+                ref = O.sweep_nodal(stored, g, k, dim, tau)
+                assert O.rel_l2(got, ref, k, len(n)) <= 1e-6, (dim, tau)
+                # the mean gets the FP32 parts' rounding only
+                assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(stored[:, 1:]))
+
+
+@pytest.mark.parametrize("store", ["fp64", "mix_fp32"])
+def test_degree_zero_nodal_is_the_centre_sweep(store):
+    """With one node per v-cell (k = 0) the node is the cell centre: the nodal
+    sweep is the plain x-sweep with the centre velocity."""
+    n, pair = (9, 6), (1, -1)
+    g = _grid(n, pair)
+    u = _rand(n, 0, 33)
+    tau = 0.71
+    hv, hx = 5.0 / 6, 1.0 / 9
+    v = -3.0 + (np.arange(6) + 0.5) * hv
+    with S.Context(g, 0, store) as a, S.Context(g, 0, store) as b:
+        a.set_coeffs(u)
+        b.set_coeffs(u)
+        a.advect_nodal(0, tau)
+        b.advect(0, 1, v * tau / hx)
+        assert np.max(np.abs(a.get_coeffs() - b.get_coeffs())) <= 1e-14 * np.max(np.abs(u))
+
+
+@pytest.mark.parametrize("store", ["fp64", "mix_fp32"])
+@pytest.mark.parametrize("cfg", ["2d", "4d"])
+def test_nodal_strang_steps_match_oracle(store, cfg):
+    p = W.config2(n=32, steps=5) if cfg == "2d" else W.config3(n=6, steps=2)
+    u0 = O.project(p.grid, p.k, p.nq, p.weights, p.params)
+    ref = O.step(u0, p.grid, p.k, "strang", p.dt, p.steps, p.field_list(), nodal_v=True)
+    with S.Context(p.grid, p.k, store) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        ctx.set_nodal_velocity(True)
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, p.steps)
+        got = ctx.get_coeffs()
+        drift = abs(ctx.mass() - m0) / abs(m0)
+    if store == "fp64":
+        assert O.rel_max(got, ref) <= 1e-12
+    else:
+        assert O.rel_l2(got, ref, p.k, p.grid.ndim) <= 1e-5
+    assert drift <= 1e-13
+
+
+@pytest.mark.parametrize("store", ["fp64", "mix_fp32"])
+def test_nodal_mass_drift_1000_steps(store):
+    p = W.config2(n=64, steps=1000)
+    with S.Context(p.grid, p.k, store) as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        ctx.set_nodal_velocity(True)
+        m0 = ctx.mass()
+        ctx.step("strang", p.dt, 1000)
+        m1 = ctx.mass()
+    assert abs(m1 - m0) / abs(m0) <= 1e-13
+
+
+def test_nodal_graph_replay_matches_step():
+    import torch
+    p = W.config2(n=24, steps=6)
+    st = torch.cuda.Stream()
+    with S.Context(p.grid, p.k, "mix_fp32", stream=st) as a, \
+            S.Context(p.grid, p.k, "mix_fp32", stream=st) as b:
+        for c in (a, b):
+            c.project(p.nq, p.weights, p.params)
+            c.set_fields(p.field_list())
+            c.set_nodal_velocity(True)
+        a.step("strang", p.dt, 6)
+        b.graph_capture("strang", p.dt, 3)
+        b.graph_launch()
+        b.graph_launch()
+        assert np.array_equal(a.get_coeffs(), b.get_coeffs())
+
+
+def test_nodal_free_streaming_beats_the_centre_velocity():
+    """Free streaming over T = 1/2 (8 x-sweeps, 32 x 32 cells, k = 2): the
+    nodal sweep on the GPU is as close to the exact solution as the oracle's
+    and far closer than one velocity per v-cell."""
+    import math
+    k, N, T, steps = 2, 32, 0.5, 8
+    g = W.Grid(n=(N, N), lo=(0.0, -1.0), hi=(1.0, 1.0), pair=(1, -1))
+    w = np.array([1.0, 0.5, 0.5])
+    terms = lambda t: np.array([[[0, 0, 0, 0], [1, 0, 0, 0]],
+                                [[0, 0, 2 * math.pi, 0], [1, 0, 2 * math.pi * t, 0]],
+                                [[0, 0, 2 * math.pi, -math.pi / 2], [1, 0, 2 * math.pi * t, -math.pi / 2]]],
+                               dtype=float)
+    ue = O.project(g, k, k + 3, w, terms(T))
+    v = -1.0 + (np.arange(N) + 0.5) * (2.0 / N)
+    with S.Context(g, k, "fp64") as a, S.Context(g, k, "fp64") as b:
+        a.project(k + 3, w, terms(0.0))
+        b.project(k + 3, w, terms(0.0))
+        for _ in range(steps):
+            a.advect_nodal(0, T / steps)
+            b.advect(0, 1, v * (T / steps) * N)
+        en = O.rel_l2(a.get_coeffs(), ue, k, 2)
+        ec = O.rel_l2(b.get_coeffs(), ue, k, 2)
+    assert en < 1e-5 and en < ec / 100, (en, ec)
+
+
+def test_nodal_rejections():
+    g1 = W.Grid(n=(8,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    with S.Context(g1, 1, "fp64") as c:
+        with pytest.raises(S.SlError) as e:
+            c.set_nodal_velocity(True)
+        assert e.value.status == S.SL_EINVAL
+    g = _grid((6, 5), (1, -1))
+    for store in ("mix_bf16", "fp32", "mix_fp32_d2"):
+        with S.Context(g, 2, store) as c:
+            with pytest.raises(S.SlError) as e:
+                c.set_nodal_velocity(True)
+            assert e.value.status == S.SL_ENOTSUP
+    with S.Context(g, 2, "fp64") as c:
+        with pytest.raises(S.SlError):
+            c.advect_nodal(1, 0.3)          # dimension 1 is the v-dimension
+        with pytest.raises(S.SlError):
+            c.advect_nodal(0, float("nan"))
