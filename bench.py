@@ -65,6 +65,8 @@ def parse_args(argv=None):
                          "(e.g. to profile one fixed kernel)")
     ap.add_argument("--nprob", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--order", type=int, default=None, help="paper1d: only the rows of this order (2 or 4)")
+    ap.add_argument("--nodal-v", action="store_true",
+                    help="4d/2d: x-sweeps with the velocity at the Gauss nodes of every v-cell")
     return ap.parse_args(argv)
 
 
@@ -319,6 +321,8 @@ class Arm:
             self.obj.project(p.nq, p.weights, p.params)
             if self.workload == "vp":      # field from the state before every v-sweep
                 self.obj.set_poisson(True)
+            if getattr(args, "nodal_v", False):
+                self.obj.set_nodal_velocity(True)
             elif p.splitting != "advect":
                 self.obj.set_fields(p.field_list())
             apply_shapes(self.obj, shapes)
@@ -455,8 +459,9 @@ def run_ours(args):
                          "the 4D k=2 workload on a 64x64x16x16 sub-grid, FP64 oracle, one thread"}
 
     if rank == 0:
-        wl = {"4d": f"4d_xxvv_{args.n}^4_k2_{args.storage}_strang",
-              "2d": f"2d_xv_{args.n}^2_k2_{args.storage}_strang",
+        nod = "_nodal_v" if args.nodal_v else ""
+        wl = {"4d": f"4d_xxvv_{args.n}^4_k2_{args.storage}_strang{nod}",
+              "2d": f"2d_xv_{args.n}^2_k2_{args.storage}_strang{nod}",
               "vp": f"2d_xv_{args.n}^2_k2_{args.storage}_strang_self_consistent_field",
               "6d": f"6d_xxxvvv_{args.n}^6_k1_{args.storage}_strang",
               "1d": f"1d_n{args.n}_k2_{args.storage}_advect_graph",
@@ -621,6 +626,8 @@ def run_e2e(S, W, p, args, stream, world, dev):
     ctx = S.Context(p.grid, p.k, args.storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
+    if args.nodal_v:
+        ctx.set_nodal_velocity(True)
     apply_shapes(ctx, args.shapes)
     mean, hi, scale = S.plane_arrays(ctx.handle)
     # pinned host copies of the planes
