@@ -181,6 +181,25 @@ sl_status sl_plane_layout(const sl_grid* grid, int degree, sl_storage storage, s
 sl_status sl_create_external(const sl_grid* grid, int degree, sl_storage storage, void* cuda_stream,
                              void* const* planes, sl_ctx** out);
 
+/* Canaries, the sanitizer of this library (no GPU fault is ever provoked):
+ * every array of a context's allocation is followed by a guard band of at
+ * least 256 bytes, and the padding of every owned plane past the last cell
+ * (up to plane_stride) is filled too, all with the byte 0xA5 at creation.  No
+ * kernel or copy of the library writes there.  *corrupted_bytes = the number
+ * of those bytes that no longer hold 0xA5 (0 for a sound run).  Synchronises.
+ * The planes of sl_create_external are the caller's and are not covered.
+ * Errors: SL_EINVAL (NULL, or during a capture), SL_ECUDA. */
+sl_status sl_check_guards(sl_ctx* ctx, int64_t* corrupted_bytes);
+/* Test hooks of the failure paths (host side only, no device fault):
+ * sl_debug_fail_alloc(n), n >= 1: the n-th device or pinned-host allocation
+ * the library makes from now on fails as if out of memory (later ones succeed
+ * again); n = 0 switches the hook off.  Process-wide.  SL_EINVAL for n < 0.
+ * sl_debug_corrupt_guard: overwrites the first byte of the context's first
+ * guard band (inside its own allocation), so that a test can see
+ * sl_check_guards report it. */
+sl_status sl_debug_fail_alloc(int64_t n);
+sl_status sl_debug_corrupt_guard(sl_ctx* ctx);
+
 /* Free the context and its device memory (after synchronising its stream).
  * NULL is ignored. */
 void sl_destroy(sl_ctx* ctx);

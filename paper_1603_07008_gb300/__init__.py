@@ -34,7 +34,8 @@ __all__ = [
     "sl_batch_autotune", "sl_batch_profile_enable", "sl_batch_profile_query", "sl_batch_profile_dims",
     "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
     "sl_field_energy", "sl_graph_capture_advect", "sl_create_external", "sl_plane_layout",
-    "sl_set_nodal_velocity", "sl_advect_nodal",
+    "sl_set_nodal_velocity", "sl_advect_nodal", "sl_check_guards", "sl_debug_fail_alloc",
+    "sl_debug_corrupt_guard", "save_checkpoint", "load_checkpoint", "autotune_cached",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -170,6 +171,9 @@ def lib():
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
             "sl_set_nodal_velocity": (st, [_vp, ctypes.c_int]),
+            "sl_check_guards": (st, [_vp, _i64p]),
+            "sl_debug_fail_alloc": (st, [ctypes.c_int64]),
+            "sl_debug_corrupt_guard": (st, [_vp]),
             "sl_advect_nodal": (st, [_vp, ctypes.c_int, ctypes.c_double]),
             "sl_create_external": (st, [ctypes.POINTER(sl_grid), ctypes.c_int, ctypes.c_int, _vp,
                                         ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
@@ -474,6 +478,22 @@ def sl_advect_nodal(ctx, dim: int, tau: float):
     _check(lib().sl_advect_nodal(ctx, int(dim), float(tau)), ctx)
 
 
+def sl_check_guards(ctx) -> int:
+    """Bytes of the context's guard bands and plane padding that lost their
+    canary value (0 after a sound run)."""
+    n = ctypes.c_int64()
+    _check(lib().sl_check_guards(ctx, ctypes.byref(n)), ctx)
+    return n.value
+
+
+def sl_debug_fail_alloc(n: int):
+    _check(lib().sl_debug_fail_alloc(int(n)))
+
+
+def sl_debug_corrupt_guard(ctx):
+    _check(lib().sl_debug_corrupt_guard(ctx), ctx)
+
+
 def sl_get_field(ctx, nx: int) -> np.ndarray:
     out = np.empty(int(nx), dtype=np.float64)
     _check(lib().sl_get_field(ctx, out.ctypes.data_as(_dp)), ctx)
@@ -592,6 +612,9 @@ class Context:
 
     def advect_nodal(self, dim, tau):
         sl_advect_nodal(self.handle, dim, tau)
+
+    def check_guards(self):
+        return sl_check_guards(self.handle)
 
     def field(self):
         nx = [n for n, pr in zip(self.grid.n, self.grid.pair) if pr >= 0][0]
@@ -788,3 +811,6 @@ class Batch:
 
     def set_tune(self, dim, **kw):
         sl_batch_set_tune(self.handle, dim, **kw)
+
+
+from .state_io import autotune_cached, load_checkpoint, save_checkpoint  # noqa: E402

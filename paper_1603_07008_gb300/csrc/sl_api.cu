@@ -6,6 +6,7 @@
 // field samples.  All device work goes to the context's stream; only calls
 // that hand results to the host synchronise it.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -13,6 +14,8 @@
 #include <string>
 #include <utility>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "sl_host.h"
 #include "sl_nodal.h"
@@ -22,6 +25,17 @@ using namespace sl::host;
 
 namespace {
 thread_local std::string g_err;
+// allocations left before the simulated failure (sl_debug_fail_alloc); 0: off
+std::atomic<int64_t> g_fail_in{0};
+
+bool simulated_failure()
+{
+    int64_t v = g_fail_in.load();
+    while (v > 0) {
+        if (g_fail_in.compare_exchange_weak(v, v - 1)) return v == 1;
+    }
+    return false;
+}
 }  // namespace
 
 namespace sl {
@@ -50,6 +64,24 @@ sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...)
     else
         g_err = buf;
     return s;
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes)
+{
+    if (simulated_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t pinned_malloc(void** p, size_t bytes)
+{
+    if (simulated_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocHost(p, bytes);
 }
 
 sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what)
@@ -132,6 +164,10 @@ int64_t state_bytes_of(int64_t cells, int64_t nlo, int64_t nhi, int mode)
 double cell_width(const sl_grid& g, int m) { return (g.hi[m] - g.lo[m]) / double(g.n[m]); }
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Guard bands of the context's allocation (sl_check_guards).
+constexpr size_t kGuard = 256;
+constexpr int kCanary = 0xA5;
 
 bool is_scaled(const sl_ctx* c) { return c->mode == M_BF16 || c->mode == M_FP16; }
 bool is_split(const sl_ctx* c) { return c->mode == M_SPLIT2 || c->mode == M_SPLIT3; }
@@ -366,8 +402,22 @@ cudaError_t launch_nodal_only(sl_ctx* c, int dim)
 }
 
 // One sweep along dim using the shift table already built on the stream.
+// Names of the NVTX ranges around each sweep launch (host-side markers that
+// profilers show on the timeline; without an attached tool they cost a
+// pointer test).
+const char* const kSweepRange[2][SL_MAX_DIM] = {
+    {"sl sweep dim 0", "sl sweep dim 1", "sl sweep dim 2", "sl sweep dim 3", "sl sweep dim 4", "sl sweep dim 5"},
+    {"sl nodal sweep dim 0", "sl nodal sweep dim 1", "sl nodal sweep dim 2", "sl nodal sweep dim 3",
+     "sl nodal sweep dim 4", "sl nodal sweep dim 5"}};
+
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 sl_status run_sweep(sl_ctx* c, int dim, int shift_dim, bool nodal = false)
 {
+    NvtxRange range(kSweepRange[nodal ? 1 : 0][dim]);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = c->prof && !c->capturing;
     if (prof) {
@@ -512,7 +562,7 @@ sl_status ensure_stage(sl_ctx* c)
     if (n < 1) n = 1;
     if (n > c->cells) n = c->cells;
     void* p = nullptr;
-    cudaError_t e = cudaMalloc(&p, size_t(n) * c->ncoef * 8);
+    cudaError_t e = dev_malloc(&p, size_t(n) * c->ncoef * 8);
     if (e != cudaSuccess) return fail(c, SL_ENOMEM, "staging allocation: %s", cudaGetErrorString(e));
     c->d_stage = static_cast<double*>(p);
     c->stage_cells = n;
@@ -739,48 +789,55 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     build_poly_table(degree, &c->poly);
     for (int m = 0; m < c->ndim; ++m) default_tune(c, m);
 
-    // layout of the single allocation (the state only when the context owns it)
+    // layout of the single allocation (the state only when the context owns
+    // it): every array 256-B aligned and followed by a guard band of at least
+    // kGuard bytes filled with kCanary (sl_check_guards)
     const size_t A = 256;
     size_t off = 0;
+    auto place = [&](size_t bytes) {
+        const size_t at = off;
+        const size_t end = at + bytes;
+        off = align_up(end + kGuard, A);
+        c->bands.push_back({end, 0, off - end, 1});
+        return at;
+    };
     size_t o_state[2][3] = {{0, 0, 0}, {0, 0, 0}};
     size_t b_mean, b_hi, b_scale;
     copy_bytes(c->cells, c->nlo, c->nhi, c->rec, c->elem, scaled, c->pstride, &b_mean, &b_hi, &b_scale);
     if (!planes)
         for (int b = 0; b < 2; ++b) {
-            o_state[b][0] = off;
-            off = align_up(off + b_mean, A);
-            o_state[b][1] = off;
-            off = align_up(off + b_hi, A);
-            o_state[b][2] = off;
-            off = align_up(off + b_scale, A);
+            o_state[b][0] = place(b_mean);
+            o_state[b][1] = place(b_hi);
+            o_state[b][2] = place(b_scale);
+            // the planes' padding past the last cell
+            const size_t pad = size_t(c->pstride - c->cells);
+            if (pad > 0) {
+                if (c->nlo > 0) c->bands.push_back({o_state[b][0] + size_t(c->cells) * 8, size_t(c->pstride) * 8, pad * 8,
+                                                    size_t(c->nlo)});
+                if (!c->rec && c->nhi > 0)
+                    c->bands.push_back({o_state[b][1] + size_t(c->cells) * c->elem, size_t(c->pstride) * c->elem,
+                                        pad * c->elem, size_t(c->nhi)});
+                if (scaled) c->bands.push_back({o_state[b][2] + size_t(c->cells) * 4, 0, pad * 4, 1});
+            }
         }
-    const size_t o_sigma = off;
-    off = align_up(off + size_t(c->maxcls) * 4, A);
-    const size_t o_alpha = off;
-    off = align_up(off + size_t(c->maxcls) * 8, A);
-    const size_t o_ab64 = off;
-    off = align_up(off + size_t(c->maxcls) * ab_stride64(c->O) * 8, A);
-    const size_t o_ab32 = off;
-    off = align_up(off + size_t(c->maxcls) * ab_stride32(c->O) * 4, A);
-    const size_t o_shifts = off;
-    off = align_up(off + size_t(c->maxcls) * 8, A);
+    const size_t o_sigma = place(size_t(c->maxcls) * 4);
+    const size_t o_alpha = place(size_t(c->maxcls) * 8);
+    const size_t o_ab64 = place(size_t(c->maxcls) * ab_stride64(c->O) * 8);
+    const size_t o_ab32 = place(size_t(c->maxcls) * ab_stride32(c->O) * 4);
+    const size_t o_shifts = place(size_t(c->maxcls) * 8);
     int64_t nf = 0;
     for (int m = 0; m < c->ndim; ++m)
         if (c->g.pair[m] >= 0) nf += c->g.n[m];
     c->nfields = nf;
-    const size_t o_fields = off;
-    off = align_up(off + size_t(std::max<int64_t>(nf, 1)) * 8, A);
+    const size_t o_fields = place(size_t(std::max<int64_t>(nf, 1)) * 8);
     c->mass_nblk = mass_blocks(uint32_t(c->cells));
-    const size_t o_part = off;
-    off = align_up(off + size_t(c->mass_nblk) * 8, A);
-    const size_t o_mass = off;
-    off = align_up(off + 8, A);
+    const size_t o_part = place(size_t(c->mass_nblk) * 8);
+    const size_t o_mass = place(8);
     const bool mapped = is_split_family(c->mode);
-    const size_t o_cmap = off;
-    if (mapped) off = align_up(off + size_t(c->ncoef) * 4, A);
+    const size_t o_cmap = mapped ? place(size_t(c->ncoef) * 4) : 0;
     c->mem_bytes = off;
 
-    cudaError_t e = cudaMalloc(&c->mem, c->mem_bytes);
+    cudaError_t e = dev_malloc(&c->mem, c->mem_bytes);
     if (e != cudaSuccess) {
         delete c;
         return fail(nullptr, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
@@ -810,7 +867,7 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     c->d_fields = reinterpret_cast<double*>(base + o_fields);
     c->d_partials = reinterpret_cast<double*>(base + o_part);
     c->d_mass = reinterpret_cast<double*>(base + o_mass);
-    e = cudaMallocHost(reinterpret_cast<void**>(&c->h_mass), 8);
+    e = pinned_malloc(reinterpret_cast<void**>(&c->h_mass), 8);
     if (e != cudaSuccess) {
         cudaFree(c->mem);
         delete c;
@@ -819,6 +876,12 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     // an owned state starts at zero (the scale plane at zero decodes to zero
     // too); a caller's planes keep their contents
     e = cudaMemsetAsync(c->mem, 0, c->mem_bytes, c->st);
+    for (const auto& bd : c->bands) {
+        if (e != cudaSuccess) break;
+        char* at = static_cast<char*>(c->mem) + bd.off;
+        e = bd.height == 1 ? cudaMemsetAsync(at, kCanary, bd.width, c->st)
+                           : cudaMemset2DAsync(at, bd.pitch, kCanary, bd.width, bd.height, c->st);
+    }
     std::vector<int32_t> cmap;
     if (mapped && e == cudaSuccess) {
         cmap = coefficient_map(c->ndim, c->O, split_q(c->mode));
@@ -868,6 +931,45 @@ sl_status sl_plane_layout(const sl_grid* grid, int degree, sl_storage storage, s
     out->mean_bytes = int64_t(bm);
     out->hi_bytes = int64_t(bh);
     out->scale_bytes = int64_t(bs);
+    return SL_OK;
+}
+
+sl_status sl_debug_fail_alloc(int64_t n)
+{
+    if (n < 0) return fail(nullptr, SL_EINVAL, "n must be >= 0");
+    g_fail_in.store(n);
+    return SL_OK;
+}
+
+sl_status sl_check_guards(sl_ctx* c, int64_t* corrupted)
+{
+    if (!c || !corrupted) return fail(c, SL_EINVAL, "NULL argument");
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot check the guards during a capture");
+    *corrupted = 0;
+    std::vector<unsigned char> buf;
+    for (const auto& bd : c->bands) {
+        if (bd.width == 0 || bd.height == 0) continue;
+        buf.resize(bd.width * bd.height);
+        const char* at = static_cast<const char*>(c->mem) + bd.off;
+        if (bd.height == 1)
+            SL_CUDA(c, cudaMemcpyAsync(buf.data(), at, bd.width, cudaMemcpyDeviceToHost, c->st));
+        else
+            SL_CUDA(c, cudaMemcpy2DAsync(buf.data(), bd.width, at, bd.pitch, bd.width, bd.height,
+                                         cudaMemcpyDeviceToHost, c->st));
+        SL_CUDA(c, cudaStreamSynchronize(c->st));
+        for (unsigned char x : buf) *corrupted += x != kCanary;
+    }
+    return SL_OK;
+}
+
+sl_status sl_debug_corrupt_guard(sl_ctx* c)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (c->bands.empty()) return fail(c, SL_EINVAL, "no guard band");
+    const unsigned char zero = 0;
+    SL_CUDA(c, cudaMemcpyAsync(static_cast<char*>(c->mem) + c->bands.front().off, &zero, 1, cudaMemcpyHostToDevice,
+                               c->st));
+    SL_CUDA(c, cudaStreamSynchronize(c->st));
     return SL_OK;
 }
 
@@ -1078,7 +1180,7 @@ sl_status sl_project(sl_ctx* c, int nq, int nterms, const double* weights, const
             c->d_proj = nullptr;
             c->proj_bytes = 0;
         }
-        cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&c->d_proj), need);
+        cudaError_t e = dev_malloc(reinterpret_cast<void**>(&c->d_proj), need);
         if (e != cudaSuccess) return fail(c, SL_ENOMEM, "projection workspace: %s", cudaGetErrorString(e));
         c->proj_bytes = need;
     }
@@ -1156,7 +1258,7 @@ static sl_status vp_alloc(sl_ctx* c)
     if (c->capturing) return fail(c, SL_EINVAL, "cannot allocate during a capture");
     const size_t nx = size_t(c->g.n[c->vp_x]);
     const size_t n = size_t(vp_chunks(uint32_t(c->g.n[c->vp_v]))) * nx + nx + 1;
-    cudaError_t e = cudaMalloc(&c->d_vp, n * sizeof(double));
+    cudaError_t e = dev_malloc(reinterpret_cast<void**>(&c->d_vp), n * sizeof(double));
     if (e != cudaSuccess) {
         c->d_vp = nullptr;
         return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", n * sizeof(double), cudaGetErrorString(e));
@@ -1214,7 +1316,7 @@ static sl_status nodal_alloc(sl_ctx* c)
     const size_t o_ab32 = off;
     off = align_up(off + size_t(maxcls) * ab_stride32(c->O) * 4, A);
     void* mem = nullptr;
-    cudaError_t e = cudaMalloc(&mem, off);
+    cudaError_t e = dev_malloc(&mem, off);
     if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
     e = cudaMemcpy(mem, vel.data(), vel.size() * 8, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -1313,6 +1415,7 @@ sl_status sl_step(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     sl_status s = check_step_args(c, sp, dt, nsteps);
     if (s != SL_OK) return s;
+    NvtxRange range("sl_step");
     return enqueue_steps(c, sp, dt, nsteps);
 }
 
@@ -1362,7 +1465,7 @@ sl_status sl_graph_capture_advect(sl_ctx* c, int dim, int shift_dim, const doubl
         if (c->d_gshifts) cudaFree(c->d_gshifts);
         c->d_gshifts = nullptr;
         c->gshifts_n = 0;
-        cudaError_t e = cudaMalloc(&c->d_gshifts, size_t(nshift) * 8);
+        cudaError_t e = dev_malloc(reinterpret_cast<void**>(&c->d_gshifts), size_t(nshift) * 8);
         if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
         c->gshifts_n = nshift;
     }

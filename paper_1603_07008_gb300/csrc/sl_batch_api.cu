@@ -141,7 +141,9 @@ sl_status rebuild_dim(sl_batch* b, int m)
         cudaFree(b->d_items[m]);
         b->d_items[m] = nullptr;
     }
-    SLB_CUDA(b, cudaMalloc(&b->d_items[m], std::max<size_t>(1, items.size()) * sizeof(BatchItem)));
+    if (dev_malloc(reinterpret_cast<void**>(&b->d_items[m]), std::max<size_t>(1, items.size()) * sizeof(BatchItem)) !=
+        cudaSuccess)
+        return bfail(b, SL_ENOMEM, "work list allocation");
     SLB_CUDA(b, cudaMemcpyAsync(b->d_items[m], items.data(), items.size() * sizeof(BatchItem),
                                 cudaMemcpyHostToDevice, b->st));
     SLB_CUDA(b, cudaStreamSynchronize(b->st));
@@ -297,7 +299,7 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
     const size_t o_md = take(sizeof(BatchMass) * nprob);
     const size_t o_m = take(sizeof(double) * nprob);
     const size_t o_ctr = take(sizeof(uint32_t) * SL_MAX_DIM);
-    if (cudaMalloc(&b->mem, off) != cudaSuccess) return cleanup(fail(nullptr, SL_ENOMEM, "batch tables"));
+    if (dev_malloc(&b->mem, off) != cudaSuccess) return cleanup(fail(nullptr, SL_ENOMEM, "batch tables"));
     char* base = static_cast<char*>(b->mem);
     b->d_args = reinterpret_cast<SweepArgs*>(base + o_args);
     b->d_kdeg = reinterpret_cast<int32_t*>(base + o_k);

@@ -26,6 +26,12 @@ struct sl_ctx {
 
     void* mem = nullptr;
     size_t mem_bytes = 0;
+    // canaries: guard bands after every array of the allocation, and the
+    // padding of the owned planes past `cells` (offsets into mem)
+    struct Band {
+        size_t off, pitch, width, height;   // height rows of width bytes, pitch apart
+    };
+    std::vector<Band> bands;
     sl::Planes planes[2]{};
     bool external = false;      // planes owned by the caller (sl_create_external)
     int cur = 0;
@@ -98,6 +104,10 @@ namespace host {
 sl_status fail(sl_ctx* c, sl_status s, const char* fmt, ...);
 sl_status fail_to(std::string* err, sl_status s, const char* fmt, ...);
 sl_status cuda_fail(sl_ctx* c, cudaError_t e, const char* what);
+// cudaMalloc / cudaMallocHost behind the allocation-failure test hook
+// (sl_debug_fail_alloc): every device or pinned allocation the library makes.
+cudaError_t dev_malloc(void** p, size_t bytes);
+cudaError_t pinned_malloc(void** p, size_t bytes);
 cudaError_t vp_field(sl_ctx* c, double* E, double* energy);
 sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c);
 bool is_scaled(const sl_ctx* c);
