@@ -321,10 +321,10 @@ class Arm:
             self.obj.project(p.nq, p.weights, p.params)
             if self.workload == "vp":      # field from the state before every v-sweep
                 self.obj.set_poisson(True)
-            if getattr(args, "nodal_v", False):
-                self.obj.set_nodal_velocity(True)
             elif p.splitting != "advect":
                 self.obj.set_fields(p.field_list())
+            if getattr(args, "nodal_v", False):
+                self.obj.set_nodal_velocity(True)
             apply_shapes(self.obj, shapes)
             self.dof = p.dof
             self.order = p.k + 1
