@@ -418,7 +418,9 @@ def run_ours(args):
     bytes_per_sweep = sweep_bytes / max(nl, 1)
     achieved_gbs = bytes_per_sweep / (avg_sweep_ms / 1000.0) / 1e9
     peak_gbs = float(peaks["hbm_gbs"])
-    traffic, traffic_note = sweep_traffic(args.workload, args.storage, bytes_per_sweep)
+    # the captured ratios are of the plain sweeps; the nodal x-sweeps have none
+    traffic, traffic_note = sweep_traffic(args.workload + ("_nodal_v" if args.nodal_v else ""), args.storage,
+                                          bytes_per_sweep)
 
     fp64 = None
     if not args.no_fp64 and args.storage != "fp64":

@@ -38,17 +38,63 @@ namespace {
 
 // Base coefficient index of 2D fibre g: its digits along the dimensions other
 // than x and v, in increasing dimension order.
+template <int O>
 __device__ __forceinline__ int nodal_fibre_base(const NodalArgs& a, int g)
 {
     int base = 0, stride = 1;
     for (int m = 0; m < a.ndim; ++m) {
         if (m != a.xdim && m != a.vdim) {
-            base += (g % a.O) * stride;
-            g /= a.O;
+            base += (g % O) * stride;
+            g /= O;
         }
-        stride *= a.O;
+        stride *= O;
     }
     return base;
+}
+
+// One class record of the node table (A then B, padded to 16 bytes), read
+// with 16-byte vector loads.
+template <int O>
+__device__ __forceinline__ void load_ab(const ShiftTable& t, uint32_t cls, float (&A)[O][O], float (&B)[O][O])
+{
+    constexpr int S = ab_stride32(O);
+    const float4* p = reinterpret_cast<const float4*>(t.ab32 + size_t(cls) * S);
+    float v[S];
+#pragma unroll
+    for (int q = 0; q < S / 4; ++q) {
+        const float4 x = __ldg(p + q);
+        v[4 * q] = x.x;
+        v[4 * q + 1] = x.y;
+        v[4 * q + 2] = x.z;
+        v[4 * q + 3] = x.w;
+    }
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            A[x][l] = v[x * O + l];
+            B[x][l] = v[O * O + x * O + l];
+        }
+}
+template <int O>
+__device__ __forceinline__ void load_ab(const ShiftTable& t, uint32_t cls, double (&A)[O][O], double (&B)[O][O])
+{
+    constexpr int S = ab_stride64(O);
+    const double2* p = reinterpret_cast<const double2*>(t.ab64 + size_t(cls) * S);
+    double v[S];
+#pragma unroll
+    for (int q = 0; q < S / 2; ++q) {
+        const double2 x = __ldg(p + q);
+        v[2 * q] = x.x;
+        v[2 * q + 1] = x.y;
+    }
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int l = 0; l < O; ++l) {
+            A[x][l] = v[x * O + l];
+            B[x][l] = v[O * O + x * O + l];
+        }
 }
 
 template <typename T>
@@ -71,54 +117,44 @@ __device__ __forceinline__ void nodal_plain(const NodalArgs& a, uint32_t c, uint
 #pragma unroll
         for (int v = 0; v < O; ++v) acc[x][v] = R(0);
     R va[O][O], vb[O][O];
-    int32_t last = -1;
     const int32_t N = int32_t(a.N);
+    auto load = [&](int32_t sig) {
+        int32_t ia = int32_t(i) - sig;
+        ia += ia < 0 ? N : 0;
+        int32_t ib = ia - 1;
+        ib += ib < 0 ? N : 0;
+        const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+#pragma unroll
+        for (int l = 0; l < O; ++l)
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                const int J = base + l * a.ostride + v * a.vstride;
+                if (has_mean && J == 0) {
+                    va[l][v] = R(__ldg(a.src.mean + ca));
+                    vb[l][v] = R(__ldg(a.src.mean + cb));
+                } else {
+                    const R* p = coef_plane<R>(a.src, a.pstride, J);
+                    va[l][v] = __ldg(p + ca);
+                    vb[l][v] = __ldg(p + cb);
+                }
+            }
+    };
+    // the nodes of a v-cell nearly always share sigma: then the sources are
+    // loaded once, else once per node
+    int32_t sg[O];
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        sg[q] = __ldg(a.tab.sigma + j * O + q);
+        same = same && sg[q] == sg[0];
+    }
+    if (same) load(sg[0]);
 #pragma unroll
     for (int q = 0; q < O; ++q) {
         const uint32_t cls = j * O + q;
-        const int32_t sig = __ldg(a.tab.sigma + cls);
-        if (sig != last) {
-            int32_t ia = int32_t(i) - sig;
-            ia += ia < 0 ? N : 0;
-            int32_t ib = ia - 1;
-            ib += ib < 0 ? N : 0;
-            const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
-#pragma unroll
-            for (int l = 0; l < O; ++l)
-#pragma unroll
-                for (int v = 0; v < O; ++v) {
-                    const int J = base + l * a.ostride + v * a.vstride;
-                    if (has_mean && J == 0) {
-                        va[l][v] = R(__ldg(a.src.mean + ca));
-                        vb[l][v] = R(__ldg(a.src.mean + cb));
-                    } else {
-                        const R* p = coef_plane<R>(a.src, a.pstride, J);
-                        va[l][v] = __ldg(p + ca);
-                        vb[l][v] = __ldg(p + cb);
-                    }
-                }
-            last = sig;
-        }
+        if (!same) load(sg[q]);
         R A[O][O], B[O][O];
-        if constexpr (sizeof(R) == 8) {
-            const double* m = a.tab.ab64 + size_t(cls) * ab_stride64(O);
-#pragma unroll
-            for (int x = 0; x < O; ++x)
-#pragma unroll
-                for (int l = 0; l < O; ++l) {
-                    A[x][l] = __ldg(m + x * O + l);
-                    B[x][l] = __ldg(m + O * O + x * O + l);
-                }
-        } else {
-            const float* m = a.tab.ab32 + size_t(cls) * ab_stride32(O);
-#pragma unroll
-            for (int x = 0; x < O; ++x)
-#pragma unroll
-                for (int l = 0; l < O; ++l) {
-                    A[x][l] = __ldg(m + x * O + l);
-                    B[x][l] = __ldg(m + O * O + x * O + l);
-                }
-        }
+        load_ab<O>(a.tab, cls, A, B);
         R ua[O], ub[O];
 #pragma unroll
         for (int l = 0; l < O; ++l) {
@@ -197,40 +233,39 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
     double up0[O];
     float va[O][O], vb[O][O];   // [l][jv], entry (0, 0) unused
     double ma = 0.0, mb = 0.0;
-    int32_t last = -1;
     const int32_t N = int32_t(a.N);
+    auto load = [&](int32_t sig) {
+        int32_t ia = int32_t(i) - sig;
+        ia += ia < 0 ? N : 0;
+        int32_t ib = ia - 1;
+        ib += ib < 0 ? N : 0;
+        const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+        ma = __ldg(a.src.mean + ca);
+        mb = __ldg(a.src.mean + cb);
+#pragma unroll
+        for (int l = 0; l < O; ++l)
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                if (l == 0 && v == 0) continue;
+                const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
+                va[l][v] = __ldg(p + ca);
+                vb[l][v] = __ldg(p + cb);
+            }
+    };
+    int32_t sg[O];
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        sg[q] = __ldg(a.tab.sigma + j * O + q);
+        same = same && sg[q] == sg[0];
+    }
+    if (same) load(sg[0]);
 #pragma unroll
     for (int q = 0; q < O; ++q) {
         const uint32_t cls = j * O + q;
-        const int32_t sig = __ldg(a.tab.sigma + cls);
-        if (sig != last) {
-            int32_t ia = int32_t(i) - sig;
-            ia += ia < 0 ? N : 0;
-            int32_t ib = ia - 1;
-            ib += ib < 0 ? N : 0;
-            const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
-            ma = __ldg(a.src.mean + ca);
-            mb = __ldg(a.src.mean + cb);
-#pragma unroll
-            for (int l = 0; l < O; ++l)
-#pragma unroll
-                for (int v = 0; v < O; ++v) {
-                    if (l == 0 && v == 0) continue;
-                    const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
-                    va[l][v] = __ldg(p + ca);
-                    vb[l][v] = __ldg(p + cb);
-                }
-            last = sig;
-        }
-        const float* m32 = a.tab.ab32 + size_t(cls) * ab_stride32(O);
+        if (!same) load(sg[q]);
         float A[O][O], B[O][O];
-#pragma unroll
-        for (int x = 0; x < O; ++x)
-#pragma unroll
-            for (int l = 0; l < O; ++l) {
-                A[x][l] = __ldg(m32 + x * O + l);
-                B[x][l] = __ldg(m32 + O * O + x * O + l);
-            }
+        load_ab<O>(a.tab, cls, A, B);
         // node values: row 0 in FP64, the others in FP32
         double ua0 = ma, ub0 = mb;
 #pragma unroll
@@ -293,25 +328,53 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
         }
 }
 
-template <int K, int MODE>
-__global__ void __launch_bounds__(256) k_sweep_nodal(const NodalArgs a)
+// PART 0: every fibre (FP64 store; fibre blockIdx.y); 1: only the mean's
+// fibre of the mixed store (two dimensions); 3: every fibre of the mixed
+// store, the blocks of the fibres interleaved in a 1D grid (block b takes
+// fibre b % nfib2), so that blocks of the mean's fibre, bound by the FP64
+// pipe, run beside blocks of FP32 fibres, bound by instruction issue.
+template <int K, int MODE, int PART>
+__global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 ? 5 : 2)
+    k_sweep_nodal(const NodalArgs a)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int O = K + 1;
+    int g = int(blockIdx.y);
+    uint32_t bx = blockIdx.x;
+    if constexpr (PART == 3) {
+        g = int(blockIdx.x % a.nfib2);
+        bx = blockIdx.x / a.nfib2;
+    }
+    const uint32_t c = bx * blockDim.x + threadIdx.x;
     if (c >= a.cells) return;
-    const int base = nodal_fibre_base(a, int(blockIdx.y));
+    const int base = nodal_fibre_base<O>(a, g);
     const uint32_t ox = a.fdInnerX.div(c);
     const uint32_t i = ox - a.fdNX.div(ox) * a.N;        // coordinate along x
     const uint32_t ov = a.fdInnerV.div(c);
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;       // v-cell
     const uint32_t line0 = c - i * a.inner_x;
-    if constexpr (MODE == M_FP64) {
+    if constexpr (MODE == M_FP64)
         nodal_plain<K, double>(a, c, i, line0, j, base);
+    else if (PART == 1 || g == 0)
+        nodal_mean_fibre<K>(a, c, i, line0, j);
+    else
+        nodal_plain<K, float>(a, c, i, line0, j, base);
+}
+
+template <int K>
+cudaError_t nodal_launch(int mode, const NodalArgs& a, int nfib2, cudaStream_t st)
+{
+    const int block = 256;
+    const uint32_t bx = (a.cells + block - 1) / block;
+    if (mode == M_FP64) {
+        k_sweep_nodal<K, M_FP64, 0><<<dim3(bx, uint32_t(nfib2)), block, 0, st>>>(a);
+    } else if (nfib2 == 1) {
+        k_sweep_nodal<K, M_F32, 1><<<dim3(bx, 1), block, 0, st>>>(a);
     } else {
-        if (base == 0)
-            nodal_mean_fibre<K>(a, c, i, line0, j);
-        else
-            nodal_plain<K, float>(a, c, i, line0, j, base);
+        const uint64_t nb = uint64_t((a.cells + 127) / 128) * uint64_t(nfib2);
+        if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
+        k_sweep_nodal<K, M_F32, 3><<<uint32_t(nb), 128, 0, st>>>(a);
     }
+    return cudaGetLastError();
 }
 
 // Gauss-Legendre nodes and weights on [-1, 1] by Newton's method on P_o from
@@ -380,28 +443,14 @@ void nodal_setup(int K, double* eta, double* weights, NodalArgs* a)
 
 cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st)
 {
-    const int block = 256;
-    const dim3 grid((a.cells + block - 1) / block, uint32_t(nfib2));
-    if (mode == M_FP64) {
-        switch (K) {
-        case 0: k_sweep_nodal<0, M_FP64><<<grid, block, 0, st>>>(a); break;
-        case 1: k_sweep_nodal<1, M_FP64><<<grid, block, 0, st>>>(a); break;
-        case 2: k_sweep_nodal<2, M_FP64><<<grid, block, 0, st>>>(a); break;
-        case 3: k_sweep_nodal<3, M_FP64><<<grid, block, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-        }
-    } else if (mode == M_F32) {
-        switch (K) {
-        case 0: k_sweep_nodal<0, M_F32><<<grid, block, 0, st>>>(a); break;
-        case 1: k_sweep_nodal<1, M_F32><<<grid, block, 0, st>>>(a); break;
-        case 2: k_sweep_nodal<2, M_F32><<<grid, block, 0, st>>>(a); break;
-        case 3: k_sweep_nodal<3, M_F32><<<grid, block, 0, st>>>(a); break;
-        default: return cudaErrorInvalidValue;
-        }
-    } else {
-        return cudaErrorInvalidValue;
+    if (mode != M_FP64 && mode != M_F32) return cudaErrorInvalidValue;
+    switch (K) {
+    case 0: return nodal_launch<0>(mode, a, nfib2, st);
+    case 1: return nodal_launch<1>(mode, a, nfib2, st);
+    case 2: return nodal_launch<2>(mode, a, nfib2, st);
+    case 3: return nodal_launch<3>(mode, a, nfib2, st);
+    default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace sl
