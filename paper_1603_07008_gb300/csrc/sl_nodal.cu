@@ -36,6 +36,11 @@ namespace sl {
 
 namespace {
 
+// FP32 fibres per thread of the mixed store's nodal sweep (as many as fit
+// the registers without spilling: measured 17% faster with 2 than with 1 at
+// k = 2).
+__host__ __device__ constexpr int nodal_ft(int K) { return K <= 1 ? 4 : K == 2 ? 2 : 1; }
+
 // Base coefficient index of 2D fibre g: its digits along the dimensions other
 // than x and v, in increasing dimension order.
 template <int O>
@@ -219,6 +224,204 @@ __device__ __forceinline__ void nodal_plain(const NodalArgs& a, uint32_t c, uint
         }
 }
 
+// FT FP32 fibres of the mixed store in one thread (bases jb[u]): the thread's
+// index arithmetic, sigma and the node tables serve all of them.
+template <int K, int FT>
+__device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
+                                                 uint32_t j, const int (&jb)[FT])
+{
+    constexpr int O = K + 1;
+    const int32_t N = int32_t(a.N);
+    float va[FT][O][O], vb[FT][O][O];
+    auto load = [&](int32_t sig) {
+        int32_t ia = int32_t(i) - sig;
+        ia += ia < 0 ? N : 0;
+        int32_t ib = ia - 1;
+        ib += ib < 0 ? N : 0;
+        const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l)
+#pragma unroll
+                for (int v = 0; v < O; ++v) {
+                    const float* p = coef_plane<float>(a.src, a.pstride, jb[u] + l * a.ostride + v * a.vstride);
+                    va[u][l][v] = __ldg(p + ca);
+                    vb[u][l][v] = __ldg(p + cb);
+                }
+    };
+    int32_t sg[O];
+    bool same = true;
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        sg[q] = __ldg(a.tab.sigma + j * O + q);
+        same = same && sg[q] == sg[0];
+    }
+    if (same) load(sg[0]);
+    float acc[FT][O][O];
+#pragma unroll
+    for (int u = 0; u < FT; ++u)
+#pragma unroll
+        for (int x = 0; x < O; ++x)
+#pragma unroll
+            for (int v = 0; v < O; ++v) acc[u][x][v] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        if (!same) load(sg[q]);
+        float A[O][O], B[O][O];
+        load_ab<O>(a.tab, j * O + q, A, B);
+#pragma unroll
+        for (int u = 0; u < FT; ++u) {
+            float ua[O], ub[O];
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+                for (int v = 0; v < O; ++v) {
+                    sa = fmaf(va[u][l][v], a.eval32[q][v], sa);
+                    sb = fmaf(vb[u][l][v], a.eval32[q][v], sb);
+                }
+                ua[l] = sa;
+                ub[l] = sb;
+            }
+#pragma unroll
+            for (int x = 0; x < O; ++x) {
+                float s = 0.0f;
+#pragma unroll
+                for (int l = 0; l < O; ++l) {
+                    s = fmaf(A[x][l], ua[l], s);
+                    s = fmaf(B[x][l], ub[l], s);
+                }
+#pragma unroll
+                for (int v = 0; v < O; ++v) acc[u][x][v] = fmaf(a.back32[v][q], s, acc[u][x][v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < FT; ++u)
+#pragma unroll
+        for (int x = 0; x < O; ++x)
+#pragma unroll
+            for (int v = 0; v < O; ++v)
+                static_cast<float*>(a.dst.hi)[int64_t(jb[u] + x * a.ostride + v * a.vstride - 1) * a.pstride + c] =
+                    acc[u][x][v];
+}
+
+// The fibre of the cell mean in the mixed store when the o nodes of the
+// v-cell share sigma (so all nodes read the same two source cells a, b).
+// In exact arithmetic, with t = m_b - m_a, delta_q(c) = sum_{jv>=1} c_{0,jv}
+// P_jv(eta_q) and G_q(c) = sum_{l>=1} A_0l(alpha_q) U_q(c, l), the weighted
+// row 0 of the nodes is
+//     c'_{0,0} = m_a + alpha_bar t + E(a) - E(b),
+//     alpha_bar = sum_q w'_q alpha_q,  E(c) = sum_q w'_q (G_q(c) - alpha_q delta_q(c)),
+// because sum_q w'_q delta_q(c) = 0 (the Gauss rule of P_jv, jv >= 1).  E is a
+// function of one cell (alpha_q and the matrices are fixed along a line), so
+// it is formed in FP32 and the FP64 differences E(a) - E(b) telescope along
+// the line: mass is conserved to FP64 rounding with seven FP64 instructions
+// per cell.  The other coefficients of row 0 take the nodes' deviations from
+// m_a + alpha_bar t, d_q = delta_q(a) + alpha_q (delta_q(b) - delta_q(a))
+// + G_q(a) - G_q(b) + (alpha_q - alpha_bar) t, in FP32.
+template <int K>
+__device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
+                                                        uint32_t j, int32_t sig)
+{
+    constexpr int O = K + 1;
+    const int32_t N = int32_t(a.N);
+    int32_t ia = int32_t(i) - sig;
+    ia += ia < 0 ? N : 0;
+    int32_t ib = ia - 1;
+    ib += ib < 0 ? N : 0;
+    const uint32_t ca = line0 + uint32_t(ia) * a.inner_x, cb = line0 + uint32_t(ib) * a.inner_x;
+    const double ma = __ldg(a.src.mean + ca), mb = __ldg(a.src.mean + cb);
+    float va[O][O], vb[O][O];   // [l][jv], entry (0, 0) unused
+#pragma unroll
+    for (int l = 0; l < O; ++l)
+#pragma unroll
+        for (int v = 0; v < O; ++v) {
+            if (l == 0 && v == 0) continue;
+            const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
+            va[l][v] = __ldg(p + ca);
+            vb[l][v] = __ldg(p + cb);
+        }
+    const double t = mb - ma;
+    const float t32 = d2f_fast(t, false);
+    float acc[O][O];   // rows jx >= 1
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) acc[x][v] = 0.0f;
+    double abar = 0.0;
+    float abar32 = 0.0f, ea = 0.0f, eb = 0.0f;
+    float dev[O], a32[O];
+#pragma unroll
+    for (int q = 0; q < O; ++q) {
+        const uint32_t cls = j * O + q;
+        const double al = __ldg(a.tab.alpha + cls);
+        abar = fma(a.wmean[q], al, abar);
+        a32[q] = d2f_fast(al, false);
+        abar32 = fmaf(a.wmean32[q], a32[q], abar32);
+        float A[O][O], B[O][O];
+        load_ab<O>(a.tab, cls, A, B);
+        // node values: delta_q of row 0, U_q(l) of the others
+        float da = 0.0f, db = 0.0f;
+#pragma unroll
+        for (int v = 1; v < O; ++v) {
+            da = fmaf(va[0][v], a.eval32[q][v], da);
+            db = fmaf(vb[0][v], a.eval32[q][v], db);
+        }
+        float ua[O], ub[O];
+#pragma unroll
+        for (int l = 1; l < O; ++l) {
+            float sa = 0.0f, sb = 0.0f;
+#pragma unroll
+            for (int v = 0; v < O; ++v) {
+                sa = fmaf(va[l][v], a.eval32[q][v], sa);
+                sb = fmaf(vb[l][v], a.eval32[q][v], sb);
+            }
+            ua[l] = sa;
+            ub[l] = sb;
+        }
+        float ga = 0.0f, gb = 0.0f;
+#pragma unroll
+        for (int l = 1; l < O; ++l) {
+            ga = fmaf(A[0][l], ua[l], ga);
+            gb = fmaf(A[0][l], ub[l], gb);
+        }
+        // E(a), E(b): the same operations on each cell's own values
+        ea = fmaf(a.wmean32[q], fmaf(-a32[q], da, ga), ea);
+        eb = fmaf(a.wmean32[q], fmaf(-a32[q], db, gb), eb);
+        dev[q] = fmaf(a32[q], db - da, da) + (ga - gb);
+        // rows jx >= 1, the l = 0 term from ua0 - ub0 = -t + da - db
+        const float d0 = (da - db) - t32;
+#pragma unroll
+        for (int x = 1; x < O; ++x) {
+            float s = A[x][0] * d0;
+#pragma unroll
+            for (int l = 1; l < O; ++l) {
+                s = fmaf(A[x][l], ua[l], s);
+                s = fmaf(B[x][l], ub[l], s);
+            }
+#pragma unroll
+            for (int v = 0; v < O; ++v) acc[x][v] = fmaf(a.back32[v][q], s, acc[x][v]);
+        }
+    }
+    a.dst.mean[c] = fma(abar, t, ma) + (f2d_fast(ea) - f2d_fast(eb));
+#pragma unroll
+    for (int v = 1; v < O; ++v) {
+        float s = 0.0f;
+#pragma unroll
+        for (int q = 0; q < O; ++q) s = fmaf(a.back32[v][q], fmaf(a32[q] - abar32, t32, dev[q]), s);
+        acc[0][v] = s;
+    }
+#pragma unroll
+    for (int x = 0; x < O; ++x)
+#pragma unroll
+        for (int v = 0; v < O; ++v) {
+            if (x == 0 && v == 0) continue;
+            static_cast<float*>(a.dst.hi)[int64_t(x * a.ostride + v * a.vstride - 1) * a.pstride + c] = acc[x][v];
+        }
+}
+
 // The fibre of the cell mean in the mixed store (see the file comment).
 template <int K>
 __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
@@ -334,15 +537,19 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
 // fibre b % nfib2), so that blocks of the mean's fibre, bound by the FP64
 // pipe, run beside blocks of FP32 fibres, bound by instruction issue.
 template <int K, int MODE, int PART>
-__global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 ? 5 : 2)
+__global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 ? 4 : 2)
     k_sweep_nodal(const NodalArgs a)
 {
     constexpr int O = K + 1;
+    constexpr int FT = nodal_ft(K);
     int g = int(blockIdx.y);
     uint32_t bx = blockIdx.x;
     if constexpr (PART == 3) {
-        g = int(blockIdx.x % a.nfib2);
-        bx = blockIdx.x / a.nfib2;
+        // group 0: the mean's fibre; group r >= 1: FP32 fibres 1 + (r - 1) FT ..
+        const uint32_t ngroups = 1 + (a.nfib2 - 2) / FT + 1;
+        const int r = int(blockIdx.x % ngroups);
+        bx = blockIdx.x / ngroups;
+        g = r == 0 ? 0 : 1 + (r - 1) * FT;
     }
     const uint32_t c = bx * blockDim.x + threadIdx.x;
     if (c >= a.cells) return;
@@ -352,12 +559,26 @@ __global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 
     const uint32_t ov = a.fdInnerV.div(c);
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;       // v-cell
     const uint32_t line0 = c - i * a.inner_x;
-    if constexpr (MODE == M_FP64)
+    if constexpr (MODE == M_FP64) {
         nodal_plain<K, double>(a, c, i, line0, j, base);
-    else if (PART == 1 || g == 0)
-        nodal_mean_fibre<K>(a, c, i, line0, j);
-    else
+    } else if (PART == 1 || g == 0) {
+        // the nodes of a v-cell nearly always share sigma
+        const int32_t s0 = __ldg(a.tab.sigma + j * O);
+        bool same = true;
+#pragma unroll
+        for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
+        if (same)
+            nodal_mean_fibre_shared<K>(a, c, i, line0, j, s0);
+        else
+            nodal_mean_fibre<K>(a, c, i, line0, j);
+    } else if constexpr (PART == 3) {
+        int jb[FT];
+#pragma unroll
+        for (int u = 0; u < FT; ++u) jb[u] = nodal_fibre_base<O>(a, min(g + u, int(a.nfib2) - 1));
+        nodal_fp32_group<K, FT>(a, c, i, line0, j, jb);
+    } else {
         nodal_plain<K, float>(a, c, i, line0, j, base);
+    }
 }
 
 template <int K>
@@ -370,7 +591,7 @@ cudaError_t nodal_launch(int mode, const NodalArgs& a, int nfib2, cudaStream_t s
     } else if (nfib2 == 1) {
         k_sweep_nodal<K, M_F32, 1><<<dim3(bx, 1), block, 0, st>>>(a);
     } else {
-        const uint64_t nb = uint64_t((a.cells + 127) / 128) * uint64_t(nfib2);
+        const uint64_t nb = uint64_t((a.cells + 127) / 128) * uint64_t(1 + (nfib2 - 2) / nodal_ft(K) + 1);
         if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
         k_sweep_nodal<K, M_F32, 3><<<uint32_t(nb), 128, 0, st>>>(a);
     }
@@ -438,7 +659,10 @@ void nodal_setup(int K, double* eta, double* weights, NodalArgs* a)
         sum += a->wmean[q];
     }
     a->wmean[o - 1] = 1.0 - sum;
-    for (int q = 0; q < o; ++q) a->back64[0][q] = a->wmean[q];
+    for (int q = 0; q < o; ++q) {
+        a->back64[0][q] = a->wmean[q];
+        a->wmean32[q] = float(a->wmean[q]);
+    }
 }
 
 cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st)

@@ -24,6 +24,7 @@ struct NodalArgs {
     double eval64[kMaxO][kMaxO];   // P_jv(eta_q) at [q][jv]
     double back64[kMaxO][kMaxO];   // (2 jv + 1) / 2 w_q P_jv(eta_q) at [jv][q]; row 0 = wmean
     double wmean[kMaxO];           // w_q / 2 rounded to sum to exactly 1
+    float wmean32[kMaxO];          // the same in FP32
     float eval32[kMaxO][kMaxO];
     float back32[kMaxO][kMaxO];
 };
