@@ -156,3 +156,28 @@ def test_create_external_rejects_bad_planes_before_device_work():
     with pytest.raises(S.SlError) as e:
         S.sl_create_external(g, 1, "fp64", [256, 512 + 8, 0, 1024, 2048, 0])   # misaligned hi_0
     assert e.value.status == S.SL_EINVAL
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3, 4, 5, 6])
+def test_split_store_layout_counts_the_fp64_block(ndim):
+    """The stores of # double = q hold q^d FP64 planes and o^d - q^d FP32
+    planes (host-side layout, no device work); invalid q for the degree is
+    rejected."""
+    g = _grid((3,) * ndim)
+    cells = 3 ** ndim
+    ps = (cells + 63) // 64 * 64
+    for k in (1, 2, 3):
+        o = k + 1
+        if o ** ndim > 4096:
+            continue
+        for store, q in (("fp32", 0), ("mix_fp32", 1), ("mix_fp32_d2", 2), ("mix_fp32_d3", 3)):
+            if q > k:
+                with pytest.raises(S.SlError):
+                    S.sl_plane_layout(g, k, store)
+                continue
+            lay = S.sl_plane_layout(g, k, store)
+            assert lay["plane_stride"] == ps
+            assert lay["mean_bytes"] == q ** ndim * ps * 8
+            assert lay["hi_bytes"] == (o ** ndim - q ** ndim) * ps * 4
+            assert S.sl_state_bytes(g, k, store) == cells * (8 * q ** ndim + 4 * (o ** ndim - q ** ndim))
+            assert S.plane_counts(ndim, k, store) == (q ** ndim, o ** ndim - q ** ndim)
