@@ -455,6 +455,10 @@ def run_ours(args):
         ms64_max, units64 = aggregate(ms64, units_local, world, dev)
         v64 = units64 / (ms64_max / 1000.0)
         nl64, sms64, sb64 = prof64
+        if nl64 == 0:   # graph replay: the step time per sweep, as for the timed arm
+            nl64 = args.steps * info64["sweeps"]
+            sms64 = ms64
+            sb64 = 2.0 * info64["state_bytes"] * nl64
         # The FP64 store's sweep is bound by the FP64 pipe, not by HBM: 2o FMAs
         # (4o flops) per DoF update against 2 FP64 FMAs per clock per SM
         # (1.25 TFLOP/s nominal at 152 SMs and 2.07 GHz).
