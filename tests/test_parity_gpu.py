@@ -693,7 +693,9 @@ def test_lie_splitting_matches_oracle(cfg, storage):
 
 
 @pytest.mark.parametrize("storage,n,k", [("mix_fp32", (9, 6), 2), ("fp64", (7, 5, 3), 1),
-                                         ("mix_bf16", (3, 2, 2, 3, 2, 2), 1), ("mix_fp16", (5, 4, 3), 2)])
+                                         ("mix_bf16", (3, 2, 2, 3, 2, 2), 1), ("mix_fp16", (5, 4, 3), 2),
+                                         ("fp32", (9, 6), 2), ("mix_fp32_d2", (7, 5, 3), 2),
+                                         ("mix_fp32_d3", (6, 5), 3)])
 def test_external_planes_give_the_same_results(storage, n, k):
     """A context over caller-owned planes (torch tensors) computes exactly
     what a context with library-owned state computes, and the current state
@@ -720,6 +722,10 @@ def test_external_planes_give_the_same_results(storage, n, k):
             b.advect(dim, -1, s)
         assert np.array_equal(a.get_coeffs(), b.get_coeffs())
         cur = len(n) % 2                       # copy holding the state after len(n) sweeps
-        mean = bufs[3 * cur].view(torch.float64)[: int(np.prod(n))].cpu().numpy()
-        assert np.array_equal(mean, b.get_coeffs()[:, 0])
+        if lay["mean_bytes"]:                  # the FP64 block starts with the cell means
+            mean = bufs[3 * cur].view(torch.float64)[: int(np.prod(n))].cpu().numpy()
+            assert np.array_equal(mean, b.get_coeffs()[:, 0])
+        else:                                  # the all-FP32 store: the means are FP32 plane 0
+            mean = bufs[3 * cur + 1].view(torch.float32)[: int(np.prod(n))].cpu().numpy()
+            assert np.array_equal(mean.astype(np.float64), b.get_coeffs()[:, 0])
     del bufs
