@@ -397,6 +397,7 @@ cudaError_t launch_nodal_only(sl_ctx* c, int dim)
     a.xdim = dim;
     a.vdim = p;
     a.nfib2 = uint32_t(ipow(c->O, c->ndim - 2));
+    a.off32 = double(c->pstride) * double(c->ncoef) < 2147483648.0 ? 1 : 0;
     double eta[kMaxO], w[kMaxO];
     nodal_setup(c->K, eta, w, &a);
     return launch_sweep_nodal(c->K, c->mode, a, int(ipow(c->O, c->ndim - 2)), c->st);

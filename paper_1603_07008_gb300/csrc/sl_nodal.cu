@@ -225,8 +225,10 @@ __device__ __forceinline__ void nodal_plain(const NodalArgs& a, uint32_t c, uint
 }
 
 // FT FP32 fibres of the mixed store in one thread (bases jb[u]): the thread's
-// index arithmetic, sigma and the node tables serve all of them.
-template <int K, int FT>
+// index arithmetic, sigma and the node tables serve all of them.  OFF32: the
+// FP32 block has fewer than 2^31 elements, so every address is the block's
+// base plus a 32-bit element offset.
+template <int K, int FT, bool OFF32>
 __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
                                                  uint32_t j, const int (&jb)[FT])
 {
@@ -245,9 +247,17 @@ __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c,
             for (int l = 0; l < O; ++l)
 #pragma unroll
                 for (int v = 0; v < O; ++v) {
-                    const float* p = coef_plane<float>(a.src, a.pstride, jb[u] + l * a.ostride + v * a.vstride);
-                    va[u][l][v] = __ldg(p + ca);
-                    vb[u][l][v] = __ldg(p + cb);
+                    const int J = jb[u] + l * a.ostride + v * a.vstride;
+                    if constexpr (OFF32) {
+                        const float* h = static_cast<const float*>(a.src.hi);
+                        const uint32_t po = uint32_t(J - 1) * uint32_t(a.pstride);
+                        va[u][l][v] = __ldg(h + (po + ca));
+                        vb[u][l][v] = __ldg(h + (po + cb));
+                    } else {
+                        const float* p = coef_plane<float>(a.src, a.pstride, J);
+                        va[u][l][v] = __ldg(p + ca);
+                        vb[u][l][v] = __ldg(p + cb);
+                    }
                 }
     };
     int32_t sg[O];
@@ -302,9 +312,13 @@ __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c,
 #pragma unroll
         for (int x = 0; x < O; ++x)
 #pragma unroll
-            for (int v = 0; v < O; ++v)
-                static_cast<float*>(a.dst.hi)[int64_t(jb[u] + x * a.ostride + v * a.vstride - 1) * a.pstride + c] =
-                    acc[u][x][v];
+            for (int v = 0; v < O; ++v) {
+                const int J = jb[u] + x * a.ostride + v * a.vstride;
+                if constexpr (OFF32)
+                    static_cast<float*>(a.dst.hi)[uint32_t(J - 1) * uint32_t(a.pstride) + c] = acc[u][x][v];
+                else
+                    static_cast<float*>(a.dst.hi)[int64_t(J - 1) * a.pstride + c] = acc[u][x][v];
+            }
 }
 
 // The fibre of the cell mean in the mixed store when the o nodes of the
@@ -575,7 +589,10 @@ __global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 
         int jb[FT];
 #pragma unroll
         for (int u = 0; u < FT; ++u) jb[u] = nodal_fibre_base<O>(a, min(g + u, int(a.nfib2) - 1));
-        nodal_fp32_group<K, FT>(a, c, i, line0, j, jb);
+        if (a.off32)
+            nodal_fp32_group<K, FT, true>(a, c, i, line0, j, jb);
+        else
+            nodal_fp32_group<K, FT, false>(a, c, i, line0, j, jb);
     } else {
         nodal_plain<K, float>(a, c, i, line0, j, base);
     }
