@@ -480,6 +480,9 @@ sl_status sl_batch_profile_dims(const sl_batch* batch, int64_t* launches, double
  *                      memory (FP64 and FP32 stores, dimensions > 0, with 1 or
  *                      2 fibres per thread, or 3 with pipeline 4; unroll
  *                      is ignored)
+ *   The stores of # double = 2, 3 (SL_MIX_FP32_D2/D3) take fibres_per_thread 1,
+ *   unroll 1 along dimension 0 and 1 or 2 elsewhere, block <= 256 / 128, no
+ *   pipeline and no block limit; SL_FP32 takes every shape of SL_MIX_FP32.
  * Every shape computes the same result; only the speed differs. */
 typedef struct {
     int32_t block;
