@@ -40,6 +40,9 @@
  *                power of two stored in an FP32 plane; arithmetic in FP32.
  *                (Not in the paper: a further compression step of the same
  *                idea.)  Requires o^d <= 128.
+ *   SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3
+ *                the paper's other "# double" columns: 0, 2 and 3 coefficients
+ *                per dimension in FP64 (see sl_storage below).
  *
  * Memory: sl_create allocates the device state (two copies, ping-pong) with
  * cudaMalloc and owns it; sl_destroy frees it.  Host arrays passed in are
@@ -73,7 +76,7 @@ typedef enum {
     SL_EINVAL = -1,    /* invalid argument (grid, degree, dimension, size, non-finite value) */
     SL_ENOMEM = -2,    /* device or host allocation failed */
     SL_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
-    SL_ETIMEOUT = -4,  /* a bounded device-side loop gave up (error flag set by a kernel) */
+    SL_ETIMEOUT = -4,  /* reserved for a bounded device-side wait; no kernel of this build waits */
     SL_ENAN = -5,      /* non-finite value in an input array */
     SL_ENOTSUP = -6    /* valid request this build does not support (e.g. scaled mode with o^d > 128) */
 } sl_status;
@@ -125,7 +128,8 @@ typedef struct {
     int64_t ncoef;          /* o^d */
     int64_t dof;            /* cells * ncoef */
     int64_t plane_stride;   /* elements between consecutive coefficient planes */
-    int64_t state_bytes;    /* algorithmic bytes of one state: cells * (8 + (o^d-1) * elem [+ 4 scale]) */
+    int64_t state_bytes;    /* algorithmic bytes of one state: cells * (8 + (o^d-1) * elem [+ 4 scale]),
+                               cells * (8 n_lo + 4 n_hi) for the split stores (sl_plane_layout) */
     int64_t alloc_bytes;    /* device bytes allocated by the context (both copies + tables) */
     int32_t degree;
     int32_t storage;        /* sl_storage */
