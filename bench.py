@@ -269,8 +269,10 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * secs / max(args.steps, 1), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "4d_xxvv_k2 Strang step on a 32x32x16x16 sub-grid of the 64^4 "
-                               "workload (CPU oracle)", "l2": "host run"},
+        "config": {"workload": "4d_xxvv_64^4_k2_mix_fp32_strang",
+                   "sample": "each step one Strang step of the oracle (FP64) on a 32x32x16x16 sub-grid of "
+                             "that workload, reported per DoF update",
+                   "l2": "host run", "parallelism": "rank 0 only"},
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{args.steps} Strang steps (6 sweeps) of the 4D k=2 workload "
                                    f"on a 32x32x16x16 sub-grid, FP64 oracle, single thread"},
