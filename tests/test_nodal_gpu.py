@@ -183,3 +183,50 @@ def test_nodal_rejections():
             c.advect_nodal(1, 0.3)          # dimension 1 is the v-dimension
         with pytest.raises(S.SlError):
             c.advect_nodal(0, float("nan"))
+
+
+def test_nodal_full_size_sampled_after_one_x_sweep():
+    """4D 64^4, k = 2, mixed store (the bench's nodal configuration): one
+    nodal x-sweep along dimension 0 over dt / 2, sampled target cells against
+    the oracle on a small (x, v) problem cut out around each: the x-cells that
+    the target's nodes read, one v-cell with the same velocity range, and the
+    nine fibres of the other two indices one by one."""
+    p = W.config3(n=64, steps=1)
+    g, k, o = p.grid, p.k, p.k + 1
+    n = g.n
+    hx = (g.hi[0] - g.lo[0]) / n[0]
+    hv = (g.hi[2] - g.lo[2]) / n[2]
+    tau = 0.5 * p.dt
+    eta, _ = O.gauss_legendre(o)
+    rng = np.random.default_rng(21)
+    cells = rng.integers(0, int(np.prod(n)), size=40).astype(np.int64)
+    cells = np.concatenate([cells, [0, int(np.prod(n)) - 1]])
+    with S.Context(g, k, "mix_fp32") as ctx:
+        ctx.project(p.nq, p.weights, p.params)
+        ctx.set_fields(p.field_list())
+        plans, need = [], []
+        for c in cells:
+            i0, i1, i2, i3 = c % 64, (c // 64) % 64, (c // 4096) % 64, c // 262144
+            sig = [O.shift_split((g.lo[2] + (i2 + 0.5 + 0.5 * e) * hv) * tau / hx)[0] for e in eta]
+            dlo, dhi = min(min(sig), 0), max(max(sig) + 1, 0)
+            xs = [(i0 - d) % 64 for d in range(dhi, dlo - 1, -1)]       # mini index 0 .. W-1
+            win = [x + 64 * (i1 + 64 * (i2 + 64 * i3)) for x in xs]
+            plans.append((i2, dhi, len(win)))
+            need.extend(win)
+        src = ctx.get_cells(np.array(need, dtype=np.int64))
+        ctx.advect_nodal(0, tau)
+        got = ctx.get_cells(cells)
+    ref = np.empty_like(got)
+    pos = 0
+    for r, (j, dhi, wlen) in enumerate(plans):
+        block = src[pos:pos + wlen]
+        pos += wlen
+        mini = W.Grid(n=(wlen, 1), lo=(0.0, g.lo[2] + j * hv), hi=(wlen * hx, g.lo[2] + (j + 1) * hv), pair=(1, -1))
+        for j1 in range(o):
+            for j3 in range(o):
+                idx = [j0 + o * j1 + o * o * j2 + o ** 3 * j3 for j2 in range(o) for j0 in range(o)]
+                u2 = block[:, idx]                        # mini coefficient j0 + o j2
+                out = O.sweep_nodal(u2, mini, k, 0, tau)
+                ref[r, idx] = out[dhi]
+    assert O.rel_l2(got, ref, k, 4) <= 1e-6
+    assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(ref[:, 1:]))

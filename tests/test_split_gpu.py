@@ -281,3 +281,32 @@ def test_self_consistent_field_reads_the_fp64_mean():
         with pytest.raises(S.SlError) as e:
             c.set_poisson(True)
         assert e.value.status == S.SL_ENOTSUP
+
+
+@pytest.mark.parametrize("storage", ["mix_fp32_d2", "mix_fp32_d3", "fp32"])
+def test_paper1d_full_size_sampled(storage):
+    """The 1D workload of the paper's tables at the bench's size (order 4,
+    N = 2^27, default shapes): one sweep, sampled target cells against the
+    oracle applied to the stored source cells of each (a two-cell periodic
+    problem with the same shift reproduces the update rule of one target)."""
+    import math
+    k, N, shift = 3, 1 << 27, 0.37
+    q = Q[storage]
+    g = W.Grid(n=(N,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    rng = np.random.default_rng(12)
+    cells = np.unique(np.concatenate([[0, 1, N - 1], rng.integers(0, N, size=61)])).astype(np.int64)
+    with S.Context(g, k, storage) as ctx:
+        ctx.project(k + 2, [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]])
+        src = ctx.get_cells(np.concatenate([cells, (cells - 1) % N]))
+        m0 = ctx.mass()
+        ctx.advect(0, -1, [shift])
+        got = ctx.get_cells(cells)
+        m1 = ctx.mass()
+    a, b = src[: cells.size], src[cells.size:]
+    ref = np.empty_like(got)
+    for r in range(cells.size):
+        u2 = np.stack([b[r], a[r]])          # cells i - 1, i of a two-cell line
+        ref[r] = O.stored_sweeps(u2, (2,), k, q, [(0, -1, [shift])])[1]
+    assert O.rel_l2(got, ref, k, 1) <= 1e-6
+    if q >= 1:
+        assert abs(m1 - m0) <= 1e-13 * abs(m0)
