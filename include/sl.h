@@ -346,6 +346,14 @@ sl_status sl_mass_noalloc(const double* d_mean, int64_t cells, double cell_volum
  * SL_ENOMEM, SL_ECUDA; sl_last_error does not cover this call. */
 sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
                                   double* d_out, int64_t* mismatches);
+/* Self-test of the device-side difference of two widened binary32 values the
+ * mean row uses: out[i] = (double)a[i] - (double)b[i], formed on the integer
+ * pipe when exact (both normal, exponents at most 28 apart) and by the FP64
+ * subtraction otherwise (binary32 subnormal inputs as in sl_selftest_conversions).
+ * *mismatches = elements on which the integer form and the FP64 subtraction
+ * disagree (must be 0).  Host arrays of n elements (1 <= n <= 2^26).
+ * Synchronous, on the default stream.  Errors: SL_EINVAL, SL_ENOMEM, SL_ECUDA. */
+sl_status sl_selftest_sub_widened(const float* a, const float* b, int64_t n, double* out, int64_t* mismatches);
 
 /* Self-consistent field (NEXT to the sweep: the Vlasov-Poisson system of
  * Sec. II in 1+1 dimensions).  For a grid with one x dimension paired with

@@ -35,7 +35,7 @@ __all__ = [
     "sl_batch_get_tune", "sl_batch_set_tune", "sl_selftest_conversions", "sl_set_poisson", "sl_get_field",
     "sl_field_energy", "sl_graph_capture_advect", "sl_create_external", "sl_plane_layout",
     "sl_set_nodal_velocity", "sl_advect_nodal", "sl_check_guards", "sl_debug_fail_alloc",
-    "sl_debug_corrupt_guard", "save_checkpoint", "load_checkpoint", "autotune_cached",
+    "sl_debug_corrupt_guard", "save_checkpoint", "load_checkpoint", "autotune_cached", "sl_selftest_sub_widened",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
@@ -172,6 +172,8 @@ def lib():
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
             "sl_set_nodal_velocity": (st, [_vp, ctypes.c_int]),
             "sl_check_guards": (st, [_vp, _i64p]),
+            "sl_selftest_sub_widened": (st, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
+                                             ctypes.c_int64, _dp, _i64p]),
             "sl_debug_fail_alloc": (st, [ctypes.c_int64]),
             "sl_debug_corrupt_guard": (st, [_vp]),
             "sl_advect_nodal": (st, [_vp, ctypes.c_int, ctypes.c_double]),
@@ -476,6 +478,19 @@ def sl_set_nodal_velocity(ctx, enable=True):
 
 def sl_advect_nodal(ctx, dim: int, tau: float):
     _check(lib().sl_advect_nodal(ctx, int(dim), float(tau)), ctx)
+
+
+def sl_selftest_sub_widened(a, b):
+    """(float64(a) - float64(b) as the library's mean row forms it, mismatches
+    between its integer-pipe and FP64 forms)."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float32)
+    out = np.empty(a.size, dtype=np.float64)
+    mm = ctypes.c_int64()
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(lib().sl_selftest_sub_widened(a.ctypes.data_as(fp), b.ctypes.data_as(fp), a.size, _ptr(out),
+                                         ctypes.byref(mm)))
+    return out, mm.value
 
 
 def sl_check_guards(ctx) -> int:

@@ -400,7 +400,45 @@ __global__ void k_conv_check(const double* __restrict__ din, const float* __rest
     if (!same) atomicAdd(mism, 1ull);
 }
 
+// sub_widened against the FP64 subtraction of the widened operands.
+__global__ void k_sub_check(const float* __restrict__ a, const float* __restrict__ b, uint32_t n,
+                            double* __restrict__ out, unsigned long long* __restrict__ mism)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double r = sub_widened(a[i], b[i]);
+    const double f = f2d_fast(a[i]) - f2d_fast(b[i]);
+    out[i] = r;
+    if (!(__double_as_longlong(r) == __double_as_longlong(f) || (r != r && f != f))) atomicAdd(mism, 1ull);
+}
+
 }  // namespace sl
+
+extern "C" sl_status sl_selftest_sub_widened(const float* a, const float* b, int64_t n, double* out,
+                                             int64_t* mismatches)
+{
+    if (!a || !b || !out || !mismatches || n < 1 || n > (int64_t(1) << 26)) return SL_EINVAL;
+    const size_t N = size_t(n);
+    char* mem = nullptr;
+    if (cudaMalloc(&mem, N * (4 + 4 + 8) + 16) != cudaSuccess) return SL_ENOMEM;
+    unsigned long long* mism = reinterpret_cast<unsigned long long*>(mem);
+    double* dout = reinterpret_cast<double*>(mem + 16);
+    float* fa = reinterpret_cast<float*>(dout + N);
+    float* fb = fa + N;
+    cudaError_t e = cudaMemset(mism, 0, 8);
+    if (e == cudaSuccess) e = cudaMemcpy(fa, a, N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(fb, b, N * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        sl::k_sub_check<<<unsigned((N + 255) / 256), 256>>>(fa, fb, uint32_t(N), dout, mism);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, N * 8, cudaMemcpyDeviceToHost);
+    unsigned long long mm = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&mm, mism, 8, cudaMemcpyDeviceToHost);
+    *mismatches = int64_t(mm);
+    cudaFree(mem);
+    return e == cudaSuccess ? SL_OK : SL_ECUDA;
+}
 
 extern "C" sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t n, float* f_out,
                                              double* d_out, int64_t* mismatches)

@@ -194,13 +194,41 @@ __device__ __forceinline__ float d2f_branch(double x, bool neg)
     return d2f_fast(x, neg);
 }
 
+// f2d_fast(a) - f2d_fast(b) for binary32 a, b.  When both are normal and
+// their exponents differ by at most 28, the difference of the two 24-bit
+// significands aligned to the smaller exponent has fewer than 53 bits, so it
+// is exact in binary64 (the FP64 subtraction would return it unrounded) and is
+// assembled here on the integer pipe; otherwise the FP64 subtraction forms it.
+// Either way the bits are those of the FP64 subtraction.
+__device__ __forceinline__ double sub_widened(float a, float b)
+{
+    const uint32_t ua = __float_as_uint(a), ub = __float_as_uint(b);
+    const uint32_t ea = (ua >> 23) & 0xffu, eb = (ub >> 23) & 0xffu;
+    const uint32_t lo = min(ea, eb);
+    if (ea - 1u >= 254u || eb - 1u >= 254u || max(ea, eb) - lo > 28u) return f2d_fast(a) - f2d_fast(b);
+    const int64_t ma = int64_t((ua & 0x7fffffu) | 0x800000u) << (ea - lo);
+    const int64_t mb = int64_t((ub & 0x7fffffu) | 0x800000u) << (eb - lo);
+    const int64_t r = ((ua >> 31) ? -ma : ma) - ((ub >> 31) ? -mb : mb);   // times 2^(lo - 150)
+    if (r == 0) return 0.0;
+    const uint64_t m = uint64_t(r < 0 ? -r : r);   // below 2^53
+    const int lz = __clzll(int64_t(m));            // at least 11
+    const uint64_t frac = (m << (lz - 11)) & 0xfffffffffffffull;
+    const uint64_t bexp = uint64_t(int(lo) - 150 + (63 - lz) + 1023);
+    return __longlong_as_double(int64_t((r < 0 ? 0x8000000000000000ull : 0ull) | (bexp << 52) | frac));
+}
+
 // New mean of a cell in the low-precision stores (conservation form, see
 // combine) from the source means ma (cell i - sigma), mb (i - sigma - 1) and
 // their per-cell FP32 sums ga = G(a), gb = G(b); dm = fl32(ma - mb) for the
-// l = 0 term of the other rows: four FP64-pipe instructions.
-// Conversion forms of the mean row, picked per kernel by measurement; both
-// give the same bits (the integer-pipe forms above).
-enum : int { CV_FLAT = 0, CV_BRANCH = 1 };
+// l = 0 term of the other rows: three FP64-pipe instructions when the
+// difference of the widened sums is formed on the integer pipe (sub_widened),
+// four with the FP64 subtraction.
+// Forms of the mean row, picked per kernel by measurement; all give the same
+// bits.  CV_FLAT: branch-free conversions, the difference of the widened sums
+// on the integer pipe (sub_widened); CV_BRANCH: the branching conversions,
+// sub_widened; CV_FP64SUB: branch-free conversions, the difference by the
+// FP64 subtraction (for kernels whose integer pipe is the busier one).
+enum : int { CV_FLAT = 0, CV_BRANCH = 1, CV_FP64SUB = 2 };
 
 template <int CV = CV_FLAT>
 __device__ __forceinline__ double mean_row_lp(double alpha, double ma, double mb, float ga, float gb, float& dm)
@@ -208,10 +236,13 @@ __device__ __forceinline__ double mean_row_lp(double alpha, double ma, double mb
     const double t = mb - ma;
     if constexpr (CV == CV_BRANCH) {
         dm = d2f_branch(t, true);
-        return fma(alpha, t, ma) + (f2d_branch(ga) - f2d_branch(gb));
-    } else {
+        return fma(alpha, t, ma) + sub_widened(ga, gb);
+    } else if constexpr (CV == CV_FP64SUB) {
         dm = d2f_fast(t, true);
         return fma(alpha, t, ma) + (f2d_fast(ga) - f2d_fast(gb));
+    } else {
+        dm = d2f_fast(t, true);
+        return fma(alpha, t, ma) + sub_widened(ga, gb);
     }
 }
 

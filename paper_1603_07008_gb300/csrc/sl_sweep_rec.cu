@@ -96,7 +96,9 @@ __device__ __forceinline__ void lg_combine(const Mats<1, MODE>& T, const LgRow& 
             ga = fmaf(T.a[0][1], a1, ga);
             gb = fmaf(T.a[0][1], b1, gb);
             float dm;
-            om = mean_row_lp(T.alpha, ra.m, rb.m, ga, gb, dm);
+            // FP64 subtraction: these kernels keep the integer pipe busier than
+            // the FP64 pipe (the integer-pipe difference measured 5% slower)
+            om = mean_row_lp<CV_FP64SUB>(T.alpha, ra.m, rb.m, ga, gb, dm);
             float acc = T.a[1][0] * dm;
             acc = fmaf(T.a[1][1], a1, acc);
             acc = fmaf(T.b[1][1], b1, acc);

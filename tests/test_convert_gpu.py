@@ -79,3 +79,30 @@ def test_conversion_selftest_rejects_bad_sizes():
         S.sl_selftest_conversions(np.zeros(3), np.zeros(2, np.float32))
     st = S.lib().sl_selftest_conversions(None, None, 0, None, None, None)
     assert st == S.SL_EINVAL
+
+
+def test_widened_difference_is_the_fp64_subtraction():
+    """The mean row's difference of two widened per-cell FP32 sums, formed on
+    the integer pipe when exact: bit for bit the IEEE FP64 subtraction of the
+    widened values (outside the binary32 subnormal range), on neighbour-like
+    pairs (close values, every sign), pairs 0..40 binades apart, equal values,
+    zeros, extremes, infinities and NaN."""
+    rng = np.random.default_rng(9)
+    n = 100000
+    x = (rng.standard_normal(n) * np.exp2(rng.integers(-120, 120, n))).astype(np.float32)
+    near = (x * (1 + rng.standard_normal(n) * np.exp2(rng.integers(-24, 0, n)))).astype(np.float32)
+    far = (x * np.exp2(rng.integers(-40, 41, n)) * rng.choice([-1.0, 1.0], n)).astype(np.float32)
+    f32 = np.finfo(np.float32)
+    special = np.array([0.0, -0.0, 1.0, -1.0, f32.max, -f32.max, f32.tiny, -f32.tiny, np.inf, -np.inf, np.nan,
+                        2.0 ** 100, 2.0 ** -100], dtype=np.float32)
+    sa, sb = np.meshgrid(special, special)
+    a = np.concatenate([x, x, x, sa.ravel()])
+    b = np.concatenate([near, far, x, sb.ravel()])
+    out, mism = S.sl_selftest_sub_widened(a, b)
+    assert mism == 0
+    want = a.astype(np.float64) - b.astype(np.float64)
+    normal = (np.abs(a) >= f32.tiny) | (a == 0) | ~np.isfinite(a)
+    normal &= (np.abs(b) >= f32.tiny) | (b == 0) | ~np.isfinite(b)
+    ok = normal & ~np.isnan(want)
+    assert np.array_equal(_bits64(out[ok]), _bits64(want[ok]))
+    assert np.all(np.isnan(out[np.isnan(want) & normal]))
