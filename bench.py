@@ -171,21 +171,21 @@ def summarise_clocks(lines):
 # traffic is reported as null.
 TRAFFIC = {
     ("4d", "mix_fp32"): {
-        "ratio": (2 * 0.98532 + 2 * 1.00212 + 2 * 1.00721) / 6,
+        "ratio": (2 * 0.98550 + 2 * 1.00206 + 2 * 1.00737) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "c25b789ce3578fbd",
+        "sha256": "ac91a006f047484d",
         "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
                    "1 fibres) against 3.483 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
     ("6d", "mix_bf16"): {
-        "ratio": (2 * 1.03611 + 7 * 1.03695) / 9,
+        "ratio": (2 * 1.03530 + 7 * 1.03691) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "24af3214783b5368",
-        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.798 / 4.802 GB per launch (dimensions 0, "
+        "sha256": "5424e174e5f11611",
+        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.795 / 4.802 GB per launch (dimensions 0, "
                    "1) against 4.631 GB algorithmic (profiles/sweep_6d_n16_lane_records_bf16.md)"},
     ("batch", "mix_fp32"): {
-        "ratio": (2 * 0.95830 + 1.04223) / 3,
+        "ratio": (2 * 0.95799 + 1.04195) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
-        "sha256": "2f4bcda6db02243b",
+        "sha256": "36d89809795b4a94",
         "capture": "64 problems, default shapes; 1.046 / 1.138 GB per launch (dimensions 0, 1) against "
                    "1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
 }
