@@ -28,8 +28,9 @@
 // The identities used are the projection's: A_00 + B_00 = 1, B_0l = -A_0l
 // (l >= 1) and B_j0 = -A_j0 (j >= 1).  F fibres are computed in FP32.
 //
-// An S fibre costs 10 (q = 2) or 20 (q = 3) FP64-pipe instructions per target
-// cell.  GB300 issues FP64 at a small fraction of its FP32 rate, so in one
+// An S fibre costs 9 (q = 2) or 19 (q = 3) FP64-pipe instructions per target
+// cell (the difference G(a) - G(b) is formed on the integer pipe, sub_widened).
+// GB300 issues FP64 at a small fraction of its FP32 rate, so in one
 // dimension these stores are bound by the FP64 pipe, not by HBM; the
 // conversions run on the integer pipe (f2d_fast, d2f_fast) and the per-cell
 // values G(c) and fl32(c_l) are formed once per source cell in the walks.
@@ -84,7 +85,7 @@ struct SCell {
     static constexpr int O = K + 1;
     double d[Q];       // entries 0 .. q-1
     float f[O - Q];    // entries q .. o-1
-    double gd;         // G(c), exactly widened
+    float g;           // G(c)
     float r[Q];        // fl32(d[l]) for l >= 1
 };
 
@@ -95,7 +96,7 @@ __device__ __forceinline__ void s_prepare(const SMats<K, Q>& M, SCell<K, Q>& v)
     float g = 0.0f;
 #pragma unroll
     for (int l = Q; l < O; ++l) g = fmaf(M.a[0][l], v.f[l - Q], g);
-    v.gd = f2d_fast(g);
+    v.g = g;
     v.r[0] = 0.0f;
 #pragma unroll
     for (int l = 1; l < Q; ++l) v.r[l] = d2f_fast(v.d[l], false);
@@ -110,7 +111,7 @@ __device__ __forceinline__ void s_combine(const SMats<K, Q>& M, const SCell<K, Q
     double r = fma(M.alpha, t0, a.d[0]);
 #pragma unroll
     for (int l = 1; l < Q; ++l) r = fma(M.a64[0][l], a.d[l] - b.d[l], r);
-    od[0] = r + (a.gd - b.gd);
+    od[0] = r + sub_widened(a.g, b.g);
 #pragma unroll
     for (int j = 1; j < Q; ++j) {
         float p = 0.0f;
