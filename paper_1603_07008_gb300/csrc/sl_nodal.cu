@@ -331,8 +331,9 @@ __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c,
 // because sum_q w'_q delta_q(c) = 0 (the Gauss rule of P_jv, jv >= 1).  E is a
 // function of one cell (alpha_q and the matrices are fixed along a line), so
 // it is formed in FP32 and the FP64 differences E(a) - E(b) telescope along
-// the line: mass is conserved to FP64 rounding with six FP64 instructions
-// per cell (the difference E(a) - E(b) on the integer pipe, sub_widened).  The other coefficients of row 0 take the nodes' deviations from
+// the line: mass is conserved to FP64 rounding with seven FP64 instructions
+// per cell (the FP64 pipe is not what bounds this kernel: the integer-pipe
+// difference of sub_widened measured 11% slower in 2D).  The other coefficients of row 0 take the nodes' deviations from
 // m_a + alpha_bar t, d_q = delta_q(a) + alpha_q (delta_q(b) - delta_q(a))
 // + G_q(a) - G_q(b) + (alpha_q - alpha_bar) t, in FP32.
 template <int K>
@@ -419,7 +420,7 @@ __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint
             for (int v = 0; v < O; ++v) acc[x][v] = fmaf(a.back32[v][q], s, acc[x][v]);
         }
     }
-    a.dst.mean[c] = fma(abar, t, ma) + sub_widened(ea, eb);
+    a.dst.mean[c] = fma(abar, t, ma) + (f2d_fast(ea) - f2d_fast(eb));
 #pragma unroll
     for (int v = 1; v < O; ++v) {
         float s = 0.0f;
@@ -510,7 +511,7 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
             gb = fmaf(A[0][l], ub[l], gb);
         }
         const double t = ub0 - ua0;
-        up0[q] = fma(__ldg(a.tab.alpha + cls), t, ua0) + sub_widened(ga, gb);
+        up0[q] = fma(__ldg(a.tab.alpha + cls), t, ua0) + (f2d_fast(ga) - f2d_fast(gb));
         // rows jx >= 1 in FP32, the l = 0 term from fl32(ua0 - ub0)
         const float dm = d2f_fast(t, true);
 #pragma unroll
