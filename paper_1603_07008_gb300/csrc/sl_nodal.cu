@@ -108,8 +108,9 @@ __device__ __forceinline__ const T* coef_plane(const Planes& p, int64_t ps, int 
     return static_cast<const T*>(p.hi) + int64_t(J - 1) * ps;
 }
 
-// FP64 store, or an FP32 fibre of the mixed store (no FP64 entry): the whole
-// computation in the store's type R.
+// Every fibre of the FP64 store (R = double), the whole computation in FP64;
+// for R = float the same steps in FP32 (the mixed store's FP32 fibres take
+// the grouped form, nodal_fp32_group).
 template <int K, typename R>
 __device__ __forceinline__ void nodal_plain(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0, uint32_t j,
                                             int base)
@@ -594,8 +595,6 @@ __global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 
             nodal_fp32_group<K, FT, true>(a, c, i, line0, j, jb);
         else
             nodal_fp32_group<K, FT, false>(a, c, i, line0, j, jb);
-    } else {
-        nodal_plain<K, float>(a, c, i, line0, j, base);
     }
 }
 
