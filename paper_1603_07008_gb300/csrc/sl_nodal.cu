@@ -11,12 +11,14 @@
 // coefficients are the o-point Gauss rule of the new nodal values,
 // c'_{jx,jv} = (2 jv + 1) / 2 sum_q w_q P_jv(eta_q) U'_q(jx) (eq. (cj) along v).
 //
-// One thread per target cell and fibre of coefficients varying in (j_m, j_p)
-// (blockIdx.y), for any x-dimension: consecutive threads take consecutive
+// One thread per target cell and group of fibres of coefficients varying in
+// (j_m, j_p), for any x-dimension: consecutive threads take consecutive
 // cells, so every plane access is coalesced; the source cells of a node are
 // the target's line shifted by sigma_q, and the nodes' source cells, equal
 // for most cells (the node shifts of one v-cell differ by h_p tau / h_m),
-// are loaded once per distinct sigma.
+// are loaded once per distinct sigma.  Along x-dimensions > 0 the FP32
+// fibres of the mixed store take a run of consecutive targets per thread
+// instead, and each source cell's node values are formed once per run.
 //
 // Stores: FP64, and the mixed FP32 store.  In the mixed store the fibre of
 // the cell mean keeps everything that reaches the mean in FP64: the node
@@ -38,8 +40,11 @@ namespace {
 
 // FP32 fibres per thread of the mixed store's nodal sweep (as many as fit
 // the registers without spilling: measured 17% faster with 2 than with 1 at
-// k = 2).
+// k = 2) ...
 __host__ __device__ constexpr int nodal_ft(int K) { return K <= 1 ? 4 : K == 2 ? 2 : 1; }
+// ... and of its walk form, which also holds the node values of two source
+// cells per fibre.
+__host__ __device__ constexpr int nodal_ftw(int K) { return K == 0 ? 4 : K == 3 ? 1 : 2; }
 
 // Base coefficient index of 2D fibre g: its digits along the dimensions other
 // than x and v, in increasing dimension order.
@@ -322,6 +327,110 @@ __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c,
             }
 }
 
+// Targets per run of the walk form (kernel part 4).
+constexpr int kNodalRun = 4;
+
+// The FT FP32 fibres of nodal_fp32_group for the run of cnt <= kNodalRun
+// consecutive targets i0 .. i0 + cnt - 1 of one x-line whose v-cell j has one
+// sigma for all its nodes.  Target i reads the source cells a = i - sigma and
+// b = i - sigma - 1, and the a of target i is the b of target i + 1, so the
+// node values U_q(l) = sum_v c_{l,v} P_v(eta_q) of each source cell are
+// formed once along the run (cnt + 1 cells) instead of twice per target.
+// Every sum is taken in the order of nodal_fp32_group, so the results are
+// the same bits.
+template <int K, int FT, bool OFF32>
+__device__ __forceinline__ void nodal_fp32_walk(const NodalArgs& a, uint32_t line0, uint32_t i0, int cnt,
+                                                uint32_t j, int32_t sig, const int (&jb)[FT])
+{
+    constexpr int O = K + 1;
+    const int32_t N = int32_t(a.N);
+    // node values of the source cell at x along the line
+    auto node_values = [&](int32_t x, float (&U)[FT][O][O]) {
+        const uint32_t cx = line0 + uint32_t(x) * a.inner_x;
+        float v[FT][O][O];
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l)
+#pragma unroll
+                for (int w = 0; w < O; ++w) {
+                    const int J = jb[u] + l * a.ostride + w * a.vstride;
+                    if constexpr (OFF32) {
+                        const float* h = static_cast<const float*>(a.src.hi);
+                        v[u][l][w] = __ldg(h + (uint32_t(J - 1) * uint32_t(a.pstride) + cx));
+                    } else {
+                        v[u][l][w] = __ldg(coef_plane<float>(a.src, a.pstride, J) + cx);
+                    }
+                }
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int q = 0; q < O; ++q)
+#pragma unroll
+                for (int l = 0; l < O; ++l) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int w = 0; w < O; ++w) s = fmaf(v[u][l][w], a.eval32[q][w], s);
+                    U[u][q][l] = s;
+                }
+    };
+    int32_t xb = int32_t(i0) - sig - 1;   // sigma is in [0, N)
+    xb += xb < 0 ? N : 0;
+    float Ub[FT][O][O], Ua[FT][O][O];
+    node_values(xb, Ub);
+    for (int r = 0; r < kNodalRun; ++r) {
+        if (r >= cnt) break;
+        int32_t xa = xb + 1;
+        xa -= xa >= N ? N : 0;
+        node_values(xa, Ua);
+        float acc[FT][O][O];
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int x = 0; x < O; ++x)
+#pragma unroll
+                for (int w = 0; w < O; ++w) acc[u][x][w] = 0.0f;
+#pragma unroll
+        for (int q = 0; q < O; ++q) {
+            float A[O][O], B[O][O];
+            load_ab<O>(a.tab, j * O + q, A, B);
+#pragma unroll
+            for (int u = 0; u < FT; ++u)
+#pragma unroll
+                for (int x = 0; x < O; ++x) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int l = 0; l < O; ++l) {
+                        s = fmaf(A[x][l], Ua[u][q][l], s);
+                        s = fmaf(B[x][l], Ub[u][q][l], s);
+                    }
+#pragma unroll
+                    for (int w = 0; w < O; ++w) acc[u][x][w] = fmaf(a.back32[w][q], s, acc[u][x][w]);
+                }
+        }
+        const uint32_t c = line0 + (i0 + uint32_t(r)) * a.inner_x;
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int x = 0; x < O; ++x)
+#pragma unroll
+                for (int w = 0; w < O; ++w) {
+                    const int J = jb[u] + x * a.ostride + w * a.vstride;
+                    if constexpr (OFF32)
+                        static_cast<float*>(a.dst.hi)[uint32_t(J - 1) * uint32_t(a.pstride) + c] = acc[u][x][w];
+                    else
+                        static_cast<float*>(a.dst.hi)[int64_t(J - 1) * a.pstride + c] = acc[u][x][w];
+                }
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int q = 0; q < O; ++q)
+#pragma unroll
+                for (int l = 0; l < O; ++l) Ub[u][q][l] = Ua[u][q][l];
+        xb = xa;
+    }
+}
+
 // The fibre of the cell mean in the mixed store when the o nodes of the
 // v-cell share sigma (so all nodes read the same two source cells a, b).
 // In exact arithmetic, with t = m_b - m_a, delta_q(c) = sum_{jv>=1} c_{0,jv}
@@ -547,21 +656,95 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
         }
 }
 
+// Mean's fibre of the mixed store for target c (at x = i of v-cell j).
+template <int K>
+__device__ __forceinline__ void nodal_mean_target(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
+                                                  uint32_t j)
+{
+    constexpr int O = K + 1;
+    // the nodes of a v-cell nearly always share sigma
+    const int32_t s0 = __ldg(a.tab.sigma + j * O);
+    bool same = true;
+#pragma unroll
+    for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
+    if (same)
+        nodal_mean_fibre_shared<K>(a, c, i, line0, j, s0);
+    else
+        nodal_mean_fibre<K>(a, c, i, line0, j);
+}
+
+// Runs of the walk form along x (PART 4): run = inner + inner_x (rx + nrunx
+// outer) covers the targets x = rx R .. of the x-line through the cell
+// inner + inner_x N outer, so neighbouring threads take neighbouring lines
+// (x-dimension > 0) or neighbouring runs of one line (x-dimension 0).
+template <int K, bool OFF32>
+__device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int g)
+{
+    constexpr int O = K + 1;
+    constexpr int FT = nodal_ftw(K);
+    const uint32_t t = a.fdInnerX.div(run);
+    const uint32_t inn = run - t * a.inner_x;
+    const uint32_t outer = a.fdRunX.div(t);
+    const uint32_t i0 = (t - outer * a.nrunx) * uint32_t(kNodalRun);
+    const int cnt = min(kNodalRun, int(a.N - i0));
+    const uint32_t line0 = inn + outer * a.N * a.inner_x;
+    const uint32_t ov = a.fdInnerV.div(line0);           // the v-cell is the same along the x-line
+    const uint32_t j = ov - a.fdNV.div(ov) * a.NV;
+    if (g == 0) {
+        for (int r = 0; r < cnt; ++r)
+            nodal_mean_target<K>(a, line0 + (i0 + uint32_t(r)) * a.inner_x, i0 + uint32_t(r), line0, j);
+        return;
+    }
+    int jb[FT];
+#pragma unroll
+    for (int u = 0; u < FT; ++u) jb[u] = nodal_fibre_base<O>(a, min(g + u, int(a.nfib2) - 1));
+    const int32_t s0 = __ldg(a.tab.sigma + j * O);
+    bool same = true;
+#pragma unroll
+    for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
+    if (same) {
+        nodal_fp32_walk<K, FT, OFF32>(a, line0, i0, cnt, j, s0, jb);
+    } else {
+        for (int r = 0; r < cnt; ++r)
+            nodal_fp32_group<K, FT, OFF32>(a, line0 + (i0 + uint32_t(r)) * a.inner_x, i0 + uint32_t(r), line0,
+                                           j, jb);
+    }
+}
+
 // PART 0: every fibre (FP64 store; fibre blockIdx.y); 1: only the mean's
-// fibre of the mixed store (two dimensions); 3: every fibre of the mixed
-// store, the blocks of the fibres interleaved in a 1D grid (block b takes
-// fibre b % nfib2), so that blocks of the mean's fibre, bound by the FP64
-// pipe, run beside blocks of FP32 fibres, bound by instruction issue.
+// fibre of the mixed store (two dimensions); 3 and 4: every fibre of the
+// mixed store, the blocks of the fibre groups interleaved in a 1D grid (block
+// b takes group b % groups), so that blocks of the mean's fibre, bound by the
+// FP64 pipe, run beside blocks of FP32 fibres, bound by instruction issue;
+// 3 takes one target per thread, 4 a run of kNodalRun targets along x.
+// Part 4 serves x-dimensions > 0, where the lanes of a warp sit on
+// neighbouring x-lines, so that every step of the runs is coalesced (measured
+// 8.5% faster than part 3 along dimension 1 of the 4D store at k = 2).  Along
+// dimension 0 the lanes of a run would read kNodalRun cells apart (21%
+// slower), so part 3 serves it.
 template <int K, int MODE, int PART>
-__global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 ? 4 : 2)
+__global__ void __launch_bounds__(PART >= 3 ? 128 : 256, K == 3 ? 1 : PART >= 3 ? 4 : 2)
     k_sweep_nodal(const NodalArgs a)
 {
     constexpr int O = K + 1;
+    if constexpr (PART == 4) {
+        constexpr int FT = nodal_ftw(K);
+        // group 0: the mean's fibre; group r >= 1: FP32 fibres 1 + (r - 1) FT ..
+        const uint32_t ngroups = 1 + (a.nfib2 - 2) / FT + 1;
+        const int r = int(blockIdx.x % ngroups);
+        const uint32_t run = (blockIdx.x / ngroups) * blockDim.x + threadIdx.x;
+        if (run >= a.nruns) return;
+        const int g = r == 0 ? 0 : 1 + (r - 1) * FT;
+        if (a.off32)
+            nodal_run<K, true>(a, run, g);
+        else
+            nodal_run<K, false>(a, run, g);
+        return;
+    }
     constexpr int FT = nodal_ft(K);
     int g = int(blockIdx.y);
     uint32_t bx = blockIdx.x;
     if constexpr (PART == 3) {
-        // group 0: the mean's fibre; group r >= 1: FP32 fibres 1 + (r - 1) FT ..
         const uint32_t ngroups = 1 + (a.nfib2 - 2) / FT + 1;
         const int r = int(blockIdx.x % ngroups);
         bx = blockIdx.x / ngroups;
@@ -569,25 +752,16 @@ __global__ void __launch_bounds__(PART == 3 ? 128 : 256, K == 3 ? 1 : PART == 3 
     }
     const uint32_t c = bx * blockDim.x + threadIdx.x;
     if (c >= a.cells) return;
-    const int base = nodal_fibre_base<O>(a, g);
     const uint32_t ox = a.fdInnerX.div(c);
     const uint32_t i = ox - a.fdNX.div(ox) * a.N;        // coordinate along x
     const uint32_t ov = a.fdInnerV.div(c);
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;       // v-cell
     const uint32_t line0 = c - i * a.inner_x;
     if constexpr (MODE == M_FP64) {
-        nodal_plain<K, double>(a, c, i, line0, j, base);
+        nodal_plain<K, double>(a, c, i, line0, j, nodal_fibre_base<O>(a, g));
     } else if (PART == 1 || g == 0) {
-        // the nodes of a v-cell nearly always share sigma
-        const int32_t s0 = __ldg(a.tab.sigma + j * O);
-        bool same = true;
-#pragma unroll
-        for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
-        if (same)
-            nodal_mean_fibre_shared<K>(a, c, i, line0, j, s0);
-        else
-            nodal_mean_fibre<K>(a, c, i, line0, j);
-    } else if constexpr (PART == 3) {
+        nodal_mean_target<K>(a, c, i, line0, j);
+    } else {
         int jb[FT];
 #pragma unroll
         for (int u = 0; u < FT; ++u) jb[u] = nodal_fibre_base<O>(a, min(g + u, int(a.nfib2) - 1));
@@ -607,10 +781,19 @@ cudaError_t nodal_launch(int mode, const NodalArgs& a, int nfib2, cudaStream_t s
         k_sweep_nodal<K, M_FP64, 0><<<dim3(bx, uint32_t(nfib2)), block, 0, st>>>(a);
     } else if (nfib2 == 1) {
         k_sweep_nodal<K, M_F32, 1><<<dim3(bx, 1), block, 0, st>>>(a);
-    } else {
+    } else if (a.inner_x == 1) {
         const uint64_t nb = uint64_t((a.cells + 127) / 128) * uint64_t(1 + (nfib2 - 2) / nodal_ft(K) + 1);
         if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
         k_sweep_nodal<K, M_F32, 3><<<uint32_t(nb), 128, 0, st>>>(a);
+    } else {
+        NodalArgs b = a;
+        b.nrunx = (a.N + kNodalRun - 1) / kNodalRun;
+        b.fdRunX.set(b.nrunx);
+        const uint64_t nruns = uint64_t(a.cells / a.N) * b.nrunx;
+        b.nruns = uint32_t(nruns);
+        const uint64_t nb = (nruns + 127) / 128 * uint64_t(1 + (nfib2 - 2) / nodal_ftw(K) + 1);
+        if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
+        k_sweep_nodal<K, M_F32, 4><<<uint32_t(nb), 128, 0, st>>>(b);
     }
     return cudaGetLastError();
 }

@@ -22,6 +22,8 @@ struct NodalArgs {
     int ndim, xdim, vdim, O;
     uint32_t nfib2;            // fibres varying in (j_x, j_v): o^(ndim - 2)
     int off32;                 // 1: plane_stride * o^ndim < 2^31 (32-bit element offsets)
+    uint32_t nrunx, nruns;     // runs of consecutive x-cells (set by the launcher): per x-line, in all
+    FastDiv fdRunX;            // run -> run along its x-line: (run / inner_x) % nrunx
     double eval64[kMaxO][kMaxO];   // P_jv(eta_q) at [q][jv]
     double back64[kMaxO][kMaxO];   // (2 jv + 1) / 2 w_q P_jv(eta_q) at [jv][q]; row 0 = wmean
     double wmean[kMaxO];           // w_q / 2 rounded to sum to exactly 1
