@@ -230,3 +230,34 @@ def test_nodal_full_size_sampled_after_one_x_sweep():
                 ref[r, idx] = out[dhi]
     assert O.rel_l2(got, ref, k, 4) <= 1e-6
     assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(ref[:, 1:]))
+
+
+def _swap01(u, n, k):
+    """The coefficients of a 4D state with dimensions 0 and 1 exchanged (cells
+    and coefficient indices), in the layout of the swapped grid."""
+    o = k + 1
+    t = u.reshape(n[3], n[2], n[1], n[0], o, o, o, o)    # axes i3 i2 i1 i0 j3 j2 j1 j0
+    return np.ascontiguousarray(t.transpose(0, 1, 3, 2, 4, 5, 7, 6)).reshape(u.shape)
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_nodal_runs_match_one_target_per_thread_bit_for_bit(k):
+    """Along x-dimension 1 the FP32 fibres of the mixed store take runs of
+    consecutive targets per thread; along x-dimension 0 one target per thread.
+    Both keep the same order of every sum, so the sweep along dimension 1
+    equals, bit for bit, the sweep along dimension 0 of the state with
+    dimensions 0 and 1 exchanged: runs cut by the line end (9 = 4 + 4 + 1),
+    wrapped sources, and v-cells whose nodes do and do not share sigma."""
+    n = (7, 9, 5, 4)
+    g = W.Grid(n=n, lo=(0.0, 0.0, -3.0, -3.0), hi=(1.0, 2.0, 2.0, 2.0), pair=(2, 3, -1, -1))
+    ns = (9, 7, 5, 4)
+    gs = W.Grid(n=ns, lo=(0.0, 0.0, -3.0, -3.0), hi=(2.0, 1.0, 2.0, 2.0), pair=(3, 2, -1, -1))
+    u = _rand(n, k, 60 + k)
+    us = _swap01(u, n, k)
+    with S.Context(g, k, "mix_fp32") as a, S.Context(gs, k, "mix_fp32") as b:
+        for tau in (0.05, 0.37, -1.3, 2.9):
+            a.set_coeffs(u)
+            b.set_coeffs(us)
+            a.advect_nodal(1, tau)
+            b.advect_nodal(0, tau)
+            assert np.array_equal(_swap01(a.get_coeffs(), n, k), b.get_coeffs()), tau
