@@ -35,7 +35,10 @@ struct NodalArgs {
 // Gauss-Legendre nodes eta[o] (ascending) and weights[o] of degree K's o = K + 1
 // points, and the node tables of a.
 void nodal_setup(int K, double* eta, double* weights, NodalArgs* a);
-// grid: cells x nfib2 (= o^(d-2) fibres of coefficients varying in (j_x, j_v)).
+// One nodal x-sweep over every cell and every one of the nfib2 = o^(d-2)
+// fibres of coefficients varying in (j_x, j_v); the launcher picks the grid
+// (per target, or runs of targets along x-dimensions > 0 in the mixed store)
+// and fills the run fields of its copy of a.
 cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st);
 
 }  // namespace sl
