@@ -261,3 +261,79 @@ def test_nodal_runs_match_one_target_per_thread_bit_for_bit(k):
             a.advect_nodal(1, tau)
             b.advect_nodal(0, tau)
             assert np.array_equal(_swap01(a.get_coeffs(), n, k), b.get_coeffs()), tau
+
+
+def _nodal_windows(g, k, xdim, tau, cells):
+    """For each sampled target cell of a 4D grid: the cells along x that its
+    nodes read in a nodal x-sweep over tau (a window around it), and the plan
+    (v-cell, target position in the window, window length)."""
+    n = g.n
+    o = k + 1
+    vdim = g.pair[xdim]
+    st = [1, n[0], n[0] * n[1], n[0] * n[1] * n[2]]
+    hx = (g.hi[xdim] - g.lo[xdim]) / n[xdim]
+    hv = (g.hi[vdim] - g.lo[vdim]) / n[vdim]
+    eta, _ = O.gauss_legendre(o)
+    plans, need = [], []
+    for c in cells:
+        ix, j = (c // st[xdim]) % n[xdim], (c // st[vdim]) % n[vdim]
+        sig = [O.shift_split((g.lo[vdim] + (j + 0.5 + 0.5 * e) * hv) * tau / hx)[0] for e in eta]
+        dlo, dhi = min(min(sig), 0), max(max(sig) + 1, 0)
+        base = c - ix * st[xdim]
+        win = [base + ((ix - d) % n[xdim]) * st[xdim] for d in range(dhi, dlo - 1, -1)]
+        plans.append((j, dhi, len(win)))
+        need.extend(win)
+    return plans, np.array(need, dtype=np.int64)
+
+
+def _nodal_sampled_reference(g, k, xdim, tau, plans, src):
+    """The oracle's nodal x-sweep at the sampled targets, each on a cut-out
+    (x, v) problem: its window along x, one v-cell of the same velocity range,
+    and the o^2 fibres of the other two indices one by one."""
+    o = k + 1
+    vdim = g.pair[xdim]
+    others = [m for m in range(4) if m not in (xdim, vdim)]
+    hx = (g.hi[xdim] - g.lo[xdim]) / g.n[xdim]
+    hv = (g.hi[vdim] - g.lo[vdim]) / g.n[vdim]
+    ref = np.empty((len(plans), o ** 4))
+    pos = 0
+    for r, (j, dhi, wlen) in enumerate(plans):
+        block = src[pos:pos + wlen]
+        pos += wlen
+        mini = W.Grid(n=(wlen, 1), lo=(0.0, g.lo[vdim] + j * hv), hi=(wlen * hx, g.lo[vdim] + (j + 1) * hv),
+                      pair=(1, -1))
+        for ja in range(o):
+            for jb in range(o):
+                idx = []
+                for jv in range(o):
+                    for jx in range(o):       # mini coefficient jx + o jv
+                        jj = [0, 0, 0, 0]
+                        jj[xdim], jj[vdim], jj[others[0]], jj[others[1]] = jx, jv, ja, jb
+                        idx.append(jj[0] + o * jj[1] + o * o * jj[2] + o ** 3 * jj[3])
+                ref[r, idx] = O.sweep_nodal(block[:, idx], mini, k, 0, tau)[dhi]
+    return ref
+
+
+@pytest.mark.parametrize("xdim", [0, 1])
+def test_nodal_sampled_with_64_bit_plane_offsets(xdim):
+    """4D 64 x 64 x 96 x 72, k = 2, mixed store: 80 FP32 planes of 28.3M
+    cells, more than 2^31 elements, so both nodal forms (one target per thread
+    along dimension 0, runs along dimension 1) address the FP32 block with
+    64-bit offsets.  One x-sweep over dt / 2; sampled targets against the
+    oracle on cut-out (x, v) problems."""
+    p = W.config3(n=64, steps=1)
+    n = (64, 64, 96, 72)
+    g = W.Grid(n=n, lo=p.grid.lo, hi=p.grid.hi, pair=p.grid.pair)
+    k, tau = p.k, 0.5 * p.dt
+    rng = np.random.default_rng(70 + xdim)
+    cells = np.concatenate([rng.integers(0, int(np.prod(n)), size=30), [0, int(np.prod(n)) - 1]]).astype(np.int64)
+    plans, need = _nodal_windows(g, k, xdim, tau, cells)
+    with S.Context(g, k, "mix_fp32") as ctx:
+        assert ctx.info["plane_stride"] * (ctx.info["ncoef"] - 1) >= 2 ** 31
+        ctx.project(p.nq, p.weights, p.params)
+        src = ctx.get_cells(need)
+        ctx.advect_nodal(xdim, tau)
+        got = ctx.get_cells(cells)
+    ref = _nodal_sampled_reference(g, k, xdim, tau, plans, src)
+    assert O.rel_l2(got, ref, k, 4) <= 1e-6
+    assert np.max(np.abs(got[:, 0] - ref[:, 0])) <= 1e-6 * np.max(np.abs(ref[:, 1:]))
