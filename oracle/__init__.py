@@ -42,6 +42,9 @@ Functions and the paper passages they follow:
   stored_sweeps                 bytes per cell, the state as that store holds
                                 it, and sweeps with the state rounded to the
                                 store after each (FP64 arithmetic)
+  l2_norm, rel_l2, rel_max   -- error measures; l2_norm is the function-space
+                                L2 norm of the expansion, the reading of the
+                                "discrete L2 norm" of Table II (Sec. III-A)
 """
 from __future__ import annotations
 
@@ -525,6 +528,18 @@ def l2_weights(k: int, ndim: int) -> np.ndarray:
             r //= o
             w[J] *= 2.0 / (2 * j + 1)
     return w
+
+
+def l2_norm(u: np.ndarray, grid, k: int) -> float:
+    """Function-space L2 norm of the expansion on the grid's box:
+    int u^2 dx = sum over cells of prod_m (h_m / 2) sum_J c_J^2 prod_m 2 / (2 j_m + 1)
+    (each cell maps to [-1, 1]^d with Jacobian prod_m h_m / 2)."""
+    ndim = len(grid.n)
+    jac = 1.0
+    for m in range(ndim):
+        jac *= 0.5 * (grid.hi[m] - grid.lo[m]) / grid.n[m]
+    v = np.asarray(u, dtype=np.float64)
+    return math.sqrt(jac * float(np.sum(v * v * l2_weights(k, ndim))))
 
 
 def rel_l2(u: np.ndarray, ref: np.ndarray, k: int, ndim: int) -> float:

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "SplitMix64", "Grid", "Problem", "config1", "config2", "config3", "config4",
-    "config5", "maxwellian_factor", "CONFIGS",
+    "config5", "maxwellian_factor", "CONFIGS", "Table2Protocol", "table2_protocol",
 ]
 
 MASK64 = (1 << 64) - 1
@@ -252,6 +252,33 @@ def config5(n: int = 20, steps: int = 10, storage: str = "mix_bf16", seed: int =
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4, 5: config5}
+
+
+@dataclass
+class Table2Protocol:
+    """The accuracy study of Table II (Sec. III-A): 10^4 steps of 1D periodic
+    advection on [0, 1) with a constant shift per step, orders 2 and 4
+    (k = 1, 3), a smooth and an oscillatory initial value.  The paper gives
+    neither N nor the CFL number; n and shift are this library's choice."""
+    n: int = 512
+    steps: int = 10_000
+    shift: float = 0.37
+    nq: int = 8
+    # profile -> (weights, params) of the separable form above
+    initial: dict = field(default_factory=lambda: {
+        # exp(-100 (x - 1/2)^2)
+        "smooth": (np.array([1.0]), np.array([[[100.0, 0.5, 0.0, 0.0]]])),
+        # 1 + cos(16 pi x + 0.3): eight periods on [0, 1), mass 1
+        "oscillatory": (np.array([1.0, 1.0]),
+                        np.array([[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]])),
+    })
+
+    def grid(self) -> "Grid":
+        return Grid(n=(self.n,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+
+
+def table2_protocol(n: int = 512, steps: int = 10_000) -> Table2Protocol:
+    return Table2Protocol(n=n, steps=steps)
 
 
 def random_coefficients(cells: int, k: int, ndim: int, seed: int, decay: float = 0.1) -> np.ndarray:

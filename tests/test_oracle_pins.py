@@ -540,3 +540,32 @@ def test_nodal_sweep_converges_to_free_streaming(k):
     assert order >= k + 0.8, (errs, order)
     assert errs[1] < errc[1] / 10, (errs, errc)
     assert math.log2(errc[0] / errc[1]) < 1.2
+
+
+# ---------------------------------------------------------------- error norm
+
+def test_l2_norm_of_projected_data():
+    """The function-space L2 norm of the expansion: 1 for the constant 1 on
+    the unit box in 1D and 2D (only c_0 = 1), the closed form
+    (pi / 200)^(1/4) for exp(-100 (x - 1/2)^2) on [0, 1) to projection
+    accuracy, and sqrt(2 / (2j + 1) * h / 2) for a single Legendre mode P_j
+    on one cell of width h (Parseval on [-1, 1])."""
+    from paper_1603_07008_gb300 import workloads as W
+    g1 = W.Grid(n=(16,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    one = O.project(g1, 2, 5, [1.0], [[[0.0, 0.0, 0.0, 0.0]]])
+    assert abs(O.l2_norm(one, g1, 2) - 1.0) < 1e-14
+    g2 = W.Grid(n=(4, 8), lo=(0.0, -1.0), hi=(2.0, 0.0), pair=(1, -1))
+    one2 = O.project(g2, 1, 5, [1.0], [[[0.0, 0.0, 0.0, 0.0], [0.0, 0.0, 0.0, 0.0]]])
+    assert abs(O.l2_norm(one2, g2, 1) - np.sqrt(2.0)) < 1e-14   # area 2
+    g = W.Grid(n=(512,), lo=(0.0,), hi=(1.0,), pair=(-1,))
+    u = O.project(g, 3, 8, [1.0], [[[100.0, 0.5, 0.0, 0.0]]])
+    # int_0^1 exp(-200 (x - 1/2)^2) dx = sqrt(pi / 200) erf(sqrt(200) / 2)
+    import math
+    want = math.sqrt(math.sqrt(math.pi / 200) * math.erf(math.sqrt(200) / 2))
+    assert abs(O.l2_norm(u, g, 3) - want) < 1e-9
+    h = 0.25
+    gc = W.Grid(n=(1,), lo=(0.0,), hi=(h,), pair=(-1,))
+    for j in range(4):
+        c = np.zeros((1, 4))
+        c[0, j] = 1.0
+        assert abs(O.l2_norm(c, gc, 3) - math.sqrt(2.0 / (2 * j + 1) * h / 2)) < 1e-15
