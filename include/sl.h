@@ -323,8 +323,12 @@ sl_status sl_mass(sl_ctx* ctx, double* out);
  *   cuda_stream  cudaStream_t the work is enqueued on (NULL = legacy default)
  * Enqueues only; the result is valid once the stream reaches it.  The first
  * call on a device looks up the scratch array's device address on that device
- * (the current one), so make that first call before any stream capture.  All
- * calls share the one scratch array: calls whose work overlaps on the GPU
+ * (the current one), so make that first call before any stream capture.  The
+ * address is kept for the life of the process and belongs to the device's
+ * primary context (the one the CUDA runtime uses): do not call this entry
+ * point under another context made current through the driver API, nor after
+ * cudaDeviceReset on that device (the kept address then names freed memory).
+ * All calls share the one scratch array: calls whose work overlaps on the GPU
  * (different streams, no ordering between them) race and may return wrong
  * sums.  Each call rewrites every scratch slot it reads, so a previous call's
  * leftovers never leak into a result.  Errors: SL_EINVAL (NULL pointer or
@@ -354,6 +358,18 @@ sl_status sl_selftest_conversions(const double* d_in, const float* f_in, int64_t
  * disagree (must be 0).  Host arrays of n elements (1 <= n <= 2^26).
  * Synchronous, on the default stream.  Errors: SL_EINVAL, SL_ENOMEM, SL_ECUDA. */
 sl_status sl_selftest_sub_widened(const float* a, const float* b, int64_t n, double* out, int64_t* mismatches);
+/* Measured FP64 arithmetic rate of the current device, the roofline of the
+ * FP64 store (its sweep costs 2o FP64 FMAs per coefficient against the
+ * 4o - 1 flops per coefficient of Sec. II-A, at the device's FP64 rate):
+ * the best of four launch shapes (8 or 16 independent FMA chains per thread,
+ * 4 or 8 resident blocks of 256 threads per multiprocessor), each timed with
+ * CUDA events on `cuda_stream` after a shorter warm-up launch; every chain
+ * runs about `iters` FMAs (8 chains) or half as many (16 chains).
+ * *flops_per_s = 2 * FMAs / seconds.  1 <= iters <= 2^24 (2^14 takes about
+ * 50 ms per shape on GB300).  Allocates 8 bytes of device memory for the
+ * duration of the call; synchronous.  Errors: SL_EINVAL, SL_ENOMEM,
+ * SL_ECUDA. */
+sl_status sl_selftest_fp64_rate(int64_t iters, void* cuda_stream, double* flops_per_s);
 
 /* Self-consistent field (NEXT to the sweep: the Vlasov-Poisson system of
  * Sec. II in 1+1 dimensions).  For a grid with one x dimension paired with
@@ -390,6 +406,28 @@ sl_status sl_set_nodal_velocity(sl_ctx* ctx, int enable);
  * (shifts v tau / h_dim at the nodes, as above).  Errors: SL_EINVAL (dim not an
  * x-dimension), SL_ENAN (tau not finite), as sl_set_nodal_velocity. */
 sl_status sl_advect_nodal(sl_ctx* ctx, int dim, double tau);
+
+/* Arithmetic of the sweeps of the stores with FP32 planes (Sec. III-A and
+ * Table II state which coefficients a store keeps in double precision, not
+ * the precision the update rule of Sec. II-A is evaluated in).
+ *   SL_ARITH_STORE (default): the rows of FP32 coefficients are computed in
+ *     FP32 arithmetic (the FP64 rows as the store's own sweeps describe);
+ *     the launch shapes of sl_set_tune / sl_autotune apply.
+ *   SL_ARITH_FP64: every row is computed in FP64 from the stored values
+ *     widened to FP64 with the FP64 matrices, and the new FP32 coefficients
+ *     are rounded once (to nearest, ties to even) on store; the store keeps
+ *     its layout and bytes.  Then a sweep differs from the FP64 store's only
+ *     by the rounding of what the store holds.  One launch shape (one fibre
+ *     per thread), bound by the FP64 pipe like the FP64 store.
+ * Takes effect for the sweeps issued after the call (a graph captured before
+ * keeps its kernels).  Stores SL_MIX_FP32, SL_FP32, SL_MIX_FP32_D2,
+ * SL_MIX_FP32_D3; for SL_FP64 both values are accepted and change nothing.
+ * Errors: SL_EINVAL (unknown value, NULL ctx, during a capture), SL_ENOTSUP
+ * (SL_ARITH_FP64 with the scaled stores or with nodal-in-velocity x-sweeps
+ * enabled; sl_set_nodal_velocity and sl_advect_nodal in turn return
+ * SL_ENOTSUP while SL_ARITH_FP64 is set). */
+typedef enum { SL_ARITH_STORE = 0, SL_ARITH_FP64 = 1 } sl_arith;
+sl_status sl_set_arithmetic(sl_ctx* ctx, int arith);
 
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
  * replay it with sl_graph_launch.  Fields must be set before capture; a later

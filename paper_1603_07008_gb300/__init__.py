@@ -36,12 +36,15 @@ __all__ = [
     "sl_field_energy", "sl_graph_capture_advect", "sl_create_external", "sl_plane_layout",
     "sl_set_nodal_velocity", "sl_advect_nodal", "sl_check_guards", "sl_debug_fail_alloc",
     "sl_debug_corrupt_guard", "save_checkpoint", "load_checkpoint", "autotune_cached", "sl_selftest_sub_widened",
+    "sl_set_arithmetic", "sl_selftest_fp64_rate",
 ]
 
 SL_OK, SL_EINVAL, SL_ENOMEM, SL_ECUDA, SL_ETIMEOUT, SL_ENAN, SL_ENOTSUP = 0, -1, -2, -3, -4, -5, -6
 SL_FP64, SL_MIX_FP32, SL_MIX_BF16, SL_MIX_FP16 = 0, 1, 2, 3
 SL_FP32, SL_MIX_FP32_D2, SL_MIX_FP32_D3 = 4, 5, 6
 SL_LIE, SL_STRANG = 0, 1
+SL_ARITH_STORE, SL_ARITH_FP64 = 0, 1
+ARITH = {"store": SL_ARITH_STORE, "fp64": SL_ARITH_FP64}
 STORAGE = {"fp64": SL_FP64, "mix_fp32": SL_MIX_FP32, "mix_bf16": SL_MIX_BF16, "mix_fp16": SL_MIX_FP16,
            "fp32": SL_FP32, "mix_fp32_d2": SL_MIX_FP32_D2, "mix_fp32_d3": SL_MIX_FP32_D3}
 # Coefficients per dimension kept in FP64 ("# double" of Sec. III-A) of the
@@ -171,6 +174,8 @@ def lib():
             "sl_mass_noalloc": (st, [_vp, ctypes.c_int64, ctypes.c_double, _vp, _vp]),
             "sl_set_poisson": (st, [_vp, ctypes.c_int]),
             "sl_set_nodal_velocity": (st, [_vp, ctypes.c_int]),
+            "sl_set_arithmetic": (st, [_vp, ctypes.c_int]),
+            "sl_selftest_fp64_rate": (st, [ctypes.c_int64, _vp, _dp]),
             "sl_check_guards": (st, [_vp, _i64p]),
             "sl_selftest_sub_widened": (st, [ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float),
                                              ctypes.c_int64, _dp, _i64p]),
@@ -480,6 +485,19 @@ def sl_advect_nodal(ctx, dim: int, tau: float):
     _check(lib().sl_advect_nodal(ctx, int(dim), float(tau)), ctx)
 
 
+def sl_selftest_fp64_rate(iters: int = 1 << 14, stream=None) -> float:
+    """Measured FP64 FLOP/s of the current device."""
+    out = ctypes.c_double()
+    _check(lib().sl_selftest_fp64_rate(int(iters), _stream_handle(stream), ctypes.byref(out)))
+    return out.value
+
+
+def sl_set_arithmetic(ctx, arith):
+    """"store" (SL_ARITH_STORE) or "fp64" (SL_ARITH_FP64), or the number."""
+    a = ARITH[arith] if isinstance(arith, str) else int(arith)
+    _check(lib().sl_set_arithmetic(ctx, a), ctx)
+
+
 def sl_selftest_sub_widened(a, b):
     """(float64(a) - float64(b) as the library's mean row forms it, mismatches
     between its integer-pipe and FP64 forms)."""
@@ -627,6 +645,9 @@ class Context:
 
     def advect_nodal(self, dim, tau):
         sl_advect_nodal(self.handle, dim, tau)
+
+    def set_arithmetic(self, arith):
+        sl_set_arithmetic(self.handle, arith)
 
     def check_guards(self):
         return sl_check_guards(self.handle)

@@ -186,13 +186,14 @@ bool rec_lanes(const sl_ctx* c, int ft) { return rec_lanes_ok(c) && ft == kRecLa
 
 // Chunk length of the strided walk: long enough to amortise the extra load at
 // the start of a chunk, short enough to give a few waves of 2048 resident
-// threads on 152 SMs, and no more than 65535 grid rows.
+// threads on every multiprocessor of the device, and no more than 65535 grid
+// rows.
 uint32_t chunk_for(const sl_ctx* c, int m, int ft, int lanes)
 {
     const int64_t N = c->g.n[m];
     const int64_t lines = c->cells / N * lanes;
     const int64_t nfg = fibre_groups(c, ft);
-    const int64_t want = int64_t(152) * 2048 * 2;
+    const int64_t want = int64_t(c->sm_count) * 2048 * 2;
     int64_t nchunk = (want + lines * nfg - 1) / (lines * nfg);
     if (nchunk < 1) nchunk = 1;
     int64_t chunk = (N + nchunk - 1) / nchunk;
@@ -358,6 +359,11 @@ cudaError_t launch_only(sl_ctx* c, int dim, int shift_dim)
     L.ndim = c->ndim;
     L.rec = c->rec;
     L.occ = dim == 0 ? 0 : c->tune[dim].occ;
+    if (c->wide) {   // FP64 arithmetic: one fibre per thread, its own walk chunk
+        L.args.nfg = int(c->nfib);
+        L.args.chunk = dim == 0 ? 0 : chunk_for(c, dim, 1, 1);
+        return launch_sweep_wide(L);
+    }
     if (is_scaled(c)) return launch_sweep_scaled(L);
     switch (c->mode) {
     case M_FP64: return launch_sweep_f64(L);
@@ -789,6 +795,15 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     c->external = planes != nullptr;
     for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
     build_poly_table(degree, &c->poly);
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || c->sm_count < 1) {
+            delete c;
+            return fail(nullptr, SL_ECUDA, "querying the device's multiprocessor count: %s", cudaGetErrorString(e));
+        }
+    }
     for (int m = 0; m < c->ndim; ++m) default_tune(c, m);
 
     // layout of the single allocation (the state only when the context owns
@@ -1343,6 +1358,7 @@ sl_status sl_set_nodal_velocity(sl_ctx* c, int enable)
         return SL_OK;
     }
     if (c->ndim < 2) return fail(c, SL_EINVAL, "the nodal-in-velocity x-sweep needs an x-dimension with a pair");
+    if (c->wide) return fail(c, SL_ENOTSUP, "the nodal-in-velocity x-sweep does not take SL_ARITH_FP64");
     sl_status s = nodal_alloc(c);
     if (s != SL_OK) return s;
     c->nodal = true;
@@ -1355,11 +1371,28 @@ sl_status sl_advect_nodal(sl_ctx* c, int dim, double tau)
     if (dim < 0 || dim >= c->ndim || c->g.pair[dim] < 0)
         return fail(c, SL_EINVAL, "dim must be an x-dimension (pair[dim] >= 0)");
     if (!std::isfinite(tau)) return fail(c, SL_ENAN, "tau is not finite");
+    if (c->wide) return fail(c, SL_ENOTSUP, "the nodal-in-velocity x-sweep does not take SL_ARITH_FP64");
     sl_status s = nodal_alloc(c);
     if (s != SL_OK) return s;
     s = nodal_table(c, dim, tau);
     if (s != SL_OK) return s;
     return run_sweep(c, dim, -1, true);
+}
+
+sl_status sl_set_arithmetic(sl_ctx* c, int arith)
+{
+    if (!c) return fail(nullptr, SL_EINVAL, "ctx is NULL");
+    if (arith != SL_ARITH_STORE && arith != SL_ARITH_FP64) return fail(c, SL_EINVAL, "unknown arithmetic %d", arith);
+    if (c->capturing) return fail(c, SL_EINVAL, "cannot change the arithmetic during a capture");
+    if (c->mode == M_FP64) return SL_OK;   // already FP64 throughout
+    if (arith == SL_ARITH_STORE) {
+        c->wide = false;
+        return SL_OK;
+    }
+    if (is_scaled(c)) return fail(c, SL_ENOTSUP, "SL_ARITH_FP64 takes the stores with FP32 planes");
+    if (c->nodal) return fail(c, SL_ENOTSUP, "SL_ARITH_FP64 does not take nodal-in-velocity x-sweeps");
+    c->wide = true;
+    return SL_OK;
 }
 
 sl_status sl_field_energy(sl_ctx* c, double* energy)

@@ -19,6 +19,7 @@ struct sl_ctx {
     cudaStream_t st = nullptr;
     int64_t cells = 0, ncoef = 1, pstride = 0, nfib = 1;
     int rec = 0;                // > 0: scaled store in cell records of rec 16-bit slots
+    int sm_count = 0;           // multiprocessors of the context's device
     size_t elem = 8;            // bytes of a low-precision (hi) element
     int64_t nlo = 1, nhi = 0;   // FP64 planes (the mean's block) and hi planes of one copy
     int32_t* d_cmap = nullptr;  // coefficient map of the stores that use one (see sl::Planes)
@@ -52,6 +53,8 @@ struct sl_ctx {
     double* d_vp = nullptr;     // [chunks][n_x] partial sums, E scratch [n_x], energy [1]
     // x-sweeps with the velocity at the Gauss nodes of every v-cell
     bool nodal = false;
+    // every row of the sweeps in FP64 arithmetic (sl_set_arithmetic)
+    bool wide = false;
     void* d_nodal = nullptr;    // node velocities per x-dimension, then the node tables
     int64_t nodal_vel_off[SL_MAX_DIM] = {0};
     int nodal_maxcls = 0;

@@ -148,6 +148,9 @@ cudaError_t launch_sweep_f64(const SweepLaunch& L);      // M_FP64
 cudaError_t launch_sweep_f32(const SweepLaunch& L);      // M_F32
 cudaError_t launch_sweep_f32all(const SweepLaunch& L);   // M_F32ALL
 cudaError_t launch_sweep_split(const SweepLaunch& L);    // M_SPLIT2, M_SPLIT3
+// The stores with FP32 planes (M_F32, M_F32ALL, M_SPLIT2, M_SPLIT3) with
+// every row in FP64 arithmetic; one fibre per thread (nfg = nfib).
+cudaError_t launch_sweep_wide(const SweepLaunch& L);
 cudaError_t launch_sweep_scaled(const SweepLaunch& L);   // M_BF16, M_FP16
 // Cell records of degree 1 in 5 or 6 dimensions with G = R/16 lanes per cell,
 // 16 slots (8 fibres) each (selected by fibres_per_thread == kRecLaneFt).

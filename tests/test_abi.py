@@ -181,3 +181,10 @@ def test_split_store_layout_counts_the_fp64_block(ndim):
             assert lay["hi_bytes"] == (o ** ndim - q ** ndim) * ps * 4
             assert S.sl_state_bytes(g, k, store) == cells * (8 * q ** ndim + 4 * (o ** ndim - q ** ndim))
             assert S.plane_counts(ndim, k, store) == (q ** ndim, o ** ndim - q ** ndim)
+
+
+def test_fp64_rate_selftest_rejects_bad_arguments_without_device_work():
+    for iters in (0, -1, (1 << 24) + 1):
+        with pytest.raises(S.SlError) as e:
+            S.sl_selftest_fp64_rate(iters)
+        assert e.value.status == S.SL_EINVAL
