@@ -9,6 +9,8 @@ consecutive calls (the shared scratch keeps the previous call's contents).
 This file is collected last so that a stop-at-first-failure run has already
 run every other test when it gets here; it also passes on its own.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -50,7 +52,36 @@ def test_noalloc_mass_matches_sl_mass_on_consecutive_calls(storage):
                 ctx.step("strang", p.dt, 2)
 
 
+@pytest.mark.gpu
+def test_noalloc_mass_at_the_block_cap_matches_the_exact_sum():
+    """3 000 000 seeded values, more than 1024 blocks of 256 threads and 8
+    cells each: every one of the 1024 scratch slots is used and the
+    reduction strides over the plane.  Two calls in a row, the second on a
+    shorter prefix, against the correctly rounded sum times the volume."""
+    import torch
+    rng = np.random.default_rng(31)
+    vals = rng.uniform(0.5, 1.5, 3_000_000)
+    vol = 0.013
+    d_mean = torch.from_numpy(vals).to("cuda")
+    out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    for cells in (vals.size, 2_500_001):
+        S.sl_mass_noalloc(d_mean.data_ptr(), cells, vol, out.data_ptr(), stream)
+        stream.synchronize()
+        exact = vol * math.fsum(vals[:cells].tolist())
+        assert abs(float(out.item()) - exact) <= 1e-14 * exact, (cells, float(out.item()), exact)
+
+
+def _library_or_skip():
+    try:
+        S.lib()
+    except Exception as e:   # no nvcc build on this host
+        pytest.skip(f"libsl.so not available: {e}")
+
+
 def test_noalloc_rejects_bad_sizes_without_device_work():
+    _library_or_skip()
     for cells in (0, -5, 2 ** 31):
         with pytest.raises(S.SlError) as e:
             S.sl_mass_noalloc(0x1000, cells, 1.0, 0x2000)
