@@ -175,19 +175,19 @@ TRAFFIC = {
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
         "sha256": "ac91a006f047484d",
         "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
-                   "1 fibres) against 3.483 GB algorithmic (profiles/sweep_4d_n48_mixed_fp32.md)"},
+                   "1 fibres) against 3.483 GB algorithmic"},
     ("6d", "mix_bf16"): {
         "ratio": (2 * 1.03530 + 7 * 1.03691) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
         "sha256": "5424e174e5f11611",
         "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.795 / 4.802 GB per launch (dimensions 0, "
-                   "1) against 4.631 GB algorithmic (profiles/sweep_6d_n16_lane_records_bf16.md)"},
+                   "1) against 4.631 GB algorithmic"},
     ("batch", "mix_fp32"): {
         "ratio": (2 * 0.95799 + 1.04195) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
         "sha256": "36d89809795b4a94",
         "capture": "64 problems, default shapes; 1.046 / 1.138 GB per launch (dimensions 0, 1) against "
-                   "1.092 GB algorithmic (profiles/batch_2d_64probs_mixed_fp32.md)"},
+                   "1.092 GB algorithmic"},
 }
 
 
@@ -239,6 +239,55 @@ def time_oracle(n_x: int, n_v: int, steps: int):
     dt = time.perf_counter() - t0
     dof_updates = steps * len(sched) * u.size
     return dof_updates / dt, dt, dof_updates, p
+
+
+# Bounds of each store against the FP64 oracle: FP64 max relative, the
+# mixed and split FP32 stores relative L2, the scaled 16-bit stores relative L2.
+ERROR_BOUND = {"fp64": ("rel_max", 1e-12), "mix_fp32": ("rel_l2", 1e-5), "fp32": ("rel_l2", 1e-5),
+               "mix_fp32_d2": ("rel_l2", 1e-5), "mix_fp32_d3": ("rel_l2", 1e-5),
+               "mix_bf16": ("rel_l2", 1e-2), "mix_fp16": ("rel_l2", 1e-2)}
+
+
+def oracle_error(samples, storage):
+    """Error of sampled cells of the timed path (Arm.samples) against the
+    FP64 oracle evaluated on their dependency cones (oracle.sample_after)
+    from the same initial projection.  Runs after the timed region, on the
+    host; the GPU values were downloaded before."""
+    if not samples:
+        return {"note": "no sampled oracle check for this workload (the self-consistent field and the "
+                        "nodal x-sweeps depend on whole lines of the state); covered by the parity tests"}
+    import oracle as O
+    t0 = time.perf_counter()
+    l2_num = l2_den = 0.0
+    max_num = max_den = 0.0
+    ncells = 0
+    for item in samples["items"]:
+        q, cells, got, nsweeps = item[:4]
+        if len(item) > 4:            # an explicit sweep list (the 1D stores of Tables III-VI)
+            sched = item[4]
+        elif q.splitting == "advect":   # the 1D workload: one constant shift per sweep
+            h = (q.grid.hi[0] - q.grid.lo[0]) / q.grid.n[0]
+            sched = [(0, -1, np.array([q.velocity * q.dt / h]))]
+        else:
+            sched = O.schedule(q.grid, "strang", q.dt, q.field_list())
+        reps = nsweeps // len(sched)
+        ref = O.sample_after(q.grid, q.k, q.nq, q.weights, q.params, sched * reps, cells)
+        w = O.l2_weights(q.k, q.grid.ndim)
+        d = np.asarray(got, dtype=np.float64) - ref
+        l2_num += float(np.sum(d * d * w))
+        l2_den += float(np.sum(ref * ref * w))
+        max_num = max(max_num, float(np.max(np.abs(d))))
+        max_den = max(max_den, float(np.max(np.abs(ref))))
+        ncells += len(cells)
+    rel_l2 = math.sqrt(l2_num / l2_den) if l2_den > 0 else math.sqrt(l2_num)
+    rel_max = max_num / max_den if max_den > 0 else max_num
+    kind, bound = ERROR_BOUND[storage]
+    val = rel_l2 if kind == "rel_l2" else rel_max
+    return {"rel_l2": rel_l2, "rel_max": rel_max, "cells": ncells, "problems": len(samples["items"]),
+            "steps": samples["steps"], "bound": {kind: bound}, "within_bound": bool(val <= bound),
+            "oracle_s": time.perf_counter() - t0,
+            "how": "sampled cells (first, last, random) after these steps from the initial projection on the "
+                   "timed context and launch path, against the FP64 oracle on their dependency cones"}
 
 
 def _oracle_worker(sample):
@@ -336,6 +385,10 @@ class Arm:
             self.sweeps = 3
             self.dt = probs[0].dt
             self.order = None
+            # the time loop replayed from a CUDA graph (one Strang step: 3 sweeps
+            # with their table launches; the batch keeps one graph per parity)
+            self.graph = True
+            self.obj.graph_capture("strang", self.dt, 1)
         else:
             p = self.p
             self.obj = S.Context(p.grid, p.k, storage, stream=stream)
@@ -344,7 +397,8 @@ class Arm:
                 self.obj.set_poisson(True)
             elif p.splitting != "advect":
                 self.obj.set_fields(p.field_list())
-            if getattr(args, "nodal_v", False):
+            self.nodal = getattr(args, "nodal_v", False)
+            if self.nodal:
                 self.obj.set_nodal_velocity(True)
             apply_shapes(self.obj, shapes)
             self.dof = p.dof
@@ -365,12 +419,49 @@ class Arm:
                 self.shift = p.velocity * p.dt / h
                 self.obj.graph_capture_advect(0, -1, [self.shift], ADVECT_GRAPH_SWEEPS)
 
-    def step(self, n):
-        if self.workload == "1d" or getattr(self, "graph", False):
+    def step(self, n, eager=False):
+        if not eager and (self.workload == "1d" or getattr(self, "graph", False)):
             for _ in range(n):
                 self.obj.graph_launch()
         else:
             self.obj.step("strang", self.dt, n)
+
+    def restart(self):
+        """Back to the initial projection (the state the timed steps started from)."""
+        if self.workload == "batch":
+            for i, q in enumerate(self.p):
+                self.obj.project(i, q.nq, q.weights, q.params)
+        else:
+            self.obj.project(self.p.nq, self.p.weights, self.p.params)
+
+    def samples(self, seed=7):
+        """Coefficients of sampled cells after a few timed-path steps from the
+        initial projection, for the error against the FP64 oracle (computed
+        by the oracle leg after the timed region).  The steps run on the same
+        context and launch path as the timed ones: 2 split steps in up to four
+        dimensions, 1 in six (each target cell depends on two source cells per
+        sweep, so the oracle evaluates a cone of at most 2^sweeps cells per
+        sample), the 1D workload's 100-sweep graph once."""
+        rng = np.random.default_rng(seed)
+        if self.workload == "vp" or getattr(self, "nodal", False):
+            return None
+        self.restart()
+        if self.workload == "batch":
+            steps = 2
+            self.step(steps)
+            picks = sorted({0, len(self.p) // 3, 2 * len(self.p) // 3, len(self.p) - 1})
+            out = []
+            for i in picks:
+                q = self.p[i]
+                cells = np.concatenate([[0, q.grid.cells - 1], rng.integers(0, q.grid.cells, 6)])
+                out.append((q, cells, self.obj.get_coeffs(i)[cells], steps * 3))
+            return {"steps": steps, "items": out}
+        q = self.p
+        steps = 1 if q.grid.ndim > 4 or self.workload == "1d" else 2
+        self.step(steps)
+        cells = np.concatenate([[0, q.grid.cells - 1], rng.integers(0, q.grid.cells, 14)])
+        nsw = steps * self.sweeps
+        return {"steps": steps, "items": [(q, cells, self.obj.get_cells(cells), nsw)]}
 
     def mass_total(self):
         m = self.obj.mass()
@@ -426,11 +517,22 @@ def run_ours(args):
         info = {"state_bytes": arm.state_bytes, "dof": arm.dof, "sweeps": arm.sweeps,
                 "tune": arm.tunes(), "order": arm.order,
                 "graph": arm.workload == "1d" or getattr(arm, "graph", False)}
+        if arm.workload == "batch":
+            # the graph has no per-sweep events: one eager, profiled step after
+            # the timed region gives the per-dimension kernel times
+            arm.obj.profile_enable(True)
+            arm.step(1, eager=True)
+            arm.obj.synchronize()
+            arm.obj.profile_query()
+            dims = arm.obj.profile_dims()
+            arm.obj.profile_enable(False)
+            info["per_dim_from"] = "one eager step after the timed region"
         if dims:
             nd, msd = dims
             info["per_dim"] = [{"dim": d, "launches": nd[d], "ms_per_launch": msd[d] / max(nd[d], 1),
                                 "gbs": 2.0 * arm.state_bytes / (msd[d] / max(nd[d], 1) / 1e3) / 1e9
                                 if nd[d] else None} for d in range(len(nd)) if nd[d]]
+        info["samples"] = arm.samples() if rank == 0 else None
         arm.obj.close()
         return ms, prof, abs(m1 - m0) / abs(m0), clk, info
 
@@ -468,18 +570,23 @@ def run_ours(args):
         if info64["order"]:          # one degree for the whole state (not the mixed batch)
             flops64 = 4.0 * info64["order"] * info64["dof"]
             mhz = (clk64 or {}).get("sm_mhz") or 2070.0
-            alu_peak = 2.0 * 2.0 * 152 * mhz * 1e6 / 1e12
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
             alu_ach = flops64 / (sms64 / max(nl64, 1) / 1000.0) / 1e12
+            alu_peak = S.sl_selftest_fp64_rate(1 << 14, stream) / 1e12
             alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
                    "frac": alu_ach / alu_peak,
-                   "peak_source": f"derived: 2 FP64 FMA/clk/SM x 152 SMs x {mhz:.0f} MHz",
+                   "peak_source": "measured in this run: sl_selftest_fp64_rate (best of 8 or 16 independent "
+                                  "FP64 FMA chains per thread at 1024 or 2048 threads per SM, CUDA events)",
+                   "derived_peak": 2.0 * 2.0 * sms * mhz * 1e6 / 1e12,
+                   "derived_peak_note": f"2 FP64 FMA/clk/SM x {sms} SMs x {mhz:.0f} MHz (sampled clock)",
                    "flops_per_launch": flops64}
         fp64 = {"value": v64, "unit": UNIT, "ms_per_step": ms64_max / args.steps,
                 "sweep_ms": sms64 / max(nl64, 1),
                 "sweep_gbs": (sb64 / max(nl64, 1)) / (sms64 / max(nl64, 1) / 1000.0) / 1e9,
                 "mass_drift": drift64, "state_bytes": info64["state_bytes"], "clocks": clk64,
                 "per_dim": info64.get("per_dim"),
-                "roofline": alu}
+                "roofline": alu,
+                "error": oracle_error(info64.get("samples"), "fp64") if rank == 0 else None}
 
     e2e = None
     if not args.no_e2e and args.workload == "4d":
@@ -518,8 +625,9 @@ def run_ours(args):
             "config": {"workload": wl, "dof": info["dof"], "sweeps_per_step": info["sweeps"],
                        "state_bytes": info["state_bytes"], "l2": l2note,
                        "parallelism": f"replicas x{world}", "tune": info["tune"],
-                       "cuda_graph": info["graph"]},
+                       "cuda_graph": info["graph"], "per_dim_from": info.get("per_dim_from")},
             "mass_drift": drift,
+            "error": oracle_error(info.get("samples"), args.storage),
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
                          "frac": achieved_gbs / peak_gbs, "traffic": traffic,
                          "traffic_note": traffic_note,
@@ -580,7 +688,8 @@ def run_paper1d(args):
     for k, store in todo:
         ctx = S.Context(g, k, store, stream=stream)
         # 1 + cos(2 pi 8 x + 0.3): the oscillatory profile of Table II
-        ctx.project(k + 2, [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]])
+        prof_w, prof_p = [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]]
+        ctx.project(k + 2, prof_w, prof_p)
         apply_shapes(ctx, args.shapes)
         m0 = ctx.mass()
         for _ in range(args.warmup):
@@ -606,6 +715,16 @@ def run_paper1d(args):
         drift = abs(ctx.mass() - m0) / abs(m0)
         info = ctx.info
         tune = ctx.get_tune(0)
+        # sampled cells after 4 sweeps from the initial projection, for the
+        # oracle leg below
+        ctx.project(k + 2, prof_w, prof_p)
+        for _ in range(4):
+            ctx.advect(0, -1, [shift])
+        rng = np.random.default_rng(7)
+        cells = np.concatenate([[0, n - 1], rng.integers(0, n, 14)])
+        q = W.Problem(name=f"1d_{store}", grid=g, k=k, storage=store, dt=0.0, steps=4, splitting="advect",
+                      weights=np.asarray(prof_w), params=np.asarray(prof_p), nq=k + 2)
+        sample = {"steps": 4, "items": [(q, cells, ctx.get_cells(cells), 4, [(0, -1, np.array([shift]))])]}
         ctx.close()
         ms_max, units = aggregate(ms, float(args.steps * info["dof"]), world, dev)
         sweep_ms = sms / max(nl, 1)
@@ -619,7 +738,8 @@ def run_paper1d(args):
                      "sweep_gbs": gbs, "frac_of_hbm": gbs / peak_gbs, "sweep_ms": sweep_ms,
                      "dof_per_s": rate, "speedup_vs_fp64": rate / r64 if r64 else None,
                      "memorydown": b64 / info["state_bytes"] if b64 else None, "mass_drift": drift,
-                     "state_bytes": info["state_bytes"], "tune": tune, "clocks": clk})
+                     "state_bytes": info["state_bytes"], "tune": tune, "clocks": clk,
+                     "error": oracle_error(sample, store) if rank == 0 else None})
         if head is None or (k == 3 and store == "mix_fp32"):
             head = rows[-1]
             head_launch = (nl, sms, sbytes)
@@ -639,6 +759,7 @@ def run_paper1d(args):
                        "l2": f"state {head['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "mass_drift": head["mass_drift"],
+            "error": head["error"],
             "roofline": {"bound": "hbm", "achieved": head["sweep_gbs"], "peak": peak_gbs, "unit": "GB/s",
                          "frac": head["sweep_gbs"] / peak_gbs, "traffic": None,
                          "traffic_note": "no ncu capture of this workload's kernels",
@@ -691,7 +812,9 @@ def run_e2e(S, W, p, args, stream, world, dev):
     ms_max, units = aggregate(secs * 1000.0, float(args.steps * sweeps * p.dof), world, dev)
     return {"value": units / (ms_max / 1000.0), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": 8,
-            "note": "per step: raw-plane upload from pinned host memory + one Strang step + mass readback"}
+            "note": "per step: raw-plane upload of the whole state from pinned host memory, one Strang "
+                    "step, mass readback; the stepped state stays in device memory (the next step "
+                    "uploads the host copy again)"}
 
 
 def main(argv=None):

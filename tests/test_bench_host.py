@@ -76,3 +76,33 @@ def test_traffic_bookkeeping():
         assert 0.9e9 < t < 1.1e9
     t, why = bench.sweep_traffic("2d", "fp64", 1.0e9)
     assert t is None and "no ncu capture" in why
+
+
+def test_oracle_error_of_exact_and_perturbed_samples():
+    """The bench line's error against the oracle: zero for the oracle's own
+    values, and the planted perturbation's size otherwise (relative L2 with
+    the Legendre weights, relative max), over a 2D and a 1D sample."""
+    import numpy as np
+    import oracle as O
+    from paper_1603_07008_gb300 import workloads as W
+    p = W.config2(n=16, steps=1)
+    cells = np.array([0, 5, 77, 255])
+    sched = O.schedule(p.grid, "strang", p.dt, p.field_list())
+    exact = O.sample_after(p.grid, p.k, p.nq, p.weights, p.params, sched * 2, cells)
+    e = bench.oracle_error({"steps": 2, "items": [(p, cells, exact.copy(), 6)]}, "mix_fp32")
+    assert e["rel_l2"] == 0.0 and e["rel_max"] == 0.0 and e["within_bound"] and e["cells"] == 4
+    bad = exact.copy()
+    bad[2, 3] += 1e-3 * np.max(np.abs(exact))
+    e = bench.oracle_error({"steps": 2, "items": [(p, cells, bad, 6)]}, "mix_fp32")
+    assert abs(e["rel_max"] - 1e-3) < 1e-12
+    w = O.l2_weights(p.k, 2)
+    want = np.sqrt(np.sum((bad - exact) ** 2 * w) / np.sum(exact ** 2 * w))
+    assert abs(e["rel_l2"] - want) <= 1e-15 and not e["within_bound"]
+    q = W.config1()
+    h = 1.0 / q.grid.n[0]
+    s1 = [(0, -1, np.array([q.velocity * q.dt / h]))]
+    c1 = np.array([3, 1000])
+    ref = O.sample_after(q.grid, q.k, q.nq, q.weights, q.params, s1 * 100, c1)
+    e = bench.oracle_error({"steps": 1, "items": [(q, c1, ref, 100)]}, "fp64")
+    assert e["rel_max"] == 0.0 and e["bound"] == {"rel_max": 1e-12}
+    assert bench.oracle_error(None, "mix_fp32")["note"]
