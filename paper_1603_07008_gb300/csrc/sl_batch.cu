@@ -95,10 +95,109 @@ __device__ __forceinline__ void unit_run_body(const SweepArgs& a, uint32_t c, ui
     }
 }
 
+// Element offsets of a fibre group's planes from hi, formed once per work
+// item in 32 bits (the problem's planes hold fewer than 2^31 elements), so
+// that every access costs one 32-bit add and one address formation instead
+// of a 64-bit product per value.
+template <int K, int MODE, int FT, bool MEAN>
+struct PlaneOffsets {
+    using T = typename St<MODE>::T;
+    static constexpr int O = K + 1;
+    int32_t off[FT][O];   // (J - 1) * pstride of value (u, l); unused for the mean
+
+    __device__ __forceinline__ void init(int64_t pstride, const int (&jb)[FT])
+    {
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) off[u][l] = int32_t(int64_t(jb[u] + l - 1) * pstride);
+    }
+    __device__ __forceinline__ void load(const Planes& p, uint32_t c, CellVals<K, MODE, FT>& cv) const
+    {
+        const T* hi = static_cast<const T*>(p.hi);
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0) {
+                    cv.m = __ldg(p.mean + c);
+                    cv.v[0][0] = 0;
+                } else {
+                    cv.v[u][l] = ld_raw(hi + (off[u][l] + int32_t(c)));
+                }
+            }
+    }
+    __device__ __forceinline__ void store(const Planes& p, uint32_t c, const CellVals<K, MODE, FT>& cv) const
+    {
+        T* hi = static_cast<T*>(p.hi);
+#pragma unroll
+        for (int u = 0; u < FT; ++u)
+#pragma unroll
+            for (int l = 0; l < O; ++l) {
+                if (MEAN && u == 0 && l == 0)
+                    p.mean[c] = cv.m;
+                else
+                    st_raw(hi + (off[u][l] + int32_t(c)), cv.v[u][l]);
+            }
+    }
+};
+
+// The runs of one work item with the plane offsets formed once (see
+// PlaneOffsets); the same arithmetic as unit_run_body, cell for cell.
+template <int K, int MODE, int FT, bool MEAN, int PC>
+__device__ __forceinline__ void unit_runs_offsets(const SweepArgs& a, uint32_t start, const int (&jb)[FT], int fbase,
+                                                  int reps)
+{
+    PlaneOffsets<K, MODE, FT, MEAN> P;
+    P.init(a.pstride, jb);
+    const int32_t N = int32_t(a.N);
+    for (int r = 0; r < reps; ++r) {
+        const uint32_t c = start + PC * (threadIdx.x + uint32_t(r) * kBatchBlock);
+        if (c >= a.cells) break;
+        const uint32_t line = a.fdN.div(c);
+        const uint32_t ls = line * a.N;
+        const uint32_t i = c - ls;
+        if (i + PC > a.N) {   // the run crosses a line end: one cell at a time
+            for (int q = 0; q < PC; ++q)
+                if (c + q < a.cells) unit_cell<K, MODE, FT>(a, c + q, fbase);
+            continue;
+        }
+        const uint32_t cls = shift_class(a, 0, line);
+        const int32_t sig = __ldg(a.tab.sigma + cls);
+        int32_t ib = int32_t(i) - sig - 1;
+        ib += ib < 0 ? N : 0;
+        ib += ib < 0 ? N : 0;
+        Mats<K, MODE> M;
+        M.template load<MEAN>(a.tab, cls);
+        CellVals<K, MODE, FT> v[PC + 1];
+#pragma unroll
+        for (int q = 0; q <= PC; ++q) {
+            int32_t x = ib + q;
+            x -= x >= N ? N : 0;
+            P.load(a.src, ls + uint32_t(x), v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < PC; ++q) {
+            CellVals<K, MODE, FT> out;
+            combine<K, MODE, FT, MEAN>(M, v[q + 1], v[q], out);
+            P.store(a.dst, c + q, out);
+        }
+    }
+}
+
 template <int K, int MODE, int FT, int PC>
 __device__ __noinline__ void unit_item_runs(const SweepArgs* __restrict__ ap, uint32_t start, int fbase, int reps)
 {
     const SweepArgs& a = *ap;
+    if (a.pstride * int64_t(a.nfib * (K + 1)) < (int64_t(1) << 31)) {
+        int jb[FT];
+        group_bases<FT>(fbase, a.nfib, K + 1, 1, jb);
+        if (fbase == 0)
+            unit_runs_offsets<K, MODE, FT, true, PC>(a, start, jb, fbase, reps);
+        else
+            unit_runs_offsets<K, MODE, FT, false, PC>(a, start, jb, fbase, reps);
+        return;
+    }
     for (int r = 0; r < reps; ++r) {
         const uint32_t c = start + PC * (threadIdx.x + uint32_t(r) * kBatchBlock);
         if (c >= a.cells) break;
@@ -128,8 +227,10 @@ __device__ __forceinline__ void unit_items(const SweepArgs* __restrict__ ap, uin
         unit_item<K, MODE, FT>(ap, start, fbase, reps);
 }
 
+// At least 6 resident blocks per SM (at most 85 registers per thread):
+// measured ahead of the unconstrained allocation with the runs above.
 template <int MODE, int FTM, int PC>
-__global__ void __launch_bounds__(kBatchBlock) k_batch_unit(const SweepArgs* __restrict__ args,
+__global__ void __launch_bounds__(kBatchBlock, 6) k_batch_unit(const SweepArgs* __restrict__ args,
                                                             const int32_t* __restrict__ kdeg,
                                                             const BatchItem* __restrict__ items,
                                                             int nitems, int reps)
