@@ -38,12 +38,10 @@ namespace sl {
 
 namespace {
 
-// FP32 fibres per thread of the mixed store's nodal sweep (as many as fit
-// the registers without spilling: measured 17% faster with 2 than with 1 at
-// k = 2) ...
-__host__ __device__ constexpr int nodal_ft(int K) { return K <= 1 ? 4 : K == 2 ? 2 : 1; }
-// ... and of its walk form, which also holds the node values of two source
-// cells per fibre.
+// FP32 fibres per thread of the mixed store's nodal sweep (its walk form holds
+// the raw values and node values of two source cells per fibre; with one
+// target per thread two fibres per thread measured 17% faster than one at
+// k = 2).
 __host__ __device__ constexpr int nodal_ftw(int K) { return K == 0 ? 4 : K == 3 ? 1 : 2; }
 
 // Base coefficient index of 2D fibre g: its digits along the dimensions other
@@ -327,10 +325,13 @@ __device__ __forceinline__ void nodal_fp32_group(const NodalArgs& a, uint32_t c,
             }
 }
 
-// Targets per run of the walk form (kernel part 4).
+// Targets per run of the walk form: kernel part 4 (x-dimensions > 0, the
+// lanes of a warp on neighbouring x-lines) and part 5 (x-dimension 0, the
+// lanes on neighbouring runs of one line, so two cells apart).
 constexpr int kNodalRun = 4;
+constexpr int kNodalRun0 = 2;
 
-// The FT FP32 fibres of nodal_fp32_group for the run of cnt <= kNodalRun
+// The FT FP32 fibres of nodal_fp32_group for the run of cnt <= RUN
 // consecutive targets i0 .. i0 + cnt - 1 of one x-line whose v-cell j has one
 // sigma for all its nodes.  Target i reads the source cells a = i - sigma and
 // b = i - sigma - 1, and the a of target i is the b of target i + 1, so the
@@ -340,7 +341,7 @@ constexpr int kNodalRun = 4;
 // step's arithmetic (measured 11% faster along dimension 1 of the 4D store
 // at k = 2).  Every sum is taken in the order of nodal_fp32_group, so the
 // results are the same bits.
-template <int K, int FT, bool OFF32>
+template <int K, int FT, bool OFF32, int RUN>
 __device__ __forceinline__ void nodal_fp32_walk(const NodalArgs& a, uint32_t line0, uint32_t i0, int cnt,
                                                 uint32_t j, int32_t sig, const int (&jb)[FT])
 {
@@ -388,7 +389,7 @@ __device__ __forceinline__ void nodal_fp32_walk(const NodalArgs& a, uint32_t lin
     int32_t xa = xb + 1;
     xa -= xa >= N ? N : 0;
     load_cell(xa, vn);
-    for (int r = 0; r < kNodalRun; ++r) {
+    for (int r = 0; r < RUN; ++r) {
         if (r >= cnt) break;
         float vc[FT][O][O];
 #pragma unroll
@@ -691,11 +692,12 @@ __device__ __forceinline__ void nodal_mean_target(const NodalArgs& a, uint32_t c
         nodal_mean_fibre<K>(a, c, i, line0, j);
 }
 
-// Runs of the walk form along x (PART 4): run = inner + inner_x (rx + nrunx
-// outer) covers the targets x = rx R .. of the x-line through the cell
-// inner + inner_x N outer, so neighbouring threads take neighbouring lines
-// (x-dimension > 0) or neighbouring runs of one line (x-dimension 0).
-template <int K, bool OFF32>
+// Runs of RUN targets of the walk form along x (PARTs 4 and 5): run = inner +
+// inner_x (rx + nrunx outer) covers the targets x = rx RUN .. of the x-line
+// through the cell inner + inner_x N outer, so neighbouring threads take
+// neighbouring lines (x-dimension > 0) or neighbouring runs of one line
+// (x-dimension 0).
+template <int K, bool OFF32, int RUN>
 __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int g)
 {
     constexpr int O = K + 1;
@@ -703,8 +705,8 @@ __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int 
     const uint32_t t = a.fdInnerX.div(run);
     const uint32_t inn = run - t * a.inner_x;
     const uint32_t outer = a.fdRunX.div(t);
-    const uint32_t i0 = (t - outer * a.nrunx) * uint32_t(kNodalRun);
-    const int cnt = min(kNodalRun, int(a.N - i0));
+    const uint32_t i0 = (t - outer * a.nrunx) * uint32_t(RUN);
+    const int cnt = min(RUN, int(a.N - i0));
     const uint32_t line0 = inn + outer * a.N * a.inner_x;
     const uint32_t ov = a.fdInnerV.div(line0);           // the v-cell is the same along the x-line
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;
@@ -721,7 +723,7 @@ __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int 
 #pragma unroll
     for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
     if (same) {
-        nodal_fp32_walk<K, FT, OFF32>(a, line0, i0, cnt, j, s0, jb);
+        nodal_fp32_walk<K, FT, OFF32, RUN>(a, line0, i0, cnt, j, s0, jb);
     } else {
         for (int r = 0; r < cnt; ++r)
             nodal_fp32_group<K, FT, OFF32>(a, line0 + (i0 + uint32_t(r)) * a.inner_x, i0 + uint32_t(r), line0,
@@ -730,23 +732,25 @@ __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int 
 }
 
 // PART 0: every fibre (FP64 store; fibre blockIdx.y); 1: only the mean's
-// fibre of the mixed store (two dimensions); 3 and 4: every fibre of the
+// fibre of the mixed store (two dimensions); 4 and 5: every fibre of the
 // mixed store, the blocks of the fibre groups interleaved in a 1D grid (block
 // b takes group b % groups), so that blocks of the mean's fibre, bound by the
 // FP64 pipe, run beside blocks of FP32 fibres, bound by instruction issue;
-// 3 takes one target per thread, 4 a run of kNodalRun targets along x.
-// Part 4 serves x-dimensions > 0, where the lanes of a warp sit on
+// the FP32 fibres take runs of consecutive targets along x.  Part 4 (runs of
+// kNodalRun) serves x-dimensions > 0, where the lanes of a warp sit on
 // neighbouring x-lines, so that every step of the runs is coalesced (measured
-// 8.5% faster than part 3 along dimension 1 of the 4D store at k = 2).  Along
-// dimension 0 the lanes of a run would read kNodalRun cells apart (21%
-// slower), so part 3 serves it.
+// 8.5% faster than one target per thread along dimension 1 of the 4D store at
+// k = 2).  Along dimension 0 the lanes of a run sit RUN cells apart: part 5
+// takes runs of kNodalRun0 = 2 there (4652 GB/s against 4090 for one target
+// per thread, 3521 and 3169 for runs of 3 and 4, in the 4D store at k = 2).
 template <int K, int MODE, int PART>
-__global__ void __launch_bounds__(PART >= 3 ? 128 : 256, K == 3 ? 1 : PART >= 3 ? 4 : 2)
+__global__ void __launch_bounds__(PART >= 4 ? 128 : 256, K == 3 ? 1 : PART >= 4 ? 4 : 2)
     k_sweep_nodal(const NodalArgs a)
 {
     constexpr int O = K + 1;
-    if constexpr (PART == 4) {
+    if constexpr (PART == 4 || PART == 5) {
         constexpr int FT = nodal_ftw(K);
+        constexpr int RUN = PART == 4 ? kNodalRun : kNodalRun0;
         // group 0: the mean's fibre; group r >= 1: FP32 fibres 1 + (r - 1) FT ..
         const uint32_t ngroups = 1 + (a.nfib2 - 2) / FT + 1;
         const int r = int(blockIdx.x % ngroups);
@@ -754,40 +758,23 @@ __global__ void __launch_bounds__(PART >= 3 ? 128 : 256, K == 3 ? 1 : PART >= 3 
         if (run >= a.nruns) return;
         const int g = r == 0 ? 0 : 1 + (r - 1) * FT;
         if (a.off32)
-            nodal_run<K, true>(a, run, g);
+            nodal_run<K, true, RUN>(a, run, g);
         else
-            nodal_run<K, false>(a, run, g);
+            nodal_run<K, false, RUN>(a, run, g);
         return;
     }
-    constexpr int FT = nodal_ft(K);
-    int g = int(blockIdx.y);
-    uint32_t bx = blockIdx.x;
-    if constexpr (PART == 3) {
-        const uint32_t ngroups = 1 + (a.nfib2 - 2) / FT + 1;
-        const int r = int(blockIdx.x % ngroups);
-        bx = blockIdx.x / ngroups;
-        g = r == 0 ? 0 : 1 + (r - 1) * FT;
-    }
-    const uint32_t c = bx * blockDim.x + threadIdx.x;
+    const int g = int(blockIdx.y);
+    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.cells) return;
     const uint32_t ox = a.fdInnerX.div(c);
     const uint32_t i = ox - a.fdNX.div(ox) * a.N;        // coordinate along x
     const uint32_t ov = a.fdInnerV.div(c);
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;       // v-cell
     const uint32_t line0 = c - i * a.inner_x;
-    if constexpr (MODE == M_FP64) {
+    if constexpr (MODE == M_FP64)
         nodal_plain<K, double>(a, c, i, line0, j, nodal_fibre_base<O>(a, g));
-    } else if (PART == 1 || g == 0) {
+    else
         nodal_mean_target<K>(a, c, i, line0, j);
-    } else {
-        int jb[FT];
-#pragma unroll
-        for (int u = 0; u < FT; ++u) jb[u] = nodal_fibre_base<O>(a, min(g + u, int(a.nfib2) - 1));
-        if (a.off32)
-            nodal_fp32_group<K, FT, true>(a, c, i, line0, j, jb);
-        else
-            nodal_fp32_group<K, FT, false>(a, c, i, line0, j, jb);
-    }
 }
 
 template <int K>
@@ -799,19 +786,20 @@ cudaError_t nodal_launch(int mode, const NodalArgs& a, int nfib2, cudaStream_t s
         k_sweep_nodal<K, M_FP64, 0><<<dim3(bx, uint32_t(nfib2)), block, 0, st>>>(a);
     } else if (nfib2 == 1) {
         k_sweep_nodal<K, M_F32, 1><<<dim3(bx, 1), block, 0, st>>>(a);
-    } else if (a.inner_x == 1) {
-        const uint64_t nb = uint64_t((a.cells + 127) / 128) * uint64_t(1 + (nfib2 - 2) / nodal_ft(K) + 1);
-        if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
-        k_sweep_nodal<K, M_F32, 3><<<uint32_t(nb), 128, 0, st>>>(a);
     } else {
+        const int run = a.inner_x == 1 ? kNodalRun0 : kNodalRun;
         NodalArgs b = a;
-        b.nrunx = (a.N + kNodalRun - 1) / kNodalRun;
+        b.nrunx = (a.N + run - 1) / run;
         b.fdRunX.set(b.nrunx);
         const uint64_t nruns = uint64_t(a.cells / a.N) * b.nrunx;
+        if (nruns > 0xffffffffu) return cudaErrorInvalidValue;
         b.nruns = uint32_t(nruns);
         const uint64_t nb = (nruns + 127) / 128 * uint64_t(1 + (nfib2 - 2) / nodal_ftw(K) + 1);
         if (nb > 0x7fffffffu) return cudaErrorInvalidValue;
-        k_sweep_nodal<K, M_F32, 4><<<uint32_t(nb), 128, 0, st>>>(b);
+        if (a.inner_x == 1)
+            k_sweep_nodal<K, M_F32, 5><<<uint32_t(nb), 128, 0, st>>>(b);
+        else
+            k_sweep_nodal<K, M_F32, 4><<<uint32_t(nb), 128, 0, st>>>(b);
     }
     return cudaGetLastError();
 }

@@ -242,12 +242,15 @@ def _swap01(u, n, k):
 
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_nodal_runs_match_one_target_per_thread_bit_for_bit(k):
-    """Along x-dimension 1 the FP32 fibres of the mixed store take runs of
-    consecutive targets per thread; along x-dimension 0 one target per thread.
-    Both keep the same order of every sum, so the sweep along dimension 1
+    """The FP32 fibres of the mixed store take runs of consecutive targets
+    per thread: four along x-dimension 1 (lanes on neighbouring x-lines), two
+    along x-dimension 0 (lanes on neighbouring runs of one line), and one
+    target at a time where the nodes of a v-cell do not share sigma.  Every
+    form keeps the same order of every sum, so the sweep along dimension 1
     equals, bit for bit, the sweep along dimension 0 of the state with
-    dimensions 0 and 1 exchanged: runs cut by the line end (9 = 4 + 4 + 1),
-    wrapped sources, and v-cells whose nodes do and do not share sigma."""
+    dimensions 0 and 1 exchanged: runs cut by the line end (9 = 4 + 4 + 1 and
+    2 + 2 + 2 + 2 + 1), wrapped sources, and v-cells whose nodes do and do
+    not share sigma."""
     n = (7, 9, 5, 4)
     g = W.Grid(n=n, lo=(0.0, 0.0, -3.0, -3.0), hi=(1.0, 2.0, 2.0, 2.0), pair=(2, 3, -1, -1))
     ns = (9, 7, 5, 4)
