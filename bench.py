@@ -171,23 +171,52 @@ def summarise_clocks(lines):
 # traffic is reported as null.
 TRAFFIC = {
     ("4d", "mix_fp32"): {
-        "ratio": (2 * 0.98550 + 2 * 1.00206 + 2 * 1.00737) / 6,
+        "ratio": (2 * 0.98530 + 1.00000 + 1.00620 + 0.99570 + 1.00000) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "ac91a006f047484d",
-        "capture": "48^4 cells, k=2; 3.431 / 3.490 / 3.507 GB per launch (vector form, walks with 2 and "
-                   "1 fibres) against 3.483 GB algorithmic"},
+        "sha256": "b172f4a8097cf141",
+        "capture": "48^4 cells, k=2, one Strang step (6 launches: vector form along dimension 0, walks with 1 fibre, "
+                   "4 cells per step along the others): 3.431-3.504 GB per launch against 3.482 GB algorithmic"},
     ("6d", "mix_bf16"): {
-        "ratio": (2 * 1.03530 + 7 * 1.03691) / 9,
+        "ratio": (2 * 1.00600 + 2 * 1.03095 + 2 * 1.02920 + 1.03020 + 1.03040 + 1.03250) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "5424e174e5f11611",
-        "capture": "16^6 cells, k=1, BF16 records, lane groups; 4.795 / 4.802 GB per launch (dimensions 0, "
-                   "1) against 4.631 GB algorithmic"},
+        "sha256": "b86df808c2738f95",
+        "capture": "16^6 cells, k=1, BF16 records, lane groups, one Strang step (9 launches): 4.660-4.781 GB per "
+                   "launch against 4.631 GB algorithmic"},
+    ("2d", "mix_fp32"): {
+        "ratio": (0.96570 + 0.97300 + 0.96310) / 3,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
+        "sha256": "b172f4a8097cf141",
+        "capture": "4096^2 cells, k=2 (the size of the workload), library default shapes, one Strang step: "
+                   "1.293-1.306 GB per launch against 1.342 GB algorithmic"},
+    ("vp", "mix_fp32"): {
+        "ratio": (0.96570 + 0.97250 + 0.96280) / 3,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
+        "sha256": "b172f4a8097cf141",
+        "capture": "4096^2 cells, k=2 (the size of the workload), self-consistent field, library default shapes, one "
+                   "Strang step (sweeps only): 1.292-1.305 GB per launch against 1.342 GB algorithmic"},
+    ("4d_nodal_v", "mix_fp32"): {
+        "ratio": (0.94760 + 0.93200 + 0.95940 + 0.94210 + 0.94250 + 0.93230) / 6,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
+        "sha256": "1b6b979d64c202da",
+        "capture": "32^4 cells, k=2, nodal x-sweeps (runs of 2 along dimension 0, of 4 along dimension 1), one "
+                   "Strang step: 0.641-0.660 GB per launch against 0.688 GB algorithmic"},
+    ("2d_nodal_v", "mix_fp32"): {
+        "ratio": (0.96890 + 0.97310 + 0.96670) / 3,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
+        "sha256": "1b6b979d64c202da",
+        "capture": "4096^2 cells, k=2 (the size of the workload), nodal x-sweep, one Strang step: 1.298-1.306 GB per "
+                   "launch against 1.342 GB algorithmic"},
+    ("paper1d", "mix_fp32"): {
+        "ratio": 0.96370,
+        "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
+        "sha256": "b172f4a8097cf141",
+        "capture": "2^25 cells, order 4, c_0 in FP64: 1.293 GB per launch against 1.342 GB algorithmic"},
     ("batch", "mix_fp32"): {
-        "ratio": (2 * 0.95799 + 1.04195) / 3,
+        "ratio": (2 * 0.96195 + 1.03940) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu"],
-        "sha256": "36d89809795b4a94",
-        "capture": "64 problems, default shapes; 1.046 / 1.138 GB per launch (dimensions 0, 1) against "
-                   "1.092 GB algorithmic"},
+        "sha256": "0f37c8d9a038b583",
+        "capture": "64 problems, shapes (3 fibres, runs of 2) / (1 fibre, 4 rows per step, 64-row items), one Strang "
+                   "step: 1.049-1.135 GB per launch against 1.092 GB algorithmic"},
 }
 
 
@@ -378,8 +407,11 @@ class Arm:
             for i, q in enumerate(probs):
                 self.obj.project(i, q.nq, q.weights, q.params)
             self.obj.set_fields([q.field_list()[0] for q in probs])
-            if shapes != "default":
+            if shapes is None:
                 self.obj.autotune(3)
+            elif shapes != "default":   # sl_batch_set_tune fields per dimension
+                for d, sh in enumerate(json.loads(shapes)):
+                    self.obj.set_tune(d, **sh)
             self.dof = self.obj.info["dof"]
             self.state_bytes = self.obj.info["state_bytes"]
             self.sweeps = 3
@@ -575,8 +607,8 @@ def run_ours(args):
             alu_peak = S.sl_selftest_fp64_rate(1 << 14, stream) / 1e12
             alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "TFLOP/s",
                    "frac": alu_ach / alu_peak,
-                   "peak_source": "measured in this run: sl_selftest_fp64_rate (best of 8 or 16 independent "
-                                  "FP64 FMA chains per thread at 1024 or 2048 threads per SM, CUDA events)",
+                   "peak_source": "measured in this run: sl_selftest_fp64_rate (8 independent chains of FP64 "
+                                  "FMAs with register operands per thread, 1024 or 2048 threads per SM, CUDA events)",
                    "derived_peak": 2.0 * 2.0 * sms * mhz * 1e6 / 1e12,
                    "derived_peak_note": f"2 FP64 FMA/clk/SM x {sms} SMs x {mhz:.0f} MHz (sampled clock)",
                    "flops_per_launch": flops64}
@@ -747,6 +779,8 @@ def run_paper1d(args):
     if rank == 0:
         nl, sms, sbytes = head_launch
         avg = sms / max(nl, 1)
+        head_traffic = sweep_traffic("paper1d", head["store"], sbytes / max(nl, 1)) if head["order"] == 4 else \
+            (None, "no ncu capture of this row's kernel")
         out = {
             "metric": METRIC, "value": head["dof_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["sweep_ms"],
@@ -761,8 +795,8 @@ def run_paper1d(args):
             "mass_drift": head["mass_drift"],
             "error": head["error"],
             "roofline": {"bound": "hbm", "achieved": head["sweep_gbs"], "peak": peak_gbs, "unit": "GB/s",
-                         "frac": head["sweep_gbs"] / peak_gbs, "traffic": None,
-                         "traffic_note": "no ncu capture of this workload's kernels",
+                         "frac": head["sweep_gbs"] / peak_gbs, "traffic": head_traffic[0],
+                         "traffic_note": head_traffic[1],
                          "kernel": "sweep along dimension 0", "peak_source": peak_src,
                          "bytes_per_launch": sbytes / max(nl, 1), "avg_launch_ms": avg, "launches": nl},
             "table": rows,
