@@ -743,8 +743,11 @@ __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int 
 // k = 2).  Along dimension 0 the lanes of a run sit RUN cells apart: part 5
 // takes runs of kNodalRun0 = 2 there (4652 GB/s against 4090 for one target
 // per thread, 3521 and 3169 for runs of 3 and 4, in the 4D store at k = 2).
+// Part 1 runs at least 4 blocks of 256 threads per SM (64 registers): in 2D
+// 4096^2 at k = 2 it measured 3820 GB/s against 2782 with 2 (96 registers)
+// and 3540 with 3.
 template <int K, int MODE, int PART>
-__global__ void __launch_bounds__(PART >= 4 ? 128 : 256, K == 3 ? 1 : PART >= 4 ? 4 : 2)
+__global__ void __launch_bounds__(PART >= 4 ? 128 : 256, K == 3 ? 1 : PART >= 4 ? 4 : PART == 1 ? 4 : 2)
     k_sweep_nodal(const NodalArgs a)
 {
     constexpr int O = K + 1;
