@@ -65,6 +65,9 @@ def parse_args(argv=None):
                          "(e.g. to profile one fixed kernel)")
     ap.add_argument("--nprob", type=int, default=256, help="problems of the batched workload")
     ap.add_argument("--order", type=int, default=None, help="paper1d: only the rows of this order (2 or 4)")
+    ap.add_argument("--arith", choices=["store", "fp64"], default="store",
+                    help="arithmetic of the timed arm's FP32 rows (sl_set_arithmetic): the store's own "
+                         "(FP32) or FP64 with FP32 storage")
     ap.add_argument("--nodal-v", action="store_true",
                     help="4d/2d: x-sweeps with the velocity at the Gauss nodes of every v-cell")
     return ap.parse_args(argv)
@@ -425,6 +428,8 @@ class Arm:
             p = self.p
             self.obj = S.Context(p.grid, p.k, storage, stream=stream)
             self.obj.project(p.nq, p.weights, p.params)
+            if storage != "fp64":
+                self.obj.set_arithmetic(getattr(args, "arith", "store"))
             if self.workload == "vp":      # field from the state before every v-sweep
                 self.obj.set_poisson(True)
             elif p.splitting != "advect":
@@ -547,6 +552,7 @@ def run_ours(args):
         arm.obj.profile_enable(False)
         m1 = arm.mass_total()
         info = {"state_bytes": arm.state_bytes, "dof": arm.dof, "sweeps": arm.sweeps,
+                "nodal_x_sweeps": 2 * len(arm.p.grid.x_dims()) if getattr(arm, "nodal", False) else 0,
                 "tune": arm.tunes(), "order": arm.order,
                 "graph": arm.workload == "1d" or getattr(arm, "graph", False)}
         if arm.workload == "batch":
@@ -582,7 +588,8 @@ def run_ours(args):
     achieved_gbs = bytes_per_sweep / (avg_sweep_ms / 1000.0) / 1e9
     peak_gbs = float(peaks["hbm_gbs"])
     # the captured ratios are of the plain sweeps; the nodal x-sweeps have none
-    traffic, traffic_note = sweep_traffic(args.workload + ("_nodal_v" if args.nodal_v else ""), args.storage,
+    traffic, traffic_note = sweep_traffic(args.workload + ("_nodal_v" if args.nodal_v else "") +
+                                          ("_arith_fp64" if args.arith == "fp64" else ""), args.storage,
                                           bytes_per_sweep)
 
     fp64 = None
@@ -657,7 +664,8 @@ def run_ours(args):
             "config": {"workload": wl, "dof": info["dof"], "sweeps_per_step": info["sweeps"],
                        "state_bytes": info["state_bytes"], "l2": l2note,
                        "parallelism": f"replicas x{world}", "tune": info["tune"],
-                       "cuda_graph": info["graph"], "per_dim_from": info.get("per_dim_from")},
+                       "cuda_graph": info["graph"], "per_dim_from": info.get("per_dim_from"),
+                       "arithmetic": args.arith},
             "mass_drift": drift,
             "error": oracle_error(info.get("samples"), args.storage),
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": peak_gbs, "unit": "GB/s",
@@ -669,7 +677,12 @@ def run_ours(args):
             "fp64": fp64,
             "speedup_mixed_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "e2e": e2e,
-            "gpu_launches": args.steps * info["sweeps"] * 2,
+            # per sweep its table build and the sweep; a nodal x-sweep of the mixed
+            # store also builds its per-v-cell alpha_bar, and the self-consistent
+            # field takes two launches (density sums, field) before the v-sweep
+            "gpu_launches": args.steps * (info["sweeps"] * 2 +
+                                          (info["nodal_x_sweeps"] if args.storage != "fp64" else 0) +
+                                          (2 if args.workload == "vp" else 0)),
             "clocks": clk,
             "cpu_baseline": cpu,
         }
@@ -719,6 +732,8 @@ def run_paper1d(args):
     head = head_launch = None
     for k, store in todo:
         ctx = S.Context(g, k, store, stream=stream)
+        if store != "fp64":
+            ctx.set_arithmetic(args.arith)
         # 1 + cos(2 pi 8 x + 0.3): the oscillatory profile of Table II
         prof_w, prof_p = [1.0, 1.0], [[[0.0, 0.0, 0.0, 0.0]], [[0.0, 0.0, 2 * math.pi * 8, 0.3]]]
         ctx.project(k + 2, prof_w, prof_p)
@@ -779,7 +794,8 @@ def run_paper1d(args):
     if rank == 0:
         nl, sms, sbytes = head_launch
         avg = sms / max(nl, 1)
-        head_traffic = sweep_traffic("paper1d", head["store"], sbytes / max(nl, 1)) if head["order"] == 4 else \
+        head_traffic = sweep_traffic("paper1d" + ("_arith_fp64" if args.arith == "fp64" else ""), head["store"],
+                                     sbytes / max(nl, 1)) if head["order"] == 4 else \
             (None, "no ncu capture of this row's kernel")
         out = {
             "metric": METRIC, "value": head["dof_per_s"], "unit": UNIT, "n_gpus": world,
@@ -790,6 +806,7 @@ def run_paper1d(args):
             "config": {"workload": f"1d_n{n}_k{head['order'] - 1}_{head['store']}_advect_cfl0.37"
                                    + (" (with every store of orders 2, 4)" if len(todo) > 1 else ""),
                        "dof": n * head["order"], "sweeps_per_step": 1, "state_bytes": head["state_bytes"],
+                       "arithmetic": args.arith,
                        "l2": f"state {head['state_bytes'] / 1e9:.2f} GB > L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "mass_drift": head["mass_drift"],
@@ -821,6 +838,8 @@ def run_e2e(S, W, p, args, stream, world, dev):
     ctx = S.Context(p.grid, p.k, args.storage, stream=stream)
     ctx.project(p.nq, p.weights, p.params)
     ctx.set_fields(p.field_list())
+    if args.storage != "fp64":
+        ctx.set_arithmetic(args.arith)
     if args.nodal_v:
         ctx.set_nodal_velocity(True)
     apply_shapes(ctx, args.shapes)

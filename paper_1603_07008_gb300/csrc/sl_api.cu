@@ -406,6 +406,7 @@ cudaError_t launch_nodal_only(sl_ctx* c, int dim)
     a.off32 = double(c->pstride) * double(c->ncoef) < 2147483648.0 ? 1 : 0;
     double eta[kMaxO], w[kMaxO];
     nodal_setup(c->K, eta, w, &a);
+    a.abar = c->d_nabar;
     return launch_sweep_nodal(c->K, c->mode, a, int(ipow(c->O, c->ndim - 2)), c->st);
 }
 
@@ -459,6 +460,13 @@ sl_status nodal_table(sl_ctx* c, int dim, double tau)
     cudaError_t e = launch_ab_build(c->K, int(c->g.n[p] * c->O), uint32_t(c->g.n[dim]), src, c->poly, c->d_nsig,
                                     c->d_nalpha, c->d_nab64, c->d_nab32, c->st);
     if (e != cudaSuccess) return cuda_fail(c, e, "node table launch");
+    if (c->mode == M_F32) {   // alpha_bar per v-cell for the mean's fibre
+        NodalArgs tmp{};
+        double eta[kMaxO], w[kMaxO];
+        nodal_setup(c->K, eta, w, &tmp);
+        e = launch_nodal_abar(c->d_nalpha, int(c->g.n[p]), c->O, tmp.wmean, c->d_nabar, c->st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "node table launch");
+    }
     return SL_OK;
 }
 
@@ -1311,10 +1319,11 @@ static sl_status nodal_alloc(sl_ctx* c)
     double eta[kMaxO], w[kMaxO];
     nodal_setup(c->K, eta, w, &tmp);
     std::vector<double> vel;
-    int maxcls = 1;
+    int maxcls = 1, maxnv = 1;
     for (int m = 0; m < c->ndim; ++m) {
         const int p = c->g.pair[m];
         if (p < 0) continue;
+        maxnv = std::max(maxnv, int(c->g.n[p]));
         c->nodal_vel_off[m] = int64_t(vel.size());
         const double hv = cell_width(c->g, p);
         for (int64_t j = 0; j < c->g.n[p]; ++j)
@@ -1332,6 +1341,8 @@ static sl_status nodal_alloc(sl_ctx* c)
     off = align_up(off + size_t(maxcls) * ab_stride64(c->O) * 8, A);
     const size_t o_ab32 = off;
     off = align_up(off + size_t(maxcls) * ab_stride32(c->O) * 4, A);
+    const size_t o_abar = off;
+    off = align_up(off + size_t(maxnv) * 8, A);
     void* mem = nullptr;
     cudaError_t e = dev_malloc(&mem, off);
     if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
@@ -1347,6 +1358,7 @@ static sl_status nodal_alloc(sl_ctx* c)
     c->d_nalpha = reinterpret_cast<double*>(b + o_alpha);
     c->d_nab64 = reinterpret_cast<double*>(b + o_ab64);
     c->d_nab32 = reinterpret_cast<float*>(b + o_ab32);
+    c->d_nabar = reinterpret_cast<double*>(b + o_abar);
     return SL_OK;
 }
 

@@ -62,6 +62,7 @@ struct sl_ctx {
     double* d_nalpha = nullptr;
     double* d_nab64 = nullptr;
     float* d_nab32 = nullptr;
+    double* d_nabar = nullptr;  // alpha_bar per v-cell of the node table (mixed store)
     double* d_partials = nullptr;
     double* d_mass = nullptr;
     int mass_nblk = 1;

@@ -460,9 +460,10 @@ __device__ __forceinline__ void nodal_fp32_walk(const NodalArgs& a, uint32_t lin
 // because sum_q w'_q delta_q(c) = 0 (the Gauss rule of P_jv, jv >= 1).  E is a
 // function of one cell (alpha_q and the matrices are fixed along a line), so
 // it is formed in FP32 and the FP64 differences E(a) - E(b) telescope along
-// the line: mass is conserved to FP64 rounding with seven FP64 instructions
-// per cell (the FP64 pipe is not what bounds this kernel: the integer-pipe
-// difference of sub_widened measured 11% slower in 2D).  The other coefficients of row 0 take the nodes' deviations from
+// the line: mass is conserved to FP64 rounding with four FP64 instructions
+// per cell, alpha_bar being formed once per v-cell (launch_nodal_abar; the
+// integer-pipe difference of sub_widened measured 11% slower in 2D).  The
+// other coefficients of row 0 take the nodes' deviations from
 // m_a + alpha_bar t, d_q = delta_q(a) + alpha_q (delta_q(b) - delta_q(a))
 // + G_q(a) - G_q(b) + (alpha_q - alpha_bar) t, in FP32.
 template <int K>
@@ -494,14 +495,13 @@ __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint
     for (int x = 0; x < O; ++x)
 #pragma unroll
         for (int v = 0; v < O; ++v) acc[x][v] = 0.0f;
-    double abar = 0.0;
+    const double abar = __ldg(a.abar + j);   // per v-cell (launch_nodal_abar)
     float abar32 = 0.0f, ea = 0.0f, eb = 0.0f;
     float dev[O], a32[O];
 #pragma unroll
     for (int q = 0; q < O; ++q) {
         const uint32_t cls = j * O + q;
         const double al = __ldg(a.tab.alpha + cls);
-        abar = fma(a.wmean[q], al, abar);
         a32[q] = d2f_fast(al, false);
         abar32 = fmaf(a.wmean32[q], a32[q], abar32);
         float A[O][O], B[O][O];
@@ -844,7 +844,31 @@ double legendre_host(int j, double x)
     return p1;
 }
 
+struct NodalWeights {
+    double w[kMaxO];
+};
+
+__global__ void k_nodal_abar(const double* __restrict__ alpha, int nv, int o, NodalWeights W,
+                             double* __restrict__ abar)
+{
+    const int j = int(blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= nv) return;
+    double s = 0.0;
+    for (int q = 0; q < o; ++q) s = fma(W.w[q], __ldg(alpha + size_t(j) * o + q), s);
+    abar[j] = s;
+}
+
 }  // namespace
+
+cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, double* abar,
+                              cudaStream_t st)
+{
+    if (nv <= 0 || o < 1 || o > kMaxO) return cudaErrorInvalidValue;
+    NodalWeights W{};
+    for (int q = 0; q < o; ++q) W.w[q] = wmean[q];
+    k_nodal_abar<<<(nv + 127) / 128, 128, 0, st>>>(alpha, nv, o, W, abar);
+    return cudaGetLastError();
+}
 
 void nodal_setup(int K, double* eta, double* weights, NodalArgs* a)
 {

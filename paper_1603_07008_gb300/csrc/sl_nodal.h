@@ -28,6 +28,7 @@ struct NodalArgs {
     double back64[kMaxO][kMaxO];   // (2 jv + 1) / 2 w_q P_jv(eta_q) at [jv][q]; row 0 = wmean
     double wmean[kMaxO];           // w_q / 2 rounded to sum to exactly 1
     float wmean32[kMaxO];          // the same in FP32
+    const double* abar;            // per v-cell: alpha_bar = sum_q wmean[q] alpha_q (launch_nodal_abar)
     float eval32[kMaxO][kMaxO];
     float back32[kMaxO][kMaxO];
 };
@@ -40,5 +41,10 @@ void nodal_setup(int K, double* eta, double* weights, NodalArgs* a);
 // (per target, or runs of targets along x-dimensions > 0 in the mixed store)
 // and fills the run fields of its copy of a.
 cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st);
+// alpha_bar of every v-cell j < nv from the node table's alpha[j * o + q]:
+// the fma chain sum_q wmean[q] alpha_q from 0, in node order (the mean's
+// fibre of the mixed store reads it instead of forming it per target).
+cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, double* abar,
+                              cudaStream_t st);
 
 }  // namespace sl
