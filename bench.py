@@ -198,15 +198,15 @@ TRAFFIC = {
         "capture": "4096^2 cells, k=2 (the size of the workload), self-consistent field, library default shapes, one "
                    "Strang step (sweeps only): 1.292-1.305 GB per launch against 1.342 GB algorithmic"},
     ("4d_nodal_v", "mix_fp32"): {
-        "ratio": (0.94760 + 0.93200 + 0.95940 + 0.94210 + 0.94250 + 0.93230) / 6,
+        "ratio": (0.94620 + 0.93200 + 0.95930 + 0.94210 + 0.94140 + 0.93180) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
-        "sha256": "1b6b979d64c202da",
+        "sha256": "013938aef0d551d2",
         "capture": "32^4 cells, k=2, nodal x-sweeps (runs of 2 along dimension 0, of 4 along dimension 1), one "
                    "Strang step: 0.641-0.660 GB per launch against 0.688 GB algorithmic"},
     ("2d_nodal_v", "mix_fp32"): {
-        "ratio": (0.96890 + 0.97310 + 0.96670) / 3,
+        "ratio": (0.96770 + 0.97310 + 0.96530) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
-        "sha256": "1b6b979d64c202da",
+        "sha256": "013938aef0d551d2",
         "capture": "4096^2 cells, k=2 (the size of the workload), nodal x-sweep, one Strang step: 1.298-1.306 GB per "
                    "launch against 1.342 GB algorithmic"},
     ("paper1d", "mix_fp32"): {
