@@ -361,14 +361,13 @@ sl_status sl_selftest_sub_widened(const float* a, const float* b, int64_t n, dou
 /* Measured FP64 arithmetic rate of the current device, the roofline of the
  * FP64 store (its sweep costs 2o FP64 FMAs per coefficient against the
  * 4o - 1 flops per coefficient of Sec. II-A, at the device's FP64 rate):
- * the best of four launch shapes (8 or 16 independent FMA chains per thread,
- * 4 or 8 resident blocks of 256 threads per multiprocessor), each timed with
- * CUDA events on `cuda_stream` after a shorter warm-up launch; every chain
- * runs about `iters` FMAs (8 chains) or half as many (16 chains).
- * *flops_per_s = 2 * FMAs / seconds.  1 <= iters <= 2^24 (2^14 takes about
- * 50 ms per shape on GB300).  Allocates 8 bytes of device memory for the
- * duration of the call; synchronous.  Errors: SL_EINVAL, SL_ENOMEM,
- * SL_ECUDA. */
+ * 8 independent chains of FP64 FMAs with register operands per thread, the
+ * better of 4 and 8 resident blocks of 256 threads per multiprocessor, each
+ * timed with CUDA events on `cuda_stream` after a shorter warm-up launch;
+ * every chain runs about `iters` FMAs.  *flops_per_s = 2 * FMAs / seconds.
+ * 1 <= iters <= 2^24 (2^14 takes about 65 ms per shape on GB300).
+ * Allocates 24 bytes of device memory for the duration of the call;
+ * synchronous.  Errors: SL_EINVAL, SL_ENOMEM, SL_ECUDA. */
 sl_status sl_selftest_fp64_rate(int64_t iters, void* cuda_stream, double* flops_per_s);
 
 /* Self-consistent field (NEXT to the sweep: the Vlasov-Poisson system of
