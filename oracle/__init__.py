@@ -34,8 +34,10 @@ Functions and the paper passages they follow:
                                 rho - rho_bar, rho = int f dv) and the split
                                 step that recomputes it before every v-sweep
   sweep_nodal,               -- x-sweep with the velocity at the Gauss nodes of
-  bruteforce_nodal              every v-cell (reading of v d_x f with v varying
-                                inside a v-cell), and the same without A, B
+  bruteforce_nodal,             every v-cell (reading of v d_x f with v varying
+  node_sigma,                   inside a v-cell), the same without A, B, and its
+  apply_cell_nodal              per-cell form for the dependency cones of
+                                sample_after
   fp64_coefficients,         -- which coefficients a store of "# double" = q
   storage_bytes,                keeps in FP64 (Sec. III-A, Tables II-VI;
   round_storage,                reading for d > 1: every index j_m < q), its
@@ -110,6 +112,13 @@ def lib():
                                      ctypes.c_int, _dp, _dp, _i64p, ctypes.c_int64, _dp]
             L.or_mass.restype = ctypes.c_double
             L.or_mass.argtypes = [ctypes.c_int, _i64p, _dp, _dp, ctypes.c_int, _dp]
+            L.or_node_sigma.restype = ctypes.c_int
+            L.or_node_sigma.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_int64, _i64p]
+            L.or_apply_cell_nodal.restype = ctypes.c_int
+            L.or_apply_cell_nodal.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int64,
+                                              ctypes.POINTER(_dp), ctypes.POINTER(_dp), _dp]
             L.or_apply_cell.restype = ctypes.c_int
             L.or_apply_cell.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp,
                                         _dp, _dp]
@@ -234,6 +243,30 @@ def sweep_nodal(u: np.ndarray, grid, k: int, dim: int, tau: float) -> np.ndarray
     return out
 
 
+def node_sigma(grid, k: int, dim: int, tau: float, j: int) -> List[int]:
+    """sigma_q of the o node shifts of v-cell j in the nodal x-sweep along dim."""
+    vdim, vlo, hv, toh = _nodal_args(grid, dim, tau)
+    out = np.zeros(k + 1, dtype=np.int64)
+    _check(lib().or_node_sigma(k, vlo, hv, toh, int(j), _p(out, _i64p)), "node_sigma")
+    return [int(x) for x in out]
+
+
+def apply_cell_nodal(grid, k: int, dim: int, tau: float, j: int, ua, ub) -> np.ndarray:
+    """New coefficients of one cell of v-cell j in the nodal x-sweep along dim
+    from its source cells: ua[q], ub[q] the coefficients of the cells
+    i - sigma_q and i - sigma_q - 1 (the same bits as sweep_nodal)."""
+    vdim, vlo, hv, toh = _nodal_args(grid, dim, tau)
+    o = k + 1
+    a_ = [_f64(x) for x in ua]
+    b_ = [_f64(x) for x in ub]
+    pa = (_dp * o)(*[_p(x) for x in a_])
+    pb = (_dp * o)(*[_p(x) for x in b_])
+    out = np.empty_like(a_[0])
+    _check(lib().or_apply_cell_nodal(len(grid.n), k, dim, vdim, vlo, hv, toh, int(j), pa, pb, _p(out)),
+           "apply_cell_nodal")
+    return out
+
+
 def bruteforce_nodal(u: np.ndarray, grid, k: int, dim: int, tau: float, nq: int = 12) -> np.ndarray:
     n_ = _i64(grid.n)
     u_ = _f64(u)
@@ -328,6 +361,15 @@ def schedule(grid, splitting: str, dt: float, fields) -> List[Tuple[int, int, np
         sd, s = line_shifts(grid, dim, tau, fields)
         out.append((dim, sd, s))
     return out
+
+
+def schedule_nodal(grid, splitting: str, dt: float, fields) -> List[tuple]:
+    """schedule() with every x-sweep a nodal one: ("nodal", dim, tau) in place
+    of (dim, shift_dim, shifts) for the x-dimensions."""
+    sched = schedule(grid, splitting, dt, fields)
+    taus = _plan_taus(grid, splitting, dt)
+    return [("nodal", dim, tau) if grid.pair[dim] >= 0 else (dim, sd, s)
+            for (dim, sd, s), tau in zip(sched, taus)]
 
 
 def step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int, fields,
@@ -458,7 +500,9 @@ def vp_step(u: np.ndarray, grid, k: int, splitting: str, dt: float, nsteps: int,
 
 def sample_after(grid, k: int, nq: int, weights, params, sweeps, cells) -> np.ndarray:
     """Coefficients of the flat cells `cells` after applying `sweeps`
-    (a list of (dim, shift_dim, shifts)) to the projected initial condition.
+    (a list of (dim, shift_dim, shifts), or ("nodal", dim, tau) for a nodal
+    x-sweep, as schedule and schedule_nodal give them) to the projected
+    initial condition.
     Each target cell depends on two source cells of the previous stage, so
     the work is 2^len(sweeps) cells per sample at most (shared cells are
     computed once)."""
@@ -467,9 +511,17 @@ def sample_after(grid, k: int, nq: int, weights, params, sweeps, cells) -> np.nd
     strides = [1] * ndim
     for m in range(1, ndim):
         strides[m] = strides[m - 1] * n[m - 1]
-    # per sweep: per class sigma and matrices
+    # per sweep: per class sigma and matrices; a nodal sweep ("nodal", dim, tau)
+    # keeps the node sigmas of each v-cell
     prepared = []
-    for dim, sd, s in sweeps:
+    for sw in sweeps:
+        if sw[0] == "nodal":
+            _, dim, tau = sw
+            vdim = grid.pair[dim]
+            prepared.append(("nodal", dim, (vdim, float(tau),
+                                            [node_sigma(grid, k, dim, tau, j) for j in range(n[vdim])])))
+            continue
+        dim, sd, s = sw
         s = np.atleast_1d(np.asarray(s, dtype=np.float64))
         cls = []
         for val in s:
@@ -484,31 +536,47 @@ def sample_after(grid, k: int, nq: int, weights, params, sweeps, cells) -> np.nd
         return (c // strides[m]) % n[m]
 
     # collect the needed cells stage by stage (backwards), then evaluate forward
+    def sources(stage, c):
+        """[(cell a, cell b)] per node (nodal) or the one pair of cell c."""
+        if stage[0] == "nodal":
+            _, dim, (vdim, tau, sigs) = stage
+            sg_list = sigs[coord(c, vdim)]
+        else:
+            dim, sd, cls = stage
+            sg_list = [cls[0 if sd < 0 else coord(c, sd)][0]]
+        i = coord(c, dim)
+        out = []
+        for sg in sg_list:
+            ia = (i - sg) % n[dim]
+            ib = (ia - 1) % n[dim]
+            out.append((c + (ia - i) * strides[dim], c + (ib - i) * strides[dim]))
+        return out
+
     need = [set() for _ in range(len(sweeps) + 1)]
     need[len(sweeps)] = set(int(c) for c in cells)
     for st in range(len(sweeps), 0, -1):
-        dim, sd, cls = prepared[st - 1]
         for c in need[st]:
-            sg = cls[0 if sd < 0 else coord(c, sd)][0]
-            i = coord(c, dim)
-            ia = (i - sg) % n[dim]
-            ib = (ia - 1) % n[dim]
-            need[st - 1].add(c + (ia - i) * strides[dim])
-            need[st - 1].add(c + (ib - i) * strides[dim])
+            for ca, cb in sources(prepared[st - 1], c):
+                need[st - 1].add(ca)
+                need[st - 1].add(cb)
     base = sorted(need[0])
     vals = project_cells(grid, k, nq, weights, params, base)
     for c, v in zip(base, vals):
         memo[0][c] = v
     for st in range(1, len(sweeps) + 1):
-        dim, sd, cls = prepared[st - 1]
+        stage = prepared[st - 1]
         for c in need[st]:
-            sg, A, B = cls[0 if sd < 0 else coord(c, sd)]
-            i = coord(c, dim)
-            ia = (i - sg) % n[dim]
-            ib = (ia - 1) % n[dim]
-            ua = memo[st - 1][c + (ia - i) * strides[dim]]
-            ub = memo[st - 1][c + (ib - i) * strides[dim]]
-            memo[st][c] = apply_cell(ndim, k, dim, A, B, ua, ub)
+            pairs = sources(stage, c)
+            if stage[0] == "nodal":
+                _, dim, (vdim, tau, _) = stage
+                memo[st][c] = apply_cell_nodal(grid, k, dim, tau, coord(c, vdim),
+                                               [memo[st - 1][a] for a, _ in pairs],
+                                               [memo[st - 1][b] for _, b in pairs])
+            else:
+                dim, sd, cls = stage
+                _, A, B = cls[0 if sd < 0 else coord(c, sd)]
+                ca, cb = pairs[0]
+                memo[st][c] = apply_cell(ndim, k, dim, A, B, memo[st - 1][ca], memo[st - 1][cb])
     return np.stack([memo[len(sweeps)][int(c)] for c in cells])
 
 

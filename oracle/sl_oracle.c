@@ -348,12 +348,49 @@ static double node_shift(double vlo, double hv, double tau_over_h, int64_t j, do
     return (vlo + ((double)j + 0.5 + half * eta) * hv) * tau_over_h;
 }
 
+/* Node q's part of the new coefficients of one cell (steps 1-3 above for
+ * node q), added to out: ua and ub are the o^ndim coefficients of the cells
+ * i - sigma_q and i - sigma_q - 1, A and B the node's matrices. */
+static void nodal_node(int o, int64_t ncoef, int64_t ostride, int64_t vstride, int q, const double* eta,
+                       const double* w, const double* A, const double* B, const double* ua, const double* ub,
+                       double* out)
+{
+    const int qe = or_mutation == 22 ? o - 1 - q : q;     /* MUTATION 22 */
+    for (int64_t base = 0; base < ncoef; ++base) {
+        if ((base / ostride) % o != 0 || (base / vstride) % o != 0) continue;
+        double Ua[OR_MAXK + 1], Ub[OR_MAXK + 1];
+        for (int l = 0; l < o; ++l) {
+            Ua[l] = 0.0;
+            Ub[l] = 0.0;
+            for (int jv = 0; jv < o; ++jv) {
+                const double p = or_legendre(jv, eta[qe]);
+                Ua[l] += ua[base + l * ostride + jv * vstride] * p;
+                Ub[l] += ub[base + l * ostride + jv * vstride] * p;
+            }
+        }
+        for (int jx = 0; jx < o; ++jx) {
+            double up = 0.0;
+            for (int l = 0; l < o; ++l) up += A[jx * o + l] * Ua[l] + B[jx * o + l] * Ub[l];
+            for (int jv = 0; jv < o; ++jv) {
+                const double norm = or_mutation == 21 ? (2.0 * jv + 1.0) : 0.5 * (2.0 * jv + 1.0);   /* MUTATION 21 */
+                out[base + jx * ostride + jv * vstride] += norm * w[q] * or_legendre(jv, eta[q]) * up;
+            }
+        }
+    }
+}
+
+static int nodal_args_ok(int ndim, int k, int dim, int vdim, double vlo, double hv, double tau_over_h)
+{
+    if (ndim < 2 || ndim > OR_MAXDIM || k < 0 || k > OR_MAXK) return 0;
+    if (dim < 0 || dim >= ndim || vdim < 0 || vdim >= ndim || vdim == dim) return 0;
+    return isfinite(vlo) && isfinite(hv) && isfinite(tau_over_h) && hv > 0.0;
+}
+
 int or_sweep_nodal(int ndim, const int64_t* n, int k, int dim, int vdim, double vlo, double hv,
                    double tau_over_h, const double* u, double* out)
 {
     if (check_grid(ndim, n, k)) return -1;
-    if (ndim < 2 || dim < 0 || dim >= ndim || vdim < 0 || vdim >= ndim || vdim == dim) return -1;
-    if (!isfinite(vlo) || !isfinite(hv) || !isfinite(tau_over_h) || !(hv > 0.0)) return -1;
+    if (!nodal_args_ok(ndim, k, dim, vdim, vlo, hv, tau_over_h)) return -1;
     const int o = k + 1;
     const int64_t ncoef = ipow(o, ndim);
     const int64_t ostride = ipow(o, dim), vstride = ipow(o, vdim);
@@ -388,33 +425,50 @@ int or_sweep_nodal(int ndim, const int64_t* n, int k, int dim, int vdim, double 
             const int64_t ib = pmod(ia - 1, n[dim]);
             const int64_t ca = c + (ia - idx[dim]) * cstride;
             const int64_t cb = c + (ib - idx[dim]) * cstride;
-            const int qe = or_mutation == 22 ? o - 1 - q : q;     /* MUTATION 22 */
-            for (int64_t base = 0; base < ncoef; ++base) {
-                if ((base / ostride) % o != 0 || (base / vstride) % o != 0) continue;
-                double Ua[OR_MAXK + 1], Ub[OR_MAXK + 1];
-                for (int l = 0; l < o; ++l) {
-                    Ua[l] = 0.0;
-                    Ub[l] = 0.0;
-                    for (int jv = 0; jv < o; ++jv) {
-                        const double p = or_legendre(jv, eta[qe]);
-                        Ua[l] += u[ca * ncoef + base + l * ostride + jv * vstride] * p;
-                        Ub[l] += u[cb * ncoef + base + l * ostride + jv * vstride] * p;
-                    }
-                }
-                for (int jx = 0; jx < o; ++jx) {
-                    double up = 0.0;
-                    for (int l = 0; l < o; ++l) up += A[jx * o + l] * Ua[l] + B[jx * o + l] * Ub[l];
-                    for (int jv = 0; jv < o; ++jv) {
-                        const double norm = or_mutation == 21 ? (2.0 * jv + 1.0) : 0.5 * (2.0 * jv + 1.0);   /* MUTATION 21 */
-                        out[c * ncoef + base + jx * ostride + jv * vstride] +=
-                            norm * w[q] * or_legendre(jv, eta[q]) * up;
-                    }
-                }
-            }
+            nodal_node(o, ncoef, ostride, vstride, q, eta, w, A, B, u + ca * ncoef, u + cb * ncoef, out + c * ncoef);
         }
     }
     free(sig);
     free(AB);
+    return 0;
+}
+
+/* The integer parts sigma_q of the o node shifts of v-cell j, as
+ * or_sweep_nodal forms them (its step 2). */
+int or_node_sigma(int k, double vlo, double hv, double tau_over_h, int64_t j, int64_t* sig)
+{
+    if (k < 0 || k > OR_MAXK || !isfinite(vlo) || !isfinite(hv) || !isfinite(tau_over_h) || !(hv > 0.0))
+        return -1;
+    const int o = k + 1;
+    double eta[OR_MAXK + 1], w[OR_MAXK + 1], alpha;
+    or_gauss_legendre(o, eta, w);
+    for (int q = 0; q < o; ++q) or_shift_split(node_shift(vlo, hv, tau_over_h, j, eta[q]), &sig[q], &alpha);
+    return 0;
+}
+
+/* The new coefficients of one cell of v-cell j in the nodal x-sweep along
+ * dim: ua[q] and ub[q] point to the o^ndim coefficients of its source cells
+ * i - sigma_q and i - sigma_q - 1 (sigma_q from or_node_sigma).  The
+ * arithmetic of or_sweep_nodal, so the result is the same bits; it lets the
+ * dependency cones of sampled cells of a large grid (sample_after) include
+ * nodal sweeps. */
+int or_apply_cell_nodal(int ndim, int k, int dim, int vdim, double vlo, double hv, double tau_over_h, int64_t j,
+                        const double* const* ua, const double* const* ub, double* out)
+{
+    if (!nodal_args_ok(ndim, k, dim, vdim, vlo, hv, tau_over_h)) return -1;
+    const int o = k + 1;
+    const int64_t ncoef = ipow(o, ndim);
+    const int64_t ostride = ipow(o, dim), vstride = ipow(o, vdim);
+    double eta[OR_MAXK + 1], w[OR_MAXK + 1];
+    or_gauss_legendre(o, eta, w);
+    for (int64_t J = 0; J < ncoef; ++J) out[J] = 0.0;
+    for (int q = 0; q < o; ++q) {
+        int64_t sg;
+        double alpha, A[(OR_MAXK + 1) * (OR_MAXK + 1)], B[(OR_MAXK + 1) * (OR_MAXK + 1)];
+        or_shift_split(node_shift(vlo, hv, tau_over_h, j, eta[q]), &sg, &alpha);
+        or_ab_matrices(k, alpha, A, B);
+        nodal_node(o, ncoef, ostride, vstride, q, eta, w, A, B, ua[q], ub[q], out);
+    }
     return 0;
 }
 

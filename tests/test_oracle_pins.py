@@ -569,3 +569,27 @@ def test_l2_norm_of_projected_data():
         c = np.zeros((1, 4))
         c[0, j] = 1.0
         assert abs(O.l2_norm(c, gc, 3) - math.sqrt(2.0 / (2 * j + 1) * h / 2)) < 1e-15
+
+
+@pytest.mark.parametrize("dt", [0.1, 2.3])
+def test_sample_after_with_nodal_sweeps_equals_the_full_grid(dt):
+    """The dependency cones of sampled cells include nodal x-sweeps: two
+    Strang steps with nodal x-sweeps, evaluated cell by cell from each target's
+    node source cells (apply_cell_nodal), equal the full-grid step bit for bit.
+    Odd v-extents put v = 0 inside a v-cell, so some v-cells have nodes on both
+    sides of it (different sigma per node); dt = 2.3 shifts by several cells."""
+    from paper_1603_07008_gb300 import workloads as W
+    for p in (W.config3(n=5, steps=1), W.config2(n=9, steps=1)):
+        g = p.grid
+        u0 = O.project(g, p.k, p.nq, p.weights, p.params)
+        full = O.step(u0, g, p.k, "strang", dt, 2, p.field_list(), nodal_v=True)
+        sched = O.schedule_nodal(g, "strang", dt, p.field_list())
+        x0 = g.x_dims()[0]
+        vd = g.pair[x0]
+        sigs = [O.node_sigma(g, p.k, x0, 0.5 * dt, j) for j in range(g.n[vd])]
+        assert any(len(set(s)) > 1 for s in sigs)            # nodes of one v-cell that differ in sigma
+        if dt > 1:
+            assert max(abs(x) for s in sigs for x in s) >= 2   # shifts of several cells
+        cells = np.arange(0, g.cells, 3)
+        got = O.sample_after(g, p.k, p.nq, p.weights, p.params, sched * 2, cells)
+        assert np.array_equal(got, full[cells])
