@@ -106,3 +106,29 @@ def test_oracle_error_of_exact_and_perturbed_samples():
     e = bench.oracle_error({"steps": 1, "items": [(q, c1, ref, 100)]}, "fp64")
     assert e["rel_max"] == 0.0 and e["bound"] == {"rel_max": 1e-12}
     assert bench.oracle_error(None, "mix_fp32")["note"]
+
+
+def test_oracle_error_of_nodal_and_whole_state_samples():
+    """The error leg's nodal cones (x-sweeps at the Gauss nodes of each
+    v-cell) and its whole-state check of the self-consistent field: zero for
+    the oracle's own values, the perturbation's size otherwise."""
+    import numpy as np
+    import oracle as O
+    from paper_1603_07008_gb300 import workloads as W
+    p = W.config3(n=6, steps=1)
+    cells = np.array([0, 100, 1295])
+    sched = O.schedule_nodal(p.grid, "strang", p.dt, p.field_list())
+    exact = O.sample_after(p.grid, p.k, p.nq, p.weights, p.params, sched * 2, cells)
+    e = bench.oracle_error({"steps": 2, "items": [(p, cells, exact.copy(), 12)], "nodal": True}, "mix_fp32")
+    assert e["rel_max"] == 0.0 and e["within_bound"]
+    plain = O.sample_after(p.grid, p.k, p.nq, p.weights, p.params,
+                           O.schedule(p.grid, "strang", p.dt, p.field_list()) * 2, cells)
+    e = bench.oracle_error({"steps": 2, "items": [(p, cells, plain, 12)], "nodal": True}, "fp64")
+    assert e["rel_max"] > 1e-6          # the centre-velocity sweep is not the nodal one
+    q = W.config2(n=16, steps=1)
+    ref = O.vp_step(O.project(q.grid, q.k, q.nq, q.weights, q.params), q.grid, q.k, "strang", q.dt, 1)
+    e = bench.oracle_error({"steps": 1, "whole": (q, ref.copy())}, "mix_fp32")
+    assert e["rel_l2"] == 0.0 and e["cells"] == 256
+    bad = ref.copy()
+    bad[5, 0] += 1e-3
+    assert bench.oracle_error({"steps": 1, "whole": (q, bad)}, "fp64")["rel_max"] > 0
