@@ -17,17 +17,28 @@ namespace sl {
 
 namespace {
 
-// Chunks of lane h of the group for a sweep along dimension M: c0 (lane-local
-// slots 0..7) and c0 + d (slots 8..15), d = 2^max(M-3, 0), c0 = h with a zero
-// bit inserted at position log2(d).
-template <int M>
+// Chunks of lane h of a group of G lanes for a sweep along dimension M: c0
+// (lane-local slots 0..7) and c0 + d (slots 8..15).  For M >= 3 the two
+// coefficients of a fibre lie 2^(M-3) chunks apart: d = 2^(M-3) and c0 = h
+// with a zero bit inserted at position log2(d).  For M < 3 they lie in one
+// chunk, so any chunks will do: c0 = h and d = G, so that each of the two
+// loads and stores of a group covers G neighbouring chunks (half a record).
+template <int M, int G>
 struct LgChunks {
     static constexpr int b = M > 3 ? M - 3 : 0;
-    static constexpr int d = 1 << b;
-    __device__ __forceinline__ static int c0(int h) { return ((h >> b) << (b + 1)) | (h & (d - 1)); }
-    // lane-local slot stride between the two coefficients of a fibre
-    static constexpr int st = M < 3 ? (1 << M) : 8;
+    static constexpr int d = M < 3 ? G : 1 << b;
+    __device__ __forceinline__ static int c0(int h)
+    {
+        return M < 3 ? h : ((h >> b) << (b + 1)) | (h & ((1 << b) - 1));
+    }
 };
+
+// Lane-local slot stride between the two coefficients of a fibre along M.
+template <int M>
+__host__ __device__ constexpr int lg_stride()
+{
+    return M < 3 ? (1 << M) : 8;
+}
 
 // This lane's two source chunks of one cell with the cell's scale and mean.
 struct LgRow {
@@ -81,7 +92,7 @@ template <int MODE, int M>
 __device__ __forceinline__ void lg_combine(const Mats<1, MODE>& T, const LgRow& ra, const LgRow& rb, int h,
                                            float (&out)[16], double& om)
 {
-    constexpr int st = LgChunks<M>::st;
+    constexpr int st = lg_stride<M>();
     om = 0.0;
 #pragma unroll
     for (int q0 = 0; q0 < 16; ++q0) {
@@ -146,7 +157,7 @@ __global__ void __launch_bounds__(256) k_sweep_rec_lg(const SweepArgs a)
 {
     constexpr int R = RecShape<1, D>::R;
     constexpr int G = R / 16;
-    using C = LgChunks<M>;
+    using C = LgChunks<M, G>;
     const uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const int h = int(threadIdx.x) & (G - 1);
     const int lane = int(threadIdx.x) & 31;
