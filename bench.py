@@ -180,16 +180,16 @@ TRAFFIC = {
         "capture": "48^4 cells, k=2, one Strang step (6 launches: vector form along dimension 0, walks with 1 fibre, "
                    "4 cells per step along the others): 3.431-3.504 GB per launch against 3.482 GB algorithmic"},
     ("6d", "mix_bf16"): {
-        "ratio": (2 * 1.00600 + 2 * 1.03095 + 2 * 1.02920 + 1.03020 + 1.03040 + 1.03250) / 9,
+        "ratio": (1.00633 + 1.03324 + 1.03142 + 1.03032 + 1.03054 + 1.03245 + 1.00559 + 1.03330 + 1.03143) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "b86df808c2738f95",
-        "capture": "16^6 cells, k=1, BF16 records, lane groups, one Strang step (9 launches): 4.660-4.781 GB per "
+        "sha256": "4515000320a5ce78",
+        "capture": "16^6 cells, k=1, BF16 records, lane groups, one Strang step (9 launches): 4.656-4.785 GB per "
                    "launch against 4.631 GB algorithmic"},
     ("6d", "mix_fp16"): {
-        "ratio": (1.00635 + 1.03084 + 1.02929 + 1.03037 + 1.03047 + 1.03257 + 1.00570 + 1.03079 + 1.02940) / 9,
+        "ratio": (1.00636 + 1.03338 + 1.03146 + 1.03028 + 1.03054 + 1.03256 + 1.00557 + 1.03324 + 1.03146) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "b86df808c2738f95",
-        "capture": "16^6 cells, k=1, FP16 records, lane groups, one Strang step (9 launches): 4.657-4.781 GB per "
+        "sha256": "4515000320a5ce78",
+        "capture": "16^6 cells, k=1, FP16 records, lane groups, one Strang step (9 launches): 4.656-4.785 GB per "
                    "launch against 4.631 GB algorithmic"},
     ("2d", "mix_fp32"): {
         "ratio": (0.96570 + 0.97300 + 0.96310) / 3,
