@@ -407,6 +407,7 @@ cudaError_t launch_nodal_only(sl_ctx* c, int dim)
     double eta[kMaxO], w[kMaxO];
     nodal_setup(c->K, eta, w, &a);
     a.abar = c->d_nabar;
+    a.na32 = c->d_nna32;
     return launch_sweep_nodal(c->K, c->mode, a, int(ipow(c->O, c->ndim - 2)), c->st);
 }
 
@@ -464,7 +465,8 @@ sl_status nodal_table(sl_ctx* c, int dim, double tau)
         NodalArgs tmp{};
         double eta[kMaxO], w[kMaxO];
         nodal_setup(c->K, eta, w, &tmp);
-        e = launch_nodal_abar(c->d_nalpha, int(c->g.n[p]), c->O, tmp.wmean, c->d_nabar, c->st);
+        e = launch_nodal_abar(c->d_nalpha, int(c->g.n[p]), c->O, tmp.wmean, tmp.wmean32, c->d_nabar, c->d_nna32,
+                              c->st);
         if (e != cudaSuccess) return cuda_fail(c, e, "node table launch");
     }
     return SL_OK;
@@ -1343,6 +1345,8 @@ static sl_status nodal_alloc(sl_ctx* c)
     off = align_up(off + size_t(maxcls) * ab_stride32(c->O) * 4, A);
     const size_t o_abar = off;
     off = align_up(off + size_t(maxnv) * 8, A);
+    const size_t o_na32 = off;
+    off = align_up(off + size_t(maxnv) * kNa32 * 4, A);
     void* mem = nullptr;
     cudaError_t e = dev_malloc(&mem, off);
     if (e != cudaSuccess) return fail(c, SL_ENOMEM, "cudaMalloc(%zu bytes): %s", off, cudaGetErrorString(e));
@@ -1359,6 +1363,7 @@ static sl_status nodal_alloc(sl_ctx* c)
     c->d_nab64 = reinterpret_cast<double*>(b + o_ab64);
     c->d_nab32 = reinterpret_cast<float*>(b + o_ab32);
     c->d_nabar = reinterpret_cast<double*>(b + o_abar);
+    c->d_nna32 = reinterpret_cast<float*>(b + o_na32);
     return SL_OK;
 }
 

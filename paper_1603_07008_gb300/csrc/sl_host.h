@@ -63,6 +63,7 @@ struct sl_ctx {
     double* d_nab64 = nullptr;
     float* d_nab32 = nullptr;
     double* d_nabar = nullptr;  // alpha_bar per v-cell of the node table (mixed store)
+    float* d_nna32 = nullptr;   // per v-cell FP32 record of the node table (kNa32 floats)
     double* d_partials = nullptr;
     double* d_mass = nullptr;
     int mass_nblk = 1;

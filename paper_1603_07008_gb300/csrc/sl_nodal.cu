@@ -111,6 +111,25 @@ __device__ __forceinline__ const T* coef_plane(const Planes& p, int64_t ps, int 
     return static_cast<const T*>(p.hi) + int64_t(J - 1) * ps;
 }
 
+// Coefficient J >= 1 of cell `cell` in the FP32 block of the source and the
+// destination (OFF32: the block's base plus a 32-bit element offset).
+template <bool OFF32>
+__device__ __forceinline__ float ld_hi(const NodalArgs& a, int J, uint32_t cell)
+{
+    if constexpr (OFF32)
+        return __ldg(static_cast<const float*>(a.src.hi) + (uint32_t(J - 1) * uint32_t(a.pstride) + cell));
+    else
+        return __ldg(coef_plane<float>(a.src, a.pstride, J) + cell);
+}
+template <bool OFF32>
+__device__ __forceinline__ void st_hi(const NodalArgs& a, int J, uint32_t cell, float v)
+{
+    if constexpr (OFF32)
+        static_cast<float*>(a.dst.hi)[uint32_t(J - 1) * uint32_t(a.pstride) + cell] = v;
+    else
+        static_cast<float*>(a.dst.hi)[int64_t(J - 1) * a.pstride + cell] = v;
+}
+
 // Every fibre of the FP64 store (R = double), the whole computation in FP64;
 // for R = float the same steps in FP32 (the mixed store's FP32 fibres take
 // the grouped form, nodal_fp32_group).
@@ -466,7 +485,7 @@ __device__ __forceinline__ void nodal_fp32_walk(const NodalArgs& a, uint32_t lin
 // other coefficients of row 0 take the nodes' deviations from
 // m_a + alpha_bar t, d_q = delta_q(a) + alpha_q (delta_q(b) - delta_q(a))
 // + G_q(a) - G_q(b) + (alpha_q - alpha_bar) t, in FP32.
-template <int K>
+template <int K, bool OFF32>
 __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
                                                         uint32_t j, int32_t sig)
 {
@@ -484,9 +503,9 @@ __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint
 #pragma unroll
         for (int v = 0; v < O; ++v) {
             if (l == 0 && v == 0) continue;
-            const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
-            va[l][v] = __ldg(p + ca);
-            vb[l][v] = __ldg(p + cb);
+            const int J = l * a.ostride + v * a.vstride;
+            va[l][v] = ld_hi<OFF32>(a, J, ca);
+            vb[l][v] = ld_hi<OFF32>(a, J, cb);
         }
     const double t = mb - ma;
     const float t32 = d2f_fast(t, false);
@@ -496,14 +515,24 @@ __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint
 #pragma unroll
         for (int v = 0; v < O; ++v) acc[x][v] = 0.0f;
     const double abar = __ldg(a.abar + j);   // per v-cell (launch_nodal_abar)
-    float abar32 = 0.0f, ea = 0.0f, eb = 0.0f;
-    float dev[O], a32[O];
+    float a32[kNa32];                         // alpha_q in FP32, then alpha_bar in FP32
+    {
+        const float4* r = reinterpret_cast<const float4*>(a.na32 + size_t(j) * kNa32);
+#pragma unroll
+        for (int h = 0; h < (na32_abar(O) + 4) / 4; ++h) {
+            const float4 x = __ldg(r + h);
+            a32[4 * h] = x.x;
+            a32[4 * h + 1] = x.y;
+            a32[4 * h + 2] = x.z;
+            a32[4 * h + 3] = x.w;
+        }
+    }
+    const float abar32 = a32[na32_abar(O)];
+    float ea = 0.0f, eb = 0.0f;
+    float dev[O];
 #pragma unroll
     for (int q = 0; q < O; ++q) {
         const uint32_t cls = j * O + q;
-        const double al = __ldg(a.tab.alpha + cls);
-        a32[q] = d2f_fast(al, false);
-        abar32 = fmaf(a.wmean32[q], a32[q], abar32);
         float A[O][O], B[O][O];
         load_ab<O>(a.tab, cls, A, B);
         // node values: delta_q of row 0, U_q(l) of the others
@@ -562,12 +591,12 @@ __device__ __forceinline__ void nodal_mean_fibre_shared(const NodalArgs& a, uint
 #pragma unroll
         for (int v = 0; v < O; ++v) {
             if (x == 0 && v == 0) continue;
-            static_cast<float*>(a.dst.hi)[int64_t(x * a.ostride + v * a.vstride - 1) * a.pstride + c] = acc[x][v];
+            st_hi<OFF32>(a, x * a.ostride + v * a.vstride, c, acc[x][v]);
         }
 }
 
 // The fibre of the cell mean in the mixed store (see the file comment).
-template <int K>
+template <int K, bool OFF32>
 __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
                                                  uint32_t j)
 {
@@ -594,9 +623,9 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
 #pragma unroll
             for (int v = 0; v < O; ++v) {
                 if (l == 0 && v == 0) continue;
-                const float* p = coef_plane<float>(a.src, a.pstride, l * a.ostride + v * a.vstride);
-                va[l][v] = __ldg(p + ca);
-                vb[l][v] = __ldg(p + cb);
+                const int J = l * a.ostride + v * a.vstride;
+                va[l][v] = ld_hi<OFF32>(a, J, ca);
+                vb[l][v] = ld_hi<OFF32>(a, J, cb);
             }
     };
     int32_t sg[O];
@@ -671,12 +700,12 @@ __device__ __forceinline__ void nodal_mean_fibre(const NodalArgs& a, uint32_t c,
 #pragma unroll
         for (int v = 0; v < O; ++v) {
             if (x == 0 && v == 0) continue;
-            static_cast<float*>(a.dst.hi)[int64_t(x * a.ostride + v * a.vstride - 1) * a.pstride + c] = acc[x][v];
+            st_hi<OFF32>(a, x * a.ostride + v * a.vstride, c, acc[x][v]);
         }
 }
 
 // Mean's fibre of the mixed store for target c (at x = i of v-cell j).
-template <int K>
+template <int K, bool OFF32>
 __device__ __forceinline__ void nodal_mean_target(const NodalArgs& a, uint32_t c, uint32_t i, uint32_t line0,
                                                   uint32_t j)
 {
@@ -687,9 +716,9 @@ __device__ __forceinline__ void nodal_mean_target(const NodalArgs& a, uint32_t c
 #pragma unroll
     for (int q = 1; q < O; ++q) same = same && __ldg(a.tab.sigma + j * O + q) == s0;
     if (same)
-        nodal_mean_fibre_shared<K>(a, c, i, line0, j, s0);
+        nodal_mean_fibre_shared<K, OFF32>(a, c, i, line0, j, s0);
     else
-        nodal_mean_fibre<K>(a, c, i, line0, j);
+        nodal_mean_fibre<K, OFF32>(a, c, i, line0, j);
 }
 
 // Runs of RUN targets of the walk form along x (PARTs 4 and 5): run = inner +
@@ -712,7 +741,7 @@ __device__ __forceinline__ void nodal_run(const NodalArgs& a, uint32_t run, int 
     const uint32_t j = ov - a.fdNV.div(ov) * a.NV;
     if (g == 0) {
         for (int r = 0; r < cnt; ++r)
-            nodal_mean_target<K>(a, line0 + (i0 + uint32_t(r)) * a.inner_x, i0 + uint32_t(r), line0, j);
+            nodal_mean_target<K, OFF32>(a, line0 + (i0 + uint32_t(r)) * a.inner_x, i0 + uint32_t(r), line0, j);
         return;
     }
     int jb[FT];
@@ -776,8 +805,10 @@ __global__ void __launch_bounds__(PART >= 4 ? 128 : 256, K == 3 ? 1 : PART >= 4 
     const uint32_t line0 = c - i * a.inner_x;
     if constexpr (MODE == M_FP64)
         nodal_plain<K, double>(a, c, i, line0, j, nodal_fibre_base<O>(a, g));
+    else if (a.off32)
+        nodal_mean_target<K, true>(a, c, i, line0, j);
     else
-        nodal_mean_target<K>(a, c, i, line0, j);
+        nodal_mean_target<K, false>(a, c, i, line0, j);
 }
 
 template <int K>
@@ -846,27 +877,41 @@ double legendre_host(int j, double x)
 
 struct NodalWeights {
     double w[kMaxO];
+    float w32[kMaxO];
 };
 
 __global__ void k_nodal_abar(const double* __restrict__ alpha, int nv, int o, NodalWeights W,
-                             double* __restrict__ abar)
+                             double* __restrict__ abar, float* __restrict__ na32)
 {
     const int j = int(blockIdx.x * blockDim.x + threadIdx.x);
     if (j >= nv) return;
     double s = 0.0;
-    for (int q = 0; q < o; ++q) s = fma(W.w[q], __ldg(alpha + size_t(j) * o + q), s);
+    float s32 = 0.0f;
+    float* r = na32 + size_t(j) * kNa32;
+    for (int q = 0; q < kNa32; ++q) r[q] = 0.0f;
+    for (int q = 0; q < o; ++q) {
+        const double al = __ldg(alpha + size_t(j) * o + q);
+        s = fma(W.w[q], al, s);
+        const float a32 = d2f_fast(al, false);
+        s32 = fmaf(W.w32[q], a32, s32);
+        r[q] = a32;
+    }
     abar[j] = s;
+    r[na32_abar(o)] = s32;
 }
 
 }  // namespace
 
-cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, double* abar,
-                              cudaStream_t st)
+cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, const float* wmean32,
+                              double* abar, float* na32, cudaStream_t st)
 {
     if (nv <= 0 || o < 1 || o > kMaxO) return cudaErrorInvalidValue;
     NodalWeights W{};
-    for (int q = 0; q < o; ++q) W.w[q] = wmean[q];
-    k_nodal_abar<<<(nv + 127) / 128, 128, 0, st>>>(alpha, nv, o, W, abar);
+    for (int q = 0; q < o; ++q) {
+        W.w[q] = wmean[q];
+        W.w32[q] = wmean32[q];
+    }
+    k_nodal_abar<<<(nv + 127) / 128, 128, 0, st>>>(alpha, nv, o, W, abar, na32);
     return cudaGetLastError();
 }
 

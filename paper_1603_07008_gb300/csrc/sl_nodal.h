@@ -6,6 +6,11 @@
 
 namespace sl {
 
+// Floats per v-cell of the FP32 node record (NodalArgs::na32) and the place of
+// its alpha_bar (after the o values alpha_q, in the first 16 bytes when o <= 3).
+constexpr int kNa32 = 8;
+__host__ __device__ constexpr int na32_abar(int o) { return o < 4 ? 3 : 4; }
+
 // One nodal x-sweep along xdim (paired with vdim) from src to dst.  tab holds
 // the classes j * o + q (v-cell j, node q).  The node tables are filled by
 // nodal_setup.
@@ -29,6 +34,8 @@ struct NodalArgs {
     double wmean[kMaxO];           // w_q / 2 rounded to sum to exactly 1
     float wmean32[kMaxO];          // the same in FP32
     const double* abar;            // per v-cell: alpha_bar = sum_q wmean[q] alpha_q (launch_nodal_abar)
+    const float* na32;             // per v-cell, kNa32 floats: alpha_q rounded to FP32, then at
+                                   // na32_abar(o) the FP32 fma chain sum_q wmean32[q] alpha32_q
     float eval32[kMaxO][kMaxO];
     float back32[kMaxO][kMaxO];
 };
@@ -42,9 +49,11 @@ void nodal_setup(int K, double* eta, double* weights, NodalArgs* a);
 // and fills the run fields of its copy of a.
 cudaError_t launch_sweep_nodal(int K, int mode, const NodalArgs& a, int nfib2, cudaStream_t st);
 // alpha_bar of every v-cell j < nv from the node table's alpha[j * o + q]:
-// the fma chain sum_q wmean[q] alpha_q from 0, in node order (the mean's
-// fibre of the mixed store reads it instead of forming it per target).
-cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, double* abar,
-                              cudaStream_t st);
+// the fma chain sum_q wmean[q] alpha_q from 0, in node order, and the FP32
+// record na32[j * kNa32 ..] (alpha_q rounded to nearest FP32, then the FP32
+// chain of wmean32[q] and those values); the mean's fibre of the mixed store
+// reads them instead of forming them per target.
+cudaError_t launch_nodal_abar(const double* alpha, int nv, int o, const double* wmean, const float* wmean32,
+                              double* abar, float* na32, cudaStream_t st);
 
 }  // namespace sl
