@@ -291,10 +291,10 @@ SweepArgs make_args_parity(sl_ctx* c, int dim, int shift_dim, int parity)
     SweepArgs a{};
     a.src = c->planes[parity];
     a.dst = c->planes[parity ^ 1];
-    a.tab.sigma = c->d_sigma;
-    a.tab.alpha = c->d_alpha;
-    a.tab.ab64 = c->d_ab64;
-    a.tab.ab32 = c->d_ab32;
+    a.tab.sigma = c->d_sigma[dim];
+    a.tab.alpha = c->d_alpha[dim];
+    a.tab.ab64 = c->d_ab64[dim];
+    a.tab.ab32 = c->d_ab32[dim];
     a.cells = uint32_t(c->cells);
     a.N = uint32_t(c->g.n[dim]);
     int64_t inner = 1;
@@ -472,12 +472,20 @@ sl_status nodal_table(sl_ctx* c, int dim, double tau)
     return SL_OK;
 }
 
-sl_status build_table(sl_ctx* c, int dim, int nclass, const ShiftSource& src)
+// The shift table of dimension dim (its own slot) on stream st.
+sl_status build_table_on(sl_ctx* c, int dim, int nclass, const ShiftSource& src, cudaStream_t st)
 {
-    cudaError_t e = launch_ab_build(c->K, nclass, uint32_t(c->g.n[dim]), src, c->poly, c->d_sigma,
-                                    c->d_alpha, c->d_ab64, c->d_ab32, c->st);
+    if (nclass < 1 || nclass > c->ncls[dim])
+        return fail(c, SL_EINVAL, "%d shift classes for dimension %d (at most %d)", nclass, dim, c->ncls[dim]);
+    cudaError_t e = launch_ab_build(c->K, nclass, uint32_t(c->g.n[dim]), src, c->poly, c->d_sigma[dim],
+                                    c->d_alpha[dim], c->d_ab64[dim], c->d_ab32[dim], st);
     if (e != cudaSuccess) return cuda_fail(c, e, "ab_build launch");
     return SL_OK;
+}
+
+sl_status build_table(sl_ctx* c, int dim, int nclass, const ShiftSource& src)
+{
+    return build_table_on(c, dim, nclass, src, c->st);
 }
 
 // The sweeps of one split step: (dim, tau factor).
@@ -522,14 +530,94 @@ cudaError_t vp_field(sl_ctx* c, double* E, double* energy)
                            c->d_vp, E, energy, c->st);
 }
 
+// Shift source of a split substep's sweep along dim over tau (not the nodal
+// x-sweep): x-dimensions take the centre velocity of their v-dimension, the
+// v-dimensions the field on the x-grid (the self-consistent field first
+// computed from the current state when `field` is set).
+sl_status substep_source(sl_ctx* c, int dim, double tau, bool field, ShiftSource* src, int* shift_dim,
+                         int* nclass)
+{
+    *src = ShiftSource{};
+    if (c->g.pair[dim] >= 0) {
+        const int p = c->g.pair[dim];
+        src->kind = 1;
+        src->lo = c->g.lo[p];
+        src->hv = cell_width(c->g, p);
+        src->tau = tau;
+        src->h = cell_width(c->g, dim);
+        *shift_dim = p;
+        *nclass = int(c->g.n[p]);
+        return SL_OK;
+    }
+    int xm = -1;
+    for (int m = 0; m < c->ndim; ++m)
+        if (c->g.pair[m] == dim) xm = m;
+    if (field && c->poisson) {   // the field of the current state
+        cudaError_t e = vp_field(c, c->d_fields + field_offset(c, xm), nullptr);
+        if (e != cudaSuccess) return cuda_fail(c, e, "self-consistent field");
+    }
+    src->kind = 2;
+    src->data = c->d_fields + field_offset(c, xm);
+    src->tau = tau;
+    src->h = cell_width(c->g, dim);
+    *shift_dim = xm;
+    *nclass = int(c->g.n[xm]);
+    return SL_OK;
+}
+
+// The split steps.  A shift table depends on its dimension, tau and the
+// fields, not on the state, so each dimension's table is built once per
+// step into its own slot (Strang's two x half-steps share theirs): the
+// x-dimensions' on the context's stream before the step's first sweep, the
+// v-dimensions' on the side stream while the x-sweeps run, joined back before
+// the first v-sweep.  With the self-consistent field (a v-table needs the
+// field of the state after the x-sweeps) every table is built right before
+// its sweep.
 sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     const std::vector<SubStep> plan = plan_of(c, sp);
+    bool ahead = !c->poisson;
+    for (const SubStep& a : plan)
+        for (const SubStep& b : plan)
+            if (a.dim == b.dim && a.frac != b.frac) ahead = false;
     for (int s = 0; s < nsteps; ++s) {
+        bool built[SL_MAX_DIM] = {false};
+        bool joined = true;
+        if (ahead) {
+            bool any_v = false;
+            for (const SubStep& ss : plan) {
+                const bool x = c->g.pair[ss.dim] >= 0;
+                if (x && c->nodal) continue;   // node tables: before each nodal sweep
+                if (!x) {
+                    any_v = true;
+                    continue;
+                }
+                if (built[ss.dim]) continue;
+                ShiftSource src;
+                int sd, nclass;
+                sl_status r = substep_source(c, ss.dim, ss.frac * dt, false, &src, &sd, &nclass);
+                if (r == SL_OK) r = build_table(c, ss.dim, nclass, src);
+                if (r != SL_OK) return r;
+                built[ss.dim] = true;
+            }
+            if (any_v) {
+                SL_CUDA(c, cudaEventRecord(c->ev_fork, c->st));
+                SL_CUDA(c, cudaStreamWaitEvent(c->st_tab, c->ev_fork, 0));
+                for (const SubStep& ss : plan) {
+                    if (c->g.pair[ss.dim] >= 0 || built[ss.dim]) continue;
+                    ShiftSource src;
+                    int sd, nclass;
+                    sl_status r = substep_source(c, ss.dim, ss.frac * dt, false, &src, &sd, &nclass);
+                    if (r == SL_OK) r = build_table_on(c, ss.dim, nclass, src, c->st_tab);
+                    if (r != SL_OK) return r;
+                    built[ss.dim] = true;
+                }
+                SL_CUDA(c, cudaEventRecord(c->ev_join, c->st_tab));
+                joined = false;
+            }
+        }
         for (const SubStep& ss : plan) {
             const double tau = ss.frac * dt;
-            ShiftSource src{};
-            int shift_dim, nclass;
             if (c->g.pair[ss.dim] >= 0 && c->nodal) {
                 // x-sweep with the velocity at the Gauss nodes of every v-cell
                 sl_status r = nodal_table(c, ss.dim, tau);
@@ -537,37 +625,21 @@ sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
                 if (r != SL_OK) return r;
                 continue;
             }
-            if (c->g.pair[ss.dim] >= 0) {
-                // x-sweep: velocity = cell centre of the paired v-dimension
-                const int p = c->g.pair[ss.dim];
-                src.kind = 1;
-                src.lo = c->g.lo[p];
-                src.hv = cell_width(c->g, p);
-                src.tau = tau;
-                src.h = cell_width(c->g, ss.dim);
-                shift_dim = p;
-                nclass = int(c->g.n[p]);
-            } else {
-                // v-sweep: velocity = E_m at the x_m cell centres
-                int xm = -1;
-                for (int m = 0; m < c->ndim; ++m)
-                    if (c->g.pair[m] == ss.dim) xm = m;
-                if (c->poisson) {   // the field of the current state
-                    cudaError_t e = vp_field(c, c->d_fields + field_offset(c, xm), nullptr);
-                    if (e != cudaSuccess) return cuda_fail(c, e, "self-consistent field");
-                }
-                src.kind = 2;
-                src.data = c->d_fields + field_offset(c, xm);
-                src.tau = tau;
-                src.h = cell_width(c->g, ss.dim);
-                shift_dim = xm;
-                nclass = int(c->g.n[xm]);
-            }
-            sl_status r = build_table(c, ss.dim, nclass, src);
+            ShiftSource src;
+            int shift_dim, nclass;
+            sl_status r = substep_source(c, ss.dim, tau, !built[ss.dim], &src, &shift_dim, &nclass);
             if (r != SL_OK) return r;
+            if (!built[ss.dim]) {
+                r = build_table(c, ss.dim, nclass, src);
+                if (r != SL_OK) return r;
+            } else if (!joined && c->g.pair[ss.dim] < 0) {
+                SL_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
+                joined = true;
+            }
             r = run_sweep(c, ss.dim, shift_dim);
             if (r != SL_OK) return r;
         }
+        if (!joined) SL_CUDA(c, cudaStreamWaitEvent(c->st, c->ev_join, 0));
     }
     return SL_OK;
 }
@@ -803,7 +875,12 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
     plane_counts(c->ndim, degree, storage, &c->nlo, &c->nhi);
     c->state_bytes = state_bytes_of(c->cells, c->nlo, c->nhi, storage);
     c->external = planes != nullptr;
-    for (int m = 0; m < SL_MAX_DIM; ++m) c->maxcls = std::max<int>(c->maxcls, int(c->g.n[m]));
+    for (int m = 0; m < c->ndim; ++m) {
+        c->ncls[m] = 1;
+        for (int q = 0; q < c->ndim; ++q)
+            if (q != m) c->ncls[m] = std::max<int>(c->ncls[m], int(c->g.n[q]));
+        c->maxcls = std::max(c->maxcls, c->ncls[m]);
+    }
     build_poly_table(degree, &c->poly);
     {
         int dev = 0;
@@ -847,10 +924,14 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
                 if (scaled) c->bands.push_back({o_state[b][2] + size_t(c->cells) * 4, 0, pad * 4, 1});
             }
         }
-    const size_t o_sigma = place(size_t(c->maxcls) * 4);
-    const size_t o_alpha = place(size_t(c->maxcls) * 8);
-    const size_t o_ab64 = place(size_t(c->maxcls) * ab_stride64(c->O) * 8);
-    const size_t o_ab32 = place(size_t(c->maxcls) * ab_stride32(c->O) * 4);
+    size_t o_sigma[SL_MAX_DIM], o_alpha[SL_MAX_DIM], o_ab64[SL_MAX_DIM], o_ab32[SL_MAX_DIM];
+    for (int m = 0; m < c->ndim; ++m) {
+        const size_t n = size_t(c->ncls[m]);
+        o_sigma[m] = place(n * 4);
+        o_alpha[m] = place(n * 8);
+        o_ab64[m] = place(n * ab_stride64(c->O) * 8);
+        o_ab32[m] = place(n * ab_stride32(c->O) * 4);
+    }
     const size_t o_shifts = place(size_t(c->maxcls) * 8);
     int64_t nf = 0;
     for (int m = 0; m < c->ndim; ++m)
@@ -886,10 +967,12 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
         }
     }
     if (mapped) c->d_cmap = reinterpret_cast<int32_t*>(base + o_cmap);
-    c->d_sigma = reinterpret_cast<int32_t*>(base + o_sigma);
-    c->d_alpha = reinterpret_cast<double*>(base + o_alpha);
-    c->d_ab64 = reinterpret_cast<double*>(base + o_ab64);
-    c->d_ab32 = reinterpret_cast<float*>(base + o_ab32);
+    for (int m = 0; m < c->ndim; ++m) {
+        c->d_sigma[m] = reinterpret_cast<int32_t*>(base + o_sigma[m]);
+        c->d_alpha[m] = reinterpret_cast<double*>(base + o_alpha[m]);
+        c->d_ab64[m] = reinterpret_cast<double*>(base + o_ab64[m]);
+        c->d_ab32[m] = reinterpret_cast<float*>(base + o_ab32[m]);
+    }
     c->d_shifts = reinterpret_cast<double*>(base + o_shifts);
     c->d_fields = reinterpret_cast<double*>(base + o_fields);
     c->d_partials = reinterpret_cast<double*>(base + o_part);
@@ -915,7 +998,12 @@ static sl_status create_ctx(const sl_grid* grid, int degree, sl_storage storage,
         e = cudaMemcpyAsync(c->d_cmap, cmap.data(), cmap.size() * 4, cudaMemcpyHostToDevice, c->st);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->st_tab, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+        if (c->st_tab) cudaStreamDestroy(c->st_tab);
         cudaFreeHost(c->h_mass);
         cudaFree(c->mem);
         delete c;
@@ -1017,6 +1105,12 @@ void sl_destroy(sl_ctx* c)
     if (c->d_gshifts) cudaFree(c->d_gshifts);
     if (c->h_mass) cudaFreeHost(c->h_mass);
     if (c->mem) cudaFree(c->mem);   // a caller's planes (sl_create_external) are not freed
+    if (c->st_tab) {
+        cudaStreamSynchronize(c->st_tab);
+        cudaStreamDestroy(c->st_tab);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -42,11 +42,13 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
 //
 // Along dimension 0 the items are short tiles of equal size, taken
 // round-robin (item blockIdx.x, blockIdx.x + gridDim.x, ...).  Along the
-// other dimensions the items (line tiles of uneven length) are sorted by
-// decreasing cost on the host and taken from a shared counter, one atomic per
-// item, so that the long ones start first and no block idles while work
-// remains.  Both loops are bounded by the item count; no block waits on
-// another.
+// other dimensions the items (tiles of 32 lines of uneven length) are sorted
+// by decreasing cost on the host and taken by each warp from a shared
+// counter, one atomic per item, so that the long ones start first and no
+// warp idles while work remains; a problem's last tile of lines leaves at
+// most 31 lanes idle (with tiles of a block's 128 lines, about a tenth of
+// the threads of the 256-problem workload were).  Both loops are bounded by
+// the item count; no block or warp waits on another.
 // One item along dimension 0: reps tiles of kBatchBlock consecutive cells.
 // Not inlined, so that each (K, FT) body gets its own register allocation
 // and reads the problem's geometry where it needs it.
@@ -259,26 +261,23 @@ __global__ void __launch_bounds__(kBatchBlock, 6) k_batch_unit(const SweepArgs* 
     }
 }
 
-// One item along dimension m > 0: kBatchBlock consecutive lines walking one
-// chunk of rows (not inlined, as unit_item).
+// One item along dimension m > 0: kBatchLines consecutive lines (one per
+// lane) walking one chunk of rows (not inlined, as unit_item).
 template <int K, int MODE, int FT, int U>
 __device__ __noinline__ void strided_item(const SweepArgs* __restrict__ ap, const BatchItem item)
 {
     const SweepArgs& a = *ap;
-    const LineSetup L = line_setup(a, item.start + threadIdx.x, item.grp, item.chunk, FT);
+    const LineSetup L = line_setup(a, item.start + (threadIdx.x & 31u), item.grp, item.chunk, FT);
     if (L.active) strided_line<K, MODE, FT, U>(a, L);
 }
 
-// Next item of this block from the launch's counter, broadcast through
-// shared memory; the second barrier keeps the slot until every thread has
-// read it.
-__device__ __forceinline__ uint32_t next_item(uint32_t* ctr, uint32_t* slot)
+// Next item of this warp from the launch's counter (lane 0 takes it, every
+// lane reads it by shuffle).
+__device__ __forceinline__ uint32_t next_item(uint32_t* ctr)
 {
-    if (threadIdx.x == 0) *slot = atomicAdd(ctr, 1u);
-    __syncthreads();
-    const uint32_t it = *slot;
-    __syncthreads();
-    return it;
+    uint32_t it = 0;
+    if ((threadIdx.x & 31u) == 0) it = atomicAdd(ctr, 1u);
+    return __shfl_sync(0xffffffffu, it, 0);
 }
 
 template <int MODE, int FTM, int U>
@@ -287,8 +286,7 @@ __global__ void __launch_bounds__(kBatchBlock) k_batch_strided(const SweepArgs* 
                                                                const BatchItem* __restrict__ items,
                                                                int nitems, uint32_t* __restrict__ ctr)
 {
-    __shared__ uint32_t slot;
-    for (uint32_t it = next_item(ctr, &slot); it < uint32_t(nitems); it = next_item(ctr, &slot)) {
+    for (uint32_t it = next_item(ctr); it < uint32_t(nitems); it = next_item(ctr)) {
         const BatchItem item = items[it];
         const SweepArgs* ap = args + item.prob;
         const int K = kdeg[item.prob];

@@ -51,6 +51,10 @@ struct sl_batch {
         int reps = 4;     // cell tiles per work item (dimension 0)
     } tune[SL_MAX_DIM];
 
+    // side stream of the v-dimensions' table builds (see batch_steps)
+    cudaStream_t st_tab = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int graph_start = -1;
     int graph_flip = 0;
@@ -112,14 +116,14 @@ sl_status rebuild_dim(sl_batch* b, int m)
             for (uint32_t g = 0; g < nfg; ++g)
                 for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * span, g, 0});
         } else {
-            const uint32_t tiles = (a.lines + kBatchBlock - 1) / kBatchBlock;
+            const uint32_t tiles = (a.lines + kBatchLines - 1) / kBatchLines;
             const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
             const int64_t ft = c->tune[m].ft;
             for (uint32_t g = 0; g < nfg; ++g)
                 for (uint32_t ch = 0; ch < nchunk; ++ch)
                     for (uint32_t i = 0; i < tiles; ++i) {
-                        items.push_back({uint32_t(p), i * kBatchBlock, g, ch});
-                        const int64_t lines = std::min<int64_t>(kBatchBlock, int64_t(a.lines) - int64_t(i) * kBatchBlock);
+                        items.push_back({uint32_t(p), i * kBatchLines, g, ch});
+                        const int64_t lines = std::min<int64_t>(kBatchLines, int64_t(a.lines) - int64_t(i) * kBatchLines);
                         const int64_t rows = std::min<int64_t>(a.chunk, int64_t(a.N) - int64_t(ch) * a.chunk);
                         const int64_t fib = std::min<int64_t>(ft, c->nfib - int64_t(g) * ft);
                         cost.push_back(lines * rows * fib * c->O);
@@ -157,10 +161,16 @@ cudaEvent_t new_event()
     return cudaEventCreate(&e) == cudaSuccess ? e : nullptr;
 }
 
-sl_status batch_sweep(sl_batch* b, int m, double tau)
+// Shift tables of every problem's dimension m over tau on stream st.
+sl_status batch_tables(sl_batch* b, int m, double tau, cudaStream_t st)
 {
-    SLB_CUDA(b, launch_batch_ab(b->d_ab + size_t(m) * b->nprob, b->d_tabs, b->nprob, b->maxcls[m], tau,
-                                b->st));
+    SLB_CUDA(b, launch_batch_ab(b->d_ab + size_t(m) * b->nprob, b->d_tabs, b->nprob, b->maxcls[m], tau, st));
+    return SL_OK;
+}
+
+// The sweep of every problem along m with the tables already built.
+sl_status batch_sweep(sl_batch* b, int m)
+{
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     const bool prof = b->prof && !b->capturing;
     if (prof) {
@@ -186,14 +196,59 @@ sl_status batch_sweep(sl_batch* b, int m, double tau)
     return SL_OK;
 }
 
+// The split steps.  As for one problem, a table depends on its dimension,
+// tau and the fields only, so each dimension's tables are built once per
+// step: the x-dimensions' before the step's first sweep, the v-dimensions'
+// on the side stream while the x-sweeps run (joined before the first
+// v-sweep); Strang's second x half-step reuses the first one's.
 sl_status batch_steps(sl_batch* b, sl_splitting sp, double dt, int nsteps)
 {
     const std::vector<SubStep> plan = plan_of(b->probs[0], sp);
-    for (int s = 0; s < nsteps; ++s)
+    const sl_ctx* c0 = b->probs[0];
+    bool ahead = true;
+    for (const SubStep& x : plan)
+        for (const SubStep& y : plan)
+            if (x.dim == y.dim && x.frac != y.frac) ahead = false;
+    for (int s = 0; s < nsteps; ++s) {
+        bool built[SL_MAX_DIM] = {false};
+        bool joined = true;
+        if (ahead) {
+            bool any_v = false;
+            for (const SubStep& ss : plan) {
+                if (c0->g.pair[ss.dim] < 0) {
+                    any_v = true;
+                } else if (!built[ss.dim]) {
+                    sl_status r = batch_tables(b, ss.dim, ss.frac * dt, b->st);
+                    if (r != SL_OK) return r;
+                    built[ss.dim] = true;
+                }
+            }
+            if (any_v) {
+                SLB_CUDA(b, cudaEventRecord(b->ev_fork, b->st));
+                SLB_CUDA(b, cudaStreamWaitEvent(b->st_tab, b->ev_fork, 0));
+                for (const SubStep& ss : plan) {
+                    if (c0->g.pair[ss.dim] >= 0 || built[ss.dim]) continue;
+                    sl_status r = batch_tables(b, ss.dim, ss.frac * dt, b->st_tab);
+                    if (r != SL_OK) return r;
+                    built[ss.dim] = true;
+                }
+                SLB_CUDA(b, cudaEventRecord(b->ev_join, b->st_tab));
+                joined = false;
+            }
+        }
         for (const SubStep& ss : plan) {
-            sl_status r = batch_sweep(b, ss.dim, ss.frac * dt);
+            if (!built[ss.dim]) {
+                sl_status r = batch_tables(b, ss.dim, ss.frac * dt, b->st);
+                if (r != SL_OK) return r;
+            } else if (!joined && c0->g.pair[ss.dim] < 0) {
+                SLB_CUDA(b, cudaStreamWaitEvent(b->st, b->ev_join, 0));
+                joined = true;
+            }
+            sl_status r = batch_sweep(b, ss.dim);
             if (r != SL_OK) return r;
         }
+        if (!joined) SLB_CUDA(b, cudaStreamWaitEvent(b->st, b->ev_join, 0));
+    }
     return SL_OK;
 }
 
@@ -309,6 +364,10 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
     b->d_mass = reinterpret_cast<double*>(base + o_m);
     b->d_ctr = reinterpret_cast<uint32_t*>(base + o_ctr);
     b->h_mass.resize(nprob);
+    if (cudaStreamCreateWithFlags(&b->st_tab, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(nullptr, SL_ECUDA, "batch side stream"));
 
     std::vector<int32_t> kd(nprob);
     std::vector<BatchAB> ab(size_t(b->ndim) * nprob);
@@ -325,10 +384,10 @@ sl_status sl_batch_create(int nprob, const sl_grid* grids, const int* degrees, s
             BatchAB& d = ab[size_t(m) * nprob + p];
             d.K = c->K;
             d.N = uint32_t(c->g.n[m]);
-            d.sigma = c->d_sigma;
-            d.alpha = c->d_alpha;
-            d.ab64 = c->d_ab64;
-            d.ab32 = c->d_ab32;
+            d.sigma = c->d_sigma[m];
+            d.alpha = c->d_alpha[m];
+            d.ab64 = c->d_ab64[m];
+            d.ab32 = c->d_ab32[m];
             d.h = cell_width(c->g, m);
             if (c->g.pair[m] >= 0) {
                 const int v = c->g.pair[m];
@@ -377,6 +436,12 @@ void sl_batch_destroy(sl_batch* b)
     if (!b) return;
     cudaStreamSynchronize(b->st);
     drop_graph(b);
+    if (b->st_tab) {
+        cudaStreamSynchronize(b->st_tab);
+        cudaStreamDestroy(b->st_tab);
+    }
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     for (auto& pr : b->ev) {
         cudaEventDestroy(pr.first);
         cudaEventDestroy(pr.second);

@@ -37,11 +37,20 @@ struct sl_ctx {
     bool external = false;      // planes owned by the caller (sl_create_external)
     int cur = 0;
 
-    int maxcls = 1;
-    int32_t* d_sigma = nullptr;
-    double* d_alpha = nullptr;
-    double* d_ab64 = nullptr;
-    float* d_ab32 = nullptr;
+    // shift tables, one per sweep dimension m with ncls[m] classes (the
+    // extent of the largest other dimension, at least 1: a line's shift
+    // depends on one orthogonal coordinate), so that the tables of a split
+    // step can be built ahead of their sweeps
+    int ncls[SL_MAX_DIM] = {0};
+    int maxcls = 1;             // max over m: host shifts staged in d_shifts
+    int32_t* d_sigma[SL_MAX_DIM] = {nullptr};
+    double* d_alpha[SL_MAX_DIM] = {nullptr};
+    double* d_ab64[SL_MAX_DIM] = {nullptr};
+    float* d_ab32[SL_MAX_DIM] = {nullptr};
+    // side stream of the v-dimensions' table builds, forked from and joined
+    // back to st by the two events within every split step
+    cudaStream_t st_tab = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double* d_shifts = nullptr;
     double* d_fields = nullptr;
     int64_t nfields = 0;

@@ -229,11 +229,12 @@ cudaError_t launch_project(const ProjectArgs& pa, const double* d_weights, const
 
 // ---------------------------------------------------------------- batches
 
-// One work item of a batched sweep: the threads cover `reps` tiles of
-// `kBatchBlock` consecutive cells (sweep along dimension 0), or
-// `kBatchBlock` consecutive lines walking one chunk of rows (other
+// One work item of a batched sweep: a block's threads cover `reps` tiles of
+// `kBatchBlock` consecutive cells (sweep along dimension 0), or a warp's
+// lanes `kBatchLines` consecutive lines walking one chunk of rows (other
 // dimensions), starting at `start` of problem `prob`, for fibre group `grp`.
 constexpr int kBatchBlock = 128;
+constexpr int kBatchLines = 32;
 constexpr int kBatchMaxK = 2;          // degrees compiled into the batched sweep
 constexpr int kBatchMaxFtUnit = 3;     // fibres per thread compiled along dimension 0
 constexpr int kBatchMaxFtStrided = 2;  // ... and along the other dimensions
@@ -269,7 +270,7 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
                             double tau, cudaStream_t st);
 // unit = 1: sweep along dimension 0, each item covering reps * kBatchBlock
 // cells.  ft is the most fibres per thread (each problem's own is
-// ceil(nfib / nfg) of its arguments).  Along the other dimensions the blocks
+// ceil(nfib / nfg) of its arguments).  Along the other dimensions the warps
 // take items from *d_ctr, which the launch first sets to zero.
 cudaError_t launch_batch_sweep(int mode, int ft, int unroll, const SweepArgs* d_args,
                                const int32_t* d_kdeg, const BatchItem* d_items, int nitems,

@@ -729,3 +729,19 @@ def test_external_planes_give_the_same_results(storage, n, k):
             mean = bufs[3 * cur + 1].view(torch.float32)[: int(np.prod(n))].cpu().numpy()
             assert np.array_equal(mean.astype(np.float64), b.get_coeffs()[:, 0])
     del bufs
+
+
+def test_shift_tables_are_sized_by_the_other_dimensions():
+    """A sweep's shift classes follow one coordinate orthogonal to it, so the
+    table of dimension m holds as many classes as the largest other extent
+    (one in 1D): a 1D context of 2^22 cells at k = 3 allocates little beyond
+    its two copies of the state (a table per cell would add 1.7 GB), and a 2D
+    one tables of a line's length only."""
+    g = _grid((1 << 22,))
+    with S.Context(g, 3, "fp64") as ctx:
+        info = ctx.info
+        assert info["alloc_bytes"] <= 2 * info["state_bytes"] + (4 << 20)
+    g2 = _grid((1 << 12, 1 << 10), pair=(1, -1))
+    with S.Context(g2, 2, "mix_fp32") as ctx:
+        info = ctx.info
+        assert info["alloc_bytes"] <= 2 * info["state_bytes"] + (8 << 20)
