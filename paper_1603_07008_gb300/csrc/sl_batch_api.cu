@@ -113,8 +113,8 @@ sl_status rebuild_dim(sl_batch* b, int m)
         if (m == 0) {
             const uint32_t span = uint32_t(kBatchBlock * t.reps * t.unroll);   // unroll: cells per thread
             const uint32_t tiles = (a.cells + span - 1) / span;
-            for (uint32_t g = 0; g < nfg; ++g)
-                for (uint32_t i = 0; i < tiles; ++i) items.push_back({uint32_t(p), i * span, g, 0});
+            for (uint32_t i = 0; i < tiles; ++i)   // the groups of a tile side by side (see unit_grid)
+                for (uint32_t g = 0; g < nfg; ++g) items.push_back({uint32_t(p), i * span, g, 0});
         } else {
             const uint32_t tiles = (a.lines + kBatchLines - 1) / kBatchLines;
             const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;

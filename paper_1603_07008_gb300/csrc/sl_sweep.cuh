@@ -583,14 +583,51 @@ __device__ __forceinline__ void unit_cell(const SweepArgs& a, uint32_t c, int fb
         unit_body<K, MODE, FT, false, CV>(a, c, ca, cb, cls, fbase);
 }
 
-// Sweep along dimension 0: one thread per target cell (and fibre group
-// blockIdx.y).
-template <int K, int MODE, int FT>
+// Grid of the sweeps along dimension 0 over `tiles` blocks of cells and nfg
+// fibre groups.  Blocks are dispatched in the order of their linear index
+// (x fastest).  With gfast (the kernels' GF) the fibre group is x and the
+// tile y (the kernels loop over tiles y, y + gridDim.y, ...), so that the
+// blocks of the mean's group, which load the FP64 pipe, run beside the other
+// groups' instead of all of them first: chosen where the mean's group alone
+// would need more than half the FP64 pipe at the memory's rate (unit_gfast).
+// Otherwise the tile is x and the group y, so that the blocks in flight read
+// few planes.
+inline dim3 unit_grid(uint32_t tiles, int nfg, int gfast)
+{
+    if (tiles < 1) tiles = 1;
+    if (gfast) return dim3(uint32_t(nfg), tiles < 65535u ? tiles : 65535u);
+    return dim3(tiles, uint32_t(nfg));
+}
+// In the mixed FP32 store the mean's group takes three FP64-pipe instructions
+// per cell and moves 2 (8 + elem (ft o - 1)) bytes per cell: more than half of
+// GB300's FP64 issue rate (2 per clock per SM) at the copy bandwidth below 64
+// bytes.  (In the FP64 store every group loads the FP64 pipe alike.)  Only
+// for a few groups (the 2D store: the mean's group is a third or a half of
+// the launch): with the 27 one-fibre groups of the 4D store at k = 2 the
+// blocks in flight then read all 81 planes at once, and dimension 0 measured
+// 5% slower than group by group.
+inline int unit_gfast(int nfg, int ft, int O, int elem)
+{
+    return nfg > 1 && nfg <= 4 && 2 * (8 + elem * (ft * O - 1)) < 64 ? 1 : 0;
+}
+
+// Sweep along dimension 0: one thread per target cell and fibre group (GF:
+// see unit_grid).
+template <int K, int MODE, int FT, bool GF>
 __global__ void __launch_bounds__(256) k_sweep_unit(const SweepArgs a)
 {
-    const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.cells) return;
-    unit_cell<K, MODE, FT>(a, c, int(blockIdx.y) * FT);
+    if constexpr (GF) {
+        const int fbase = int(blockIdx.x) * FT;
+        for (uint32_t t = blockIdx.y; t * blockDim.x < a.cells; t += gridDim.y) {
+            const uint32_t c = t * blockDim.x + threadIdx.x;
+            if (c >= a.cells) break;
+            unit_cell<K, MODE, FT>(a, c, fbase);
+        }
+    } else {
+        const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+        if (c >= a.cells) return;
+        unit_cell<K, MODE, FT>(a, c, int(blockIdx.y) * FT);
+    }
 }
 
 // ---------------------------------------------------------------- unit stride, 128-bit vectors
@@ -736,21 +773,32 @@ __device__ __forceinline__ void unit_vec_body(const SweepArgs& a, uint32_t c0, u
 }
 
 // Sweep along dimension 0 with 16-byte vectors: one thread per V consecutive
-// target cells and fibre group (blockIdx.y); needs n_0 divisible by V.
-template <int K, int MODE, int FT>
+// target cells and fibre group (see unit_grid); needs n_0 divisible by V.
+template <int K, int MODE, int FT, bool GF>
 __global__ void __launch_bounds__(256) k_sweep_unit_vec(const SweepArgs a)
 {
     constexpr int V = 16 / sizeof(typename St<MODE>::T);
-    const uint32_t c0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
-    if (c0 >= a.cells) return;
-    const int fbase = int(blockIdx.y) * FT;
-    const uint32_t line = a.fdN.div(c0);
-    const uint32_t i0 = c0 - line * a.N;
-    const uint32_t cls = shift_class(a, 0, line);
-    if (St<MODE>::mean64 && fbase == 0)
-        unit_vec_body<K, MODE, FT, true>(a, c0, i0, cls, fbase);
-    else
-        unit_vec_body<K, MODE, FT, false>(a, c0, i0, cls, fbase);
+    auto body = [&](uint32_t c0, int fbase) {
+        const uint32_t line = a.fdN.div(c0);
+        const uint32_t i0 = c0 - line * a.N;
+        const uint32_t cls = shift_class(a, 0, line);
+        if (St<MODE>::mean64 && fbase == 0)
+            unit_vec_body<K, MODE, FT, true>(a, c0, i0, cls, fbase);
+        else
+            unit_vec_body<K, MODE, FT, false>(a, c0, i0, cls, fbase);
+    };
+    if constexpr (GF) {
+        const int fbase = int(blockIdx.x) * FT;
+        for (uint32_t t = blockIdx.y; t * blockDim.x * V < a.cells; t += gridDim.y) {
+            const uint32_t c0 = (t * blockDim.x + threadIdx.x) * V;
+            if (c0 >= a.cells) break;
+            body(c0, fbase);
+        }
+    } else {
+        const uint32_t c0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+        if (c0 >= a.cells) return;
+        body(c0, int(blockIdx.y) * FT);
+    }
 }
 
 // ---------------------------------------------------------------- strided

@@ -58,7 +58,7 @@ cudaError_t launch_one(const SweepLaunch& L)
     if (a.nfib != NF || a.nfg != 1) return cudaErrorInvalidValue;
     if (L.unit) {
         dim3 grid((a.cells + L.block - 1) / L.block, 1);
-        k_sweep_unit<K, MODE, NF><<<grid, L.block, 0, L.stream>>>(a);
+        k_sweep_unit<K, MODE, NF, false><<<grid, L.block, 0, L.stream>>>(a);
     } else {
         const uint32_t nchunk = (a.N + a.chunk - 1) / a.chunk;
         dim3 grid((a.lines + L.block - 1) / L.block, nchunk);
