@@ -229,10 +229,12 @@ __device__ __forceinline__ void unit_items(const SweepArgs* __restrict__ ap, uin
         unit_item<K, MODE, FT>(ap, start, fbase, reps);
 }
 
-// At least 6 resident blocks per SM (at most 85 registers per thread):
-// measured ahead of the unconstrained allocation with the runs above.
+// At least 7 resident blocks per SM in the mixed store (at most 72 registers
+// per thread, a few spilled: 4940 GB/s on the 256-problem workload against
+// 4854 with 6 blocks, 4717 with 8 and 4684 with 5), 6 in the FP64 store (at 7
+// its runs spill about 1 KB per thread).
 template <int MODE, int FTM, int PC>
-__global__ void __launch_bounds__(kBatchBlock, 6) k_batch_unit(const SweepArgs* __restrict__ args,
+__global__ void __launch_bounds__(kBatchBlock, MODE == M_FP64 ? 6 : 7) k_batch_unit(const SweepArgs* __restrict__ args,
                                                             const int32_t* __restrict__ kdeg,
                                                             const BatchItem* __restrict__ items,
                                                             int nitems, int reps)
