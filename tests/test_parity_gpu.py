@@ -363,7 +363,7 @@ ASYNC_SHAPES = [(1, 4), (1, 8), (2, 4), (2, 8), (3, 4)]
 
 @pytest.mark.parametrize("storage", ["fp64", "mix_fp32"])
 @pytest.mark.parametrize("n,k", [((37, 5, 3), 2), ((6, 9, 4), 1), ((3, 4, 5), 3), ((8, 3, 5), 2),
-                                 ((4, 6, 2), 1), ((12, 2, 3), 3)])
+                                 ((4, 6, 2), 1), ((12, 2, 3), 3), ((16, 12), 2), ((20, 6), 1)])
 def test_every_launch_shape_gives_identical_results(storage, n, k):
     """Fibres per thread, unroll, block size and chunk length change only the
     work distribution: every shape must give bit-identical output, and the
@@ -745,3 +745,31 @@ def test_shift_tables_are_sized_by_the_other_dimensions():
     with S.Context(g2, 2, "mix_fp32") as ctx:
         info = ctx.info
         assert info["alloc_bytes"] <= 2 * info["state_bytes"] + (8 << 20)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_fibre_groups_side_by_side_over_many_tiles(k):
+    """In the 2D mixed store the unit-stride sweep puts the fibre groups side by
+    side in the launch order and loops over tiles when there are more than
+    65535 of them (4096 x 1040 cells in blocks of 64 threads: 66 560 tiles).
+    One fibre per thread that way must give the same bits as the whole cell per
+    thread (one group, tiles in x)."""
+    n = (4096, 1040)
+    g = _grid(n)
+    u = _rand(n, k, 23)
+    s = np.random.default_rng(24).uniform(-3.0 * n[0], 3.0 * n[0], size=n[1])
+    with S.Context(g, k, "mix_fp32") as ctx:
+        outs = []
+        for ft in (1, k + 1):
+            ctx.set_tune(0, block=64, fibres_per_thread=ft)
+            ctx.set_coeffs(u)
+            ctx.advect(0, 1, s)
+            outs.append(ctx.get_coeffs())
+        assert np.array_equal(outs[0], outs[1])
+        # and the sampled cells against the oracle on their own lines
+        rows = [0, 517, n[1] - 1]
+        for j in rows:
+            line = u[j * n[0]:(j + 1) * n[0]]
+            ref = O.sweep(ctx_stored(line, "mix_fp32"), [n[0], 1], k, 0, 1, [s[j]])
+            got = outs[0][j * n[0]:(j + 1) * n[0]]
+            assert O.rel_l2(got, ref, k, 2) <= 1e-6, j
