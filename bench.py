@@ -229,6 +229,26 @@ TRAFFIC = {
 }
 
 
+def launches_per_step(args, info):
+    """Kernels one bench step launches.  A split step builds each dimension's
+    shift table once (Strang's two x half-steps share theirs) besides its
+    sweeps; a nodal x-sweep builds its node table before it (and, in the mixed
+    store, the per-v-cell record); the self-consistent field builds every table
+    right before its sweep and takes two launches (density sums, field) before
+    the v-sweep; the 1D advection graph is (table build, sweep) pairs."""
+    sweeps = info["sweeps"]
+    if args.workload == "1d":
+        return 2 * sweeps
+    if args.workload == "vp":
+        return 2 * sweeps + 2
+    nodal = info.get("nodal_x_sweeps", 0)
+    if nodal:
+        x_dims = info["ndim"] // 2
+        per_nodal = 2 if args.storage == "fp64" else 3
+        return nodal * per_nodal + (sweeps - nodal) + (info["ndim"] - x_dims)
+    return sweeps + info["ndim"]
+
+
 def sweep_traffic(workload, storage, bytes_per_launch):
     """DRAM bytes per sweep launch at this size, or (None, why)."""
     import hashlib
@@ -574,6 +594,7 @@ def run_ours(args):
         m1 = arm.mass_total()
         info = {"state_bytes": arm.state_bytes, "dof": arm.dof, "sweeps": arm.sweeps,
                 "nodal_x_sweeps": 2 * len(arm.p.grid.x_dims()) if getattr(arm, "nodal", False) else 0,
+                "ndim": 2 if arm.workload == "batch" else len(arm.p.grid.n),
                 "tune": arm.tunes(), "order": arm.order,
                 "graph": arm.workload == "1d" or getattr(arm, "graph", False)}
         if arm.workload == "batch":
@@ -698,12 +719,7 @@ def run_ours(args):
             "fp64": fp64,
             "speedup_mixed_vs_fp64": (value / fp64["value"]) if fp64 else None,
             "e2e": e2e,
-            # per sweep its table build and the sweep; a nodal x-sweep of the mixed
-            # store also builds its per-v-cell alpha_bar, and the self-consistent
-            # field takes two launches (density sums, field) before the v-sweep
-            "gpu_launches": args.steps * (info["sweeps"] * 2 +
-                                          (info["nodal_x_sweeps"] if args.storage != "fp64" else 0) +
-                                          (2 if args.workload == "vp" else 0)),
+            "gpu_launches": args.steps * launches_per_step(args, info),
             "clocks": clk,
             "cpu_baseline": cpu,
         }
