@@ -235,10 +235,12 @@ def launches_per_step(args, info):
     sweeps; a nodal x-sweep builds its node table before it (and, in the mixed
     store, the per-v-cell record); the self-consistent field builds every table
     right before its sweep and takes two launches (density sums, field) before
-    the v-sweep; the 1D advection graph is (table build, sweep) pairs."""
+    the v-sweep; the 1D advection graph is one thread-block cluster launch in
+    the FP64 store (every step's table built in the kernel), (table build,
+    sweep) pairs otherwise."""
     sweeps = info["sweeps"]
     if args.workload == "1d":
-        return 2 * sweeps
+        return 1 if args.storage == "fp64" else 2 * sweeps
     if args.workload == "vp":
         return 2 * sweeps + 2
     nodal = info.get("nodal_x_sweeps", 0)
@@ -480,8 +482,9 @@ class Arm:
             self.dof = p.dof
             self.order = p.k + 1
             self.state_bytes = self.obj.info["state_bytes"]
-            # the 1D workload: one bench step is the whole 100-step run (one graph
-            # of 100 sweeps, each with its table build)
+            # the 1D workload: one bench step is the whole 100-step run (one graph:
+            # in the FP64 store a single cluster launch that builds every step's
+            # table and runs its sweep)
             self.sweeps = ADVECT_GRAPH_SWEEPS if p.splitting == "advect" else \
                 2 * len(p.grid.x_dims()) + len(p.grid.v_dims())
             self.dt = p.dt

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["sl_api.cu", "sl_aux.cu", "sl_sweep_f64.cu", "sl_sweep_f32.cu", "sl_sweep_scaled.cu", "sl_poly.cpp",
            "sl_noalloc.cu", "sl_batch.cu", "sl_batch_api.cu", "sl_sweep_rec.cu", "sl_vp.cu", "sl_sweep_f32all.cu",
-           "sl_sweep_split.cu", "sl_nodal.cu", "sl_sweep_wide.cu"]
+           "sl_sweep_split.cu", "sl_nodal.cu", "sl_sweep_wide.cu", "sl_sweep_1d.cu"]
 HEADERS = ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_ab.cuh", "sl_host.h", "sl_nodal.h"]
 
 NVCC_FLAGS = ["-std=c++17", "-O3", "-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo",

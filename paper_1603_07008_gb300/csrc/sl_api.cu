@@ -1617,7 +1617,19 @@ sl_status sl_graph_capture_advect(sl_ctx* c, int dim, int shift_dim, const doubl
     }
     SL_CUDA(c, cudaMemcpyAsync(c->d_gshifts, shifts, size_t(nshift) * 8, cudaMemcpyHostToDevice, c->st));
     SL_CUDA(c, cudaStreamSynchronize(c->st));
+    // a short 1D line of the FP64 store with one shift: every step in one
+    // cluster launch (sl_sweep_1d.cu), each step building its matrices
+    const bool one_launch = c->ndim == 1 && c->mode == M_FP64 && !c->wide && shift_dim < 0 &&
+                            sweep_1d_cluster_ok(c->K, uint32_t(c->g.n[0]));
     return capture_graphs(c, nsteps, [&]() -> sl_status {
+        if (one_launch) {
+            cudaError_t e = launch_sweep_1d_cluster(c->K, c->planes[c->cur], c->planes[c->cur ^ (nsteps & 1)],
+                                                    c->pstride, uint32_t(c->g.n[0]), c->d_gshifts, c->poly,
+                                                    nsteps, c->st);
+            if (e != cudaSuccess) return cuda_fail(c, e, "1D cluster sweep launch");
+            c->cur ^= nsteps & 1;
+            return SL_OK;
+        }
         for (int q = 0; q < nsteps; ++q) {
             ShiftSource src{};
             src.kind = 0;

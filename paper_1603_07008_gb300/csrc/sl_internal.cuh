@@ -175,6 +175,15 @@ struct PolyTab {
 };
 void build_poly_table(int K, PolyTab* out);   // host, exact rational arithmetic
 
+// nsteps sweeps with one shift (*shift, device) of a 1D line of N cells of the
+// FP64 store by one thread-block cluster holding the line in shared memory
+// (sl_sweep_1d.cu): reads src, writes the state after the last step to dst
+// (src itself allowed).  sweep_1d_cluster_ok: the line fits.
+size_t sweep_1d_cluster_smem(int K, uint32_t N);
+bool sweep_1d_cluster_ok(int K, uint32_t N);
+cudaError_t launch_sweep_1d_cluster(int K, const Planes& src, const Planes& dst, int64_t pstride, uint32_t N,
+                                    const double* shift, const PolyTab& tab, int nsteps, cudaStream_t st);
+
 // Where the shift of class c comes from.
 struct ShiftSource {
     int kind;            // 0: shifts[c]; 1: (lo + (c+1/2) hv) * tau / h; 2: field[c] * tau / h

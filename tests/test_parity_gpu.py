@@ -773,3 +773,39 @@ def test_fibre_groups_side_by_side_over_many_tiles(k):
             ref = O.sweep(ctx_stored(line, "mix_fp32"), [n[0], 1], k, 0, 1, [s[j]])
             got = outs[0][j * n[0]:(j + 1) * n[0]]
             assert O.rel_l2(got, ref, k, 2) <= 1e-6, j
+
+
+@pytest.mark.parametrize("n,k", [(1024, 2), (1000, 3), (37, 1), (5, 0), (2048, 2)])
+def test_one_launch_1d_graph_matches_advect_calls_bit_for_bit(n, k):
+    """A captured advection of a short 1D line of the FP64 store runs every
+    step in one thread-block cluster launch, each step building its matrices
+    in the kernel: it must give the same bits as the same number of sl_advect
+    calls (a table build and a sweep each), for shifts with and without a
+    fractional part, negative ones, shifts of more than the line, and an odd
+    number of steps (two graphs, one per buffer parity)."""
+    import torch
+    g = _grid((n,))
+    u = _rand((n,), k, 31)
+    st = torch.cuda.Stream()
+    for s, steps in ((0.37, 100), (-2.75, 7), (3.0, 4), (2.5 * n + 0.4, 3)):
+        with S.Context(g, k, "fp64", stream=st) as a, S.Context(g, k, "fp64", stream=st) as b:
+            a.set_coeffs(u)
+            b.set_coeffs(u)
+            for _ in range(steps):
+                a.advect(0, -1, [s])
+            b.graph_capture_advect(0, -1, [s], steps)
+            b.graph_launch()
+            assert np.array_equal(a.get_coeffs(), b.get_coeffs()), (s, steps)
+            b.graph_launch()
+            for _ in range(steps):
+                a.advect(0, -1, [s])
+            assert np.array_equal(a.get_coeffs(), b.get_coeffs()), (s, steps)
+    # against the oracle: the first configuration's 100 steps
+    ref = u
+    for _ in range(100):
+        ref = O.sweep(ref, [n], k, 0, -1, [0.37])
+    with S.Context(g, k, "fp64", stream=st) as b:
+        b.set_coeffs(u)
+        b.graph_capture_advect(0, -1, [0.37], 100)
+        b.graph_launch()
+        assert O.rel_max(b.get_coeffs(), ref) <= FP64_TOL
