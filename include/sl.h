@@ -436,7 +436,11 @@ sl_status sl_graph_launch(sl_ctx* ctx);
 /* Capture nsteps sweeps of sl_advect(ctx, dim, shift_dim, shifts, nshift),
  * each with its table build, into a CUDA graph (replacing a previous graph)
  * that sl_graph_launch replays.  The graph keeps its own device copy of the
- * shifts.  Same argument checks as sl_advect; nsteps >= 1. */
+ * shifts.  Same argument checks as sl_advect; nsteps >= 1.  A 1D context of
+ * the FP64 store with one shift (shift_dim = -1) whose line fits one
+ * thread-block cluster's shared memory (about 8000 cells at degree 2) runs
+ * the nsteps sweeps, each building its matrices, in one kernel launch; the
+ * results are the same bits as nsteps sl_advect calls. */
 sl_status sl_graph_capture_advect(sl_ctx* ctx, int dim, int shift_dim, const double* shifts, int64_t nshift,
                                   int nsteps);
 
