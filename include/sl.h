@@ -76,9 +76,9 @@ typedef enum {
     SL_EINVAL = -1,    /* invalid argument (grid, degree, dimension, size, non-finite value) */
     SL_ENOMEM = -2,    /* device or host allocation failed */
     SL_ECUDA = -3,     /* a CUDA runtime call or kernel launch failed */
-    SL_ETIMEOUT = -4,  /* reserved for a bounded device-side wait; no kernel of this build waits */
+    SL_ETIMEOUT = -4,  /* reserved for a bounded device-side wait; no kernel of this library spins on a flag */
     SL_ENAN = -5,      /* non-finite value in an input array */
-    SL_ENOTSUP = -6    /* valid request this build does not support (e.g. scaled mode with o^d > 128) */
+    SL_ENOTSUP = -6    /* valid request this library does not support (e.g. scaled mode with o^d > 128) */
 } sl_status;
 
 /* Storage of the Legendre coefficients c_{j_0..j_{d-1}} of a cell (Sec. III-A,
@@ -548,7 +548,7 @@ typedef struct {
 } sl_tune;
 
 sl_status sl_get_tune(const sl_ctx* ctx, int dim, sl_tune* out);
-/* Errors: SL_EINVAL for a shape this build does not provide. */
+/* Errors: SL_EINVAL for a shape this library does not provide. */
 sl_status sl_set_tune(sl_ctx* ctx, int dim, const sl_tune* tune);
 
 /* Autotuner: for every dimension, time each provided launch shape `reps`
@@ -567,7 +567,7 @@ sl_status sl_batch_get_tune(const sl_batch* batch, int dim, sl_tune* out);
  * 1 or 2, or 1..2 with 4, and chunk a multiple of 128 x unroll up to
  * 8 x 128 x unroll cells per item; the other dimensions take
  * fibres_per_thread 1..2, unroll 1, 2 or 4 and chunk >= 1 rows per item.
- * Errors: SL_EINVAL for a shape this build does not provide. */
+ * Errors: SL_EINVAL for a shape this library does not provide. */
 sl_status sl_batch_set_tune(sl_batch* batch, int dim, const sl_tune* tune);
 
 /* ---------------------------------------------------------------- profiling */

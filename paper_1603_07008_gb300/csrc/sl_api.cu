@@ -138,7 +138,7 @@ sl_status check_grid(const sl_grid* g, int degree, int storage, sl_ctx* c)
         if (used[p]++) return fail(c, SL_EINVAL, "v-dimension %d paired twice", p);
     }
     if (cells > double(0x7fffffff))
-        return fail(c, SL_ENOTSUP, "grid has %.0f cells; this build indexes cells with 31 bits", cells);
+        return fail(c, SL_ENOTSUP, "grid has %.0f cells; this library indexes cells with 31 bits", cells);
     const int64_t nc = ipow(degree + 1, g->ndim);
     if ((storage == SL_MIX_BF16 || storage == SL_MIX_FP16) && nc > kMaxScaledCoef)
         return fail(c, SL_ENOTSUP, "scaled storage needs o^d <= %d (got %lld)", kMaxScaledCoef,

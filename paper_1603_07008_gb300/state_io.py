@@ -154,7 +154,7 @@ def autotune_cached(ctx, path, reps: int = 3, device: Optional[str] = None) -> b
             for d, sh in enumerate(shapes):
                 ctx.set_tune(d, **sh)
             return True
-        except Exception:     # a shape this build does not provide: tune again
+        except Exception:     # a shape this library does not provide: tune again
             pass
     ctx.autotune(reps)
     data[key] = [dict(ctx.get_tune(d)) for d in range(len(g.n))]
