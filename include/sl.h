@@ -429,8 +429,10 @@ typedef enum { SL_ARITH_STORE = 0, SL_ARITH_FP64 = 1 } sl_arith;
 sl_status sl_set_arithmetic(sl_ctx* ctx, int arith);
 
 /* Capture nsteps of sl_step into a CUDA graph (replacing a previous one) and
- * replay it with sl_graph_launch.  Fields must be set before capture; a later
- * sl_set_fields is not seen by the graph until it is captured again. */
+ * replay it with sl_graph_launch.  Fields must be set before capture.  Every
+ * replay builds its shift tables from the context's field array as it is
+ * then, so fields set later with sl_set_fields (ordered on the context's
+ * stream) are used from the next replay on. */
 sl_status sl_graph_capture(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
 sl_status sl_graph_launch(sl_ctx* ctx);
 /* Capture nsteps sweeps of sl_advect(ctx, dim, shift_dim, shifts, nshift),
@@ -481,6 +483,9 @@ sl_status sl_batch_set_fields(sl_batch* batch, const double* fields, int64_t cou
 sl_status sl_batch_step(sl_batch* batch, sl_splitting splitting, double dt, int nsteps);
 /* Mass of every problem into out[nprob]; synchronises. */
 sl_status sl_batch_mass(sl_batch* batch, double* out);
+/* As sl_graph_capture / sl_graph_launch for the batch: each replay builds the
+ * problems' tables from their fields as they are then (sl_batch_set_fields
+ * between replays is used by the next one). */
 sl_status sl_batch_graph_capture(sl_batch* batch, sl_splitting splitting, double dt, int nsteps);
 sl_status sl_batch_graph_launch(sl_batch* batch);
 sl_status sl_batch_synchronize(sl_batch* batch);

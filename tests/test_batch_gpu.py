@@ -201,3 +201,33 @@ def test_batch_lie_matches_single_problems():
             c.set_fields(p.field_list())
             c.step("lie", 0.1, 3)
             assert np.array_equal(got[i], c.get_coeffs()), i
+
+
+def test_batch_fields_changed_between_graph_replays_are_used():
+    """The batch builds every problem's tables once per split step from the
+    fields as they are then, also inside a captured step: after sl_set_fields
+    a replayed graph uses the new fields, bit for bit as the problems stepped
+    alone with the same fields."""
+    import torch
+    probs = _problems(SIZES, DEGS, "mix_fp32")
+    f1 = [p.field_list()[0] for p in probs]
+    f2 = [-2.0 * f + 0.03 for f in f1]
+    st = torch.cuda.Stream()
+    with S.Batch([p.grid for p in probs], [p.k for p in probs], "mix_fp32", stream=st) as b:
+        for i, p in enumerate(probs):
+            b.project(i, p.nq, p.weights, p.params)
+        b.set_fields(f1)
+        b.graph_capture("strang", 0.1, 1)
+        b.graph_launch()
+        b.set_fields(f2)
+        b.graph_launch()
+        got = [b.get_coeffs(i) for i in range(len(probs))]
+    for i, p in enumerate(probs):
+        with S.Context(p.grid, p.k, "mix_fp32") as c:
+            c.project(p.nq, p.weights, p.params)
+            c.set_fields([f1[i]])
+            c.step("strang", 0.1, 1)
+            c.set_fields([f2[i]])
+            c.step("strang", 0.1, 1)
+            alone = c.get_coeffs()
+        assert np.array_equal(got[i], alone), i
