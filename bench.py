@@ -233,16 +233,16 @@ def launches_per_step(args, info):
     """Kernels one bench step launches.  A split step builds each dimension's
     shift table once (Strang's two x half-steps share theirs) besides its
     sweeps; a nodal x-sweep builds its node table before it (and, in the mixed
-    store, the per-v-cell record); the self-consistent field builds every table
-    right before its sweep and takes two launches (density sums, field) before
-    the v-sweep; the 1D advection graph is one thread-block cluster launch in
+    store, the per-v-cell record); the self-consistent field builds its v-table
+    right before the v-sweep, after two launches (density sums, field); the 1D
+    advection graph is one thread-block cluster launch in
     the FP64 store (every step's table built in the kernel), (table build,
     sweep) pairs otherwise."""
     sweeps = info["sweeps"]
     if args.workload == "1d":
         return 1 if args.storage == "fp64" else 2 * sweeps
     if args.workload == "vp":
-        return 2 * sweeps + 2
+        return sweeps + info["ndim"] + 2
     nodal = info.get("nodal_x_sweeps", 0)
     if nodal:
         x_dims = info["ndim"] // 2

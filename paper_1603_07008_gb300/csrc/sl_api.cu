@@ -570,13 +570,13 @@ sl_status substep_source(sl_ctx* c, int dim, double tau, bool field, ShiftSource
 // step into its own slot (Strang's two x half-steps share theirs): the
 // x-dimensions' on the context's stream before the step's first sweep, the
 // v-dimensions' on the side stream while the x-sweeps run, joined back before
-// the first v-sweep.  With the self-consistent field (a v-table needs the
-// field of the state after the x-sweeps) every table is built right before
-// its sweep.
+// the first v-sweep.  With the self-consistent field a v-table needs the
+// field of the state after the x-sweeps, so it is built right before its
+// sweep, after the field.
 sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
 {
     const std::vector<SubStep> plan = plan_of(c, sp);
-    bool ahead = !c->poisson;
+    bool ahead = true;
     for (const SubStep& a : plan)
         for (const SubStep& b : plan)
             if (a.dim == b.dim && a.frac != b.frac) ahead = false;
@@ -589,7 +589,7 @@ sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
                 const bool x = c->g.pair[ss.dim] >= 0;
                 if (x && c->nodal) continue;   // node tables: before each nodal sweep
                 if (!x) {
-                    any_v = true;
+                    any_v = any_v || !c->poisson;
                     continue;
                 }
                 if (built[ss.dim]) continue;
@@ -604,7 +604,7 @@ sl_status enqueue_steps(sl_ctx* c, sl_splitting sp, double dt, int nsteps)
                 SL_CUDA(c, cudaEventRecord(c->ev_fork, c->st));
                 SL_CUDA(c, cudaStreamWaitEvent(c->st_tab, c->ev_fork, 0));
                 for (const SubStep& ss : plan) {
-                    if (c->g.pair[ss.dim] >= 0 || built[ss.dim]) continue;
+                    if (c->g.pair[ss.dim] >= 0 || built[ss.dim] || c->poisson) continue;
                     ShiftSource src;
                     int sd, nclass;
                     sl_status r = substep_source(c, ss.dim, ss.frac * dt, false, &src, &sd, &nclass);
