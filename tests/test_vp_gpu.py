@@ -20,11 +20,14 @@ def _landau(nx, nv, k=2):
     return p, g
 
 
-@pytest.mark.parametrize("swap", [False, True])
-def test_field_matches_oracle(swap):
-    p, g = _landau(48, 40)
+@pytest.mark.parametrize("swap,nx", [(False, 48), (True, 48), (False, 5), (False, 1003)])
+def test_field_matches_oracle(swap, nx):
+    """The field is computed by a cluster of 8 blocks, each taking a segment
+    of the x-cells: 48 cells (6 per block), 5 (three blocks without cells)
+    and 1003 (uneven segments)."""
+    p, g = _landau(nx, 40)
     if swap:   # v along dimension 0, x along dimension 1
-        g = W.Grid(n=(40, 48), lo=(g.lo[1], g.lo[0]), hi=(g.hi[1], g.hi[0]), pair=(-1, 0))
+        g = W.Grid(n=(40, nx), lo=(g.lo[1], g.lo[0]), hi=(g.hi[1], g.hi[0]), pair=(-1, 0))
     rng = np.random.default_rng(3)
     u = rng.standard_normal((g.cells, 9)) * 0.1
     u[:, 0] += 1.0
@@ -35,7 +38,7 @@ def test_field_matches_oracle(swap):
     ref = O.poisson_field(u, g, 2)
     # both sum n_v terms per density and n_x terms per field value in FP64,
     # in different orders: |difference| <= 2 (n_x + n_v) eps h_x sum_i |rho_i|
-    nx, nv = (48, 40)
+    nv = 40
     hx = 4 * math.pi / nx
     rho_abs = 12.0 / nv * np.sum(np.abs(u[:, 0]))
     assert np.max(np.abs(E - ref)) <= 2 * (nx + nv) * np.finfo(float).eps * hx * rho_abs
