@@ -10,31 +10,69 @@ namespace sl {
 
 // ---------------------------------------------------------------- A, B
 
-// One thread per shift class; the arithmetic is in sl_ab.cuh.
-// One thread per shift class, in blocks of one warp so that the classes of a
-// line family (a few hundred to a few thousand) spread over many SMs: the
-// evaluation is a chain of dependent FP64 multiply-adds.
+// The table of a single problem: one thread per entry of A and B of a class
+// (2 o^2 threads per class, each splitting the class's shift itself, the
+// shift decomposition and Horner evaluation of sl_ab.cuh's ab_class_k entry
+// by entry, so the same bits).  A problem has a few thousand classes at most,
+// and one thread per class left one warp per SM running some 800 instructions
+// of dependent latency (7.5 us for 512 classes; 4.1-5.0 us this way).  The
+// batch, with 10^5 classes, keeps one thread per class (k_batch_ab): there the
+// FP64 pipe, not latency, bounds the build.
 template <int K>
-__global__ void __launch_bounds__(32) k_ab_build(int nclass, uint32_t N, ShiftSource src, PolyTab tab,
-                                                 int32_t* __restrict__ sigma, double* __restrict__ alpha,
-                                                 double* __restrict__ ab64, float* __restrict__ ab32)
+__global__ void __launch_bounds__(128) k_ab_build_entries(int nclass, uint32_t N, ShiftSource src, PolyTab tab,
+                                                          int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                                                          double* __restrict__ ab64, float* __restrict__ ab32)
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int O = K + 1;
+    constexpr int E = 2 * O * O;
+    constexpr int deg = 2 * K + 1;
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = item / E;
     if (c >= nclass) return;
-    ab_class_k<K>(shift_of(src, c), N, tab, c, sigma, alpha, ab64, ab32);
+    const int e = item - c * E;
+    const double s = shift_of(src, c);
+    const double f = floor(s);
+    double a = s - f;
+    long long sg = (long long)f;
+    if (a >= 1.0) {
+        sg += 1;
+        a = 0.0;
+    }
+    if (e == 0) {
+        long long r = sg % (long long)N;
+        if (r < 0) r += N;
+        sigma[c] = int32_t(r);
+        alpha[c] = a;
+    }
+    const bool isb = e >= O * O;
+    const int jl = isb ? e - O * O : e;
+    const int j = jl / O, l = jl - (jl / O) * O;
+    double v;
+    if (a == 0.0) {
+        v = isb ? 0.0 : (j == l ? 1.0 : 0.0);
+    } else {
+        const double t = a - 0.5;
+        const double* pc = isb ? tab.b[j][l] : tab.a[j][l];
+        v = pc[deg];
+#pragma unroll
+        for (int p = deg - 1; p >= 0; --p) v = fma(v, t, pc[p]);
+    }
+    ab64[size_t(c) * ab_stride64(O) + e] = v;
+    ab32[size_t(c) * ab_stride32(O) + e] = __double2float_rn(v);
 }
 
 cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,
                             const PolyTab& tab, int32_t* sigma, double* alpha, double* ab64,
                             float* ab32, cudaStream_t st)
 {
-    const int block = 32;
-    const int grid = (nclass + block - 1) / block;
+    const int block = 128;
+    const int E = 2 * (K + 1) * (K + 1);
+    const int grid = int((int64_t(nclass) * E + block - 1) / block);
     switch (K) {
-    case 0: k_ab_build<0><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
-    case 1: k_ab_build<1><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
-    case 2: k_ab_build<2><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
-    case 3: k_ab_build<3><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 0: k_ab_build_entries<0><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 1: k_ab_build_entries<1><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 2: k_ab_build_entries<2><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+    case 3: k_ab_build_entries<3><<<grid, block, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -27,7 +27,7 @@ cudaError_t launch_batch_ab(const BatchAB* d_desc, const PolyTab* d_tabs, int np
                             double tau, cudaStream_t st)
 {
     if (nprob <= 0) return cudaSuccess;
-    const int b = 32;   // one warp per block: see k_ab_build
+    const int b = 32;   // one warp per block, so the classes spread over the SMs
     dim3 grid((maxclass + b - 1) / b, nprob);
     k_batch_ab<<<grid, b, 0, st>>>(d_desc, d_tabs, tau);
     return cudaGetLastError();
