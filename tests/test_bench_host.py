@@ -132,3 +132,26 @@ def test_oracle_error_of_nodal_and_whole_state_samples():
     bad = ref.copy()
     bad[5, 0] += 1e-3
     assert bench.oracle_error({"steps": 1, "whole": (q, bad)}, "fp64")["rel_max"] > 0
+
+
+def test_launch_counts_per_step():
+    """gpu_launches counts the kernels of the timed steps: a split step builds
+    each dimension's table once besides its sweeps; nodal x-sweeps build their
+    node table (and, in the mixed store, the per-v-cell record) before each;
+    the self-consistent field adds its two launches and builds the v-table
+    after them; the 1D FP64 advection graph is one cluster launch."""
+    from types import SimpleNamespace as NS
+
+    def n(workload, storage, **info):
+        return bench.launches_per_step(NS(workload=workload, storage=storage), info)
+
+    assert n("4d", "mix_fp32", sweeps=6, ndim=4) == 10          # 6 sweeps + 4 tables
+    assert n("6d", "mix_bf16", sweeps=9, ndim=6) == 15
+    assert n("2d", "mix_fp32", sweeps=3, ndim=2) == 5
+    assert n("batch", "mix_fp32", sweeps=3, ndim=2) == 5
+    assert n("vp", "mix_fp32", sweeps=3, ndim=2) == 7           # + density and field
+    # 4D nodal: 4 nodal x-sweeps (table + record + sweep), 2 v-sweeps, 2 v-tables
+    assert n("4d", "mix_fp32", sweeps=6, ndim=4, nodal_x_sweeps=4) == 16
+    assert n("4d", "fp64", sweeps=6, ndim=4, nodal_x_sweeps=4) == 12
+    assert n("1d", "fp64", sweeps=100, ndim=1) == 1
+    assert n("1d", "mix_fp32", sweeps=100, ndim=1) == 200
