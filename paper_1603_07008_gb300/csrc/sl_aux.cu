@@ -10,7 +10,8 @@ namespace sl {
 
 // ---------------------------------------------------------------- A, B
 
-// The table of a single problem: one thread per entry of A and B of a class
+// The table of a single problem of at most kAbEntryClasses classes: one thread
+// per entry of A and B of a class
 // (2 o^2 threads per class, each splitting the class's shift itself, the
 // shift decomposition and Horner evaluation of sl_ab.cuh's ab_class_k entry
 // by entry, so the same bits).  A problem has a few thousand classes at most,
@@ -61,10 +62,37 @@ __global__ void __launch_bounds__(128) k_ab_build_entries(int nclass, uint32_t N
     ab32[size_t(c) * ab_stride32(O) + e] = __double2float_rn(v);
 }
 
+// One thread per class (ab_class_k), in one-warp blocks: for tables of many
+// classes, where the per-entry form would repeat the shift split 2 o^2 times
+// per class on the FP64 pipe.
+template <int K>
+__global__ void __launch_bounds__(32) k_ab_build_classes(int nclass, uint32_t N, ShiftSource src, PolyTab tab,
+                                                         int32_t* __restrict__ sigma, double* __restrict__ alpha,
+                                                         double* __restrict__ ab64, float* __restrict__ ab32)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nclass) return;
+    ab_class_k<K>(shift_of(src, c), N, tab, c, sigma, alpha, ab64, ab32);
+}
+
+// Classes up to which the table takes one thread per entry.
+constexpr int kAbEntryClasses = 8192;
+
 cudaError_t launch_ab_build(int K, int nclass, uint32_t N, const ShiftSource& src,
                             const PolyTab& tab, int32_t* sigma, double* alpha, double* ab64,
                             float* ab32, cudaStream_t st)
 {
+    if (nclass > kAbEntryClasses) {
+        const int grid = (nclass + 31) / 32;
+        switch (K) {
+        case 0: k_ab_build_classes<0><<<grid, 32, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+        case 1: k_ab_build_classes<1><<<grid, 32, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+        case 2: k_ab_build_classes<2><<<grid, 32, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+        case 3: k_ab_build_classes<3><<<grid, 32, 0, st>>>(nclass, N, src, tab, sigma, alpha, ab64, ab32); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     const int block = 128;
     const int E = 2 * (K + 1) * (K + 1);
     const int grid = int((int64_t(nclass) * E + block - 1) / block);

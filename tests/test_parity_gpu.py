@@ -835,3 +835,20 @@ def test_fields_changed_between_steps_are_used(storage, tol):
         assert O.rel_max(got, ref) <= tol
     else:
         assert O.rel_l2(got, ref, p.k, 4) <= tol
+
+
+@pytest.mark.parametrize("nv", [8192, 9001])
+def test_table_of_many_classes(nv):
+    """A table of up to 8192 classes is built one thread per matrix entry,
+    a larger one one thread per class: both against the oracle (FP64 store,
+    4 x nv cells, k = 2, per-line shifts from the orthogonal coordinate)."""
+    n = (4, nv)
+    k = 2
+    u = _rand(n, k, 41)
+    s = np.random.default_rng(42).uniform(-9.0, 9.0, size=nv)
+    with S.Context(_grid(n), k, "fp64") as ctx:
+        ctx.set_coeffs(u)
+        ctx.advect(0, 1, s)
+        got = ctx.get_coeffs()
+    ref = O.sweep(u, n, k, 0, 1, s)
+    assert O.rel_max(got, ref) <= FP64_TOL
