@@ -297,7 +297,10 @@ sl_status sl_set_fields(sl_ctx* ctx, const double* fields, int64_t count);
  * over the x/v pairs of the grid.  x-sweep along m: shift v_j tau / h_m with
  * v_j the cell centre of v-dimension pair[m]; v-sweep along pair[m]: shift
  * E_m(x_i) tau / h_{pair[m]}.  Needs sl_set_fields when the grid has pairs.
- * Enqueues only. */
+ * Enqueues only.  Each step builds every dimension's A/B table once (the
+ * v-dimensions' on a stream of the context's own, forked from and joined
+ * back to the context's stream within the step), so all of a step's work is
+ * ordered on the context's stream as seen from outside. */
 sl_status sl_step(sl_ctx* ctx, sl_splitting splitting, double dt, int nsteps);
 
 /* Mass M = (prod_m h_m) sum_i c_{i;0..0} (Sec. II-A: c_0 is the cell mean),
