@@ -176,54 +176,54 @@ TRAFFIC = {
     ("4d", "mix_fp32"): {
         "ratio": (0.98529 + 1.00005 + 1.00636 + 0.99558 + 0.98462 + 1.00005) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "083c0ba6ebb12899",
+        "sha256": "455d482ff0cd9efd",
         "capture": "48^4 cells, k=2, one Strang step (6 launches: vector form along dimension 0, walks with 1 fibre, "
                    "4 cells per step along the others): 3.431-3.504 GB per launch against 3.482 GB algorithmic"},
     ("6d", "mix_bf16"): {
         "ratio": (1.00631 + 1.03328 + 1.03146 + 1.03033 + 1.03041 + 1.03252 + 1.00555 + 1.03325 + 1.03157) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "ceb1c64e63eb4e26",
+        "sha256": "ef12c01954e28a04",
         "capture": "16^6 cells, k=1, BF16 records, lane groups, one Strang step (9 launches): 4.656-4.785 GB per "
                    "launch against 4.631 GB algorithmic"},
     ("6d", "mix_fp16"): {
         "ratio": (1.00630 + 1.03332 + 1.03149 + 1.03040 + 1.03058 + 1.03263 + 1.00563 + 1.03329 + 1.03147) / 9,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_rec.cu"],
-        "sha256": "ceb1c64e63eb4e26",
+        "sha256": "ef12c01954e28a04",
         "capture": "16^6 cells, k=1, FP16 records, lane groups, one Strang step (9 launches): 4.656-4.785 GB per "
                    "launch against 4.631 GB algorithmic"},
     ("2d", "mix_fp32"): {
         "ratio": (0.96416 + 0.97316 + 0.96173) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "083c0ba6ebb12899",
+        "sha256": "455d482ff0cd9efd",
         "capture": "4096^2 cells, k=2 (the size of the workload), library default shapes, one Strang step: "
                    "1.291-1.306 GB per launch against 1.342 GB algorithmic"},
     ("vp", "mix_fp32"): {
         "ratio": (0.96424 + 0.97247 + 0.96162) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "083c0ba6ebb12899",
+        "sha256": "455d482ff0cd9efd",
         "capture": "4096^2 cells, k=2 (the size of the workload), self-consistent field, library default shapes, one "
                    "Strang step (sweeps only): 1.291-1.305 GB per launch against 1.342 GB algorithmic"},
     ("4d_nodal_v", "mix_fp32"): {
         "ratio": (0.94464 + 0.93238 + 0.95927 + 0.94212 + 0.94070 + 0.93180) / 6,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
-        "sha256": "a1cffdb83f2bddc1",
+        "sha256": "2515eb9747e6448e",
         "capture": "32^4 cells, k=2, nodal x-sweeps (runs of 2 along dimension 0, of 4 along dimension 1), one "
                    "Strang step: 0.641-0.660 GB per launch against 0.688 GB algorithmic"},
     ("2d_nodal_v", "mix_fp32"): {
         "ratio": (0.96784 + 0.97304 + 0.96557) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu", "sl_nodal.h", "sl_nodal.cu"],
-        "sha256": "a1cffdb83f2bddc1",
+        "sha256": "2515eb9747e6448e",
         "capture": "4096^2 cells, k=2 (the size of the workload), nodal x-sweep, one Strang step: 1.296-1.306 GB per "
                    "launch against 1.342 GB algorithmic"},
     ("paper1d", "mix_fp32"): {
         "ratio": 0.96349,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_sweep_fp.inc", "sl_sweep_f32.cu"],
-        "sha256": "083c0ba6ebb12899",
+        "sha256": "455d482ff0cd9efd",
         "capture": "2^25 cells, order 4, c_0 in FP64: 1.293 GB per launch against 1.342 GB algorithmic"},
     ("batch", "mix_fp32"): {
         "ratio": (0.96774 + 1.04429 + 0.96494) / 3,
         "sources": ["sl_internal.cuh", "sl_sweep.cuh", "sl_batch.cu", "sl_batch_api.cu"],
-        "sha256": "75bd9fafc6ca92ee",
+        "sha256": "5771a059f0504081",
         "capture": "64 problems, shapes (3 fibres, runs of 2) / (1 fibre, 4 rows per step, 32-line by 32-row items), "
                    "one Strang step: 1.054-1.140 GB per launch against 1.092 GB algorithmic"},
 }
